@@ -1,0 +1,214 @@
+/*
+ * oras.h -- C ABI of a single-GPU (GB300, sm_103a) solver for the linear systems that
+ * degree-r Nedelec edge elements give for the time-harmonic Maxwell equations, solved by
+ * flexible GMRES right-preconditioned with the Optimized Restricted Additive Schwarz
+ * (ORAS) method.
+ *
+ * Paper: M. Bonazzoli, V. Dolean, F. Rapetti, P.-H. Tournier, "Parallel preconditioners
+ * for high order discretizations arising from full system modeling for brain microwave
+ * imaging", arXiv:1605.04521.
+ *   Sec. 2  : curl-curl equation, impedance boundary condition, variational formulation.
+ *   Sec. 3  : generators lambda^k w^e of degree r and their DOFs.
+ *   Sec. 4  : M^{-1}_ORAS = sum_s R_s^T D_s A_s^{-1} R_s with impedance transmission.
+ *   Sec. 5  : GMRES preconditioned by ORAS; pseudo-block treatment of many right-hand sides.
+ *
+ * Conventions shared by every entry point:
+ *   - Complex numbers are interleaved (re, im) doubles: oras_complex is layout-compatible
+ *     with C99 double _Complex and std::complex<double>.
+ *   - Multi-vector arguments (rhs, x, v, z) are N x k column-major: vector j starts at
+ *     offset j*N, N = oras_ndof(h).
+ *   - `mem` selects where a data pointer lives: ORAS_MEM_HOST (pageable or pinned host
+ *     memory) or ORAS_MEM_DEVICE (device memory of the current CUDA device, e.g. a torch
+ *     tensor's data_ptr()).  Device pointers are read/written on the handle's stream.
+ *   - The caller owns every buffer it passes; the library copies what it keeps.  The
+ *     library owns all device memory it allocates and frees it in oras_destroy().
+ *   - Return codes: 0 = ORAS_OK, > 0 = warning, < 0 = error.  Nothing throws across the
+ *     ABI.  oras_last_error(h) (or oras_last_error(NULL) before a handle exists) gives a
+ *     message for the last failing call on this thread.
+ *   - Local numbering: the vertices of each tetrahedron are sorted by global id; the n_loc
+ *     local DOFs are the 6 edges (0,1),(0,2),(0,3),(1,2),(1,3),(2,3) (r each), the 4 faces
+ *     (0,1,2),(0,1,3),(0,2,3),(1,2,3) (r(r-1) each) and the volume (r(r-1)(r-2)/2).
+ *     Global numbering: edge DOFs (edges sorted by vertex pair), then face DOFs (faces
+ *     sorted by vertex triple), then volume DOFs (tetrahedron order).
+ */
+#ifndef ORAS_H
+#define ORAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } oras_complex;
+
+typedef struct oras_handle oras_handle;
+
+enum {
+  ORAS_OK = 0,
+  ORAS_NOT_CONVERGED = 1,        /* x holds the best iterate of the last cycle           */
+  ORAS_ERR_INVALID_ARG = -1,
+  ORAS_ERR_BAD_MESH = -2,        /* index out of range, repeated vertex, zero volume     */
+  ORAS_ERR_OUT_OF_MEMORY = -3,
+  ORAS_ERR_SINGULAR_LOCAL = -4,  /* a local matrix A_s had an exactly zero pivot column */
+  ORAS_ERR_DEVICE_TIMEOUT = -5,  /* a bounded device-side wait gave up                   */
+  ORAS_ERR_CUDA = -6,
+  ORAS_ERR_REJECTED = -7,        /* request over the admission budget (serving)          */
+  ORAS_ERR_UNSUPPORTED = -8,
+  ORAS_ERR_STATE = -9            /* call order: e.g. solve before factor                 */
+};
+
+enum { ORAS_MEM_HOST = 0, ORAS_MEM_DEVICE = 1 };
+enum { ORAS_WEIGHTS_POU = 0 /* ORAS: R_s^T D_s */, ORAS_WEIGHTS_NONE = 1 /* OAS, Sec. 4 */ };
+enum { ORAS_OVERLAP_VERTEX = 0, ORAS_OVERLAP_FACE = 1 };
+
+/* Problem statement (Sec. 2-4).  All pointers are host pointers, read during the call. */
+typedef struct {
+  int64_t nv;                 /* number of vertices                                     */
+  const double* xyz;          /* [nv][3] vertex coordinates                             */
+  int64_t nt;                 /* number of tetrahedra                                   */
+  const int32_t* tets;        /* [nt][4] vertex ids (any order; sorted internally)      */
+  const oras_complex* eps_r;  /* [nt] relative permittivity, e^{i w t} convention:      */
+                              /*      lossy media have Im(eps_r) < 0 (Sec. 2)            */
+  const oras_complex* mu_r;   /* [nt] relative permeability, NULL -> 1                  */
+  double k0;                  /* free-space wave number omega sqrt(eps0 mu0), mesh units */
+  int32_t r;                  /* polynomial degree of the edge elements, 1..3 (Sec. 3)  */
+  int32_t nsub;               /* number of subdomains N_sub (Sec. 4)                    */
+  int32_t overlap;            /* overlap layers delta >= 0                              */
+  const int32_t* part;        /* [nt] subdomain of each tetrahedron, or NULL for        */
+                              /*      recursive coordinate bisection into nsub parts    */
+} oras_problem;
+
+/* Solver options.  Zero-initialised fields take the defaults given in brackets. */
+typedef struct {
+  int32_t restart;            /* FGMRES restart length m [50]                           */
+  int32_t max_iter;           /* total Arnoldi steps per right-hand side [5000]         */
+  int32_t factor_bits;        /* 32: complex FP32 local factors; 64: complex FP64 [32]  */
+  int32_t weights;            /* ORAS_WEIGHTS_POU [default] or ORAS_WEIGHTS_NONE        */
+  int32_t overlap_kind;       /* ORAS_OVERLAP_VERTEX [default] or ORAS_OVERLAP_FACE     */
+  int32_t reserved[11];
+} oras_options;
+
+/* Per right-hand-side outcome of oras_solve. */
+typedef struct {
+  int32_t iterations;         /* Arnoldi steps taken                                    */
+  int32_t restarts;           /* completed FGMRES cycles                                */
+  int32_t converged;          /* 1 if the true relative residual <= tol                 */
+  int32_t pad;
+  double relres;              /* true FP64 ||b - A x|| / ||b|| of the returned x        */
+} oras_info;
+
+/* Message of the last failing call on this thread for h (NULL: calls without a handle). */
+const char* oras_last_error(const oras_handle* h);
+
+/* Version of the ABI described here. */
+int32_t oras_abi_version(void);
+
+/* ---------------------------------------------------------------- set-up */
+
+/* Integer set-up of Sec. 3-4 on the host, no device work: sorted tetrahedra, edge and
+ * face tables, global DOF numbering, outer boundary faces, partition (given or recursive
+ * coordinate bisection), overlapping sets Omega_s^delta, ordered unknown sets N_s (Sec. 4,
+ * R_s), Boolean partition of unity D_s (sum_s R_s^T D_s R_s = I), interface faces and the
+ * CSR pattern of A.  p->eps_r, p->mu_r, p->k0 are ignored here.
+ * Errors: INVALID_ARG (r not in 1..3, nsub < 1 or > nt, overlap < 0, NULL arrays),
+ * BAD_MESH (vertex id out of range, repeated vertex, zero-volume tetrahedron, part entry
+ * out of range), UNSUPPORTED (more than 2^31-1 DOFs or 2^21 vertices). */
+int oras_create(const oras_problem* p, const oras_options* o, oras_handle** out);
+
+/* Numeric set-up on the GPU for one material set (Sec. 2-4): element matrices
+ *   A_T = mu_r^{-1} int curl w_a . curl w_b - k0^2 eps_r int w_a . w_b      (FP64, exact)
+ * plus i beta int (w_a x n).(w_b x n) on outer faces, beta = k0 sqrt(Re mu_r Re eps_r) of
+ * the adjacent tetrahedron; global CSR matrix A; dense local matrices A_s with impedance
+ * transmission i omega~ on interface faces (omega~ from the tetrahedron inside Omega_s);
+ * batched LU with pivoting of every A_s in the factor precision.  eps_r, mu_r: [nt] arrays
+ * in `mem` (mu_r may be NULL -> 1).  May be called again with new materials (the mesh,
+ * partition and device buffers are reused).  Errors: STATE, OUT_OF_MEMORY, CUDA,
+ * SINGULAR_LOCAL, DEVICE_TIMEOUT. */
+int oras_factor(oras_handle* h, const oras_complex* eps_r, const oras_complex* mu_r, double k0,
+                int32_t mem);
+
+/* oras_create followed by oras_factor(p->eps_r, p->mu_r, p->k0, ORAS_MEM_HOST). */
+int oras_setup(const oras_problem* p, const oras_options* o, oras_handle** out);
+
+/* Frees host and device memory of h (NULL is ignored). */
+void oras_destroy(oras_handle* h);
+
+/* Stream for all device work of h (a cudaStream_t; NULL = legacy default stream). */
+int oras_set_stream(oras_handle* h, void* stream);
+
+/* ---------------------------------------------------------------- solve (Sec. 5) */
+
+/* Solves A x_j = b_j for the k columns of rhs by FGMRES(m), x0 = 0, right-preconditioned
+ * by ORAS, with FP64 Arnoldi (modified Gram-Schmidt), FP64 Givens rotations and an FP64
+ * true-residual check at the end of every cycle; the k recurrences run together (pseudo-
+ * block, Sec. 5).  rhs, x: N x k column-major in `mem`; info: k host structs or NULL.
+ * Returns ORAS_OK when every column reached ||b - A x|| / ||b|| <= tol,
+ * ORAS_NOT_CONVERGED when max_iter ran out for some column.  Errors: STATE (no
+ * oras_factor yet), INVALID_ARG (k < 1 or > 64, tol <= 0), CUDA, OUT_OF_MEMORY. */
+int oras_solve(oras_handle* h, const oras_complex* rhs, int32_t k, double tol, oras_complex* x,
+               oras_info* info, int32_t mem);
+
+/* ---------------------------------------------------------------- right-hand sides */
+
+/* Impedance data of Sec. 2 for the plane wave E = p exp(-i gamma d.x),
+ * gamma = k0 sqrt(mu_r eps_r) (principal root), on every outer face:
+ * g = mu_r^{-1} (curl E) x n + i beta n x (E x n),  b_a = int_boundary g . w_a.
+ * d: unit direction [3], p: polarisation [3] (host).  b: N values in `mem`. */
+int oras_rhs_plane_wave(oras_handle* h, const double* d, const oras_complex* p, oras_complex* b,
+                        int32_t mem);
+
+/* Point dipole: b_a = w_a(x0) . dir in the lowest-index tetrahedron whose barycentric
+ * coordinates of x0 are all >= -1e-12.  x0, dir: [3] host.  b: N values in `mem`.
+ * Error INVALID_ARG if x0 lies in no tetrahedron. */
+int oras_rhs_dipole(oras_handle* h, const double* x0, const double* dir, oras_complex* b,
+                    int32_t mem);
+
+/* ---------------------------------------------------------------- queries (host data) */
+
+int64_t oras_ndof(const oras_handle* h);            /* N, or -1                          */
+int32_t oras_nlocal(const oras_handle* h);          /* n_loc = r(r+2)(r+3)/2, or -1      */
+int32_t oras_nsub(const oras_handle* h);            /* N_sub, or -1                      */
+/* out: [nt][n_loc] global DOF ids (local numbering in the header comment). */
+int oras_dofmap(const oras_handle* h, int32_t* out);
+/* out: [nt] non-overlapping subdomain of each tetrahedron. */
+int oras_partition(const oras_handle* h, int32_t* out);
+/* Sizes of subdomain s: #N_s, #Omega_s^delta tetrahedra, padded factor order. */
+int oras_subdomain_size(const oras_handle* h, int32_t s, int64_t* ndof, int64_t* ntet,
+                        int64_t* npad);
+/* dofs: [#N_s] ascending global ids of N_s (R_s); pou: [#N_s] D_s diagonal (0/1) or NULL;
+ * tets: [#Omega_s^delta] ascending tetrahedron ids or NULL. */
+int oras_subdomain(const oras_handle* h, int32_t s, int32_t* dofs, uint8_t* pou, int32_t* tets);
+/* Number of stored nonzeros of A. */
+int64_t oras_nnz(const oras_handle* h);
+/* Bytes of the local-factor arena (device), 0 before oras_factor. */
+int64_t oras_arena_bytes(const oras_handle* h);
+
+/* ---------------------------------------------------------------- operator access */
+
+/* Element matrices A_T (without boundary-face terms) of `count` tetrahedra `tets` (host),
+ * copied from the device into out[count][n_loc][n_loc] (host). Requires oras_factor. */
+int oras_element_matrices(oras_handle* h, const int32_t* tets, int64_t count, oras_complex* out);
+/* CSR of A (host arrays): rowptr [N+1], cols [nnz], vals [nnz]; any may be NULL. */
+int oras_global_csr(oras_handle* h, int64_t* rowptr, int32_t* cols, oras_complex* vals);
+/* y = A x for k columns (N x k column-major, `mem`). */
+int oras_matvec(oras_handle* h, const oras_complex* x, oras_complex* y, int32_t k, int32_t mem);
+/* z = M^{-1}_ORAS v for k columns (N x k column-major, `mem`), Sec. 4. */
+int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k, int32_t mem);
+
+/* ---------------------------------------------------------------- instrumentation */
+
+/* Device time (ms, CUDA events) of the phases of the last oras_factor / oras_solve:
+ * t[0] element matrices, t[1] global CSR values, t[2] local assembly, t[3] LU,
+ * t[4] solve total, t[5] preconditioner applies, t[6] SpMV, t[7] orthogonalisation,
+ * t[8] number of preconditioner applies, t[9] number of SpMVs.  n: entries of t. */
+int oras_timings(const oras_handle* h, double* t, int32_t n);
+/* Enables (1) / disables (0) per-phase event timing (default 0: no events recorded). */
+int oras_set_timing(oras_handle* h, int32_t on);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ORAS_H */

@@ -13,7 +13,8 @@ Readings where the paper is silent (the paper names the objects, not their const
   axis = largest centroid extent (ties -> x, then y, then z); stable order by
   (coordinate, tet id); child 0 takes floor(m * p0 / p) tets, p0 = floor(p / 2) parts;
   subdomain ids depth-first, child 0 first;
-* overlap: delta layers, each adds every tetrahedron sharing a vertex with the set;
+* overlap: delta layers, each adds every tetrahedron sharing a vertex with the set (a
+  face-sharing variant is available as an option);
 * N_s: all DOFs on entities of the tetrahedra of Omega_s^delta, ascending global id;
 * D_s: Boolean ownership; a DOF belongs to the non-overlapping subdomain of the
   lowest-index tetrahedron carrying it;
@@ -63,15 +64,24 @@ def rcb(xyz, st, nsub):
     return part
 
 
-def overlap_tets(st, nv, part, nsub, delta):
-    """Omega_s^delta for every s: ascending tet ids."""
+def overlap_tets(st, nv, part, nsub, delta, kind="vertex", face_tets=None, tet_faces=None):
+    """Omega_s^delta for every s: ascending tet ids.  kind="vertex": a layer adds every
+    tetrahedron sharing a vertex with the set; kind="face": sharing a face."""
     out = []
     for s in range(nsub):
         mark = part == s
         for _ in range(delta):
-            vm = np.zeros(nv, dtype=bool)
-            vm[st[mark].ravel()] = True
-            mark = vm[st].any(axis=1)
+            if kind == "face":
+                nxt = mark.copy()
+                f = tet_faces[mark].ravel()
+                for q in range(2):
+                    o = face_tets[f, q]
+                    nxt[o[o >= 0]] = True
+                mark = nxt
+            else:
+                vm = np.zeros(nv, dtype=bool)
+                vm[st[mark].ravel()] = True
+                mark = vm[st].any(axis=1)
         out.append(np.nonzero(mark)[0])
     return out
 
@@ -86,11 +96,11 @@ class Decomposition:
     iface: list = field(default_factory=list)  # per s: (tet, local face) arrays of interface faces
 
 
-def decompose(topo: Topology, xyz, nsub, delta, part=None) -> Decomposition:
+def decompose(topo: Topology, xyz, nsub, delta, part=None, kind="vertex") -> Decomposition:
     if part is None:
         part = rcb(xyz, topo.st, nsub)
     part = np.asarray(part, dtype=np.int64)
-    tets = overlap_tets(topo.st, topo.nv, part, nsub, delta)
+    tets = overlap_tets(topo.st, topo.nv, part, nsub, delta, kind, topo.face_tets, topo.tet_faces)
     owner = part[dof_min_tet(topo)]
     dofs, pou, iface = [], [], []
     for s in range(nsub):

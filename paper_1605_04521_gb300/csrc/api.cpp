@@ -1,0 +1,704 @@
+// C ABI of the ORAS-FGMRES solver: handle lifecycle, device upload, numeric set-up (element
+// matrices, A, A_s, batched LU) and the right-preconditioned FGMRES(m) driver (Sec. 4-5).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace oras {
+// kernels (assemble.cu, lu.cu, apply.cu, krylov.cu)
+int launch_element(const oras_handle* h, double k0);
+int launch_faces(const oras_handle* h);
+int launch_global_rows(const oras_handle* h, double k0);
+int launch_local_rows(const oras_handle* h, double k0);
+int launch_dipole(const oras_handle* h, const double* x0, const double* dir, cplx* b, int* found);
+int launch_plane(const oras_handle* h, const double* dvec, const oras_complex* pvec, double k0,
+                 const double* qs, const double* qw, int nq, cplx* bface, cplx* b);
+int launch_lu(oras_handle* h);
+int lu_max_chunks(int64_t max_np, int factor_bits);
+int launch_apply_f64out(const oras_handle* h, const cplx* v, cplx* z, int k);
+int launch_apply_f32out(const oras_handle* h, const cplx* v, void* z, int k);
+size_t apply_yglob_bytes(const oras_handle* h);
+void launch_spmv_f64(const oras_handle* h, const cplx* x, cplx* y, int k);
+void launch_spmv_f32(const oras_handle* h, const void* x, cplx* y, int k);
+void launch_dot(const oras_handle* h, const cplx* a, const cplx* b, cplx* partials, int k);
+void launch_mgs_step(const oras_handle* h, int k, int m, int i, int j, const cplx* Vi, const cplx* Vn, cplx* w,
+                     const cplx* pin, cplx* pout, cplx* H);
+void launch_mgs_finish(const oras_handle* h, int k, int m, int j, const cplx* w, cplx* Vn, const cplx* pin,
+                       cplx* H, double* cs, cplx* sn, cplx* g, double* res);
+void launch_hsolve(const oras_handle* h, int k, int m, int kk, const cplx* H, const cplx* g, const int32_t* active,
+                   cplx* y);
+void launch_xupdate_f64(const oras_handle* h, int k, int m, int kk, const cplx* Z, const cplx* y, cplx* x);
+void launch_xupdate_f32(const oras_handle* h, int k, int m, int kk, const void* Z, const cplx* y, cplx* x);
+void launch_residual(const oras_handle* h, int k, const cplx* b, cplx* r, cplx* partials);
+void launch_norms(const oras_handle* h, int k, const cplx* partials, double* out);
+void launch_restart(const oras_handle* h, int k, int m, const cplx* rv, const double* beta, const int32_t* active,
+                    cplx* V0, cplx* g);
+void launch_to_internal(const oras_handle* h, int k, const cplx* src, cplx* dst);
+void launch_to_external(const oras_handle* h, int k, const cplx* src, cplx* dst);
+int red_blocks();
+}  // namespace oras
+
+using namespace oras;
+
+static thread_local std::string g_err;
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                                 \
+      return e_ == cudaErrorMemoryAllocation ? ORAS_ERR_OUT_OF_MEMORY : ORAS_ERR_CUDA;              \
+    }                                                                                              \
+  } while (0)
+
+template <typename T>
+static cudaError_t dalloc(T*& p, size_t n) {
+  if (p) { cudaFree(p); p = nullptr; }
+  if (n == 0) n = 1;
+  return cudaMalloc((void**)&p, n * sizeof(T));
+}
+template <typename T>
+static cudaError_t dput(T*& p, const std::vector<T>& v, cudaStream_t s) {
+  cudaError_t e = dalloc(p, v.size());
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+  return e;
+}
+
+static void dfree_all(Device& d) {
+  void* ptrs[] = {d.xyz, d.st, d.dofmap, d.tinc_ptr, d.tinc, d.if_tet0, d.if_lf0, d.if_tet1, d.if_dofs,
+                  d.finc_ptr, d.finc, d.rowptr, d.cols, d.sub_ns, d.sub_np, d.sub_ns_off, d.sub_tile_off,
+                  d.sub_dofs, d.sub_pou, d.member, d.cm, d.ck, d.cs, d.fl, d.tc, d.ta, d.tm, d.eps, d.mu,
+                  d.elem, d.fmat, d.vals, d.arena, d.perm, d.gidx, d.sub_np_off, d.lu_cand, d.lu_cnt,
+                  d.lu_ipiv, d.lu_diag, d.status, d.V, d.Zf, d.Zd, d.w, d.xk, d.bk, d.tmp, d.H, d.gcs, d.gsn,
+                  d.g, d.red, d.scal, d.ybuf, d.io};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (d.host_pinned) cudaFreeHost(d.host_pinned);
+  d = Device();
+}
+
+static int upload(oras_handle* h) {
+  auto& m = h->mesh;
+  auto& d = h->dev;
+  auto& T = h->tab;
+  cudaStream_t s = d.stream;
+  CK(cudaGetDevice(&d.device));
+  CK(dput(d.xyz, m.xyz, s));
+  CK(dput(d.st, m.st, s));
+  CK(dput(d.dofmap, m.dofmap, s));
+  CK(dput(d.tinc_ptr, m.tinc_ptr, s));
+  CK(dput(d.tinc, m.tinc, s));
+  CK(dput(d.if_tet0, m.if_tet0, s));
+  CK(dput(d.if_lf0, m.if_lf0, s));
+  CK(dput(d.if_tet1, m.if_tet1, s));
+  CK(dput(d.if_dofs, m.if_dofs, s));
+  CK(dput(d.finc_ptr, m.finc_ptr, s));
+  CK(dput(d.finc, m.finc, s));
+  CK(dput(d.rowptr, m.rowptr, s));
+  CK(dput(d.cols, m.cols, s));
+  CK(dput(d.sub_ns, m.sub_ns, s));
+  CK(dput(d.sub_np, m.sub_np, s));
+  CK(dput(d.sub_ns_off, m.sub_ns_off, s));
+  CK(dput(d.sub_tile_off, m.sub_tile_off, s));
+  CK(dput(d.sub_dofs, m.sub_dofs, s));
+  CK(dput(d.sub_pou, m.sub_pou, s));
+  CK(dput(d.member, m.member, s));
+  std::vector<int64_t> npoff(m.nsub + 1, 0);
+  for (int q = 0; q < m.nsub; ++q) npoff[q + 1] = npoff[q] + m.sub_np[q];
+  CK(dput(d.sub_np_off, npoff, s));
+  CK(dput(d.cm, T.cm, s));
+  CK(dput(d.ck, T.ck, s));
+  CK(dput(d.cs, T.cs, s));
+  std::vector<int32_t> fl(T.fl.begin(), T.fl.end()), ta(T.ta.begin(), T.ta.end()), tm(T.tm.begin(), T.tm.end());
+  CK(dput(d.fl, fl, s));
+  CK(dput(d.tc, T.tc, s));
+  CK(dput(d.ta, ta, s));
+  CK(dput(d.tm, tm, s));
+  CK(dalloc(d.eps, m.nt));
+  CK(dalloc(d.elem, (size_t)m.nt * m.nl * m.nl));
+  CK(dalloc(d.fmat, (size_t)std::max<int64_t>(1, m.nif) * m.nfl * m.nfl));
+  CK(dalloc(d.vals, m.cols.size()));
+  CK(dalloc(d.perm, npoff[m.nsub]));
+  CK(dalloc(d.gidx, npoff[m.nsub]));
+  CK(dalloc(d.status, 8));
+  CK(cudaMallocHost((void**)&d.host_pinned, 4096 * sizeof(double)));
+  d.uploaded = true;
+  return ORAS_OK;
+}
+
+static int alloc_factor_space(oras_handle* h, int bits) {
+  auto& m = h->mesh;
+  auto& d = h->dev;
+  size_t el = bits == 64 ? 16 : 8;
+  size_t bytes = (size_t)m.arena_tiles * TB * TB * el;
+  if (d.arena && d.factor_bits == bits && d.arena_bytes == bytes) return ORAS_OK;
+  if (d.arena) { cudaFree(d.arena); d.arena = nullptr; }
+  cudaError_t e = cudaMalloc(&d.arena, bytes);
+  if (e != cudaSuccess) {
+    h->err = "local-factor arena of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e);
+    d.arena = nullptr;
+    return e == cudaErrorMemoryAllocation ? ORAS_ERR_OUT_OF_MEMORY : ORAS_ERR_CUDA;
+  }
+  d.arena_bytes = bytes;
+  d.factor_bits = bits;
+  d.lu_max_chunks = lu_max_chunks(m.max_np, bits);
+  int slots = 2 * d.lu_max_chunks + 16;
+  CK(dalloc(d.lu_cand, (size_t)m.nsub * slots * TB));
+  CK(dalloc(d.lu_cnt, (size_t)m.nsub * slots));
+  CK(cudaMemsetAsync(d.lu_cnt, 0, (size_t)m.nsub * slots * sizeof(int32_t), d.stream));
+  CK(dalloc(d.lu_ipiv, (size_t)m.nsub * (2 * TB * 2 + 1)));
+  CK(cudaMalloc(&d.lu_diag, (size_t)m.nsub * TB * TB * el));
+  size_t yb = apply_yglob_bytes(h);
+  if (d.ybuf) { cudaFree(d.ybuf); d.ybuf = nullptr; }
+  if (yb) CK(cudaMalloc(&d.ybuf, yb));
+  d.ybuf_bytes = yb;
+  return ORAS_OK;
+}
+
+struct Timer {
+  oras_handle* h;
+  cudaEvent_t a = nullptr, b = nullptr;
+  explicit Timer(oras_handle* hh) : h(hh) {
+    if (h->timing) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, h->dev.stream);
+    }
+  }
+  double stop() {
+    if (!h->timing) return 0.0;
+    cudaEventRecord(b, h->dev.stream);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+  }
+};
+
+static int sync_status(oras_handle* h) {
+  auto& d = h->dev;
+  int32_t st[8];
+  CK(cudaMemcpyAsync(st, d.status, sizeof(st), cudaMemcpyDeviceToHost, d.stream));
+  CK(cudaStreamSynchronize(d.stream));
+  if (st[ST_ERR] == DEV_SINGULAR) {
+    h->err = "local matrix of subdomain " + std::to_string(st[ST_SUB]) + " has a zero pivot column";
+    return ORAS_ERR_SINGULAR_LOCAL;
+  }
+  if (st[ST_ERR] == DEV_TIMEOUT) {
+    h->err = "a bounded device wait gave up";
+    return ORAS_ERR_DEVICE_TIMEOUT;
+  }
+  return ORAS_OK;
+}
+
+extern "C" {
+
+int32_t oras_abi_version(void) { return 1; }
+
+const char* oras_last_error(const oras_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+int oras_create(const oras_problem* p, const oras_options* o, oras_handle** out) {
+  if (!out) { g_err = "oras_create: out is NULL"; return ORAS_ERR_INVALID_ARG; }
+  *out = nullptr;
+  oras_handle* h = new (std::nothrow) oras_handle();
+  if (!h) { g_err = "oras_create: host allocation failed"; return ORAS_ERR_OUT_OF_MEMORY; }
+  if (o) h->opt = *o;
+  if (h->opt.restart <= 0) h->opt.restart = 50;
+  if (h->opt.max_iter <= 0) h->opt.max_iter = 5000;
+  if (h->opt.factor_bits == 0) h->opt.factor_bits = 32;
+  if (h->opt.factor_bits != 32 && h->opt.factor_bits != 64) {
+    g_err = "oras_create: factor_bits must be 32 or 64";
+    delete h;
+    return ORAS_ERR_INVALID_ARG;
+  }
+  if (h->opt.weights != ORAS_WEIGHTS_POU && h->opt.weights != ORAS_WEIGHTS_NONE) {
+    g_err = "oras_create: unknown weights";
+    delete h;
+    return ORAS_ERR_INVALID_ARG;
+  }
+  int rc;
+  try {
+    rc = host_setup(p, h->opt.overlap_kind, h->mesh, g_err);
+    if (rc == ORAS_OK) h->tab = make_tables(p->r);
+  } catch (const std::bad_alloc&) {
+    g_err = "oras_create: host allocation failed";
+    rc = ORAS_ERR_OUT_OF_MEMORY;
+  } catch (const std::exception& e) {
+    g_err = std::string("oras_create: ") + e.what();
+    rc = ORAS_ERR_INVALID_ARG;
+  }
+  if (rc != ORAS_OK) { delete h; return rc; }
+  *out = h;
+  return ORAS_OK;
+}
+
+int oras_set_stream(oras_handle* h, void* stream) {
+  if (!h) return ORAS_ERR_INVALID_ARG;
+  h->dev.stream = (cudaStream_t)stream;
+  return ORAS_OK;
+}
+
+int oras_set_timing(oras_handle* h, int32_t on) {
+  if (!h) return ORAS_ERR_INVALID_ARG;
+  h->timing = on != 0;
+  return ORAS_OK;
+}
+
+int oras_timings(const oras_handle* h, double* t, int32_t n) {
+  if (!h || !t) return ORAS_ERR_INVALID_ARG;
+  for (int i = 0; i < n && i < 16; ++i) t[i] = h->timings[i];
+  return ORAS_OK;
+}
+
+int oras_factor(oras_handle* h, const oras_complex* eps_r, const oras_complex* mu_r, double k0, int32_t mem) {
+  if (!h || !eps_r) { if (h) h->err = "oras_factor: eps_r is NULL"; return ORAS_ERR_INVALID_ARG; }
+  if (!(k0 > 0.0)) { h->err = "oras_factor: k0 must be positive"; return ORAS_ERR_INVALID_ARG; }
+  auto& m = h->mesh;
+  auto& d = h->dev;
+  if (!d.uploaded) {
+    int rc = upload(h);
+    if (rc) return rc;
+  }
+  int rc = alloc_factor_space(h, h->opt.factor_bits);
+  if (rc) return rc;
+  cudaMemcpyKind kind = mem == ORAS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(d.eps, eps_r, sizeof(cplx) * m.nt, kind, d.stream));
+  if (mu_r) {
+    if (!d.mu) CK(dalloc(d.mu, m.nt));
+    CK(cudaMemcpyAsync(d.mu, mu_r, sizeof(cplx) * m.nt, kind, d.stream));
+  } else if (d.mu) {
+    cudaFree(d.mu);
+    d.mu = nullptr;
+  }
+  CK(cudaMemsetAsync(d.status, 0, 8 * sizeof(int32_t), d.stream));
+  h->k0 = k0;
+  {
+    Timer t(h);
+    if (launch_element(h, k0) || launch_faces(h)) CK(cudaGetLastError());
+    h->timings[0] = t.stop();
+  }
+  {
+    Timer t(h);
+    if (launch_global_rows(h, k0)) CK(cudaGetLastError());
+    h->timings[1] = t.stop();
+  }
+  {
+    Timer t(h);
+    CK(cudaMemsetAsync(d.arena, 0, d.arena_bytes, d.stream));
+    if (launch_local_rows(h, k0)) CK(cudaGetLastError());
+    h->timings[2] = t.stop();
+  }
+  {
+    Timer t(h);
+    if (launch_lu(h)) CK(cudaGetLastError());
+    h->timings[3] = t.stop();
+  }
+  rc = sync_status(h);
+  if (rc) return rc;
+  h->factored = true;
+  return ORAS_OK;
+}
+
+int oras_setup(const oras_problem* p, const oras_options* o, oras_handle** out) {
+  int rc = oras_create(p, o, out);
+  if (rc) return rc;
+  rc = oras_factor(*out, p->eps_r, p->mu_r, p->k0, ORAS_MEM_HOST);
+  if (rc) {
+    g_err = (*out)->err;
+    oras_destroy(*out);
+    *out = nullptr;
+  }
+  return rc;
+}
+
+void oras_destroy(oras_handle* h) {
+  if (!h) return;
+  if (h->dev.uploaded) {
+    cudaStreamSynchronize(h->dev.stream);
+    dfree_all(h->dev);
+  }
+  delete h;
+}
+
+int64_t oras_ndof(const oras_handle* h) { return h ? h->mesh.ndof : -1; }
+int32_t oras_nlocal(const oras_handle* h) { return h ? h->mesh.nl : -1; }
+int32_t oras_nsub(const oras_handle* h) { return h ? h->mesh.nsub : -1; }
+int64_t oras_nnz(const oras_handle* h) { return h ? (int64_t)h->mesh.cols.size() : -1; }
+int64_t oras_arena_bytes(const oras_handle* h) { return h ? (int64_t)h->dev.arena_bytes : -1; }
+
+int oras_dofmap(const oras_handle* h, int32_t* out) {
+  if (!h || !out) return ORAS_ERR_INVALID_ARG;
+  std::memcpy(out, h->mesh.dofmap.data(), h->mesh.dofmap.size() * sizeof(int32_t));
+  return ORAS_OK;
+}
+
+int oras_partition(const oras_handle* h, int32_t* out) {
+  if (!h || !out) return ORAS_ERR_INVALID_ARG;
+  std::memcpy(out, h->mesh.part.data(), h->mesh.part.size() * sizeof(int32_t));
+  return ORAS_OK;
+}
+
+int oras_subdomain_size(const oras_handle* h, int32_t s, int64_t* ndof, int64_t* ntet, int64_t* npad) {
+  if (!h || s < 0 || s >= h->mesh.nsub) return ORAS_ERR_INVALID_ARG;
+  if (ndof) *ndof = h->mesh.sub_ns[s];
+  if (ntet) *ntet = h->mesh.sub_nt_off[s + 1] - h->mesh.sub_nt_off[s];
+  if (npad) *npad = h->mesh.sub_np[s];
+  return ORAS_OK;
+}
+
+int oras_subdomain(const oras_handle* h, int32_t s, int32_t* dofs, uint8_t* pou, int32_t* tets) {
+  if (!h || s < 0 || s >= h->mesh.nsub) return ORAS_ERR_INVALID_ARG;
+  const auto& m = h->mesh;
+  int64_t o = m.sub_ns_off[s], n = m.sub_ns[s];
+  if (dofs) std::memcpy(dofs, m.sub_dofs.data() + o, n * sizeof(int32_t));
+  if (pou) std::memcpy(pou, m.sub_pou.data() + o, n);
+  if (tets) {
+    int64_t t0 = m.sub_nt_off[s], t1 = m.sub_nt_off[s + 1];
+    std::memcpy(tets, m.sub_tets.data() + t0, (t1 - t0) * sizeof(int32_t));
+  }
+  return ORAS_OK;
+}
+
+int oras_element_matrices(oras_handle* h, const int32_t* tets, int64_t count, oras_complex* out) {
+  if (!h || (!tets && count) || (!out && count)) return ORAS_ERR_INVALID_ARG;
+  if (!h->factored) { h->err = "oras_element_matrices: call oras_factor first"; return ORAS_ERR_STATE; }
+  const auto& m = h->mesh;
+  size_t per = (size_t)m.nl * m.nl;
+  for (int64_t q = 0; q < count; ++q) {
+    if (tets[q] < 0 || tets[q] >= m.nt) { h->err = "oras_element_matrices: tet out of range"; return ORAS_ERR_INVALID_ARG; }
+    CK(cudaMemcpyAsync(out + q * per, h->dev.elem + (size_t)tets[q] * per, per * sizeof(cplx),
+                       cudaMemcpyDeviceToHost, h->dev.stream));
+  }
+  CK(cudaStreamSynchronize(h->dev.stream));
+  return ORAS_OK;
+}
+
+int oras_global_csr(oras_handle* h, int64_t* rowptr, int32_t* cols, oras_complex* vals) {
+  if (!h) return ORAS_ERR_INVALID_ARG;
+  const auto& m = h->mesh;
+  if (rowptr) std::memcpy(rowptr, m.rowptr.data(), m.rowptr.size() * sizeof(int64_t));
+  if (cols) std::memcpy(cols, m.cols.data(), m.cols.size() * sizeof(int32_t));
+  if (vals) {
+    if (!h->factored) { h->err = "oras_global_csr: call oras_factor first"; return ORAS_ERR_STATE; }
+    CK(cudaMemcpyAsync(vals, h->dev.vals, m.cols.size() * sizeof(cplx), cudaMemcpyDeviceToHost, h->dev.stream));
+    CK(cudaStreamSynchronize(h->dev.stream));
+  }
+  return ORAS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ Krylov workspace
+static int ensure_ws(oras_handle* h, int k, int m) {
+  auto& d = h->dev;
+  const int64_t N = h->mesh.ndof;
+  if (d.ws_k >= k && d.ws_m >= m && d.V) return ORAS_OK;
+  int kk = std::max(k, d.ws_k), mm = std::max(m, d.ws_m);
+  size_t nk = (size_t)N * kk;
+  CK(dalloc(d.V, nk * (mm + 1)));
+  if (d.factor_bits == 64) {
+    CK(dalloc(d.Zd, nk * mm));
+  } else {
+    if (d.Zf) cudaFree(d.Zf);
+    d.Zf = nullptr;
+    CK(cudaMalloc((void**)&d.Zf, nk * mm * 2 * sizeof(float)));
+  }
+  CK(dalloc(d.w, nk));
+  CK(dalloc(d.xk, nk));
+  CK(dalloc(d.bk, nk));
+  CK(dalloc(d.tmp, nk));
+  CK(dalloc(d.H, (size_t)kk * (mm + 1) * mm));
+  CK(dalloc(d.gcs, (size_t)kk * mm));
+  CK(dalloc(d.gsn, (size_t)kk * mm));
+  CK(dalloc(d.g, (size_t)kk * (mm + 1)));
+  CK(dalloc(d.red, (size_t)2 * red_blocks() * kk * 2));
+  CK(dalloc(d.scal, (size_t)kk * 8 + (size_t)kk * mm * 2 + 64));
+  d.ws_k = kk;
+  d.ws_m = mm;
+  return ORAS_OK;
+}
+
+static int ensure_io(oras_handle* h, size_t elems) {
+  auto& d = h->dev;
+  if (d.io_elems >= elems && d.io) return ORAS_OK;
+  CK(dalloc(d.io, elems));
+  d.io_elems = elems;
+  return ORAS_OK;
+}
+
+// Copy an N x k column-major input (host or device) into the internal [N][k] buffer dst.
+static int load_input(oras_handle* h, const oras_complex* src, int k, int mem, cplx* dst) {
+  auto& d = h->dev;
+  const int64_t N = h->mesh.ndof;
+  int rc = ensure_io(h, (size_t)N * k);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(d.io, src, sizeof(cplx) * N * k,
+                     mem == ORAS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, d.stream));
+  launch_to_internal(h, k, d.io, dst);
+  return ORAS_OK;
+}
+
+static int store_output(oras_handle* h, const cplx* src, int k, int mem, oras_complex* dst) {
+  auto& d = h->dev;
+  const int64_t N = h->mesh.ndof;
+  int rc = ensure_io(h, (size_t)N * k);
+  if (rc) return rc;
+  launch_to_external(h, k, src, d.io);
+  CK(cudaMemcpyAsync(dst, d.io, sizeof(cplx) * N * k,
+                     mem == ORAS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, d.stream));
+  if (mem != ORAS_MEM_DEVICE) CK(cudaStreamSynchronize(d.stream));
+  return ORAS_OK;
+}
+
+static void precond_to_z(oras_handle* h, const cplx* v, int k, int j) {
+  auto& d = h->dev;
+  size_t nk = (size_t)h->mesh.ndof * k;
+  if (d.factor_bits == 64) launch_apply_f64out(h, v, d.Zd + nk * j, k);
+  else launch_apply_f32out(h, v, (char*)d.Zf + nk * j * 2 * sizeof(float), k);
+}
+
+static void spmv_z(oras_handle* h, int k, int j, cplx* y) {
+  auto& d = h->dev;
+  size_t nk = (size_t)h->mesh.ndof * k;
+  if (d.factor_bits == 64) launch_spmv_f64(h, d.Zd + nk * j, y, k);
+  else launch_spmv_f32(h, (char*)d.Zf + nk * j * 2 * sizeof(float), y, k);
+}
+
+// FGMRES(m) on internal [N][k] vectors: b = d.bk, solution in d.xk.
+static int fgmres(oras_handle* h, int k, double tol, oras_info* info) {
+  auto& d = h->dev;
+  const int64_t N = h->mesh.ndof;
+  const int m = h->opt.restart, max_iter = h->opt.max_iter;
+  int rc = ensure_ws(h, k, m);
+  if (rc) return rc;
+  const size_t nk = (size_t)N * k;
+  cplx* pA = (cplx*)d.red;
+  cplx* pB = pA + (size_t)red_blocks() * k;
+  double* beta_d = d.scal;                     // [k]
+  double* res_d = d.scal + k;                  // [k]
+  int32_t* active_d = (int32_t*)(d.scal + 2 * k);
+  cplx* y_d = (cplx*)(d.scal + 3 * k + 8);     // [k][m]
+  double* hp = d.host_pinned;                  // [0,k): norms; [k,2k): res
+  std::vector<double> bnorm(k), relres(k);
+  std::vector<int32_t> active(k, 1), iters(k, 0), cycles(k, 0), conv(k, 0);
+  double t_apply = 0, t_spmv = 0, t_orth = 0;
+  int n_apply = 0, n_spmv = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->timing) { cudaEventCreate(&e0); cudaEventCreate(&e1); }
+  auto tic = [&]() { if (h->timing) cudaEventRecord(e0, d.stream); };
+  auto toc = [&](double& acc) {
+    if (!h->timing) return;
+    cudaEventRecord(e1, d.stream);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    acc += ms;
+  };
+  // ||b||
+  CK(cudaMemsetAsync(d.xk, 0, nk * sizeof(cplx), d.stream));
+  CK(cudaMemsetAsync(d.tmp, 0, nk * sizeof(cplx), d.stream));
+  launch_residual(h, k, d.bk, d.tmp, pA);
+  launch_norms(h, k, pA, beta_d);
+  CK(cudaMemcpyAsync(hp, beta_d, k * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
+  CK(cudaStreamSynchronize(d.stream));
+  for (int r = 0; r < k; ++r) {
+    bnorm[r] = hp[r];
+    if (!(bnorm[r] > 0.0)) { active[r] = 0; conv[r] = 1; relres[r] = 0.0; }
+  }
+  bool first = true;
+  while (true) {
+    if (!first) {
+      // true residual r = b - A x
+      tic();
+      launch_spmv_f64(h, d.xk, d.tmp, k);
+      toc(t_spmv);
+      ++n_spmv;
+      launch_residual(h, k, d.bk, d.tmp, pA);
+      launch_norms(h, k, pA, beta_d);
+      CK(cudaMemcpyAsync(hp, beta_d, k * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
+      CK(cudaStreamSynchronize(d.stream));
+    }
+    first = false;
+    bool any = false;
+    for (int r = 0; r < k; ++r) {
+      if (!(bnorm[r] > 0.0)) continue;
+      relres[r] = hp[r] / bnorm[r];
+      if (relres[r] <= tol) { active[r] = 0; conv[r] = 1; }
+      else if (iters[r] >= max_iter) active[r] = 0;
+      else active[r] = 1;
+      any |= active[r] != 0;
+    }
+    if (!any) break;
+    CK(cudaMemcpyAsync(active_d, active.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, d.stream));
+    launch_restart(h, k, m, d.tmp, beta_d, active_d, d.V, d.g);
+    int kk = 0;
+    for (int j = 0; j < m; ++j) {
+      cplx* Vj = d.V + nk * j;
+      cplx* Vn = d.V + nk * (j + 1);
+      tic();
+      precond_to_z(h, Vj, k, j);
+      toc(t_apply);
+      ++n_apply;
+      tic();
+      spmv_z(h, k, j, d.w);
+      toc(t_spmv);
+      ++n_spmv;
+      tic();
+      launch_dot(h, d.V, d.w, pA, k);
+      cplx* pin = pA;
+      cplx* pout = pB;
+      for (int i = 0; i <= j; ++i) {
+        launch_mgs_step(h, k, m, i, j, d.V + nk * i, i < j ? d.V + nk * (i + 1) : nullptr, d.w, pin, pout, d.H);
+        std::swap(pin, pout);
+      }
+      launch_mgs_finish(h, k, m, j, d.w, Vn, pin, d.H, d.gcs, d.gsn, d.g, res_d);
+      toc(t_orth);
+      kk = j + 1;
+      for (int r = 0; r < k; ++r)
+        if (active[r]) ++iters[r];
+      CK(cudaMemcpyAsync(hp + k, res_d, k * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
+      CK(cudaStreamSynchronize(d.stream));
+      bool more = false;
+      for (int r = 0; r < k; ++r)
+        if (active[r] && hp[k + r] / bnorm[r] > tol && iters[r] < max_iter) more = true;
+      if (!more) break;
+    }
+    launch_hsolve(h, k, m, kk, d.H, d.g, active_d, y_d);
+    if (d.factor_bits == 64) launch_xupdate_f64(h, k, m, kk, d.Zd, y_d, d.xk);
+    else launch_xupdate_f32(h, k, m, kk, d.Zf, y_d, d.xk);
+    for (int r = 0; r < k; ++r)
+      if (active[r]) ++cycles[r];
+    CK(cudaGetLastError());
+  }
+  if (e0) { cudaEventDestroy(e0); cudaEventDestroy(e1); }
+  h->timings[5] = t_apply;
+  h->timings[6] = t_spmv;
+  h->timings[7] = t_orth;
+  h->timings[8] = n_apply;
+  h->timings[9] = n_spmv;
+  bool all = true;
+  for (int r = 0; r < k; ++r) {
+    if (info) {
+      info[r].iterations = iters[r];
+      info[r].restarts = cycles[r];
+      info[r].converged = conv[r];
+      info[r].relres = relres[r];
+      info[r].pad = 0;
+    }
+    all &= conv[r] != 0;
+  }
+  return all ? ORAS_OK : ORAS_NOT_CONVERGED;
+}
+
+extern "C" {
+
+int oras_solve(oras_handle* h, const oras_complex* rhs, int32_t k, double tol, oras_complex* x, oras_info* info,
+               int32_t mem) {
+  if (!h) return ORAS_ERR_INVALID_ARG;
+  if (!h->factored) { h->err = "oras_solve: call oras_factor first"; return ORAS_ERR_STATE; }
+  if (k < 1 || k > MAX_RHS || !rhs || !x || !(tol > 0.0)) { h->err = "oras_solve: bad k, tol or NULL vector"; return ORAS_ERR_INVALID_ARG; }
+  Timer t(h);
+  int rc = ensure_ws(h, k, h->opt.restart);
+  if (rc) return rc;
+  rc = load_input(h, rhs, k, mem, h->dev.bk);
+  if (rc) return rc;
+  rc = fgmres(h, k, tol, info);
+  if (rc < 0) return rc;
+  int rc2 = store_output(h, h->dev.xk, k, mem, x);
+  if (rc2) return rc2;
+  h->timings[4] = t.stop();
+  return rc;
+}
+
+int oras_matvec(oras_handle* h, const oras_complex* x, oras_complex* y, int32_t k, int32_t mem) {
+  if (!h || !x || !y || k < 1 || k > MAX_RHS) return ORAS_ERR_INVALID_ARG;
+  if (!h->factored) { h->err = "oras_matvec: call oras_factor first"; return ORAS_ERR_STATE; }
+  int rc = ensure_ws(h, k, h->opt.restart);
+  if (rc) return rc;
+  rc = load_input(h, x, k, mem, h->dev.bk);
+  if (rc) return rc;
+  launch_spmv_f64(h, h->dev.bk, h->dev.tmp, k);
+  return store_output(h, h->dev.tmp, k, mem, y);
+}
+
+int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k, int32_t mem) {
+  if (!h || !v || !z || k < 1 || k > MAX_RHS) return ORAS_ERR_INVALID_ARG;
+  if (!h->factored) { h->err = "oras_precond: call oras_factor first"; return ORAS_ERR_STATE; }
+  int rc = ensure_ws(h, k, h->opt.restart);
+  if (rc) return rc;
+  rc = load_input(h, v, k, mem, h->dev.bk);
+  if (rc) return rc;
+  launch_apply_f64out(h, h->dev.bk, h->dev.tmp, k);
+  return store_output(h, h->dev.tmp, k, mem, z);
+}
+
+int oras_rhs_dipole(oras_handle* h, const double* x0, const double* dir, oras_complex* b, int32_t mem) {
+  if (!h || !x0 || !dir || !b) return ORAS_ERR_INVALID_ARG;
+  if (!h->dev.uploaded) { h->err = "oras_rhs_dipole: call oras_factor first"; return ORAS_ERR_STATE; }
+  auto& d = h->dev;
+  int rc = ensure_ws(h, 1, h->opt.restart);
+  if (rc) return rc;
+  int* found = (int*)(d.scal + 4);
+  if (launch_dipole(h, x0, dir, d.tmp, found)) CK(cudaGetLastError());
+  int hf = 0;
+  CK(cudaMemcpyAsync(&hf, found, sizeof(int), cudaMemcpyDeviceToHost, d.stream));
+  CK(cudaStreamSynchronize(d.stream));
+  if (hf == 0x7fffffff) { h->err = "oras_rhs_dipole: source point lies in no tetrahedron"; return ORAS_ERR_INVALID_ARG; }
+  CK(cudaMemcpyAsync(b, d.tmp, sizeof(cplx) * h->mesh.ndof,
+                     mem == ORAS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, d.stream));
+  CK(cudaStreamSynchronize(d.stream));
+  return ORAS_OK;
+}
+
+// Gauss-Legendre nodes/weights on [0, 1] by Newton's method on the Legendre recurrence.
+static void gauss_legendre01(int n, double* x, double* w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int q = 2; q <= n; ++q) {
+        double p2 = ((2.0 * q - 1.0) * z * p1 - (q - 1.0) * p0) / q;
+        p0 = p1;
+        p1 = p2;
+      }
+      double pn = n == 1 ? z : p1, pm = n == 1 ? 1.0 : p0;
+      dp = n * (z * pn - pm) / (z * z - 1.0);
+      double dz = pn / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = 0.5 * (1.0 - z);
+    w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+int oras_rhs_plane_wave(oras_handle* h, const double* dvec, const oras_complex* pvec, oras_complex* b, int32_t mem) {
+  if (!h || !dvec || !pvec || !b) return ORAS_ERR_INVALID_ARG;
+  if (!h->factored) { h->err = "oras_rhs_plane_wave: call oras_factor first"; return ORAS_ERR_STATE; }
+  auto& d = h->dev;
+  int rc = ensure_ws(h, 1, h->opt.restart);
+  if (rc) return rc;
+  const int nq = 12;
+  double qs[16], qw[16];
+  gauss_legendre01(nq, qs, qw);
+  cplx* bface = nullptr;
+  CK(dalloc(bface, (size_t)std::max<int64_t>(1, h->mesh.nif) * h->mesh.nfl));
+  rc = launch_plane(h, dvec, pvec, h->k0, qs, qw, nq, bface, d.tmp);
+  cudaError_t e = cudaMemcpyAsync(b, d.tmp, sizeof(cplx) * h->mesh.ndof,
+                                  mem == ORAS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, d.stream);
+  cudaStreamSynchronize(d.stream);
+  cudaFree(bface);
+  if (rc || e != cudaSuccess) { h->err = "oras_rhs_plane_wave: launch failed"; return ORAS_ERR_CUDA; }
+  return ORAS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Internal declarations of the ORAS-FGMRES library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/oras.h"
+
+namespace oras {
+
+constexpr int TB = 64;            // tile order of the local-factor arena (TB x TB complex)
+constexpr int MAX_NFL = 15;       // face-local DOFs r(r+2) for r <= 3
+constexpr int MAX_NL = 45;        // tet-local DOFs for r <= 3
+constexpr int MAX_RHS = 64;
+
+struct cplx { double re, im; };
+
+// device status flags (Device::status): [0] error code, [1] detail, [2] subdomain
+enum { ST_ERR = 0, ST_DETAIL = 1, ST_SUB = 2 };
+enum { DEV_OK = 0, DEV_SINGULAR = 1, DEV_TIMEOUT = 2 };
+
+
+// ------------------------------------------------------------------ local DOF convention
+struct LocalDof {
+  char kind;      // 'e', 'f', 'v'
+  int ent, q;     // local entity index and index inside the entity
+  int i, j;       // Whitney edge (local vertices, i < j)
+  int k[4];       // exponents of lambda^k
+};
+std::vector<LocalDof> local_dofs(int r);
+int n_local(int r);
+int n_face_local(int r);                       // r(r+2)
+// tet-local indices of the face-local DOFs of local face lf (intrinsic face order:
+// edges (a,b), (a,c), (b,c), then the face's own DOFs)
+std::vector<int> face_local_dofs(int r, int lf);
+
+// Exact integration tables of the element and face matrices (see tables.cpp).
+struct Tables {
+  int r = 0, nl = 0, nfl = 0;
+  std::vector<double> cm;   // [nl][nl][10]   mass, unique Gram pairs p <= q
+  std::vector<double> ck;   // [nl][nl][21]   stiffness, unique pairs of the 6 cross products
+  std::vector<double> cs;   // [4][nfl][nfl][10] face tangential mass per local face
+  std::vector<int> fl;      // [4][nfl] tet-local index of each face-local DOF
+  // basis-value term table: DOF a = sum_t c * lambda^alpha * grad(lambda_m), 2 terms each
+  std::vector<double> tc;   // [nl][2]
+  std::vector<int> ta;      // [nl][2][4]
+  std::vector<int> tm;      // [nl][2]
+};
+Tables make_tables(int r);
+
+// ------------------------------------------------------------------ host integer set-up
+struct HostMesh {
+  int r = 0, nl = 0, nfl = 0;
+  int64_t nv = 0, nt = 0, ne = 0, nf = 0, ndof = 0;
+  int nsub = 0, overlap = 0, overlap_kind = 0;
+  std::vector<double> xyz;        // [nv][3]
+  std::vector<int32_t> st;        // [nt][4] sorted vertex ids
+  std::vector<int32_t> tet_faces; // [nt][4]
+  std::vector<int32_t> face_tets; // [nf][2]
+  std::vector<int32_t> dofmap;    // [nt][nl]
+  std::vector<int32_t> part;      // [nt]
+  // global row incidence: (t*nl + a) for every tet t carrying DOF g, ascending t
+  std::vector<int64_t> tinc_ptr;  // [ndof+1]
+  std::vector<int32_t> tinc;
+  // impedance faces (outer boundary + every interface face of some subdomain)
+  int64_t nif = 0;
+  std::vector<int32_t> if_face, if_tet0, if_lf0, if_tet1;  // tet1 = -1 on the outer boundary
+  std::vector<int32_t> if_dofs;   // [nif][nfl] global DOFs, intrinsic face order
+  std::vector<int64_t> finc_ptr;  // [ndof+1]
+  std::vector<int32_t> finc;      // slot*nfl + a_f
+  // CSR pattern of A
+  std::vector<int64_t> rowptr;    // [ndof+1]
+  std::vector<int32_t> cols;
+  int max_row_nnz = 0;
+  // subdomains
+  std::vector<int64_t> sub_ns, sub_np, sub_ns_off, sub_tile_off, sub_nt_off;
+  std::vector<int32_t> sub_dofs;  // concatenated N_s
+  std::vector<uint8_t> sub_pou;   // concatenated D_s
+  std::vector<int32_t> sub_tets;  // concatenated Omega_s^delta
+  std::vector<uint32_t> member;   // [nsub][words] tet membership bitmaps
+  int64_t member_words = 0;
+  int64_t arena_tiles = 0;
+  int64_t max_np = 0;
+};
+
+// Returns ORAS_OK or an error code with `err` filled.
+int host_setup(const oras_problem* p, int overlap_kind, HostMesh& m, std::string& err);
+
+// ------------------------------------------------------------------ device state
+template <typename T> struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+struct Device {
+  bool uploaded = false;
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  // mesh
+  double* xyz = nullptr;
+  int32_t* st = nullptr;
+  int32_t* dofmap = nullptr;
+  int64_t* tinc_ptr = nullptr;
+  int32_t* tinc = nullptr;
+  int32_t* if_tet0 = nullptr; int32_t* if_lf0 = nullptr; int32_t* if_tet1 = nullptr;
+  int32_t* if_dofs = nullptr;
+  int64_t* finc_ptr = nullptr;
+  int32_t* finc = nullptr;
+  int64_t* rowptr = nullptr;
+  int32_t* cols = nullptr;
+  int64_t* sub_ns = nullptr; int64_t* sub_np = nullptr; int64_t* sub_ns_off = nullptr;
+  int64_t* sub_tile_off = nullptr;
+  int32_t* sub_dofs = nullptr;
+  uint8_t* sub_pou = nullptr;
+  uint32_t* member = nullptr;
+  // tables
+  double* cm = nullptr; double* ck = nullptr; double* cs = nullptr; int32_t* fl = nullptr;
+  double* tc = nullptr; int32_t* ta = nullptr; int32_t* tm = nullptr;
+  // numeric
+  cplx* eps = nullptr; cplx* mu = nullptr;      // [nt]
+  cplx* elem = nullptr;                         // [nt][nl][nl]
+  double* fmat = nullptr;                       // [nif][nfl][nfl]
+  cplx* vals = nullptr;                         // [nnz]
+  void* arena = nullptr;                        // tiles, complex float or double
+  size_t arena_bytes = 0;
+  int factor_bits = 0;
+  int32_t* perm = nullptr;                      // [sum np] row permutation of P A = L U
+  int32_t* gidx = nullptr;                      // [sum np] N_s[perm[i]] or -1
+  int64_t* sub_np_off = nullptr;                // prefix of np (device)
+  // LU workspace
+  int32_t* lu_cand = nullptr;                   // tournament candidates
+  int32_t* lu_cnt = nullptr;                    // tournament arrival counters
+  int32_t* lu_ipiv = nullptr;                   // [nsub][TB] interchanges of the current step
+  void* lu_diag = nullptr;                      // [nsub] factored diagonal tile of the step
+  int32_t* status = nullptr;                    // device error flags [8]
+  int lu_max_chunks = 0;
+  // Krylov workspace
+  int ws_k = 0, ws_m = 0;
+  cplx* V = nullptr;                            // [(m+1)][N][k]
+  float* Zf = nullptr;                          // [m][N][k] complex FP32 (factor_bits 32)
+  cplx* Zd = nullptr;                           // [m][N][k] complex FP64 (factor_bits 64)
+  cplx* w = nullptr; cplx* xk = nullptr; cplx* bk = nullptr; cplx* tmp = nullptr;  // [N][k]
+  cplx* H = nullptr;                            // [k][(m+1)][m]
+  double* gcs = nullptr; cplx* gsn = nullptr;   // Givens [k][m]
+  cplx* g = nullptr;                            // [k][m+1]
+  double* red = nullptr;                        // reduction partials
+  double* scal = nullptr;                       // small scalars [k][8]
+  void* ybuf = nullptr;                         // apply: per-subdomain local vectors
+  size_t ybuf_bytes = 0;
+  cplx* io = nullptr;                           // staging for host I/O [N][k] col-major
+  size_t io_elems = 0;
+  double* host_pinned = nullptr;                // small pinned host scalars
+};
+
+}  // namespace oras
+
+struct oras_handle {
+  oras::HostMesh mesh;
+  oras::Tables tab;
+  oras::Device dev;
+  oras_options opt{};
+  std::string err;
+  bool factored = false;
+  double k0 = 0.0;
+  bool timing = false;
+  double timings[16] = {0};
+};

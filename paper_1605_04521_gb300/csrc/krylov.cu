@@ -1,0 +1,318 @@
+// FP64 Krylov kernels of the right-preconditioned FGMRES(m) (Sec. 5): complex CSR SpMV,
+// modified Gram-Schmidt Arnoldi with fused (axpy + next dot) passes, complex Givens rotations
+// on the device, the small triangular solve and the solution update.  Multi-vectors are
+// stored [N][k] (the k right-hand sides of a pseudo-block solve adjacent in memory).
+// Every reduction is a fixed two-stage sum (block partials, then a fixed-order sum), so the
+// results do not depend on scheduling.
+#include "dev.cuh"
+
+namespace oras {
+
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int RED_THREADS = 256;
+
+template <typename XT> __device__ __forceinline__ cplx ld_c(const XT* p, int64_t i);
+template <> __device__ __forceinline__ cplx ld_c<cplx>(const cplx* p, int64_t i) { return p[i]; }
+template <> __device__ __forceinline__ cplx ld_c<CT<float>>(const CT<float>* p, int64_t i) {
+  CT<float> v = p[i];
+  return {(double)v.re, (double)v.im};
+}
+
+// y = A x  (x: [N][k] in XT, y: [N][k] FP64).  One warp per row, up to 8 RHS per pass.
+template <typename XT>
+__global__ void k_spmv(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ cols,
+                       const cplx* __restrict__ vals, const XT* __restrict__ x, cplx* __restrict__ y,
+                       int k, int r0, int kc) {
+  int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  cplx acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = {0.0, 0.0};
+  for (int64_t p = rowptr[row] + lane; p < rowptr[row + 1]; p += 32) {
+    cplx a = vals[p];
+    int64_t c = cols[p];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q < kc) acc[q] = cadd(acc[q], cmul(a, ld_c<XT>(x, c * k + r0 + q)));
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (q >= kc) break;
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[q].re += __shfl_down_sync(0xffffffffu, acc[q].re, o);
+      acc[q].im += __shfl_down_sync(0xffffffffu, acc[q].im, o);
+    }
+    if (lane == 0) y[row * k + r0 + q] = acc[q];
+  }
+}
+
+// partials[b][r] = sum over this block's slice of conj(a) * b  (complex), or |a|^2 if b == nullptr
+__device__ void block_reduce_store(cplx* vals, int k, cplx* partials) {
+  // vals: per-thread accumulators for r in 0..k-1 are reduced across the block
+  __shared__ cplx sh[RED_THREADS / 32][MAX_RHS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = 0; r < k; ++r) {
+    cplx v = vals[r];
+    for (int o = 16; o > 0; o >>= 1) {
+      v.re += __shfl_down_sync(0xffffffffu, v.re, o);
+      v.im += __shfl_down_sync(0xffffffffu, v.im, o);
+    }
+    if (lane == 0) sh[warp][r] = v;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    cplx t = {0.0, 0.0};
+    for (int w = 0; w < RED_THREADS / 32; ++w) t = cadd(t, sh[w][r]);
+    partials[(int64_t)blockIdx.x * k + r] = t;
+  }
+}
+
+// Fixed-order sum of the block partials of the previous pass.
+__device__ __forceinline__ cplx sum_partials(const cplx* partials, int k, int r) {
+  cplx t = {0.0, 0.0};
+  for (int b = 0; b < RED_BLOCKS; ++b) t = cadd(t, partials[(int64_t)b * k + r]);
+  return t;
+}
+
+// first dot of step j: partial <V_0, w>
+__global__ void __launch_bounds__(RED_THREADS) k_dot(int64_t nk, int k, const cplx* __restrict__ a,
+                                                     const cplx* __restrict__ b, cplx* __restrict__ partials) {
+  cplx acc[MAX_RHS];
+  for (int r = 0; r < k; ++r) acc[r] = {0.0, 0.0};
+  // nk = N * k; element e belongs to RHS e % k.  Stride keeps e % k fixed per thread when
+  // the total thread count is a multiple of k (k divides 64 * ... is not assumed: loop over r).
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(e % k);
+    cplx x = a[e], y = b[e];
+    acc[r].re += x.re * y.re + x.im * y.im;
+    acc[r].im += x.re * y.im - x.im * y.re;
+  }
+  block_reduce_store(acc, k, partials);
+}
+
+// h = sum(partials_in) (H[r][i][j] stored by block 0); w -= h V_i; then partial <V_next, w> or |w|^2.
+__global__ void __launch_bounds__(RED_THREADS) k_mgs_step(int64_t nk, int k, int m, int i, int j,
+                                                          const cplx* __restrict__ Vi, const cplx* __restrict__ Vn,
+                                                          cplx* __restrict__ w, const cplx* __restrict__ pin,
+                                                          cplx* __restrict__ pout, cplx* __restrict__ H) {
+  __shared__ cplx hs[MAX_RHS];
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    hs[r] = sum_partials(pin, k, r);
+    if (blockIdx.x == 0) H[((int64_t)r * (m + 1) + i) * m + j] = hs[r];
+  }
+  __syncthreads();
+  cplx acc[MAX_RHS];
+  for (int r = 0; r < k; ++r) acc[r] = {0.0, 0.0};
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(e % k);
+    cplx h = hs[r], v = Vi[e], x = w[e];
+    x.re -= h.re * v.re - h.im * v.im;
+    x.im -= h.re * v.im + h.im * v.re;
+    w[e] = x;
+    if (Vn) {
+      cplx u = Vn[e];
+      acc[r].re += u.re * x.re + u.im * x.im;
+      acc[r].im += u.re * x.im - u.im * x.re;
+    } else {
+      acc[r].re += x.re * x.re + x.im * x.im;
+    }
+  }
+  block_reduce_store(acc, k, pout);
+}
+
+// h_{j+1,j} = ||w||; V_{j+1} = w / h (0 if h == 0); block 0 then runs the Givens update of
+// every RHS: apply rotations 0..j-1 to column j of H, build rotation j, update g, res = |g_{j+1}|.
+__global__ void __launch_bounds__(RED_THREADS) k_mgs_finish(int64_t nk, int k, int m, int j,
+                                                            const cplx* __restrict__ w, cplx* __restrict__ Vn,
+                                                            const cplx* __restrict__ pin, cplx* __restrict__ H,
+                                                            double* __restrict__ cs, cplx* __restrict__ sn,
+                                                            cplx* __restrict__ g, double* __restrict__ res) {
+  __shared__ double hn[MAX_RHS];
+  for (int r = threadIdx.x; r < k; r += blockDim.x) hn[r] = sqrt(sum_partials(pin, k, r).re);
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(e % k);
+    double h = hn[r];
+    cplx x = w[e];
+    Vn[e] = h > 0.0 ? cplx{x.re / h, x.im / h} : cplx{0.0, 0.0};
+  }
+  if (blockIdx.x != 0) return;
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    cplx* Hr = H + (int64_t)r * (m + 1) * m;
+    double* c = cs + (int64_t)r * m;
+    cplx* s = sn + (int64_t)r * m;
+    cplx* gr = g + (int64_t)r * (m + 1);
+    Hr[(int64_t)(j + 1) * m + j] = {hn[r], 0.0};
+    for (int q = 0; q < j; ++q) {
+      cplx a = Hr[(int64_t)q * m + j], b = Hr[(int64_t)(q + 1) * m + j];
+      cplx t = cadd(cscale(a, c[q]), cmul(s[q], b));
+      cplx u = csub(cscale(b, c[q]), cmul(cconj(s[q]), a));
+      Hr[(int64_t)q * m + j] = t;
+      Hr[(int64_t)(q + 1) * m + j] = u;
+    }
+    cplx a = Hr[(int64_t)j * m + j];
+    double bb = hn[r];
+    double aa = hypot(a.re, a.im);
+    double cj;
+    cplx sj;
+    if (bb == 0.0) { cj = 1.0; sj = {0.0, 0.0}; }
+    else if (aa == 0.0) { cj = 0.0; sj = {1.0, 0.0}; }
+    else {
+      double den = hypot(aa, bb);
+      cj = aa / den;
+      sj = {a.re / aa * bb / den, a.im / aa * bb / den};
+    }
+    c[j] = cj;
+    s[j] = sj;
+    Hr[(int64_t)j * m + j] = cadd(cscale(a, cj), cscale(sj, bb));
+    Hr[(int64_t)(j + 1) * m + j] = {0.0, 0.0};
+    cplx gj = gr[j];
+    gr[j + 1] = cscale(cmul(cconj(sj), gj), -1.0);
+    gr[j] = cscale(gj, cj);
+    res[r] = hypot(gr[j + 1].re, gr[j + 1].im);
+  }
+}
+
+// y = H(0:kk,0:kk)^{-1} g(0:kk) per RHS (back substitution), y = 0 for inactive RHS.
+__global__ void k_hsolve(int k, int m, int kk, const cplx* __restrict__ H, const cplx* __restrict__ g,
+                         const int32_t* __restrict__ active, cplx* __restrict__ y) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k) return;
+  const cplx* Hr = H + (int64_t)r * (m + 1) * m;
+  cplx* yr = y + (int64_t)r * m;
+  if (!active[r]) {
+    for (int q = 0; q < kk; ++q) yr[q] = {0.0, 0.0};
+    return;
+  }
+  for (int q = kk - 1; q >= 0; --q) {
+    cplx t = g[(int64_t)r * (m + 1) + q];
+    for (int l = q + 1; l < kk; ++l) t = csub(t, cmul(Hr[(int64_t)q * m + l], yr[l]));
+    cplx d = Hr[(int64_t)q * m + q];
+    double dd = d.re * d.re + d.im * d.im;
+    yr[q] = dd > 0.0 ? cplx{(t.re * d.re + t.im * d.im) / dd, (t.im * d.re - t.re * d.im) / dd} : cplx{0.0, 0.0};
+  }
+}
+
+// x += sum_q y_q Z_q   (Z: [m][N][k])
+template <typename ZT>
+__global__ void k_xupdate(int64_t nk, int k, int m, int kk, const ZT* __restrict__ Z, const cplx* __restrict__ y,
+                          cplx* __restrict__ x) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nk) return;
+  int r = (int)(e % k);
+  cplx acc = x[e];
+  for (int q = 0; q < kk; ++q) acc = cadd(acc, cmul(y[(int64_t)r * m + q], ld_c<ZT>(Z, (int64_t)q * nk + e)));
+  x[e] = acc;
+}
+
+// r = b - A x (SpMV output in r already holds A x): r = b - r; partial |r|^2
+__global__ void __launch_bounds__(RED_THREADS) k_residual(int64_t nk, int k, const cplx* __restrict__ b,
+                                                          cplx* __restrict__ r, cplx* __restrict__ partials) {
+  cplx acc[MAX_RHS];
+  for (int q = 0; q < k; ++q) acc[q] = {0.0, 0.0};
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
+    int q = (int)(e % k);
+    cplx v = csub(b[e], r[e]);
+    r[e] = v;
+    acc[q].re += v.re * v.re + v.im * v.im;
+  }
+  block_reduce_store(acc, k, partials);
+}
+
+// norms[r] = sqrt(sum partials) (single block)
+__global__ void k_norms(int k, const cplx* __restrict__ partials, double* __restrict__ out) {
+  int r = threadIdx.x;
+  if (r < k) out[r] = sqrt(sum_partials(partials, k, r).re);
+}
+
+// V0 = r / beta for active RHS (0 otherwise); g = (beta, 0, ...)
+__global__ void k_restart(int64_t nk, int k, int m, const cplx* __restrict__ rv, const double* __restrict__ beta,
+                          const int32_t* __restrict__ active, cplx* __restrict__ V0, cplx* __restrict__ g) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nk) {
+    int q = (int)(e % k);
+    double b = beta[q];
+    V0[e] = (active[q] && b > 0.0) ? cplx{rv[e].re / b, rv[e].im / b} : cplx{0.0, 0.0};
+  }
+  if (e < k) {
+    for (int l = 0; l <= m; ++l) g[(int64_t)e * (m + 1) + l] = {0.0, 0.0};
+    g[(int64_t)e * (m + 1)] = {active[e] ? beta[e] : 0.0, 0.0};
+  }
+}
+
+// column-major host layout [k][N] <-> internal [N][k]
+__global__ void k_to_internal(int64_t n, int k, const cplx* __restrict__ src, cplx* __restrict__ dst) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * k) return;
+  int64_t g = e / k;
+  int r = (int)(e % k);
+  dst[e] = src[(int64_t)r * n + g];
+}
+__global__ void k_to_external(int64_t n, int k, const cplx* __restrict__ src, cplx* __restrict__ dst) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * k) return;
+  int64_t g = e / k;
+  int r = (int)(e % k);
+  dst[(int64_t)r * n + g] = src[e];
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename XT>
+static void spmv_t(const oras_handle* h, const XT* x, cplx* y, int k) {
+  const auto& m = h->mesh;
+  const auto& d = h->dev;
+  int64_t blocks = (m.ndof * 32 + 255) / 256;
+  for (int r0 = 0; r0 < k; r0 += 8) {
+    int kc = k - r0 < 8 ? k - r0 : 8;
+    k_spmv<XT><<<(unsigned)blocks, 256, 0, d.stream>>>(m.ndof, d.rowptr, d.cols, d.vals, x, y, k, r0, kc);
+  }
+}
+void launch_spmv_f64(const oras_handle* h, const cplx* x, cplx* y, int k) { spmv_t<cplx>(h, x, y, k); }
+void launch_spmv_f32(const oras_handle* h, const void* x, cplx* y, int k) { spmv_t<CT<float>>(h, (const CT<float>*)x, y, k); }
+
+void launch_dot(const oras_handle* h, const cplx* a, const cplx* b, cplx* partials, int k) {
+  k_dot<<<RED_BLOCKS, RED_THREADS, 0, h->dev.stream>>>(h->mesh.ndof * k, k, a, b, partials);
+}
+void launch_mgs_step(const oras_handle* h, int k, int m, int i, int j, const cplx* Vi, const cplx* Vn, cplx* w,
+                     const cplx* pin, cplx* pout, cplx* H) {
+  k_mgs_step<<<RED_BLOCKS, RED_THREADS, 0, h->dev.stream>>>(h->mesh.ndof * k, k, m, i, j, Vi, Vn, w, pin, pout, H);
+}
+void launch_mgs_finish(const oras_handle* h, int k, int m, int j, const cplx* w, cplx* Vn, const cplx* pin,
+                       cplx* H, double* cs, cplx* sn, cplx* g, double* res) {
+  k_mgs_finish<<<RED_BLOCKS, RED_THREADS, 0, h->dev.stream>>>(h->mesh.ndof * k, k, m, j, w, Vn, pin, H, cs, sn, g, res);
+}
+void launch_hsolve(const oras_handle* h, int k, int m, int kk, const cplx* H, const cplx* g, const int32_t* active,
+                   cplx* y) {
+  k_hsolve<<<1, 64, 0, h->dev.stream>>>(k, m, kk, H, g, active, y);
+}
+void launch_xupdate_f64(const oras_handle* h, int k, int m, int kk, const cplx* Z, const cplx* y, cplx* x) {
+  int64_t nk = h->mesh.ndof * k;
+  k_xupdate<cplx><<<(unsigned)((nk + 255) / 256), 256, 0, h->dev.stream>>>(nk, k, m, kk, Z, y, x);
+}
+void launch_xupdate_f32(const oras_handle* h, int k, int m, int kk, const void* Z, const cplx* y, cplx* x) {
+  int64_t nk = h->mesh.ndof * k;
+  k_xupdate<CT<float>><<<(unsigned)((nk + 255) / 256), 256, 0, h->dev.stream>>>(nk, k, m, kk, (const CT<float>*)Z, y, x);
+}
+void launch_residual(const oras_handle* h, int k, const cplx* b, cplx* r, cplx* partials) {
+  k_residual<<<RED_BLOCKS, RED_THREADS, 0, h->dev.stream>>>(h->mesh.ndof * k, k, b, r, partials);
+}
+void launch_norms(const oras_handle* h, int k, const cplx* partials, double* out) {
+  k_norms<<<1, 64, 0, h->dev.stream>>>(k, partials, out);
+}
+void launch_restart(const oras_handle* h, int k, int m, const cplx* rv, const double* beta, const int32_t* active,
+                    cplx* V0, cplx* g) {
+  int64_t nk = h->mesh.ndof * k;
+  k_restart<<<(unsigned)((nk + 255) / 256), 256, 0, h->dev.stream>>>(nk, k, m, rv, beta, active, V0, g);
+}
+void launch_to_internal(const oras_handle* h, int k, const cplx* src, cplx* dst) {
+  int64_t nk = h->mesh.ndof * k;
+  k_to_internal<<<(unsigned)((nk + 255) / 256), 256, 0, h->dev.stream>>>(h->mesh.ndof, k, src, dst);
+}
+void launch_to_external(const oras_handle* h, int k, const cplx* src, cplx* dst) {
+  int64_t nk = h->mesh.ndof * k;
+  k_to_external<<<(unsigned)((nk + 255) / 256), 256, 0, h->dev.stream>>>(h->mesh.ndof, k, src, dst);
+}
+int red_blocks() { return RED_BLOCKS; }
+
+}  // namespace oras

@@ -1,0 +1,446 @@
+// Batched dense LU with row pivoting of the local matrices A_s (Sec. 4: the A_s^{-1} of ORAS),
+// P_s A_s = L_s U_s, over the tiled arena (TB x TB complex tiles, column-major inside a tile).
+//
+// Right-looking blocked LU, panel width TB.  Each panel step k, for every subdomain at once:
+//  1. tournament pivoting of the tall panel (tile column k): chunks of rows are reduced with
+//     partial pivoting (pivot = max |Re| + |Im|, first on ties) to TB candidate rows each; pairs
+//     of candidate sets are merged the same way up a binary tree; the root's choice is the pivot
+//     sequence of the step and its factored TB x TB block is L11\U11.  This is communication-
+//     avoiding LU (Grigori, Demmel, Xiang 2011): the chosen rows differ from column-by-column
+//     partial pivoting only in which rows win, not in the factorisation it produces.
+//  2. the row interchanges of the step are applied to every column (one permutation of at most
+//     2 TB rows);
+//  3. L21 = A21 U11^{-1} and U12 = L11^{-1} A12 (triangular solves on tiles);
+//  4. A22 -= L21 U12 (tile GEMMs).
+// The tree merge uses "last arriver continues" counters, so no block ever waits for another.
+#include <cstdio>
+
+#include "dev.cuh"
+
+namespace oras {
+
+template <typename R> __device__ __forceinline__ CT<R> mulc(CT<R> a, CT<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R> __device__ __forceinline__ CT<R> subc(CT<R> a, CT<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R> __device__ __forceinline__ CT<R> invc(CT<R> a) {
+  R d = a.re * a.re + a.im * a.im;
+  return {a.re / d, -a.im / d};
+}
+template <typename R> __device__ __forceinline__ R abs1(CT<R> a) { return fabs(a.re) + fabs(a.im); }
+
+template <typename R> struct LuCfg;
+template <> struct LuCfg<float> { static constexpr int CH = 256; };
+template <> struct LuCfg<double> { static constexpr int CH = 128; };
+
+constexpr int PS = TB + 1;  // padded row stride of the panel in shared memory
+constexpr int LU_THREADS = 256;
+
+struct LuArgs {
+  int nsub;
+  int k;
+  const int64_t* np;        // [nsub] padded order
+  const int64_t* tile_off;  // [nsub]
+  const int64_t* np_off;    // [nsub] prefix of np (perm arrays)
+  int32_t* perm;            // [sum np]
+  int32_t* cand;            // [nsub][slots][TB]
+  int32_t* cnt;             // [nsub][slots]
+  int slots;
+  int32_t* pairs;           // [nsub][2*TB][2] (dst, src) + count in pairs_n
+  int32_t* pairs_n;         // [nsub]
+  void* diag;               // [nsub][TB*TB] factored diagonal tile (column-major)
+  int32_t* status;
+};
+
+template <typename R>
+__device__ __forceinline__ CT<R>* tile_ptr(void* arena, const LuArgs& a, int s, int64_t I, int64_t J) {
+  int64_t nts = a.np[s] / TB;
+  return (CT<R>*)arena + (a.tile_off[s] + I * nts + J) * (int64_t)TB * TB;
+}
+
+// Partial-pivoting elimination of an m x TB panel P (row stride PS) held in shared memory,
+// carrying row ids.  On return rows 0..TB-1 are the chosen pivot rows in order, factored.
+template <typename R>
+__device__ void gepp_panel(CT<R>* P, int32_t* ids, int m, R* rv, int* ri) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int ncol = m < TB ? m : TB;
+  for (int c = 0; c < ncol; ++c) {
+    // pivot search over rows c..m-1
+    R best = -1;
+    int bi = 0x7fffffff;
+    for (int i = c + tid; i < m; i += nthr) {
+      R v = abs1(P[i * PS + c]);
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      R ov = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((tid & 31) == 0) { rv[tid >> 5] = best; ri[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      R b = rv[0];
+      int i0 = ri[0];
+      for (int w = 1; w < nthr / 32; ++w)
+        if (rv[w] > b || (rv[w] == b && ri[w] < i0)) { b = rv[w]; i0 = ri[w]; }
+      ri[0] = (b > 0) ? i0 : c;  // exactly zero column: keep the row in place
+    }
+    __syncthreads();
+    const int p = ri[0];
+    if (p != c) {
+      for (int j = tid; j < TB; j += nthr) {
+        CT<R> t = P[c * PS + j];
+        P[c * PS + j] = P[p * PS + j];
+        P[p * PS + j] = t;
+      }
+      if (tid == 0) { int32_t t = ids[c]; ids[c] = ids[p]; ids[p] = t; }
+    }
+    __syncthreads();
+    CT<R> piv = P[c * PS + c];
+    if (abs1(piv) > R(0)) {
+      CT<R> inv = invc(piv);
+      for (int i = c + 1 + tid; i < m; i += nthr) {
+        CT<R> l = mulc(P[i * PS + c], inv);
+        P[i * PS + c] = l;
+        for (int j = c + 1; j < TB; ++j) P[i * PS + j] = subc(P[i * PS + j], mulc(l, P[c * PS + j]));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Load panel rows `rows[0..m)` (matrix row indices) of tile column k into P.
+template <typename R>
+__device__ void load_rows(void* arena, const LuArgs& a, int s, const int32_t* rows, int m, CT<R>* P) {
+  for (int e = threadIdx.x; e < m * TB; e += blockDim.x) {
+    int i = e % m, j = e / m;
+    int32_t r = rows[i];
+    const CT<R>* t = tile_ptr<R>(arena, a, s, r / TB, a.k);
+    P[i * PS + j] = t[j * TB + (r % TB)];
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(LU_THREADS) k_lu_tournament(LuArgs a, void* arena) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int CH = LuCfg<R>::CH;
+  CT<R>* P = (CT<R>*)smem_raw;                         // [CH][PS]
+  int32_t* ids = (int32_t*)(P + CH * PS);              // [CH]
+  R* rv = (R*)(ids + CH);                              // [32]
+  int* ri = (int*)(rv + 32);                           // [32]
+  __shared__ int s_old;
+  const int s = blockIdx.y;
+  const int64_t np = a.np[s], nts = np / TB;
+  if (a.k >= nts) return;
+  const int64_t R0 = (int64_t)a.k * TB;
+  const int64_t rows_total = np - R0;
+  const int nch = (int)((rows_total + CH - 1) / CH);
+  int c = blockIdx.x;
+  if (c >= nch) return;
+  int64_t mrem = rows_total - (int64_t)c * CH;
+  int m = (int)(mrem < CH ? mrem : CH);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) ids[i] = (int32_t)(R0 + (int64_t)c * CH + i);
+  __syncthreads();
+  load_rows<R>(arena, a, s, ids, m, P);
+  __syncthreads();
+  gepp_panel<R>(P, ids, m, rv, ri);
+  int32_t* cand = a.cand + (int64_t)s * a.slots * TB;
+  int32_t* cnt = a.cnt + (int64_t)s * a.slots;
+  int level_off = 0, n_l = nch, j = c;
+  if (n_l > 1)
+    for (int i = threadIdx.x; i < TB; i += blockDim.x) cand[(level_off + j) * TB + i] = ids[i];
+  while (n_l > 1) {
+    const int n_next = (n_l + 1) >> 1;
+    const int parent = j >> 1, sib = j ^ 1;
+    const int next_off = level_off + n_l;
+    if (sib >= n_l) {  // odd one out: pass the candidates up unchanged
+      for (int i = threadIdx.x; i < TB; i += blockDim.x) cand[(next_off + parent) * TB + i] = ids[i];
+      level_off = next_off; n_l = n_next; j = parent;
+      continue;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_old = atomicAdd(&cnt[next_off + parent], 1);
+    __syncthreads();
+    if (s_old == 0) return;  // the sibling will merge
+    if (threadIdx.x == 0) cnt[next_off + parent] = 0;
+    __threadfence();
+    const int left = j & ~1;
+    for (int i = threadIdx.x; i < 2 * TB; i += blockDim.x) {
+      int child = left + (i >= TB);
+      ids[i] = ((volatile int32_t*)cand)[(level_off + child) * TB + (i % TB)];
+    }
+    __syncthreads();
+    load_rows<R>(arena, a, s, ids, 2 * TB, P);
+    __syncthreads();
+    gepp_panel<R>(P, ids, 2 * TB, rv, ri);
+    level_off = next_off; n_l = n_next; j = parent;
+    if (n_l > 1)
+      for (int i = threadIdx.x; i < TB; i += blockDim.x) cand[(level_off + j) * TB + i] = ids[i];
+  }
+  // root: ids[0..TB) are the pivot rows, P[0..TB) the factored diagonal block
+  CT<R>* dg = (CT<R>*)a.diag + (int64_t)s * TB * TB;
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int i = e % TB, jj = e / TB;
+    dg[jj * TB + i] = P[i * PS + jj];
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < TB; ++i)
+      if (!(abs1(P[i * PS + i]) > R(0))) {
+        atomicCAS(&a.status[ST_ERR], DEV_OK, DEV_SINGULAR);
+        a.status[ST_SUB] = s;
+      }
+  }
+  // permutation of the step: position R0+i receives row ids[i]; the displaced rows of the top
+  // block fill the vacated pivot positions (LAPACK interchange order).
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t* mpos = ri;  // reuse: up to 2*TB modified positions -> contents
+    int32_t posv[2 * TB], rowv[2 * TB];
+    int nm = 0;
+    auto row_at = [&](int32_t pos) {
+      for (int q = 0; q < nm; ++q)
+        if (posv[q] == pos) return rowv[q];
+      return pos;
+    };
+    auto pos_of = [&](int32_t row) {
+      for (int q = 0; q < nm; ++q)
+        if (rowv[q] == row) return posv[q];
+      return row;  // untouched row is still at its own position
+    };
+    auto set = [&](int32_t pos, int32_t row) {
+      for (int q = 0; q < nm; ++q)
+        if (posv[q] == pos) { rowv[q] = row; return; }
+      posv[nm] = pos; rowv[nm] = row; ++nm;
+    };
+    for (int i = 0; i < TB; ++i) {
+      int32_t tgt = (int32_t)(R0 + i);
+      int32_t pr = pos_of(ids[i]);
+      if (pr != tgt) {
+        int32_t ra = row_at(tgt), rb = row_at(pr);
+        set(tgt, rb);
+        set(pr, ra);
+      }
+    }
+    int32_t* pr = a.pairs + (int64_t)s * 2 * TB * 2;
+    int np_ = 0;
+    for (int q = 0; q < nm; ++q)
+      if (posv[q] != rowv[q]) { pr[np_ * 2] = posv[q]; pr[np_ * 2 + 1] = rowv[q]; ++np_; }
+    a.pairs_n[s] = np_;
+    (void)mpos;
+  }
+}
+
+// Apply the step's row permutation to every column of the matrix and to perm.
+template <typename R>
+__global__ void k_lu_swap(LuArgs a, void* arena) {
+  extern __shared__ unsigned char smem_raw[];
+  CT<R>* buf = (CT<R>*)smem_raw;  // [2*TB][TB]
+  const int s = blockIdx.y;
+  const int64_t nts = a.np[s] / TB;
+  if (a.k >= nts) return;
+  const int J = blockIdx.x;
+  if (J > nts) return;
+  const int n = a.pairs_n[s];
+  if (n == 0) return;
+  const int32_t* pr = a.pairs + (int64_t)s * 2 * TB * 2;
+  if (J == nts) {  // perm vector
+    int32_t* perm = a.perm + a.np_off[s];
+    __shared__ int32_t pv[2 * TB];
+    for (int q = threadIdx.x; q < n; q += blockDim.x) pv[q] = perm[pr[q * 2 + 1]];
+    __syncthreads();
+    for (int q = threadIdx.x; q < n; q += blockDim.x) perm[pr[q * 2]] = pv[q];
+    return;
+  }
+  for (int e = threadIdx.x; e < n * TB; e += blockDim.x) {
+    int q = e % n, j = e / n;
+    int32_t src = pr[q * 2 + 1];
+    buf[q * TB + j] = tile_ptr<R>(arena, a, s, src / TB, J)[j * TB + (src % TB)];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * TB; e += blockDim.x) {
+    int q = e % n, j = e / n;
+    int32_t dst = pr[q * 2];
+    tile_ptr<R>(arena, a, s, dst / TB, J)[j * TB + (dst % TB)] = buf[q * TB + j];
+  }
+}
+
+// blockIdx.x == 0: write the factored diagonal tile; 1..nrem: L tiles below; nrem+1..2 nrem: U tiles.
+template <typename R>
+__global__ void __launch_bounds__(TB) k_lu_trsm(LuArgs a, void* arena) {
+  extern __shared__ unsigned char smem_raw[];
+  CT<R>* D = (CT<R>*)smem_raw;       // [TB][PS] diagonal, column-major with padding
+  CT<R>* X = D + TB * PS;            // [TB][PS] work tile, column-major with padding
+  const int s = blockIdx.y;
+  const int64_t nts = a.np[s] / TB;
+  const int k = a.k;
+  if (k >= nts) return;
+  const int nrem = (int)(nts - k - 1);
+  const int b = blockIdx.x;
+  if (b > 2 * nrem) return;
+  const CT<R>* dg = (const CT<R>*)a.diag + (int64_t)s * TB * TB;
+  const int t = threadIdx.x;
+  if (b == 0) {
+    CT<R>* dst = tile_ptr<R>(arena, a, s, k, k);
+    for (int e = t; e < TB * TB; e += blockDim.x) dst[e] = dg[e];
+    return;
+  }
+  for (int e = t; e < TB * TB; e += blockDim.x) D[(e / TB) * PS + (e % TB)] = dg[e];
+  const bool lower = b <= nrem;
+  const int64_t I = lower ? k + b : k, J = lower ? k : k + (b - nrem);
+  CT<R>* tp = tile_ptr<R>(arena, a, s, I, J);
+  for (int e = t; e < TB * TB; e += blockDim.x) X[(e / TB) * PS + (e % TB)] = tp[e];
+  __syncthreads();
+  if (lower) {
+    // row t of X: x U = a, forward over columns
+    for (int j = 0; j < TB; ++j) {
+      CT<R> acc = X[j * PS + t];
+      for (int l = 0; l < j; ++l) acc = subc(acc, mulc(X[l * PS + t], D[j * PS + l]));
+      X[j * PS + t] = mulc(acc, invc(D[j * PS + j]));
+    }
+  } else {
+    // column t of X: L y = a, unit lower
+    for (int i = 1; i < TB; ++i) {
+      CT<R> acc = X[t * PS + i];
+      for (int l = 0; l < i; ++l) acc = subc(acc, mulc(D[l * PS + i], X[t * PS + l]));
+      X[t * PS + i] = acc;
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < TB * TB; e += blockDim.x) tp[e] = X[(e / TB) * PS + (e % TB)];
+}
+
+// C_IJ -= L_Ik U_kJ for I, J > k.  16x16 threads, each a 4x4 block of complex outputs.
+template <typename R>
+__global__ void __launch_bounds__(256) k_lu_update(LuArgs a, void* arena) {
+  extern __shared__ unsigned char smem_raw[];
+  CT<R>* As = (CT<R>*)smem_raw;  // [TB][TB] column-major: A(i,l) at l*TB+i
+  CT<R>* Bs = As + TB * TB;      // [TB][TB] row-major:    B(l,j) at l*TB+j
+  const int s = blockIdx.y;
+  const int64_t nts = a.np[s] / TB;
+  const int k = a.k;
+  if (k >= nts) return;
+  const int64_t nrem = nts - k - 1;
+  const int64_t e0 = blockIdx.x;
+  if (e0 >= nrem * nrem) return;
+  const int64_t I = k + 1 + e0 / nrem, J = k + 1 + e0 % nrem;
+  const CT<R>* L = tile_ptr<R>(arena, a, s, I, k);
+  const CT<R>* U = tile_ptr<R>(arena, a, s, k, J);
+  const int t = threadIdx.x;
+  for (int e = t; e < TB * TB; e += 256) {
+    As[e] = L[e];
+    int j = e / TB, l = e % TB;  // U stored column-major: element (l, j) at j*TB + l
+    Bs[l * TB + j] = U[e];
+  }
+  __syncthreads();
+  const int ty = t / 16, tx = t % 16;
+  CT<R> acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = {R(0), R(0)};
+  for (int l = 0; l < TB; ++l) {
+    CT<R> av[4], bv[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) av[p] = As[l * TB + ty * 4 + p];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bv[q] = Bs[l * TB + tx * 4 + q];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[p][q].re += av[p].re * bv[q].re - av[p].im * bv[q].im;
+        acc[p][q].im += av[p].re * bv[q].im + av[p].im * bv[q].re;
+      }
+  }
+  CT<R>* C = tile_ptr<R>(arena, a, s, I, J);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      int i = ty * 4 + p, j = tx * 4 + q;
+      CT<R> c = C[j * TB + i];
+      C[j * TB + i] = {c.re - acc[p][q].re, c.im - acc[p][q].im};
+    }
+}
+
+__global__ void k_iota_perm(int64_t total, int32_t* perm, const int64_t* np_off, int nsub) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int lo = 0, hi = nsub - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (np_off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  perm[i] = (int32_t)(i - np_off[lo]);
+}
+
+// gidx[i] = N_s[perm[i]] for perm[i] < n_s, else -1 (padding)
+__global__ void k_gidx(int64_t total, const int32_t* perm, const int64_t* np_off, const int64_t* ns,
+                       const int64_t* ns_off, const int32_t* sub_dofs, int nsub, int32_t* gidx) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int lo = 0, hi = nsub - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (np_off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  int32_t p = perm[i];
+  gidx[i] = p < ns[lo] ? sub_dofs[ns_off[lo] + p] : -1;
+}
+
+template <typename R>
+static int lu_run(oras_handle* h) {
+  auto& m = h->mesh;
+  auto& d = h->dev;
+  constexpr int CH = LuCfg<R>::CH;
+  LuArgs a;
+  a.nsub = m.nsub;
+  a.np = d.sub_np;
+  a.tile_off = d.sub_tile_off;
+  a.np_off = d.sub_np_off;
+  a.perm = d.perm;
+  a.cand = d.lu_cand;
+  a.cnt = d.lu_cnt;
+  a.slots = 2 * d.lu_max_chunks + 16;
+  a.pairs = d.lu_ipiv;
+  a.pairs_n = d.lu_ipiv + (int64_t)m.nsub * 2 * TB * 2;
+  a.diag = d.lu_diag;
+  a.status = d.status;
+  int64_t total = d.sub_np_off ? 0 : 0;
+  for (int s = 0; s < m.nsub; ++s) total += m.sub_np[s];
+  k_iota_perm<<<(unsigned)((total + 255) / 256), 256, 0, d.stream>>>(total, d.perm, d.sub_np_off, m.nsub);
+  const int max_nts = (int)(m.max_np / TB);
+  size_t smem_t = (size_t)CH * PS * sizeof(CT<R>) + CH * sizeof(int32_t) + 32 * sizeof(R) + 32 * sizeof(int);
+  size_t smem_s = (size_t)2 * TB * TB * sizeof(CT<R>);
+  size_t smem_r = (size_t)2 * TB * PS * sizeof(CT<R>);
+  size_t smem_u = (size_t)2 * TB * TB * sizeof(CT<R>);
+  cudaFuncSetAttribute(k_lu_tournament<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+  cudaFuncSetAttribute(k_lu_swap<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+  cudaFuncSetAttribute(k_lu_trsm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
+  cudaFuncSetAttribute(k_lu_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_u);
+  for (int k = 0; k < max_nts; ++k) {
+    a.k = k;
+    int64_t rows_max = m.max_np - (int64_t)k * TB;
+    int nch = (int)((rows_max + CH - 1) / CH);
+    int64_t nrem = max_nts - k - 1;
+    k_lu_tournament<R><<<dim3(nch, m.nsub), LU_THREADS, smem_t, d.stream>>>(a, d.arena);
+    k_lu_swap<R><<<dim3(max_nts + 1, m.nsub), 256, smem_s, d.stream>>>(a, d.arena);
+    k_lu_trsm<R><<<dim3((unsigned)(2 * nrem + 1), m.nsub), TB, smem_r, d.stream>>>(a, d.arena);
+    if (nrem > 0)
+      k_lu_update<R><<<dim3((unsigned)(nrem * nrem), m.nsub), 256, smem_u, d.stream>>>(a, d.arena);
+  }
+  k_gidx<<<(unsigned)((total + 255) / 256), 256, 0, d.stream>>>(total, d.perm, d.sub_np_off, d.sub_ns,
+                                                              d.sub_ns_off, d.sub_dofs, m.nsub, d.gidx);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_lu(oras_handle* h) { return h->dev.factor_bits == 64 ? lu_run<double>(h) : lu_run<float>(h); }
+
+int lu_max_chunks(int64_t max_np, int factor_bits) {
+  int ch = factor_bits == 64 ? LuCfg<double>::CH : LuCfg<float>::CH;
+  return (int)((max_np + ch - 1) / ch);
+}
+
+}  // namespace oras

@@ -1,0 +1,320 @@
+"""ctypes binding of the C ABI declared in include/oras.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Arrays are numpy arrays
+(host) or torch CUDA tensors (device, `mem=ORAS_MEM_DEVICE`); complex arrays are complex128.
+The library must be built (paper_1605_04521_gb300.build.build()); there is no fallback: if
+the shared object is missing or fails to load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liboras_gb300.so")
+
+ORAS_OK = 0
+ORAS_NOT_CONVERGED = 1
+ORAS_ERR_INVALID_ARG = -1
+ORAS_ERR_BAD_MESH = -2
+ORAS_ERR_OUT_OF_MEMORY = -3
+ORAS_ERR_SINGULAR_LOCAL = -4
+ORAS_ERR_DEVICE_TIMEOUT = -5
+ORAS_ERR_CUDA = -6
+ORAS_ERR_REJECTED = -7
+ORAS_ERR_UNSUPPORTED = -8
+ORAS_ERR_STATE = -9
+ORAS_MEM_HOST = 0
+ORAS_MEM_DEVICE = 1
+ORAS_WEIGHTS_POU = 0
+ORAS_WEIGHTS_NONE = 1
+ORAS_OVERLAP_VERTEX = 0
+ORAS_OVERLAP_FACE = 1
+
+
+class oras_complex(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class oras_problem(C.Structure):
+    _fields_ = [("nv", C.c_int64), ("xyz", C.c_void_p), ("nt", C.c_int64), ("tets", C.c_void_p),
+                ("eps_r", C.c_void_p), ("mu_r", C.c_void_p), ("k0", C.c_double), ("r", C.c_int32),
+                ("nsub", C.c_int32), ("overlap", C.c_int32), ("part", C.c_void_p)]
+
+
+class oras_options(C.Structure):
+    _fields_ = [("restart", C.c_int32), ("max_iter", C.c_int32), ("factor_bits", C.c_int32),
+                ("weights", C.c_int32), ("overlap_kind", C.c_int32), ("reserved", C.c_int32 * 11)]
+
+
+class oras_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
+                ("pad", C.c_int32), ("relres", C.c_double)]
+
+
+EXPORTS = {
+    "oras_last_error": (C.c_char_p, [C.c_void_p]),
+    "oras_abi_version": (C.c_int32, []),
+    "oras_create": (C.c_int, [C.POINTER(oras_problem), C.POINTER(oras_options), C.POINTER(C.c_void_p)]),
+    "oras_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32]),
+    "oras_setup": (C.c_int, [C.POINTER(oras_problem), C.POINTER(oras_options), C.POINTER(C.c_void_p)]),
+    "oras_destroy": (None, [C.c_void_p]),
+    "oras_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "oras_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
+                             C.POINTER(oras_info), C.c_int32]),
+    "oras_rhs_plane_wave": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "oras_rhs_dipole": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "oras_ndof": (C.c_int64, [C.c_void_p]),
+    "oras_nlocal": (C.c_int32, [C.c_void_p]),
+    "oras_nsub": (C.c_int32, [C.c_void_p]),
+    "oras_dofmap": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "oras_partition": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "oras_subdomain_size": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_int64)]),
+    "oras_subdomain": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "oras_nnz": (C.c_int64, [C.c_void_p]),
+    "oras_arena_bytes": (C.c_int64, [C.c_void_p]),
+    "oras_element_matrices": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "oras_global_csr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "oras_matvec": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
+    "oras_precond": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
+    "oras_timings": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "oras_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1605_04521_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class OrasError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"oras error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+def _check(h, rc, allow=(ORAS_OK,)):
+    if rc in allow:
+        return rc
+    msg = lib.oras_last_error(h)
+    raise OrasError(rc, msg.decode() if msg else "")
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    keep = [xyz, tets]
+    p = oras_problem()
+    p.nv, p.xyz, p.nt, p.tets = xyz.shape[0], xyz.ctypes.data, tets.shape[0], tets.ctypes.data
+    if eps_r is not None:
+        e = _c128(eps_r)
+        keep.append(e)
+        p.eps_r = e.ctypes.data
+    if mu_r is not None:
+        m = _c128(mu_r)
+        keep.append(m)
+        p.mu_r = m.ctypes.data
+    p.k0, p.r, p.nsub, p.overlap = float(k0), int(r), int(nsub), int(overlap)
+    if part is not None:
+        pa = np.ascontiguousarray(part, dtype=np.int32)
+        keep.append(pa)
+        p.part = pa.ctypes.data
+    return p, keep
+
+
+def _options(restart=0, max_iter=0, factor_bits=0, weights=0, overlap_kind=0):
+    o = oras_options()
+    o.restart, o.max_iter, o.factor_bits, o.weights, o.overlap_kind = restart, max_iter, factor_bits, weights, overlap_kind
+    return o
+
+
+def oras_create(xyz, tets, r, nsub, overlap, part=None, **opts):
+    """Host integer set-up; returns the handle (c_void_p)."""
+    p, keep = _problem(xyz, tets, None, None, 1.0, r, nsub, overlap, part)
+    o = _options(**opts)
+    h = C.c_void_p()
+    _check(None, lib.oras_create(C.byref(p), C.byref(o), C.byref(h)))
+    del keep
+    return h
+
+
+def oras_setup(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part=None, **opts):
+    p, keep = _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part)
+    o = _options(**opts)
+    h = C.c_void_p()
+    _check(None, lib.oras_setup(C.byref(p), C.byref(o), C.byref(h)))
+    del keep
+    return h
+
+
+def oras_factor(h, eps_r, mu_r, k0, mem=ORAS_MEM_HOST):
+    if mem == ORAS_MEM_HOST:
+        eps_r = _c128(eps_r)
+        mu_r = None if mu_r is None else _c128(mu_r)
+    return _check(h, lib.oras_factor(h, _ptr(eps_r), _ptr(mu_r), float(k0), mem))
+
+
+def oras_destroy(h):
+    lib.oras_destroy(h)
+
+
+def oras_set_stream(h, stream_ptr):
+    return _check(h, lib.oras_set_stream(h, C.c_void_p(stream_ptr)))
+
+
+def oras_set_timing(h, on):
+    return _check(h, lib.oras_set_timing(h, int(on)))
+
+
+def oras_timings(h, n=10):
+    t = np.zeros(n)
+    _check(h, lib.oras_timings(h, _ptr(t), n))
+    return t
+
+
+def oras_ndof(h):
+    return int(lib.oras_ndof(h))
+
+
+def oras_nlocal(h):
+    return int(lib.oras_nlocal(h))
+
+
+def oras_nsub(h):
+    return int(lib.oras_nsub(h))
+
+
+def oras_nnz(h):
+    return int(lib.oras_nnz(h))
+
+
+def oras_arena_bytes(h):
+    return int(lib.oras_arena_bytes(h))
+
+
+def oras_dofmap(h, nt):
+    out = np.empty((nt, oras_nlocal(h)), dtype=np.int32)
+    _check(h, lib.oras_dofmap(h, _ptr(out)))
+    return out
+
+
+def oras_partition(h, nt):
+    out = np.empty(nt, dtype=np.int32)
+    _check(h, lib.oras_partition(h, _ptr(out)))
+    return out
+
+
+def oras_subdomain_size(h, s):
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(h, lib.oras_subdomain_size(h, s, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def oras_subdomain(h, s):
+    n, nt, _ = oras_subdomain_size(h, s)
+    dofs = np.empty(n, dtype=np.int32)
+    pou = np.empty(n, dtype=np.uint8)
+    tets = np.empty(nt, dtype=np.int32)
+    _check(h, lib.oras_subdomain(h, s, _ptr(dofs), _ptr(pou), _ptr(tets)))
+    return dofs, pou, tets
+
+
+def oras_element_matrices(h, tets):
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    nl = oras_nlocal(h)
+    out = np.empty((len(tets), nl, nl), dtype=np.complex128)
+    _check(h, lib.oras_element_matrices(h, _ptr(tets), len(tets), _ptr(out)))
+    return out
+
+
+def oras_global_csr(h):
+    n = oras_ndof(h)
+    nnz = oras_nnz(h)
+    rowptr = np.empty(n + 1, dtype=np.int64)
+    cols = np.empty(nnz, dtype=np.int32)
+    vals = np.empty(nnz, dtype=np.complex128)
+    _check(h, lib.oras_global_csr(h, _ptr(rowptr), _ptr(cols), _ptr(vals)))
+    return rowptr, cols, vals
+
+
+def _vec_call(fn, h, x, k, mem, out=None):
+    n = oras_ndof(h)
+    if mem == ORAS_MEM_HOST:
+        x = np.asfortranarray(np.asarray(x, dtype=np.complex128).reshape(n, k) if k > 1 else
+                              np.asarray(x, dtype=np.complex128).reshape(n, 1))
+        y = np.empty((n, k), dtype=np.complex128, order="F")
+        _check(h, fn(h, _ptr(x), _ptr(y), k, mem))
+        return y if k > 1 else y[:, 0]
+    _check(h, fn(h, _ptr(x), _ptr(out), k, mem))
+    return out
+
+
+def oras_matvec(h, x, k=1, mem=ORAS_MEM_HOST, out=None):
+    return _vec_call(lib.oras_matvec, h, x, k, mem, out)
+
+
+def oras_precond(h, v, k=1, mem=ORAS_MEM_HOST, out=None):
+    return _vec_call(lib.oras_precond, h, v, k, mem, out)
+
+
+def oras_solve(h, rhs, tol, k=1, mem=ORAS_MEM_HOST, out=None):
+    """Returns (x, infos, rc); host: rhs (N,) or (N, k) complex; device: torch tensors,
+    column-major N x k (i.e. shape (k, N) contiguous)."""
+    n = oras_ndof(h)
+    info = (oras_info * k)()
+    if mem == ORAS_MEM_HOST:
+        b = np.asfortranarray(np.asarray(rhs, dtype=np.complex128).reshape(n, k))
+        x = np.empty((n, k), dtype=np.complex128, order="F")
+        rc = _check(h, lib.oras_solve(h, _ptr(b), k, float(tol), _ptr(x), info, mem),
+                    allow=(ORAS_OK, ORAS_NOT_CONVERGED))
+        x = x if k > 1 else x[:, 0]
+    else:
+        rc = _check(h, lib.oras_solve(h, _ptr(rhs), k, float(tol), _ptr(out), info, mem),
+                    allow=(ORAS_OK, ORAS_NOT_CONVERGED))
+        x = out
+    infos = [dict(iterations=i.iterations, restarts=i.restarts, converged=bool(i.converged),
+                  relres=i.relres) for i in info]
+    return x, infos, rc
+
+
+def oras_rhs_dipole(h, x0, direction, mem=ORAS_MEM_HOST, out=None):
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    d = np.ascontiguousarray(direction, dtype=np.float64)
+    if mem == ORAS_MEM_HOST:
+        out = np.empty(oras_ndof(h), dtype=np.complex128)
+    _check(h, lib.oras_rhs_dipole(h, _ptr(x0), _ptr(d), _ptr(out), mem))
+    return out
+
+
+def oras_rhs_plane_wave(h, d, p, mem=ORAS_MEM_HOST, out=None):
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    p = _c128(p)
+    if mem == ORAS_MEM_HOST:
+        out = np.empty(oras_ndof(h), dtype=np.complex128)
+    _check(h, lib.oras_rhs_plane_wave(h, _ptr(d), _ptr(p), _ptr(out), mem))
+    return out

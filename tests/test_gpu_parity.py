@@ -1,0 +1,228 @@
+"""GPU path (C ABI) against the CPU oracle on the same seeded inputs.
+
+Bars: integer arrays bit-exact; element matrices, A, right-hand sides and A x within 1e-12
+relative; true FP64 residual of the GPU field <= 1e-8 measured with the oracle's own A; GPU
+field within 1e-6 (relative L2) of the oracle's field.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import synth
+from oracle import assemble, dd, elements, problem, topology
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def O():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1605_04521_gb300 import build
+    build.build()
+    from paper_1605_04521_gb300 import oras
+    return oras
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def gpu_handle(O, w, factor_bits=32, **kw):
+    xyz, tets = w.mesh()
+    eps, mu = w.materials(xyz, tets)
+    return O.oras_setup(xyz, tets, eps, mu, w.k0, w.r, w.nsub, w.overlap, factor_bits=factor_bits,
+                        restart=w.restart, **kw)
+
+
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_element_matrices(O, r):
+    w = synth.small(n=3, r=r, nsub=2, overlap=0)
+    h = gpu_handle(O, w)
+    try:
+        xyz, tets = w.mesh()
+        eps, mu = w.materials(xyz, tets)
+        topo = topology.build(tets, len(xyz), r)
+        ref = elements.element_matrices(xyz, topo.st, r, eps, mu, w.k0)
+        got = O.oras_element_matrices(h, np.arange(len(tets)))
+        err = np.abs(got - ref).max(axis=(1, 2)) / np.abs(ref).max(axis=(1, 2))
+        assert err.max() <= 1e-12, err.max()
+    finally:
+        O.oras_destroy(h)
+
+
+@pytest.mark.parametrize("r,n", [(1, 4), (2, 3), (3, 2)])
+def test_global_matrix_and_matvec(O, r, n):
+    w = synth.small(n=n, r=r, nsub=4, overlap=1)
+    h = gpu_handle(O, w)
+    try:
+        p = problem.from_workload(w, with_oras=False)
+        A = p.A.tocsr()
+        A.sort_indices()
+        rowptr, cols, vals = O.oras_global_csr(h)
+        assert np.array_equal(rowptr, A.indptr) and np.array_equal(cols, A.indices)
+        assert np.abs(vals - A.data).max() <= 1e-12 * np.abs(A.data).max()
+        rng = np.random.default_rng(11)
+        X = rng.normal(size=(A.shape[0], 3)) + 1j * rng.normal(size=(A.shape[0], 3))
+        Y = O.oras_matvec(h, X, k=3)
+        assert rel(Y, A @ X) <= 1e-13
+    finally:
+        O.oras_destroy(h)
+
+
+def test_right_hand_sides(O):
+    w = synth.config(0)
+    h = gpu_handle(O, w, factor_bits=64)
+    try:
+        xyz, tets = w.mesh()
+        eps, mu = w.materials(xyz, tets)
+        topo = topology.build(tets, len(xyz), w.r)
+        bp = assemble.plane_wave_load(topo, xyz, eps, mu, w.k0, synth.PLANE_D, synth.PLANE_P, nq=12)
+        gp = O.oras_rhs_plane_wave(h, synth.PLANE_D, synth.PLANE_P.astype(np.complex128))
+        assert rel(gp, bp) <= 1e-12
+        for x0 in synth.dipole_ring(3):
+            bd = assemble.dipole_load(topo, xyz, x0, [0, 0, 1.0])
+            gd = O.oras_rhs_dipole(h, x0, [0, 0, 1.0])
+            assert rel(gd, bd) <= 1e-12
+        with pytest.raises(O.OrasError):
+            O.oras_rhs_dipole(h, [2.0, 0.5, 0.5], [0, 0, 1.0])
+    finally:
+        O.oras_destroy(h)
+
+
+@pytest.mark.parametrize("bits,tol", [(64, 1e-9), (32, 2e-3)])
+def test_preconditioner_apply(O, bits, tol):
+    """z = M^-1 v against the oracle's ORAS (FP64 LU, partial pivoting)."""
+    w = synth.small(n=4, r=2, nsub=8, overlap=1)
+    h = gpu_handle(O, w, factor_bits=bits)
+    try:
+        p = problem.from_workload(w)
+        rng = np.random.default_rng(12)
+        v = rng.normal(size=p.topo.ndof) + 1j * rng.normal(size=p.topo.ndof)
+        z = O.oras_precond(h, v)
+        assert rel(z, p.oras.apply(v)) <= tol
+    finally:
+        O.oras_destroy(h)
+
+
+CASES = [
+    dict(w=synth.config(0), bits=64),                                                   # 8^3, r=1, plane wave
+    dict(w=synth.small(n=4, r=2, nsub=8, overlap=1), bits=32),                          # head, r=2
+    dict(w=synth.small(n=3, r=3, nsub=4, overlap=1), bits=32),                          # r=3
+    dict(w=synth.small(n=5, r=1, nsub=7, overlap=2, head=False, source="plane"), bits=32),  # nsub not 2^k
+    dict(w=synth.small(n=3, r=2, nsub=1, overlap=0), bits=64),                          # one subdomain
+    dict(w=synth.small(n=4, r=2, nsub=8, overlap=0), bits=32),                          # zero overlap
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_solve_matches_oracle(O, case):
+    w, bits = CASES[case]["w"], CASES[case]["bits"]
+    p = problem.from_workload(w)
+    b = p.B[:, 0]
+    h = gpu_handle(O, w, factor_bits=bits)
+    try:
+        x, info, rc = O.oras_solve(h, b, w.tol)
+        assert rc == O.ORAS_OK and info[0]["converged"]
+        true_res = np.linalg.norm(b - p.A @ x) / np.linalg.norm(b)
+        assert true_res <= 1e-8
+        assert abs(info[0]["relres"] - true_res) <= 1e-9
+        xo = problem.solve(p, tol=w.tol, m=w.restart)[0]
+        xd = spla.spsolve(p.A.tocsc(), b)
+        assert rel(x, xo.x) <= 1e-6
+        assert rel(x, xd) <= 1e-6
+        if w.nsub == 1:
+            assert info[0]["iterations"] == 1
+    finally:
+        O.oras_destroy(h)
+
+
+def test_multi_rhs_alone_and_batched(O):
+    w = synth.small(n=4, r=2, nsub=8, overlap=1, nrhs=4)
+    p = problem.from_workload(w)
+    h = gpu_handle(O, w)
+    try:
+        X, info, rc = O.oras_solve(h, p.B, w.tol, k=4)
+        assert rc == O.ORAS_OK
+        for j in range(4):
+            b = p.B[:, j]
+            assert np.linalg.norm(b - p.A @ X[:, j]) / np.linalg.norm(b) <= 1e-8
+            xj, _, _ = O.oras_solve(h, b, w.tol)
+            assert rel(X[:, j], xj) <= 1e-6
+            assert rel(X[:, j], spla.spsolve(p.A.tocsc(), b)) <= 1e-6
+    finally:
+        O.oras_destroy(h)
+
+
+def test_zero_rhs_and_device_pointers(O):
+    import torch
+    w = synth.small(n=3, r=2, nsub=4, overlap=1)
+    p = problem.from_workload(w)
+    h = gpu_handle(O, w)
+    try:
+        n = p.topo.ndof
+        x, info, rc = O.oras_solve(h, np.zeros(n), 1e-8)
+        assert rc == O.ORAS_OK and np.all(x == 0) and info[0]["iterations"] == 0
+        xh, _, _ = O.oras_solve(h, p.B[:, 0], 1e-8)
+        bt = torch.from_numpy(p.B[:, 0].copy()).cuda()
+        xt = torch.empty_like(bt)
+        O.oras_solve(h, bt, 1e-8, mem=O.ORAS_MEM_DEVICE, out=xt)
+        torch.cuda.synchronize()
+        assert np.array_equal(xt.cpu().numpy(), xh)
+    finally:
+        O.oras_destroy(h)
+
+
+def test_refactor_equals_fresh_setup(O):
+    """New materials on the same mesh handle give the same operator as a fresh set-up."""
+    w = synth.small(n=4, r=2, nsub=8, overlap=1)
+    xyz, tets = w.mesh()
+    eps, mu = w.materials(xyz, tets)
+    eps2 = eps.copy()
+    eps2[::7] = 55 - 22j
+    h1 = O.oras_setup(xyz, tets, eps, mu, w.k0, 2, 8, 1)
+    h2 = O.oras_setup(xyz, tets, eps2, mu, w.k0, 2, 8, 1)
+    try:
+        O.oras_factor(h1, eps2, mu, w.k0)
+        b = O.oras_rhs_dipole(h1, synth.dipole_ring(1)[0], [0, 0, 1.0])
+        x1, _, _ = O.oras_solve(h1, b, 1e-8)
+        x2, _, _ = O.oras_solve(h2, b, 1e-8)
+        assert np.array_equal(x1, x2)
+        assert np.array_equal(O.oras_global_csr(h1)[2], O.oras_global_csr(h2)[2])
+    finally:
+        O.oras_destroy(h1)
+        O.oras_destroy(h2)
+
+
+def test_full_size_head16_r2_workload(O):
+    """The 16^3 x 6, r = 2, 64-subdomain, 2-layer workload (163,424 DOFs): integer arrays
+    bit-exact, sampled element matrices and the whole A within 1e-12, dipole load within
+    1e-12, and the GPU field's true residual <= 1e-8 with the oracle's independently assembled A."""
+    w = synth.config(1)
+    xyz, tets = w.mesh()
+    eps, mu = w.materials(xyz, tets)
+    h = gpu_handle(O, w)
+    try:
+        topo = topology.build(tets, len(xyz), w.r)
+        assert np.array_equal(O.oras_dofmap(h, len(tets)), topo.dofmap)
+        part = dd.rcb(xyz, topo.st, w.nsub)
+        assert np.array_equal(O.oras_partition(h, len(tets)), part)
+        sample = np.random.default_rng(3).choice(len(tets), 64, replace=False)
+        ref = elements.element_matrices(xyz, topo.st[sample], w.r, eps[sample], mu[sample], w.k0)
+        got = O.oras_element_matrices(h, sample)
+        assert (np.abs(got - ref).max(axis=(1, 2)) / np.abs(ref).max(axis=(1, 2))).max() <= 1e-12
+        A = assemble.global_matrix(topo, xyz, eps, mu, w.k0)
+        A.sort_indices()
+        _, cols, vals = O.oras_global_csr(h)
+        assert np.array_equal(cols, A.indices)
+        assert np.abs(vals - A.data).max() <= 1e-12 * np.abs(A.data).max()
+        x0 = synth.dipole_ring(1)[0]
+        b = assemble.dipole_load(topo, xyz, x0, [0, 0, 1.0])
+        assert rel(O.oras_rhs_dipole(h, x0, [0, 0, 1.0]), b) <= 1e-12
+        x, info, rc = O.oras_solve(h, b, w.tol)
+        assert rc == O.ORAS_OK
+        assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1e-8
+    finally:
+        O.oras_destroy(h)

@@ -1,0 +1,116 @@
+"""CPU-only checks of the CUDA library: it loads, exports every symbol of include/oras.h, and
+its host integer set-up (DOF numbering, partition, overlap, N_s, D_s) is bit-exact against
+the oracle.  No GPU call is made here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dd, topology
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def O():
+    from paper_1605_04521_gb300 import build
+    build.build()
+    from paper_1605_04521_gb300 import oras
+    return oras
+
+
+def test_exports_every_declared_symbol(O):
+    hdr = open(os.path.join(ROOT, "include", "oras.h")).read()
+    declared = sorted(set(re.findall(r"\b(oras_[a-z_0-9]+)\s*\(", hdr)))
+    assert len(declared) >= 25
+    for name in declared:
+        assert hasattr(O.lib, name), name
+        assert name in O.EXPORTS, name
+
+
+@pytest.mark.parametrize("n,r,nsub,delta,kind", [
+    (4, 2, 8, 1, "vertex"), (8, 1, 8, 1, "vertex"), (3, 3, 4, 2, "vertex"), (5, 2, 16, 1, "vertex"),
+    (4, 2, 8, 2, "face"), (6, 1, 7, 1, "vertex"), (2, 3, 1, 0, "vertex"), (16, 2, 64, 2, "vertex")])
+def test_host_setup_bit_exact(O, n, r, nsub, delta, kind):
+    xyz, tets = synth.kuhn_cube(n)
+    h = O.oras_create(xyz, tets, r, nsub, delta,
+                      overlap_kind=O.ORAS_OVERLAP_FACE if kind == "face" else O.ORAS_OVERLAP_VERTEX)
+    try:
+        topo = topology.build(tets, len(xyz), r)
+        dec = dd.decompose(topo, xyz, nsub, delta, kind=kind)
+        assert O.oras_ndof(h) == topo.ndof
+        assert np.array_equal(O.oras_dofmap(h, len(tets)), topo.dofmap)
+        assert np.array_equal(O.oras_partition(h, len(tets)), dec.part)
+        for s in range(nsub):
+            dofs, pou, tt = O.oras_subdomain(h, s)
+            assert np.array_equal(dofs, dec.dofs[s])
+            assert np.array_equal(pou, dec.pou[s].astype(np.uint8))
+            assert np.array_equal(tt, dec.tets[s])
+            _, _, npad = O.oras_subdomain_size(h, s)
+            assert npad % 64 == 0 and npad >= len(dofs) > npad - 64
+    finally:
+        O.oras_destroy(h)
+
+
+def test_user_partition_and_csr_pattern(O):
+    """A caller-given partition is used as is; the CSR pattern equals the oracle's."""
+    import scipy.sparse as sp
+    xyz, tets = synth.kuhn_cube(3)
+    rng = np.random.default_rng(0)
+    part = rng.integers(0, 5, size=len(tets)).astype(np.int32)
+    part[:5] = np.arange(5)
+    h = O.oras_create(xyz, tets, 2, 5, 1, part=part)
+    try:
+        assert np.array_equal(O.oras_partition(h, len(tets)), part)
+        rowptr = np.empty(O.oras_ndof(h) + 1, dtype=np.int64)
+        cols = np.empty(O.oras_nnz(h), dtype=np.int32)
+        O._check(h, O.lib.oras_global_csr(h, O._ptr(rowptr), O._ptr(cols), None))
+        topo = topology.build(tets, len(xyz), 2)
+        nl = topo.dofmap.shape[1]
+        rows = np.repeat(topo.dofmap, nl, axis=1).ravel()
+        cc = np.tile(topo.dofmap, (1, nl)).ravel()
+        P = sp.coo_matrix((np.ones(len(rows)), (rows, cc)), shape=(topo.ndof,) * 2).tocsr()
+        P.sort_indices()
+        assert np.array_equal(rowptr, P.indptr) and np.array_equal(cols, P.indices)
+    finally:
+        O.oras_destroy(h)
+
+
+def test_error_codes(O):
+    xyz, tets = synth.kuhn_cube(2)
+    bad = tets.copy()
+    bad[3, 1] = len(xyz) + 7
+    with pytest.raises(O.OrasError) as e:
+        O.oras_create(xyz, bad, 1, 2, 0)
+    assert e.value.code == O.ORAS_ERR_BAD_MESH
+    rep = tets.copy()
+    rep[0, 1] = rep[0, 0]
+    with pytest.raises(O.OrasError) as e:
+        O.oras_create(xyz, rep, 1, 2, 0)
+    assert e.value.code == O.ORAS_ERR_BAD_MESH
+    flat = xyz.copy()
+    flat[:, 2] = 0.0
+    with pytest.raises(O.OrasError) as e:
+        O.oras_create(flat, tets, 1, 2, 0)
+    assert e.value.code == O.ORAS_ERR_BAD_MESH
+    for kw in (dict(r=4, nsub=2, overlap=0), dict(r=1, nsub=0, overlap=0),
+               dict(r=1, nsub=len(tets) + 1, overlap=0), dict(r=1, nsub=2, overlap=-1)):
+        with pytest.raises(O.OrasError) as e:
+            O.oras_create(xyz, tets, kw["r"], kw["nsub"], kw["overlap"])
+        assert e.value.code == O.ORAS_ERR_INVALID_ARG
+    with pytest.raises(O.OrasError) as e:
+        O.oras_create(xyz, tets, 1, 2, 0, factor_bits=16)
+    assert e.value.code == O.ORAS_ERR_INVALID_ARG
+    # numeric calls before the numeric set-up report a state error without touching a GPU
+    h = O.oras_create(xyz, tets, 1, 2, 0)
+    try:
+        with pytest.raises(O.OrasError) as e:
+            O.oras_solve(h, np.ones(O.oras_ndof(h)), 1e-8)
+        assert e.value.code == O.ORAS_ERR_STATE
+        with pytest.raises(O.OrasError) as e:
+            O.oras_matvec(h, np.ones(O.oras_ndof(h)))
+        assert e.value.code == O.ORAS_ERR_STATE
+    finally:
+        O.oras_destroy(h)
