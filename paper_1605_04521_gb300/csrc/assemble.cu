@@ -398,6 +398,7 @@ int launch_element(const oras_handle* h, double k0) {
   int64_t blocks = (m.nt + EL_TETS - 1) / EL_TETS;
   k_element<<<(unsigned)blocks, 256, 0, d.stream>>>(m.nt, m.nl, d.xyz, d.st, d.eps, d.mu, k0 * k0,
                                                     d.cm, d.ck, d.elem);
+  count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -407,6 +408,7 @@ int launch_faces(const oras_handle* h) {
   if (m.nif == 0) return 0;
   k_faces<<<(unsigned)m.nif, 256, 0, d.stream>>>(m.nif, m.nfl, d.xyz, d.st, d.if_tet0, d.if_lf0, d.cs,
                                                  d.fmat);
+  count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -433,6 +435,7 @@ int launch_global_rows(const oras_handle* h, double k0) {
   int64_t blocks = (m.ndof + ROW_WARPS - 1) / ROW_WARPS;
   k_global_rows<<<(unsigned)blocks, ROW_WARPS * 32, smem, h->dev.stream>>>(A, m.ndof, m.max_row_nnz,
                                                                           h->dev.vals);
+  count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -450,6 +453,7 @@ static int launch_local_rows_t(const oras_handle* h, double k0) {
   k_local_rows<R><<<(unsigned)blocks, ROW_WARPS * 32, smem, d.stream>>>(
       A, m.nsub, total, d.sub_np_off, d.sub_ns, d.sub_np, d.sub_ns_off, d.sub_tile_off, d.sub_dofs,
       m.max_row_nnz, (CT<R>*)d.arena);
+  count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -464,8 +468,10 @@ int launch_dipole(const oras_handle* h, const double* x0, const double* dir, cpl
   cudaMemcpyAsync(found, &init, sizeof(int), cudaMemcpyHostToDevice, d.stream);
   cudaMemsetAsync(b, 0, sizeof(cplx) * m.ndof, d.stream);
   k_locate<<<(unsigned)((m.nt + 255) / 256), 256, 0, d.stream>>>(m.nt, d.xyz, d.st, x0[0], x0[1], x0[2], found);
+  count_launches(1);
   k_dipole<<<1, 64, 0, d.stream>>>(m.nl, d.xyz, d.st, d.dofmap, found, x0[0], x0[1], x0[2], dir[0],
                                    dir[1], dir[2], d.tc, d.ta, d.tm, b);
+  count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -485,8 +491,10 @@ int launch_plane(const oras_handle* h, const double* dvec, const oras_complex* p
     k_plane_faces<<<(unsigned)m.nif, 32, 0, d.stream>>>(m.nif, m.nfl, d.xyz, d.st, d.if_tet0, d.if_lf0,
                                                         d.if_tet1, d.fl, d.eps, d.mu, d.tc, d.ta, d.tm,
                                                         P, bface);
+  count_launches(1);
   k_gather_faces<<<(unsigned)((m.ndof + 255) / 256), 256, 0, d.stream>>>(m.ndof, m.nfl, d.finc_ptr, d.finc,
                                                                         bface, b);
+  count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

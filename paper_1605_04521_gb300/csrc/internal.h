@@ -155,6 +155,14 @@ struct Device {
   double* host_pinned = nullptr;                // small pinned host scalars
 };
 
+// ------------------------------------------------------------------ instrumentation
+// Kernel classes timed with CUDA event pairs on the handle's stream when timing is on.
+enum KClass { KC_ELEMENT = 0, KC_GLOBAL_ROWS, KC_LOCAL_ROWS, KC_LU_TOURNAMENT, KC_LU_SWAP, KC_LU_TRSM,
+              KC_LU_UPDATE, KC_APPLY, KC_SPMV, KC_ORTH, KC_OTHER, KC_COUNT };
+int prof_begin(const oras_handle* h);                 // -1 when timing is off
+void prof_end(const oras_handle* h, int cls, int begin, int launches);
+void count_launches(int n);                           // process-wide launch counter
+
 }  // namespace oras
 
 struct oras_handle {
@@ -167,4 +175,9 @@ struct oras_handle {
   double k0 = 0.0;
   bool timing = false;
   double timings[16] = {0};
+  mutable std::vector<cudaEvent_t> evpool;
+  mutable size_t ev_used = 0;
+  mutable std::vector<int> marks;                    // (class, begin event, end event, launches)*
+  double cls_ms[oras::KC_COUNT] = {0};
+  double cls_n[oras::KC_COUNT] = {0};
 };

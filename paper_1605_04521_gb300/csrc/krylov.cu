@@ -266,6 +266,7 @@ static void spmv_t(const oras_handle* h, const XT* x, cplx* y, int k) {
   for (int r0 = 0; r0 < k; r0 += 8) {
     int kc = k - r0 < 8 ? k - r0 : 8;
     k_spmv<XT><<<(unsigned)blocks, 256, 0, d.stream>>>(m.ndof, d.rowptr, d.cols, d.vals, x, y, k, r0, kc);
+    count_launches(1);
   }
 }
 void launch_spmv_f64(const oras_handle* h, const cplx* x, cplx* y, int k) { spmv_t<cplx>(h, x, y, k); }
@@ -273,45 +274,56 @@ void launch_spmv_f32(const oras_handle* h, const void* x, cplx* y, int k) { spmv
 
 void launch_dot(const oras_handle* h, const cplx* a, const cplx* b, cplx* partials, int k) {
   k_dot<<<RED_BLOCKS, RED_THREADS, 0, h->dev.stream>>>(h->mesh.ndof * k, k, a, b, partials);
+  count_launches(1);
 }
 void launch_mgs_step(const oras_handle* h, int k, int m, int i, int j, const cplx* Vi, const cplx* Vn, cplx* w,
                      const cplx* pin, cplx* pout, cplx* H) {
   k_mgs_step<<<RED_BLOCKS, RED_THREADS, 0, h->dev.stream>>>(h->mesh.ndof * k, k, m, i, j, Vi, Vn, w, pin, pout, H);
+  count_launches(1);
 }
 void launch_mgs_finish(const oras_handle* h, int k, int m, int j, const cplx* w, cplx* Vn, const cplx* pin,
                        cplx* H, double* cs, cplx* sn, cplx* g, double* res) {
   k_mgs_finish<<<RED_BLOCKS, RED_THREADS, 0, h->dev.stream>>>(h->mesh.ndof * k, k, m, j, w, Vn, pin, H, cs, sn, g, res);
+  count_launches(1);
 }
 void launch_hsolve(const oras_handle* h, int k, int m, int kk, const cplx* H, const cplx* g, const int32_t* active,
                    cplx* y) {
   k_hsolve<<<1, 64, 0, h->dev.stream>>>(k, m, kk, H, g, active, y);
+  count_launches(1);
 }
 void launch_xupdate_f64(const oras_handle* h, int k, int m, int kk, const cplx* Z, const cplx* y, cplx* x) {
   int64_t nk = h->mesh.ndof * k;
   k_xupdate<cplx><<<(unsigned)((nk + 255) / 256), 256, 0, h->dev.stream>>>(nk, k, m, kk, Z, y, x);
+  count_launches(1);
 }
 void launch_xupdate_f32(const oras_handle* h, int k, int m, int kk, const void* Z, const cplx* y, cplx* x) {
   int64_t nk = h->mesh.ndof * k;
   k_xupdate<CT<float>><<<(unsigned)((nk + 255) / 256), 256, 0, h->dev.stream>>>(nk, k, m, kk, (const CT<float>*)Z, y, x);
+  count_launches(1);
 }
 void launch_residual(const oras_handle* h, int k, const cplx* b, cplx* r, cplx* partials) {
   k_residual<<<RED_BLOCKS, RED_THREADS, 0, h->dev.stream>>>(h->mesh.ndof * k, k, b, r, partials);
+  count_launches(1);
 }
 void launch_norms(const oras_handle* h, int k, const cplx* partials, double* out) {
   k_norms<<<1, 64, 0, h->dev.stream>>>(k, partials, out);
+  count_launches(1);
 }
 void launch_restart(const oras_handle* h, int k, int m, const cplx* rv, const double* beta, const int32_t* active,
                     cplx* V0, cplx* g) {
   int64_t nk = h->mesh.ndof * k;
   k_restart<<<(unsigned)((nk + 255) / 256), 256, 0, h->dev.stream>>>(nk, k, m, rv, beta, active, V0, g);
+  count_launches(1);
 }
 void launch_to_internal(const oras_handle* h, int k, const cplx* src, cplx* dst) {
   int64_t nk = h->mesh.ndof * k;
   k_to_internal<<<(unsigned)((nk + 255) / 256), 256, 0, h->dev.stream>>>(h->mesh.ndof, k, src, dst);
+  count_launches(1);
 }
 void launch_to_external(const oras_handle* h, int k, const cplx* src, cplx* dst) {
   int64_t nk = h->mesh.ndof * k;
   k_to_external<<<(unsigned)((nk + 255) / 256), 256, 0, h->dev.stream>>>(h->mesh.ndof, k, src, dst);
+  count_launches(1);
 }
 int red_blocks() { return RED_BLOCKS; }
 

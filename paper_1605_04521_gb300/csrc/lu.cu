@@ -425,12 +425,24 @@ static int lu_run(oras_handle* h) {
     int64_t rows_max = m.max_np - (int64_t)k * TB;
     int nch = (int)((rows_max + CH - 1) / CH);
     int64_t nrem = max_nts - k - 1;
+    int pb = prof_begin(h);
     k_lu_tournament<R><<<dim3(nch, m.nsub), LU_THREADS, smem_t, d.stream>>>(a, d.arena);
+    prof_end(h, KC_LU_TOURNAMENT, pb, 1);
+    pb = prof_begin(h);
     k_lu_swap<R><<<dim3(max_nts + 1, m.nsub), 256, smem_s, d.stream>>>(a, d.arena);
+    prof_end(h, KC_LU_SWAP, pb, 1);
+    pb = prof_begin(h);
     k_lu_trsm<R><<<dim3((unsigned)(2 * nrem + 1), m.nsub), TB, smem_r, d.stream>>>(a, d.arena);
-    if (nrem > 0)
+    prof_end(h, KC_LU_TRSM, pb, 1);
+    count_launches(3);
+    if (nrem > 0) {
+      pb = prof_begin(h);
       k_lu_update<R><<<dim3((unsigned)(nrem * nrem), m.nsub), 256, smem_u, d.stream>>>(a, d.arena);
+      prof_end(h, KC_LU_UPDATE, pb, 1);
+      count_launches(1);
+    }
   }
+  count_launches(2);
   k_gidx<<<(unsigned)((total + 255) / 256), 256, 0, d.stream>>>(total, d.perm, d.sub_np_off, d.sub_ns,
                                                               d.sub_ns_off, d.sub_dofs, m.nsub, d.gidx);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -82,6 +82,8 @@ EXPORTS = {
     "oras_precond": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "oras_timings": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "oras_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+    "oras_reset_timings": (C.c_int, [C.c_void_p]),
+    "oras_launch_count": (C.c_int64, []),
 }
 
 
@@ -191,10 +193,24 @@ def oras_set_timing(h, on):
     return _check(h, lib.oras_set_timing(h, int(on)))
 
 
-def oras_timings(h, n=10):
+KERNEL_CLASSES = ["element", "global_rows", "local_rows", "lu_tournament", "lu_swap", "lu_trsm",
+                  "lu_update", "apply", "spmv", "orth", "other"]
+
+
+def oras_timings(h):
+    """{class: (milliseconds, launches)} accumulated since the last reset."""
+    n = 2 * len(KERNEL_CLASSES)
     t = np.zeros(n)
     _check(h, lib.oras_timings(h, _ptr(t), n))
-    return t
+    return {c: (t[2 * i], int(t[2 * i + 1])) for i, c in enumerate(KERNEL_CLASSES)}
+
+
+def oras_reset_timings(h):
+    return _check(h, lib.oras_reset_timings(h))
+
+
+def oras_launch_count():
+    return int(lib.oras_launch_count())
 
 
 def oras_ndof(h):
