@@ -197,6 +197,23 @@ int oras_matvec(oras_handle* h, const oras_complex* x, oras_complex* y, int32_t 
 /* z = M^{-1}_ORAS v for k columns (N x k column-major, `mem`), Sec. 4. */
 int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k, int32_t mem);
 
+/* Allocation-free preconditioner apply: z = M^{-1}_ORAS v for k columns, the same result as
+ * oras_precond, for callers that must not allocate device memory during the call -- a serving
+ * process whose device memory is entirely pre-reserved by a pool allocator (a raw cudaMalloc
+ * would fail or fragment the pool), or a latency-bound loop where cudaMalloc/cudaFree would
+ * synchronise the device and stall the other requests in flight.  The paper has no counterpart;
+ * this is an interface convenience.  v, z: device pointers (current device = the handle's
+ * device), N x k column-major, complex FP64, on the handle's stream; the call is asynchronous.
+ * The local vectors live in one fixed 16 MiB device array compiled into the library (every GPU
+ * that loads the library holds it until exit); sum over subdomains of the padded order times
+ * the factor entry size (8 B FP32, 16 B FP64) must fit, else INVALID_ARG with the needed size.
+ * The first call on a device resolves the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call shares the array and leaves its last
+ * contents there; each call writes every entry before reading it.  Calls that overlap on the
+ * GPU (other streams, other threads) race on the array.  Nothing is allocated or freed.
+ * Errors: STATE (no oras_factor yet), INVALID_ARG, CUDA. */
+int oras_precond_noalloc(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k);
+
 /* ---------------------------------------------------------------- instrumentation */
 
 /* Device time accumulated by kernel class since the last oras_reset_timings, measured with

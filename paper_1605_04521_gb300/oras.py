@@ -84,6 +84,7 @@ EXPORTS = {
     "oras_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "oras_reset_timings": (C.c_int, [C.c_void_p]),
     "oras_launch_count": (C.c_int64, []),
+    "oras_precond_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
 }
 
 
@@ -334,3 +335,9 @@ def oras_rhs_plane_wave(h, d, p, mem=ORAS_MEM_HOST, out=None):
         out = np.empty(oras_ndof(h), dtype=np.complex128)
     _check(h, lib.oras_rhs_plane_wave(h, _ptr(d), _ptr(p), _ptr(out), mem))
     return out
+
+
+def oras_precond_noalloc(h, v, z, k=1):
+    """z = M^{-1} v without any device allocation; v, z: torch CUDA complex128 tensors holding
+    N x k column-major data (shape (k, N) contiguous, or (N,) for k = 1)."""
+    return _check(h, lib.oras_precond_noalloc(h, _ptr(v), _ptr(z), int(k)))
