@@ -203,7 +203,7 @@ template <typename R>
 __global__ void k_local_rows(RowArgs A, int nsub, int64_t total_rows, const int64_t* __restrict__ np_off,
                              const int64_t* __restrict__ sub_ns, const int64_t* __restrict__ sub_np,
                              const int64_t* __restrict__ ns_off, const int64_t* __restrict__ tile_off,
-                             const int32_t* __restrict__ sub_dofs, int maxnnz, CT<R>* __restrict__ arena) {
+                             const int32_t* __restrict__ sub_dofs, int maxnnz, void* __restrict__ arena) {
   extern __shared__ cplx sacc[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t row = (int64_t)blockIdx.x * ROW_WARPS + w;
@@ -216,12 +216,16 @@ __global__ void k_local_rows(RowArgs A, int nsub, int64_t total_rows, const int6
   const int s = lo;
   const int64_t li = row - np_off[s];
   const int64_t ns = sub_ns[s], np = sub_np[s], nts = np / TB;
-  CT<R>* base = arena + tile_off[s] * (int64_t)TB * TB;
-  auto at = [&](int64_t i, int64_t j) -> CT<R>& {
-    return base[((i / TB) * nts + (j / TB)) * (int64_t)TB * TB + (j % TB) * TB + (i % TB)];
+  R* base = (R*)arena + tile_off[s] * 2 * TILE_PLANE;
+  auto put = [&](int64_t i, int64_t j, R re, R im) {
+    const int64_t I = i / TB, J = j / TB;
+    R* t = base + (I * nts + J) * 2 * TILE_PLANE;
+    const int64_t e = tile_elem(tile_rowmajor(I, J), i % TB, j % TB);
+    t[e] = re;
+    t[TILE_PLANE + e] = im;
   };
   if (li >= ns) {  // padding row: identity
-    if (lane == 0) at(li, li) = {R(1), R(0)};
+    if (lane == 0) put(li, li, R(1), R(0));
     return;
   }
   const int32_t* Ns = sub_dofs + ns_off[s];
@@ -233,7 +237,7 @@ __global__ void k_local_rows(RowArgs A, int nsub, int64_t total_rows, const int6
   accumulate_row<true>(A, g, s, acc, rn, rc);
   for (int p = lane; p < rn; p += 32) {
     int lj = bsearch32(Ns, (int)ns, rc[p]);
-    if (lj >= 0) at(li, lj) = {R(acc[p].re), R(acc[p].im)};
+    if (lj >= 0) put(li, lj, R(acc[p].re), R(acc[p].im));
   }
 }
 
@@ -452,7 +456,7 @@ static int launch_local_rows_t(const oras_handle* h, double k0) {
   int64_t blocks = (total + ROW_WARPS - 1) / ROW_WARPS;
   k_local_rows<R><<<(unsigned)blocks, ROW_WARPS * 32, smem, d.stream>>>(
       A, m.nsub, total, d.sub_np_off, d.sub_ns, d.sub_np, d.sub_ns_off, d.sub_tile_off, d.sub_dofs,
-      m.max_row_nnz, (CT<R>*)d.arena);
+      m.max_row_nnz, d.arena);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

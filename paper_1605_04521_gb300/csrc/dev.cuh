@@ -11,6 +11,17 @@ namespace oras {
 // complex helpers (interleaved re, im)
 template <typename R> struct CT { R re, im; };
 
+// Local-factor arena tiles: each TB x TB complex tile is two planes of TB*TB reals (real part,
+// then imaginary part).  Tiles on or below the block diagonal (I >= J) store their planes
+// row-major, tiles above it column-major, so that in the trailing update C_IJ -= L_Ik U_kJ both
+// operands are contiguous along the contraction index k (K-major for the tensor cores), the
+// forward substitution streams rows of L and the backward substitution streams columns of U.
+__device__ __forceinline__ bool tile_rowmajor(int64_t I, int64_t J) { return I >= J; }
+__device__ __forceinline__ int64_t tile_elem(bool rm, int64_t i, int64_t j) {
+  return rm ? i * TB + j : j * TB + i;
+}
+constexpr int64_t TILE_PLANE = (int64_t)TB * TB;
+
 __device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
 __device__ __forceinline__ cplx cadd(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
 __device__ __forceinline__ cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }

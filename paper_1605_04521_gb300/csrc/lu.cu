@@ -1,18 +1,25 @@
 // Batched dense LU with row pivoting of the local matrices A_s (Sec. 4: the A_s^{-1} of ORAS),
-// P_s A_s = L_s U_s, over the tiled arena (TB x TB complex tiles, column-major inside a tile).
+// P_s A_s = L_s U_s, over the tiled arena (TB x TB complex tiles, split re/im planes, row-major
+// on and below the block diagonal, column-major above it).
 //
-// Right-looking blocked LU, panel width TB.  Each panel step k, for every subdomain at once:
-//  1. tournament pivoting of the tall panel (tile column k): chunks of rows are reduced with
-//     partial pivoting (pivot = max |Re| + |Im|, first on ties) to TB candidate rows each; pairs
-//     of candidate sets are merged the same way up a binary tree; the root's choice is the pivot
-//     sequence of the step and its factored TB x TB block is L11\U11.  This is communication-
-//     avoiding LU (Grigori, Demmel, Xiang 2011): the chosen rows differ from column-by-column
-//     partial pivoting only in which rows win, not in the factorisation it produces.
-//  2. the row interchanges of the step are applied to every column (one permutation of at most
+// Two-level right-looking blocked LU.  Outer panels are W tile columns wide; inside a panel,
+// every tile column k is processed for all subdomains at once by
+//  1. tournament pivoting of the tall panel column: chunks of rows are reduced with partial
+//     pivoting (pivot = max |Re| + |Im|, first on ties) to TB candidate rows each; pairs of
+//     candidate sets are merged the same way up a binary tree; the root's choice is the pivot
+//     sequence of the step and its factored TB x TB block is L11\U11 (communication-avoiding
+//     LU, Grigori, Demmel, Xiang 2011);
+//  2. the row interchanges of the step, applied to every column (one permutation of at most
 //     2 TB rows);
-//  3. L21 = A21 U11^{-1} and U12 = L11^{-1} A12 (triangular solves on tiles);
-//  4. A22 -= L21 U12 (tile GEMMs).
+//  3. L21 = A21 U11^{-1} below and U12 = L11^{-1} A12 along the whole tile row;
+//  4. the inner update: tiles of the panel's remaining columns, and of the panel's remaining
+//     rows right of the panel, get -= L_Ik U_kJ.
+// After the W columns of a panel, the trailing matrix gets one update with a W-tile-deep
+// contraction, C_IJ -= sum_k L_Ik U_kJ, which reads and writes every trailing tile once per
+// panel instead of once per column.
 // The tree merge uses "last arriver continues" counters, so no block ever waits for another.
+#include <algorithm>
+#include <climits>
 #include <cstdio>
 
 #include "dev.cuh"
@@ -46,16 +53,36 @@ struct LuArgs {
   int32_t* cand;            // [nsub][slots][TB]
   int32_t* cnt;             // [nsub][slots]
   int slots;
-  int32_t* pairs;           // [nsub][2*TB][2] (dst, src) + count in pairs_n
+  int32_t* pairs;           // [nsub][2*TB][2] (dst, src)
   int32_t* pairs_n;         // [nsub]
-  void* diag;               // [nsub][TB*TB] factored diagonal tile (column-major)
+  void* diag;               // [nsub][TB*TB] factored diagonal tile (complex, column-major)
   int32_t* status;
 };
 
+// Rectangular set of output tiles [i0, i1) x [j0, j1); an end of INT_MAX means the subdomain's
+// tile count.
+struct Region { int i0, i1, j0, j1; };
+struct UpdArgs {
+  int kk0, kk1;             // contraction over tile columns [kk0, kk1)
+  int nreg;
+  Region reg[2];
+};
+
 template <typename R>
-__device__ __forceinline__ CT<R>* tile_ptr(void* arena, const LuArgs& a, int s, int64_t I, int64_t J) {
+__device__ __forceinline__ R* tile_base(void* arena, const LuArgs& a, int s, int64_t I, int64_t J) {
   int64_t nts = a.np[s] / TB;
-  return (CT<R>*)arena + (a.tile_off[s] + I * nts + J) * (int64_t)TB * TB;
+  return (R*)arena + (a.tile_off[s] + I * nts + J) * 2 * TILE_PLANE;
+}
+template <typename R>
+__device__ __forceinline__ CT<R> tload(const R* t, bool rm, int64_t i, int64_t j) {
+  int64_t e = tile_elem(rm, i, j);
+  return {t[e], t[TILE_PLANE + e]};
+}
+template <typename R>
+__device__ __forceinline__ void tstore(R* t, bool rm, int64_t i, int64_t j, CT<R> v) {
+  int64_t e = tile_elem(rm, i, j);
+  t[e] = v.re;
+  t[TILE_PLANE + e] = v.im;
 }
 
 // Partial-pivoting elimination of an m x TB panel P (row stride PS) held in shared memory,
@@ -65,7 +92,6 @@ __device__ void gepp_panel(CT<R>* P, int32_t* ids, int m, R* rv, int* ri) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int ncol = m < TB ? m : TB;
   for (int c = 0; c < ncol; ++c) {
-    // pivot search over rows c..m-1
     R best = -1;
     int bi = 0x7fffffff;
     for (int i = c + tid; i < m; i += nthr) {
@@ -110,14 +136,14 @@ __device__ void gepp_panel(CT<R>* P, int32_t* ids, int m, R* rv, int* ri) {
   }
 }
 
-// Load panel rows `rows[0..m)` (matrix row indices) of tile column k into P.
+// Load panel rows `rows[0..m)` (matrix row indices, all in tile rows >= k) of tile column k.
 template <typename R>
 __device__ void load_rows(void* arena, const LuArgs& a, int s, const int32_t* rows, int m, CT<R>* P) {
   for (int e = threadIdx.x; e < m * TB; e += blockDim.x) {
-    int i = e % m, j = e / m;
+    int i = e / TB, j = e % TB;
     int32_t r = rows[i];
-    const CT<R>* t = tile_ptr<R>(arena, a, s, r / TB, a.k);
-    P[i * PS + j] = t[j * TB + (r % TB)];
+    const R* t = tile_base<R>(arena, a, s, r / TB, a.k);
+    P[i * PS + j] = tload<R>(t, true, r % TB, j);
   }
 }
 
@@ -196,7 +222,6 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_tournament(LuArgs a, void* ar
   // block fill the vacated pivot positions (LAPACK interchange order).
   __syncthreads();
   if (threadIdx.x == 0) {
-    int32_t* mpos = ri;  // reuse: up to 2*TB modified positions -> contents
     int32_t posv[2 * TB], rowv[2 * TB];
     int nm = 0;
     auto row_at = [&](int32_t pos) {
@@ -228,7 +253,6 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_tournament(LuArgs a, void* ar
     for (int q = 0; q < nm; ++q)
       if (posv[q] != rowv[q]) { pr[np_ * 2] = posv[q]; pr[np_ * 2 + 1] = rowv[q]; ++np_; }
     a.pairs_n[s] = np_;
-    (void)mpos;
   }
 }
 
@@ -254,15 +278,17 @@ __global__ void k_lu_swap(LuArgs a, void* arena) {
     return;
   }
   for (int e = threadIdx.x; e < n * TB; e += blockDim.x) {
-    int q = e % n, j = e / n;
+    int q = e / TB, j = e % TB;
     int32_t src = pr[q * 2 + 1];
-    buf[q * TB + j] = tile_ptr<R>(arena, a, s, src / TB, J)[j * TB + (src % TB)];
+    int64_t I = src / TB;
+    buf[q * TB + j] = tload<R>(tile_base<R>(arena, a, s, I, J), tile_rowmajor(I, J), src % TB, j);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < n * TB; e += blockDim.x) {
-    int q = e % n, j = e / n;
+    int q = e / TB, j = e % TB;
     int32_t dst = pr[q * 2];
-    tile_ptr<R>(arena, a, s, dst / TB, J)[j * TB + (dst % TB)] = buf[q * TB + j];
+    int64_t I = dst / TB;
+    tstore<R>(tile_base<R>(arena, a, s, I, J), tile_rowmajor(I, J), dst % TB, j, buf[q * TB + j]);
   }
 }
 
@@ -282,15 +308,19 @@ __global__ void __launch_bounds__(TB) k_lu_trsm(LuArgs a, void* arena) {
   const CT<R>* dg = (const CT<R>*)a.diag + (int64_t)s * TB * TB;
   const int t = threadIdx.x;
   if (b == 0) {
-    CT<R>* dst = tile_ptr<R>(arena, a, s, k, k);
-    for (int e = t; e < TB * TB; e += blockDim.x) dst[e] = dg[e];
+    R* dst = tile_base<R>(arena, a, s, k, k);
+    for (int e = t; e < TB * TB; e += blockDim.x) tstore<R>(dst, true, e % TB, e / TB, dg[e]);
     return;
   }
   for (int e = t; e < TB * TB; e += blockDim.x) D[(e / TB) * PS + (e % TB)] = dg[e];
   const bool lower = b <= nrem;
   const int64_t I = lower ? k + b : k, J = lower ? k : k + (b - nrem);
-  CT<R>* tp = tile_ptr<R>(arena, a, s, I, J);
-  for (int e = t; e < TB * TB; e += blockDim.x) X[(e / TB) * PS + (e % TB)] = tp[e];
+  const bool rm = tile_rowmajor(I, J);
+  R* tp = tile_base<R>(arena, a, s, I, J);
+  for (int e = t; e < TB * TB; e += blockDim.x) {
+    int i = rm ? e / TB : e % TB, j = rm ? e % TB : e / TB;  // coalesced in storage order
+    X[j * PS + i] = tload<R>(tp, rm, i, j);
+  }
   __syncthreads();
   if (lower) {
     // row t of X: x U = a, forward over columns
@@ -308,60 +338,81 @@ __global__ void __launch_bounds__(TB) k_lu_trsm(LuArgs a, void* arena) {
     }
   }
   __syncthreads();
-  for (int e = t; e < TB * TB; e += blockDim.x) tp[e] = X[(e / TB) * PS + (e % TB)];
+  for (int e = t; e < TB * TB; e += blockDim.x) {
+    int i = rm ? e / TB : e % TB, j = rm ? e % TB : e / TB;
+    tstore<R>(tp, rm, i, j, X[j * PS + i]);
+  }
 }
 
-// C_IJ -= L_Ik U_kJ for I, J > k.  16x16 threads, each a 4x4 block of complex outputs.
+__device__ __forceinline__ bool region_tile(const UpdArgs& u, int64_t nts, int64_t e, int64_t& I, int64_t& J) {
+  for (int q = 0; q < u.nreg; ++q) {
+    int64_t i0 = u.reg[q].i0, i1 = u.reg[q].i1 == INT_MAX ? nts : u.reg[q].i1;
+    int64_t j0 = u.reg[q].j0, j1 = u.reg[q].j1 == INT_MAX ? nts : u.reg[q].j1;
+    if (i1 > nts) i1 = nts;
+    if (j1 > nts) j1 = nts;
+    int64_t ni = i1 > i0 ? i1 - i0 : 0, nj = j1 > j0 ? j1 - j0 : 0;
+    if (e < ni * nj) {
+      I = i0 + e / nj;
+      J = j0 + e % nj;
+      return true;
+    }
+    e -= ni * nj;
+  }
+  return false;
+}
+
+// C_IJ -= sum_{kk in [kk0, kk1)} L_I,kk U_kk,J over the update regions.  16x16 threads, each a
+// 4x4 block of complex outputs; C is read and written once per launch.
 template <typename R>
-__global__ void __launch_bounds__(256) k_lu_update(LuArgs a, void* arena) {
+__global__ void __launch_bounds__(256) k_lu_update(LuArgs a, UpdArgs u, void* arena) {
   extern __shared__ unsigned char smem_raw[];
-  CT<R>* As = (CT<R>*)smem_raw;  // [TB][TB] column-major: A(i,l) at l*TB+i
-  CT<R>* Bs = As + TB * TB;      // [TB][TB] row-major:    B(l,j) at l*TB+j
+  CT<R>* As = (CT<R>*)smem_raw;  // [TB][TB]: A(i,l) at l*TB+i
+  CT<R>* Bs = As + TB * TB;      // [TB][TB]: B(l,j) at l*TB+j
   const int s = blockIdx.y;
   const int64_t nts = a.np[s] / TB;
-  const int k = a.k;
-  if (k >= nts) return;
-  const int64_t nrem = nts - k - 1;
-  const int64_t e0 = blockIdx.x;
-  if (e0 >= nrem * nrem) return;
-  const int64_t I = k + 1 + e0 / nrem, J = k + 1 + e0 % nrem;
-  const CT<R>* L = tile_ptr<R>(arena, a, s, I, k);
-  const CT<R>* U = tile_ptr<R>(arena, a, s, k, J);
+  int64_t I, J;
+  if (!region_tile(u, nts, blockIdx.x, I, J)) return;
   const int t = threadIdx.x;
-  for (int e = t; e < TB * TB; e += 256) {
-    As[e] = L[e];
-    int j = e / TB, l = e % TB;  // U stored column-major: element (l, j) at j*TB + l
-    Bs[l * TB + j] = U[e];
-  }
-  __syncthreads();
   const int ty = t / 16, tx = t % 16;
   CT<R> acc[4][4];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[p][q] = {R(0), R(0)};
-  for (int l = 0; l < TB; ++l) {
-    CT<R> av[4], bv[4];
+  for (int kk = u.kk0; kk < u.kk1 && kk < nts; ++kk) {
+    const R* L = tile_base<R>(arena, a, s, I, kk);   // I > kk: row-major planes
+    const R* U = tile_base<R>(arena, a, s, kk, J);   // kk < J: column-major planes
+    __syncthreads();
+    for (int e = t; e < TB * TB; e += 256) {
+      int hi = e / TB, lo = e % TB;                    // storage order
+      As[lo * TB + hi] = {L[e], L[TILE_PLANE + e]};    // L(i=hi, l=lo)
+      Bs[lo * TB + hi] = {U[e], U[TILE_PLANE + e]};    // U(l=lo, j=hi)
+    }
+    __syncthreads();
+    for (int l = 0; l < TB; ++l) {
+      CT<R> av[4], bv[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) av[p] = As[l * TB + ty * 4 + p];
+      for (int p = 0; p < 4; ++p) av[p] = As[l * TB + ty * 4 + p];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) bv[q] = Bs[l * TB + tx * 4 + q];
+      for (int q = 0; q < 4; ++q) bv[q] = Bs[l * TB + tx * 4 + q];
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+      for (int p = 0; p < 4; ++p)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc[p][q].re += av[p].re * bv[q].re - av[p].im * bv[q].im;
-        acc[p][q].im += av[p].re * bv[q].im + av[p].im * bv[q].re;
-      }
+        for (int q = 0; q < 4; ++q) {
+          acc[p][q].re += av[p].re * bv[q].re - av[p].im * bv[q].im;
+          acc[p][q].im += av[p].re * bv[q].im + av[p].im * bv[q].re;
+        }
+    }
   }
-  CT<R>* C = tile_ptr<R>(arena, a, s, I, J);
+  R* C = tile_base<R>(arena, a, s, I, J);
+  const bool rm = tile_rowmajor(I, J);
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
+    for (int q = 0; q < 4; ++q) {
       int i = ty * 4 + p, j = tx * 4 + q;
-      CT<R> c = C[j * TB + i];
-      C[j * TB + i] = {c.re - acc[p][q].re, c.im - acc[p][q].im};
+      CT<R> c = tload<R>(C, rm, i, j);
+      tstore<R>(C, rm, i, j, {c.re - acc[p][q].re, c.im - acc[p][q].im});
     }
 }
 
@@ -390,6 +441,20 @@ __global__ void k_gidx(int64_t total, const int32_t* perm, const int64_t* np_off
   gidx[i] = p < ns[lo] ? sub_dofs[ns_off[lo] + p] : -1;
 }
 
+// number of output tiles of the update regions for the largest subdomain
+static int64_t region_blocks(const UpdArgs& u, int64_t nts) {
+  int64_t tot = 0;
+  for (int q = 0; q < u.nreg; ++q) {
+    int64_t i1 = u.reg[q].i1 == INT_MAX ? nts : std::min<int64_t>(u.reg[q].i1, nts);
+    int64_t j1 = u.reg[q].j1 == INT_MAX ? nts : std::min<int64_t>(u.reg[q].j1, nts);
+    int64_t ni = std::max<int64_t>(0, i1 - u.reg[q].i0), nj = std::max<int64_t>(0, j1 - u.reg[q].j0);
+    tot += ni * nj;
+  }
+  return tot;
+}
+
+constexpr int OUTER_W = 4;  // outer panel width in tile columns
+
 template <typename R>
 static int lu_run(oras_handle* h) {
   auto& m = h->mesh;
@@ -408,7 +473,7 @@ static int lu_run(oras_handle* h) {
   a.pairs_n = d.lu_ipiv + (int64_t)m.nsub * 2 * TB * 2;
   a.diag = d.lu_diag;
   a.status = d.status;
-  int64_t total = d.sub_np_off ? 0 : 0;
+  int64_t total = 0;
   for (int s = 0; s < m.nsub; ++s) total += m.sub_np[s];
   k_iota_perm<<<(unsigned)((total + 255) / 256), 256, 0, d.stream>>>(total, d.perm, d.sub_np_off, m.nsub);
   const int max_nts = (int)(m.max_np / TB);
@@ -420,31 +485,51 @@ static int lu_run(oras_handle* h) {
   cudaFuncSetAttribute(k_lu_swap<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
   cudaFuncSetAttribute(k_lu_trsm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
   cudaFuncSetAttribute(k_lu_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_u);
-  for (int k = 0; k < max_nts; ++k) {
-    a.k = k;
-    int64_t rows_max = m.max_np - (int64_t)k * TB;
-    int nch = (int)((rows_max + CH - 1) / CH);
-    int64_t nrem = max_nts - k - 1;
+  auto update = [&](const UpdArgs& u) {
+    int64_t blocks = region_blocks(u, max_nts);
+    if (blocks <= 0) return;
     int pb = prof_begin(h);
-    k_lu_tournament<R><<<dim3(nch, m.nsub), LU_THREADS, smem_t, d.stream>>>(a, d.arena);
-    prof_end(h, KC_LU_TOURNAMENT, pb, 1);
-    pb = prof_begin(h);
-    k_lu_swap<R><<<dim3(max_nts + 1, m.nsub), 256, smem_s, d.stream>>>(a, d.arena);
-    prof_end(h, KC_LU_SWAP, pb, 1);
-    pb = prof_begin(h);
-    k_lu_trsm<R><<<dim3((unsigned)(2 * nrem + 1), m.nsub), TB, smem_r, d.stream>>>(a, d.arena);
-    prof_end(h, KC_LU_TRSM, pb, 1);
-    count_launches(3);
-    if (nrem > 0) {
+    k_lu_update<R><<<dim3((unsigned)blocks, m.nsub), 256, smem_u, d.stream>>>(a, u, d.arena);
+    prof_end(h, KC_LU_UPDATE, pb, 1);
+    count_launches(1);
+  };
+  for (int k0 = 0; k0 < max_nts; k0 += OUTER_W) {
+    const int kend = k0 + OUTER_W;
+    for (int k = k0; k < kend && k < max_nts; ++k) {
+      a.k = k;
+      int64_t rows_max = m.max_np - (int64_t)k * TB;
+      int nch = (int)((rows_max + CH - 1) / CH);
+      int64_t nrem = max_nts - k - 1;
+      int pb = prof_begin(h);
+      k_lu_tournament<R><<<dim3(nch, m.nsub), LU_THREADS, smem_t, d.stream>>>(a, d.arena);
+      prof_end(h, KC_LU_TOURNAMENT, pb, 1);
       pb = prof_begin(h);
-      k_lu_update<R><<<dim3((unsigned)(nrem * nrem), m.nsub), 256, smem_u, d.stream>>>(a, d.arena);
-      prof_end(h, KC_LU_UPDATE, pb, 1);
-      count_launches(1);
+      k_lu_swap<R><<<dim3(max_nts + 1, m.nsub), 256, smem_s, d.stream>>>(a, d.arena);
+      prof_end(h, KC_LU_SWAP, pb, 1);
+      pb = prof_begin(h);
+      k_lu_trsm<R><<<dim3((unsigned)(2 * nrem + 1), m.nsub), TB, smem_r, d.stream>>>(a, d.arena);
+      prof_end(h, KC_LU_TRSM, pb, 1);
+      count_launches(3);
+      // inner update: the panel's remaining columns below, and the panel's remaining rows
+      // to the right of the panel
+      UpdArgs u;
+      u.kk0 = k;
+      u.kk1 = k + 1;
+      u.nreg = 2;
+      u.reg[0] = {k + 1, INT_MAX, k + 1, kend};
+      u.reg[1] = {k + 1, kend, kend, INT_MAX};
+      update(u);
     }
+    UpdArgs u;  // outer update of the trailing matrix
+    u.kk0 = k0;
+    u.kk1 = kend;
+    u.nreg = 1;
+    u.reg[0] = {kend, INT_MAX, kend, INT_MAX};
+    update(u);
   }
-  count_launches(2);
   k_gidx<<<(unsigned)((total + 255) / 256), 256, 0, d.stream>>>(total, d.perm, d.sub_np_off, d.sub_ns,
                                                               d.sub_ns_off, d.sub_dofs, m.nsub, d.gidx);
+  count_launches(2);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
