@@ -119,7 +119,7 @@ static void dfree_all(Device& d) {
                   d.finc_ptr, d.finc, d.rowptr, d.cols, d.sub_ns, d.sub_np, d.sub_ns_off, d.sub_tile_off,
                   d.sub_dofs, d.sub_pou, d.member, d.cm, d.ck, d.cs, d.fl, d.tc, d.ta, d.tm, d.eps, d.mu,
                   d.elem, d.fmat, d.vals, d.arena, d.perm, d.gidx, d.sub_np_off, d.lu_cand, d.lu_cnt,
-                  d.lu_ipiv, d.lu_diag, d.status, d.V, d.Zf, d.Zd, d.w, d.xk, d.bk, d.tmp, d.H, d.gcs, d.gsn,
+                  d.lu_ipiv, d.lu_diag, d.dinv, d.sub_inv_off, d.status, d.V, d.Zf, d.Zd, d.w, d.xk, d.bk, d.tmp, d.H, d.gcs, d.gsn,
                   d.g, d.red, d.scal, d.ybuf, d.io};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -198,6 +198,14 @@ static int alloc_factor_space(oras_handle* h, int bits) {
   CK(cudaMemsetAsync(d.lu_cnt, 0, (size_t)m.nsub * slots * sizeof(int32_t), d.stream));
   CK(dalloc(d.lu_ipiv, (size_t)m.nsub * (2 * TB * 2 + 1)));
   CK(cudaMalloc(&d.lu_diag, (size_t)m.nsub * TB * TB * el));
+  {
+    std::vector<int64_t> inv_off(m.nsub + 1, 0);
+    for (int q = 0; q < m.nsub; ++q) inv_off[q + 1] = inv_off[q] + m.sub_np[q] / TB;
+    CK(dput(d.sub_inv_off, inv_off, d.stream));
+    if (d.dinv) { cudaFree(d.dinv); d.dinv = nullptr; }
+    d.dinv_bytes = (size_t)inv_off[m.nsub] * 2 * TB * TB * el;
+    CK(cudaMalloc(&d.dinv, d.dinv_bytes));
+  }
   size_t yb = apply_yglob_bytes(h);
   if (d.ybuf) { cudaFree(d.ybuf); d.ybuf = nullptr; }
   if (yb) CK(cudaMalloc(&d.ybuf, yb));

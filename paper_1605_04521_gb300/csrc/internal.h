@@ -135,6 +135,9 @@ struct Device {
   int32_t* lu_cnt = nullptr;                    // tournament arrival counters
   int32_t* lu_ipiv = nullptr;                   // [nsub][TB] interchanges of the current step
   void* lu_diag = nullptr;                      // [nsub] factored diagonal tile of the step
+  void* dinv = nullptr;                         // inverted diagonal blocks, 2 tiles per block row
+  size_t dinv_bytes = 0;
+  int64_t* sub_inv_off = nullptr;               // [nsub] prefix of block rows (device)
   int32_t* status = nullptr;                    // device error flags [8]
   int lu_max_chunks = 0;
   // Krylov workspace

@@ -441,6 +441,64 @@ __global__ void k_gidx(int64_t total, const int32_t* perm, const int64_t* np_off
   gidx[i] = p < ns[lo] ? sub_dofs[ns_off[lo] + p] : -1;
 }
 
+// Inverses of the diagonal blocks of the factors: Linv_I = L_II^{-1} (unit lower) stored with
+// row-major planes and Uinv_I = U_II^{-1} stored with column-major planes, so that the in-block
+// substitution steps of the preconditioner apply become tile matrix-vector products like the
+// off-diagonal ones (block substitution with inverted diagonal blocks).
+template <typename R>
+__global__ void __launch_bounds__(2 * TB) k_lu_diag_inv(LuArgs a, void* arena, void* inv, const int64_t* inv_off) {
+  extern __shared__ unsigned char smem_raw[];
+  CT<R>* D = (CT<R>*)smem_raw;  // [TB][PS]: D[j*PS+i] = LU(i,j)
+  CT<R>* X = D + TB * PS;       // [2][TB][PS]: columns of L^{-1}, then of U^{-1}
+  const int s = blockIdx.y;
+  const int64_t nts = a.np[s] / TB;
+  const int64_t I = blockIdx.x;
+  if (I >= nts) return;
+  const R* T = tile_base<R>(arena, a, s, I, I);
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int i = e / TB, j = e % TB;
+    D[j * PS + i] = tload<R>(T, true, i, j);
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  const CT<R> zero = {R(0), R(0)}, one = {R(1), R(0)};
+  if (t < TB) {  // column t of L^{-1}: L x = e_t, unit lower
+    CT<R>* x = X + t * PS;
+    for (int i = 0; i < TB; ++i) {
+      if (i < t) { x[i] = zero; continue; }
+      if (i == t) { x[i] = one; continue; }
+      CT<R> acc = zero;
+      for (int l = t; l < i; ++l) {
+        CT<R> p = mulc(D[l * PS + i], x[l]);
+        acc.re += p.re;
+        acc.im += p.im;
+      }
+      x[i] = {-acc.re, -acc.im};
+    }
+  } else {  // column j of U^{-1}: U x = e_j
+    const int j = t - TB;
+    CT<R>* x = X + TB * PS + j * PS;
+    for (int i = TB - 1; i >= 0; --i) {
+      if (i > j) { x[i] = zero; continue; }
+      CT<R> acc = i == j ? one : zero;
+      for (int l = i + 1; l <= j; ++l) acc = subc(acc, mulc(D[l * PS + i], x[l]));
+      x[i] = mulc(acc, invc(D[i * PS + i]));
+    }
+  }
+  __syncthreads();
+  R* Li = (R*)inv + (inv_off[s] + I) * 4 * TILE_PLANE;
+  R* Ui = Li + 2 * TILE_PLANE;
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    const int hi = e / TB, lo = e % TB;
+    const CT<R> l = X[lo * PS + hi];                // Linv(i = hi, j = lo): row-major storage
+    const CT<R> u = X[TB * PS + hi * PS + lo];      // Uinv(i = lo, j = hi): column-major storage
+    Li[e] = l.re;
+    Li[TILE_PLANE + e] = l.im;
+    Ui[e] = u.re;
+    Ui[TILE_PLANE + e] = u.im;
+  }
+}
+
 // number of output tiles of the update regions for the largest subdomain
 static int64_t region_blocks(const UpdArgs& u, int64_t nts) {
   int64_t tot = 0;
@@ -529,7 +587,14 @@ static int lu_run(oras_handle* h) {
   }
   k_gidx<<<(unsigned)((total + 255) / 256), 256, 0, d.stream>>>(total, d.perm, d.sub_np_off, d.sub_ns,
                                                               d.sub_ns_off, d.sub_dofs, m.nsub, d.gidx);
-  count_launches(2);
+  {
+    size_t smem_i = (size_t)3 * TB * PS * sizeof(CT<R>);
+    cudaFuncSetAttribute(k_lu_diag_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_i);
+    int pb = prof_begin(h);
+    k_lu_diag_inv<R><<<dim3(max_nts, m.nsub), 2 * TB, smem_i, d.stream>>>(a, d.arena, d.dinv, d.sub_inv_off);
+    prof_end(h, KC_LU_TRSM, pb, 1);
+  }
+  count_launches(3);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -20,15 +20,15 @@ static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_apply_noalloc(ApplyGeom a, int64_t n, int k, void* scratch,
-                                                       const cplx* __restrict__ v, cplx* __restrict__ z) {
-  extern __shared__ unsigned char smem_raw[];
-  __shared__ CT<R> red[8][TB];
-  CT<R>* dg = (CT<R>*)smem_raw;                            // [TB][DPS]
-  CT<R>* y = (CT<R>*)scratch + a.np_off[blockIdx.x];        // this subdomain's slice
-  for (int r = 0; r < k; ++r)  // columns one after the other: the slice is reused
-    apply_subdomain<R, cplx>(a, blockIdx.x, v, 1, z, 1, (int64_t)r * n, y, dg, red);
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(APPLY_THREADS)
+    k_apply_noalloc(ApplyGeom a, int64_t n, int k, void* scratch, const cplx* __restrict__ v,
+                    cplx* __restrict__ z) {
+  for (int r = 0; r < k; ++r)  // columns one after the other: the scratch slices are reused
+    apply_cluster<R, cplx>(a, blockIdx.x / 2, v, 1, z, 1, (int64_t)r * n, (CT<R>*)scratch);
 }
+
+ApplyGeom apply_geom(const oras_handle* h);
+void apply_noalloc_config(const oras_handle* h, int* S, size_t* smem);
 
 }  // namespace oras
 
@@ -74,23 +74,21 @@ extern "C" int oras_precond_noalloc(oras_handle* h, const oras_complex* v, oras_
     }
     scratch = g_noalloc_ptr[dev];
   }
-  ApplyGeom a;
-  a.ns = d.sub_ns; a.np = d.sub_np; a.np_off = d.sub_np_off; a.ns_off = d.sub_ns_off;
-  a.tile_off = d.sub_tile_off;
-  a.gidx = d.gidx; a.sub_dofs = d.sub_dofs; a.pou = d.sub_pou;
-  a.arena = d.arena;
-  a.weights = h->opt.weights;
+  ApplyGeom a = apply_geom(h);
+  size_t smem = 0;
+  apply_noalloc_config(h, &a.stages, &smem);
   if (a.weights != ORAS_WEIGHTS_POU) {
     e = cudaMemsetAsync(z, 0, sizeof(cplx) * (size_t)m.ndof * k, d.stream);
     if (e != cudaSuccess) { h->err = std::string("oras_precond_noalloc: ") + cudaGetErrorString(e); return ORAS_ERR_CUDA; }
   }
   if (d.factor_bits == 64) {
-    const size_t smem = (size_t)TB * DPS * sizeof(CT<double>);
     cudaFuncSetAttribute(k_apply_noalloc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_apply_noalloc<double><<<m.nsub, 256, smem, d.stream>>>(a, m.ndof, k, scratch, (const cplx*)v, (cplx*)z);
+    k_apply_noalloc<double><<<2 * m.nsub, APPLY_THREADS, smem, d.stream>>>(a, m.ndof, k, scratch, (const cplx*)v,
+                                                                           (cplx*)z);
   } else {
-    const size_t smem = (size_t)TB * DPS * sizeof(CT<float>);
-    k_apply_noalloc<float><<<m.nsub, 256, smem, d.stream>>>(a, m.ndof, k, scratch, (const cplx*)v, (cplx*)z);
+    cudaFuncSetAttribute(k_apply_noalloc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_apply_noalloc<float><<<2 * m.nsub, APPLY_THREADS, smem, d.stream>>>(a, m.ndof, k, scratch, (const cplx*)v,
+                                                                         (cplx*)z);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) { h->err = std::string("oras_precond_noalloc: launch: ") + cudaGetErrorString(e); return ORAS_ERR_CUDA; }
