@@ -62,6 +62,7 @@ enum {
 enum { ORAS_MEM_HOST = 0, ORAS_MEM_DEVICE = 1 };
 enum { ORAS_WEIGHTS_POU = 0 /* ORAS: R_s^T D_s */, ORAS_WEIGHTS_NONE = 1 /* OAS, Sec. 4 */ };
 enum { ORAS_OVERLAP_VERTEX = 0, ORAS_OVERLAP_FACE = 1 };
+enum { ORAS_LU_AUTO = 0 /* tensor cores for FP32 factors */, ORAS_LU_CUDA_CORES = 1 };
 
 /* Problem statement (Sec. 2-4).  All pointers are host pointers, read during the call. */
 typedef struct {
@@ -87,7 +88,10 @@ typedef struct {
   int32_t factor_bits;        /* 32: complex FP32 local factors; 64: complex FP64 [32]  */
   int32_t weights;            /* ORAS_WEIGHTS_POU [default] or ORAS_WEIGHTS_NONE        */
   int32_t overlap_kind;       /* ORAS_OVERLAP_VERTEX [default] or ORAS_OVERLAP_FACE     */
-  int32_t reserved[11];
+  int32_t lu_engine;          /* ORAS_LU_AUTO [default]: trailing updates of FP32 factors */
+                              /*   on tcgen05 tensor cores (TF32 inputs, FP32 accumulate);*/
+                              /*   ORAS_LU_CUDA_CORES: FP32 CUDA-core updates             */
+  int32_t reserved[10];
 } oras_options;
 
 /* Per right-hand-side outcome of oras_solve. */

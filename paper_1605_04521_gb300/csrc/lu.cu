@@ -22,7 +22,7 @@
 #include <climits>
 #include <cstdio>
 
-#include "dev.cuh"
+#include "lu.cuh"
 
 namespace oras {
 
@@ -59,14 +59,6 @@ struct LuArgs {
   int32_t* status;
 };
 
-// Rectangular set of output tiles [i0, i1) x [j0, j1); an end of INT_MAX means the subdomain's
-// tile count.
-struct Region { int i0, i1, j0, j1; };
-struct UpdArgs {
-  int kk0, kk1;             // contraction over tile columns [kk0, kk1)
-  int nreg;
-  Region reg[2];
-};
 
 template <typename R>
 __device__ __forceinline__ R* tile_base(void* arena, const LuArgs& a, int s, int64_t I, int64_t J) {
@@ -543,7 +535,12 @@ static int lu_run(oras_handle* h) {
   cudaFuncSetAttribute(k_lu_swap<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
   cudaFuncSetAttribute(k_lu_trsm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
   cudaFuncSetAttribute(k_lu_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_u);
+  const bool tc = sizeof(R) == 4 && h->opt.lu_engine == ORAS_LU_AUTO && tc_update_available(h);
   auto update = [&](const UpdArgs& u) {
+    if (tc) {
+      launch_update_tc(h, u, max_nts);
+      return;
+    }
     int64_t blocks = region_blocks(u, max_nts);
     if (blocks <= 0) return;
     int pb = prof_begin(h);

@@ -1,0 +1,327 @@
+// Trailing update of the batched LU on the 5th-generation tensor cores (tcgen05, TF32 inputs,
+// FP32 accumulation in tensor memory):  C_IJ -= sum_{kk in [kk0, kk1)} L_I,kk U_kk,J.
+//
+// Complex product as real products of the split planes (Gauss's real-split form):
+//   C_re -= L_re U_re - L_im U_im ,   C_im -= L_re U_im + L_im U_re .
+// L tiles (below the diagonal) store row-major planes and U tiles (above it) column-major
+// planes, so both operands are K-major: an L plane is an M x K matrix with K contiguous and a
+// U plane is the N x K transpose of the K x N operand.  Each CTA owns a 128 x 128 complex output
+// block (2 x 2 tiles): D_re and D_im are 128 x 128 FP32 accumulators in 256 tensor-memory
+// columns.  The -L_im U_im term uses the instruction's negate-B bit.
+//
+// Warp roles (128 threads): warp 0 lane 0 loads operand chunks with TMA (one tensor map over
+// the whole arena, 128-byte swizzle); warp 1 lane 0 issues the MMAs and commits them to the
+// stage's "empty" barrier; after the last commit all four warps read their 32 accumulator rows
+// from tensor memory and subtract them from C.  Stages hold one 32-float K-chunk of all four
+// operand planes (64 KB).  Waits are bounded; a timeout sets the device status flag.
+#include <cuda.h>
+
+#include <cstdio>
+#include <mutex>
+
+#include "lu.cuh"
+
+namespace oras {
+
+constexpr int TC_THREADS = 128;
+constexpr int TC_STAGES = 3;
+constexpr uint32_t TC_BOX_BYTES = 64 * 32 * 4;          // 64 rows x 32 floats
+constexpr uint32_t TC_STAGE_BYTES = 8 * TC_BOX_BYTES;   // A_re, A_im (2 tiles each), B_re, B_im
+constexpr uint32_t TC_TMEM_COLS = 256;
+
+struct TcArgs {
+  const int64_t* np;
+  const int64_t* tile_off;
+  float* arena;
+  UpdArgs u;
+  int32_t* status;
+};
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | (1ull << 16) | (64ull << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 128.
+__device__ __forceinline__ uint32_t idesc_tf32(bool negate_b) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((negate_b ? 1u : 0u) << 14) | ((128u >> 3) << 17) |
+         ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+      ::"r"(dtmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// Map the block index to a 2 x 2-tile output block of one region of subdomain s.
+__device__ __forceinline__ bool tc_block(const UpdArgs& u, int64_t nts, int64_t e, int64_t& I0, int64_t& J0,
+                                         int& ni, int& nj) {
+  for (int q = 0; q < u.nreg; ++q) {
+    int64_t i0, i1, j0, j1;
+    region_clip(u.reg[q], nts, i0, i1, j0, j1);
+    const int64_t nbi = (i1 - i0 + 1) / 2, nbj = (j1 - j0 + 1) / 2;
+    if (e < nbi * nbj) {
+      I0 = i0 + 2 * (e / nbj);
+      J0 = j0 + 2 * (e % nbj);
+      ni = (int)((i1 - I0) < 2 ? (i1 - I0) : 2);
+      nj = (int)((j1 - J0) < 2 ? (j1 - J0) : 2);
+      return true;
+    }
+    e -= nbi * nbj;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ uint64_t full[TC_STAGES], empty[TC_STAGES], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int s = blockIdx.y;
+  const int64_t nts = a.np[s] / TB;
+  int64_t I0, J0;
+  int ni, nj;
+  if (!tc_block(a.u, nts, blockIdx.x, I0, J0, ni, nj)) return;
+  int64_t kk1 = a.u.kk1 < nts ? a.u.kk1 : nts;
+  const int64_t kk0 = a.u.kk0;
+  if (kk1 <= kk0) return;
+  const int nchunks = (int)(2 * (kk1 - kk0));
+  // dynamic shared memory base rounded up to 1024 B for the swizzle atoms
+  unsigned char* stages = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int q = 0; q < TC_STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    mbar_init(&done, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = tmem_base;
+  const int64_t toff = a.tile_off[s];
+  // operand tiles (clamped to a valid tile when the block is ragged; results discarded)
+  const int64_t Ia = I0, Ib = ni > 1 ? I0 + 1 : I0, Ja = J0, Jb = nj > 1 ? J0 + 1 : J0;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int c = 0; c < nchunks; ++c) {
+      const int st = c % TC_STAGES;
+      if (c >= TC_STAGES && !mbar_wait(&empty[st], (uint32_t)(((c / TC_STAGES) - 1) & 1))) {
+        abort_flag = 1;
+        break;
+      }
+      const int64_t kk = kk0 + c / 2;
+      const int x = (c & 1) * 32;
+      unsigned char* sb = stages + (size_t)st * TC_STAGE_BYTES;
+      mbar_expect_tx(&full[st], TC_STAGE_BYTES);
+      const int zA0 = (int)(toff + Ia * nts + kk), zA1 = (int)(toff + Ib * nts + kk);
+      const int zB0 = (int)(toff + kk * nts + Ja), zB1 = (int)(toff + kk * nts + Jb);
+      tma_load_3d(sb + 0 * TC_BOX_BYTES, &tmap, x, 0, zA0, &full[st]);    // A_re rows 0..63
+      tma_load_3d(sb + 1 * TC_BOX_BYTES, &tmap, x, 0, zA1, &full[st]);    // A_re rows 64..127
+      tma_load_3d(sb + 2 * TC_BOX_BYTES, &tmap, x, 64, zA0, &full[st]);   // A_im
+      tma_load_3d(sb + 3 * TC_BOX_BYTES, &tmap, x, 64, zA1, &full[st]);
+      tma_load_3d(sb + 4 * TC_BOX_BYTES, &tmap, x, 0, zB0, &full[st]);    // B_re cols 0..63
+      tma_load_3d(sb + 5 * TC_BOX_BYTES, &tmap, x, 0, zB1, &full[st]);    // B_re cols 64..127
+      tma_load_3d(sb + 6 * TC_BOX_BYTES, &tmap, x, 64, zB0, &full[st]);   // B_im
+      tma_load_3d(sb + 7 * TC_BOX_BYTES, &tmap, x, 64, zB1, &full[st]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t id_pos = idesc_tf32(false), id_neg = idesc_tf32(true);
+    const uint32_t d_re = tbase, d_im = tbase + 128;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int st = c % TC_STAGES;
+      if (!mbar_wait(&full[st], (uint32_t)((c / TC_STAGES) & 1))) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sb = smem_u32(stages + (size_t)st * TC_STAGE_BYTES);
+      const uint64_t are = sdesc(sb), aim = sdesc(sb + 2 * TC_BOX_BYTES);
+      const uint64_t bre = sdesc(sb + 4 * TC_BOX_BYTES), bim = sdesc(sb + 6 * TC_BOX_BYTES);
+#pragma unroll
+      for (int k8 = 0; k8 < 4; ++k8) {  // K = 8 TF32 = 32 B per instruction
+        const uint64_t dk = (uint64_t)(k8 * 32) >> 4;
+        const uint32_t first = (c == 0 && k8 == 0) ? 0u : 1u;
+        mma_tf32(d_re, are + dk, bre + dk, id_pos, first);
+        mma_tf32(d_re, aim + dk, bim + dk, id_neg, 1u);
+        mma_tf32(d_im, are + dk, bim + dk, id_pos, first);
+        mma_tf32(d_im, aim + dk, bre + dk, id_pos, 1u);
+      }
+      mma_commit(&empty[st]);
+    }
+    if (!ok) abort_flag = 1;
+    mma_commit(&done);
+  }
+  __syncwarp();
+  // ---------------- epilogue: all four warps
+  const bool fin = mbar_wait(&done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!fin || abort_flag) {
+    if (tid == 0) atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
+  } else {
+    const int row = warp * 32 + lane;           // accumulator row = TMEM lane
+    const int ti = row >> 6, li = row & 63;
+    const int64_t I = I0 + ti;
+#pragma unroll 1
+    for (int cb = 0; cb < 4; ++cb) {            // 32-column chunks of the 128 complex columns
+      float re[32], im[32];
+      const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+      tmem_ld32(tbase + lane_off + cb * 32, re);
+      tmem_ld32(tbase + lane_off + 128 + cb * 32, im);
+      const int tj = cb >> 1, lj0 = (cb & 1) * 32;
+      const int64_t J = J0 + tj;
+      if (ti >= ni || tj >= nj) continue;
+      float* C = a.arena + (toff + I * nts + J) * 2 * TILE_PLANE;
+      if (I >= J) {  // row-major planes: 32 contiguous floats per thread
+        float4* cr = (float4*)(C + li * TB + lj0);
+        float4* ci = (float4*)(C + TILE_PLANE + li * TB + lj0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float4 x = cr[q], y = ci[q];
+          x.x -= re[4 * q]; x.y -= re[4 * q + 1]; x.z -= re[4 * q + 2]; x.w -= re[4 * q + 3];
+          y.x -= im[4 * q]; y.y -= im[4 * q + 1]; y.z -= im[4 * q + 2]; y.w -= im[4 * q + 3];
+          cr[q] = x;
+          ci[q] = y;
+        }
+      } else {       // column-major planes: lanes cover consecutive rows
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int64_t e = (int64_t)(lj0 + q) * TB + li;
+          C[e] -= re[q];
+          C[TILE_PLANE + e] -= im[q];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TC_TMEM_COLS));
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+struct TcState {
+  CUtensorMap map;
+  void* base = nullptr;
+  int64_t tiles = 0;
+  bool ok = false;
+};
+static TcState g_tc_cache[64];
+static std::mutex g_tc_mu;
+
+// Tensor map over the arena viewed as [tiles][2 planes x 64 rows][64 floats].
+static bool make_map(const oras_handle* h, CUtensorMap* map) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const int64_t tiles = h->mesh.arena_tiles;
+  if (tiles >= (int64_t(1) << 31)) return false;
+  cuuint64_t dims[3] = {64, 128, (cuuint64_t)tiles};
+  cuuint64_t strides[2] = {64 * sizeof(float), 128 * 64 * sizeof(float)};
+  cuuint32_t box[3] = {32, 64, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->dev.arena, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool tc_update_available(const oras_handle* h) {
+  if (h->dev.factor_bits != 32 || !h->dev.arena) return false;
+  int dev = h->dev.device;
+  if (dev < 0 || dev >= 64) return false;
+  std::lock_guard<std::mutex> lock(g_tc_mu);
+  TcState& st = g_tc_cache[dev];
+  if (st.base != h->dev.arena || st.tiles != h->mesh.arena_tiles) {
+    st.ok = make_map(h, &st.map);
+    st.base = h->dev.arena;
+    st.tiles = h->mesh.arena_tiles;
+  }
+  return st.ok;
+}
+
+int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts) {
+  const auto& m = h->mesh;
+  const auto& d = h->dev;
+  int64_t blocks = 0;
+  for (int q = 0; q < u.nreg; ++q) {
+    int64_t i0, i1, j0, j1;
+    region_clip(u.reg[q], max_nts, i0, i1, j0, j1);
+    blocks += ((i1 - i0 + 1) / 2) * ((j1 - j0 + 1) / 2);
+  }
+  if (blocks <= 0) return 0;
+  CUtensorMap map;
+  {
+    std::lock_guard<std::mutex> lock(g_tc_mu);
+    map = g_tc_cache[d.device].map;
+  }
+  TcArgs a;
+  a.np = d.sub_np;
+  a.tile_off = d.sub_tile_off;
+  a.arena = (float*)d.arena;
+  a.u = u;
+  a.status = d.status;
+  const size_t smem = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
+  cudaFuncSetAttribute(k_lu_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int pb = prof_begin(h);
+  k_lu_update_tc<<<dim3((unsigned)blocks, m.nsub), TC_THREADS, smem, d.stream>>>(map, a);
+  prof_end(h, KC_LU_UPDATE, pb, 1);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace oras
