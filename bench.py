@@ -50,14 +50,22 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="head16", choices=["head16", "cube8"])
+    ap.add_argument("--workload", default="head16", choices=["head16", "cube8", "head8"],
+                    help="head16: the benchmark workload; cube8: 8^3 r=1 plane wave (FP64 factors); "
+                         "head8: 8^3 r=2 8 subdomains (1.9 GB arena, for kernel profiles)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     return ap.parse_args()
 
 
 def workload(name):
-    return synth.config(1) if name == "head16" else synth.config(0)
+    if name == "head16":
+        return synth.config(1)
+    if name == "head8":
+        w = synth.small(n=8, r=2, nsub=8, overlap=1, restart=100)
+        w.name = "head8_r2_s8_d1_profile"
+        return w
+    return synth.config(0)
 
 
 def peaks():

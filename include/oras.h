@@ -91,7 +91,9 @@ typedef struct {
   int32_t lu_engine;          /* ORAS_LU_AUTO [default]: trailing updates of FP32 factors */
                               /*   on tcgen05 tensor cores (TF32 inputs, FP32 accumulate);*/
                               /*   ORAS_LU_CUDA_CORES: FP32 CUDA-core updates             */
-  int32_t reserved[10];
+  int32_t lu_panel;           /* outer LU panel width in 64-column tiles [8]: the trailing */
+                              /*   matrix is updated once per panel                        */
+  int32_t reserved[9];
 } oras_options;
 
 /* Per right-hand-side outcome of oras_solve. */

@@ -503,7 +503,6 @@ static int64_t region_blocks(const UpdArgs& u, int64_t nts) {
   return tot;
 }
 
-constexpr int OUTER_W = 4;  // outer panel width in tile columns
 
 template <typename R>
 static int lu_run(oras_handle* h) {
@@ -548,8 +547,9 @@ static int lu_run(oras_handle* h) {
     prof_end(h, KC_LU_UPDATE, pb, 1);
     count_launches(1);
   };
-  for (int k0 = 0; k0 < max_nts; k0 += OUTER_W) {
-    const int kend = k0 + OUTER_W;
+  const int W = h->opt.lu_panel > 0 ? h->opt.lu_panel : 8;  // outer panel width in tile columns
+  for (int k0 = 0; k0 < max_nts; k0 += W) {
+    const int kend = k0 + W;
     for (int k = k0; k < kend && k < max_nts; ++k) {
       a.k = k;
       int64_t rows_max = m.max_np - (int64_t)k * TB;
