@@ -224,6 +224,11 @@ static int sync_status(oras_handle* h) {
     h->err = "local matrix of subdomain " + std::to_string(st[ST_SUB]) + " has a zero pivot column";
     return ORAS_ERR_SINGULAR_LOCAL;
   }
+  if (st[ST_ERR] == DEV_BADINDEX) {
+    h->err = "internal index check failed in a device kernel (code " + std::to_string(st[ST_DETAIL]) +
+             ", subdomain " + std::to_string(st[ST_SUB]) + ")";
+    return ORAS_ERR_CUDA;
+  }
   if (st[ST_ERR] == DEV_TIMEOUT) {
     h->err = "a bounded device wait gave up";
     return ORAS_ERR_DEVICE_TIMEOUT;

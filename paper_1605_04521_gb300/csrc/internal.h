@@ -20,7 +20,7 @@ struct cplx { double re, im; };
 
 // device status flags (Device::status): [0] error code, [1] detail, [2] subdomain
 enum { ST_ERR = 0, ST_DETAIL = 1, ST_SUB = 2 };
-enum { DEV_OK = 0, DEV_SINGULAR = 1, DEV_TIMEOUT = 2 };
+enum { DEV_OK = 0, DEV_SINGULAR = 1, DEV_TIMEOUT = 2, DEV_BADINDEX = 3 };
 
 
 // ------------------------------------------------------------------ local DOF convention

@@ -248,6 +248,202 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_tournament(LuArgs a, void* ar
   }
 }
 
+// ------------------------------------------------------------------ FP32 tournament, rows in registers
+// Same tournament as above, with the elimination done on register-resident rows: thread t owns
+// candidate row t (64 complex values in registers).  No row is moved: the chosen pivot row is
+// marked and broadcast through shared memory for the rank-1 update of the rows not yet chosen.
+// Pivot choice: max |Re| + |Im| over unchosen rows, ties to the lowest candidate position.
+struct RegGepp {
+  float pr[2][TB], pi[2][TB];   // pivot row broadcast, double buffered by column parity
+  float wv[2][8];
+  int wi[2][8];
+  int order[TB];                // pivot rank -> candidate position
+};
+
+__device__ __forceinline__ void gepp_regs(float (&xr)[TB], float (&xi)[TB], bool valid, RegGepp& g, int& myrank,
+                                          float& mypiv) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  bool chosen = false;
+  myrank = -1;
+  mypiv = 0.0f;
+  if (t < TB) g.order[t] = -1;
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < TB; ++c) {
+    const int b = c & 1;
+    float v = (valid && !chosen) ? fabsf(xr[c]) + fabsf(xi[c]) : -1.0f;
+    if (v != v) v = 0.0f;  // a non-finite entry still lets a row be chosen
+    int key = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_down_sync(0xffffffffu, v, o);
+      const int ok = __shfl_down_sync(0xffffffffu, key, o);
+      if (ov > v || (ov == v && ok < key)) { v = ov; key = ok; }
+    }
+    if (lane == 0) { g.wv[b][warp] = v; g.wi[b][warp] = key; }
+    __syncthreads();
+    float bv = g.wv[b][0];
+    int bk = g.wi[b][0];
+#pragma unroll
+    for (int w = 1; w < LU_THREADS / 32; ++w)
+      if (g.wv[b][w] > bv || (g.wv[b][w] == bv && g.wi[b][w] < bk)) { bv = g.wv[b][w]; bk = g.wi[b][w]; }
+    if (t == bk && bv >= 0.0f) {
+      chosen = true;
+      myrank = c;
+      mypiv = bv;
+      g.order[c] = t;
+#pragma unroll
+      for (int j = c; j < TB; ++j) { g.pr[b][j] = xr[j]; g.pi[b][j] = xi[j]; }
+    }
+    __syncthreads();
+    if (bv > 0.0f && valid && !chosen) {
+      const float dr = g.pr[b][c], di = g.pi[b][c], den = dr * dr + di * di;
+      const float lr = (xr[c] * dr + xi[c] * di) / den, li = (xi[c] * dr - xr[c] * di) / den;
+      xr[c] = lr;
+      xi[c] = li;
+#pragma unroll
+      for (int j = c + 1; j < TB; ++j) {
+        const float ur = g.pr[b][j], ui = g.pi[b][j];
+        xr[j] -= lr * ur - li * ui;
+        xi[j] -= lr * ui + li * ur;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void flag_bad(const LuArgs& a, int s, int code) {
+  if (atomicCAS(&a.status[ST_ERR], DEV_OK, DEV_BADINDEX) == DEV_OK) {
+    a.status[ST_DETAIL] = code;
+    a.status[ST_SUB] = s;
+  }
+}
+
+// ids[order] when order names a candidate position holding a row of the panel, else a flagged
+// fallback (the first panel row) so that no later access leaves the matrix.
+__device__ __forceinline__ int32_t pick_checked(const LuArgs& a, int s, const int32_t* ids, int order, int64_t R0,
+                                                int64_t np, int code) {
+  if (order >= 0 && order < LU_THREADS) {
+    const int32_t r = ids[order];
+    if (r >= R0 && r < np) return r;
+  }
+  flag_bad(a, s, code);
+  return (int32_t)R0;
+}
+
+__device__ __forceinline__ void load_row_regs(void* arena, const LuArgs& a, int s, int32_t row, float (&xr)[TB],
+                                              float (&xi)[TB]) {
+  const float* T = tile_base<float>(arena, a, s, row / TB, a.k) + (row % TB) * TB;
+#pragma unroll
+  for (int j = 0; j < TB; j += 4) {
+    const float4 r = *(const float4*)(T + j), i = *(const float4*)(T + TILE_PLANE + j);
+    xr[j] = r.x; xr[j + 1] = r.y; xr[j + 2] = r.z; xr[j + 3] = r.w;
+    xi[j] = i.x; xi[j + 1] = i.y; xi[j + 2] = i.z; xi[j + 3] = i.w;
+  }
+}
+
+__global__ void __launch_bounds__(LU_THREADS, 1) k_lu_tournament_rg(LuArgs a, void* arena) {
+  constexpr int CH = LU_THREADS;  // one candidate row per thread
+  __shared__ RegGepp g;
+  __shared__ int32_t ids[CH];
+  __shared__ int32_t nids[TB];
+  __shared__ int s_old;
+  const int s = blockIdx.y, t = threadIdx.x;
+  const int64_t np = a.np[s], nts = np / TB;
+  if (a.k >= nts) return;
+  const int64_t R0 = (int64_t)a.k * TB;
+  const int64_t rows_total = np - R0;
+  const int nch = (int)((rows_total + CH - 1) / CH);
+  int c = blockIdx.x;
+  if (c >= nch) return;
+  int64_t mrem = rows_total - (int64_t)c * CH;
+  const int m = (int)(mrem < CH ? mrem : CH);
+  float xr[TB], xi[TB];
+  int myrank;
+  float mypiv;
+  ids[t] = t < m ? (int32_t)(R0 + (int64_t)c * CH + t) : -1;
+  if (t < m) load_row_regs(arena, a, s, ids[t], xr, xi);
+  __syncthreads();
+  gepp_regs(xr, xi, t < m, g, myrank, mypiv);
+  if (t < TB) nids[t] = pick_checked(a, s, ids, g.order[t], R0, np, 1);
+  __syncthreads();
+  int32_t* cand = a.cand + (int64_t)s * a.slots * TB;
+  int32_t* cnt = a.cnt + (int64_t)s * a.slots;
+  int level_off = 0, n_l = nch, j = c;
+  if (n_l > 1 && t < TB) cand[(level_off + j) * TB + t] = nids[t];
+  while (n_l > 1) {
+    const int n_next = (n_l + 1) >> 1;
+    const int parent = j >> 1, sib = j ^ 1;
+    const int next_off = level_off + n_l;
+    if (sib >= n_l) {  // odd one out: pass the candidates up unchanged
+      if (t < TB) cand[(next_off + parent) * TB + t] = nids[t];
+      level_off = next_off; n_l = n_next; j = parent;
+      continue;
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_old = atomicAdd(&cnt[next_off + parent], 1);
+    __syncthreads();
+    if (s_old == 0) return;  // the sibling will merge
+    if (t == 0) cnt[next_off + parent] = 0;
+    __threadfence();
+    const int left = j & ~1;
+    ids[t] = t < 2 * TB ? ((volatile int32_t*)cand)[(level_off + left + (t >= TB)) * TB + (t % TB)] : -1;
+    __syncthreads();
+    bool okrow = t < 2 * TB && ids[t] >= R0 && ids[t] < np;
+    if (t < 2 * TB && !okrow) flag_bad(a, s, 2);
+    if (okrow) load_row_regs(arena, a, s, ids[t], xr, xi);
+    gepp_regs(xr, xi, okrow, g, myrank, mypiv);
+    if (t < TB) nids[t] = pick_checked(a, s, ids, g.order[t], R0, np, 3);
+    __syncthreads();
+    level_off = next_off; n_l = n_next; j = parent;
+    if (n_l > 1 && t < TB) cand[(level_off + j) * TB + t] = nids[t];
+  }
+  // root: the chosen rows, in pivot order, are L11\U11 of the step
+  CT<float>* dg = (CT<float>*)a.diag + (int64_t)s * TB * TB;
+  if (myrank >= 0) {
+#pragma unroll
+    for (int q = 0; q < TB; ++q) dg[q * TB + myrank] = {xr[q], xi[q]};
+    if (!(mypiv > 0.0f)) {
+      atomicCAS(&a.status[ST_ERR], DEV_OK, DEV_SINGULAR);
+      a.status[ST_SUB] = s;
+    }
+  }
+  __syncthreads();
+  if (t == 0) {
+    int32_t posv[2 * TB], rowv[2 * TB];
+    int nm = 0;
+    auto row_at = [&](int32_t pos) {
+      for (int q = 0; q < nm; ++q)
+        if (posv[q] == pos) return rowv[q];
+      return pos;
+    };
+    auto pos_of = [&](int32_t row) {
+      for (int q = 0; q < nm; ++q)
+        if (rowv[q] == row) return posv[q];
+      return row;
+    };
+    auto set = [&](int32_t pos, int32_t row) {
+      for (int q = 0; q < nm; ++q)
+        if (posv[q] == pos) { rowv[q] = row; return; }
+      posv[nm] = pos; rowv[nm] = row; ++nm;
+    };
+    for (int i = 0; i < TB; ++i) {
+      int32_t tgt = (int32_t)(R0 + i);
+      int32_t pr = pos_of(nids[i]);
+      if (pr != tgt) {
+        int32_t ra = row_at(tgt), rb = row_at(pr);
+        set(tgt, rb);
+        set(pr, ra);
+      }
+    }
+    int32_t* pp = a.pairs + (int64_t)s * 2 * TB * 2;
+    int np_ = 0;
+    for (int q = 0; q < nm; ++q)
+      if (posv[q] != rowv[q]) { pp[np_ * 2] = posv[q]; pp[np_ * 2 + 1] = rowv[q]; ++np_; }
+    a.pairs_n[s] = np_;
+  }
+}
+
 // Apply the step's row permutation to every column of the matrix and to perm.
 template <typename R>
 __global__ void k_lu_swap(LuArgs a, void* arena) {
@@ -556,7 +752,10 @@ static int lu_run(oras_handle* h) {
       int nch = (int)((rows_max + CH - 1) / CH);
       int64_t nrem = max_nts - k - 1;
       int pb = prof_begin(h);
-      k_lu_tournament<R><<<dim3(nch, m.nsub), LU_THREADS, smem_t, d.stream>>>(a, d.arena);
+      if (sizeof(R) == 4)
+        k_lu_tournament_rg<<<dim3(nch, m.nsub), LU_THREADS, 0, d.stream>>>(a, d.arena);
+      else
+        k_lu_tournament<R><<<dim3(nch, m.nsub), LU_THREADS, smem_t, d.stream>>>(a, d.arena);
       prof_end(h, KC_LU_TOURNAMENT, pb, 1);
       pb = prof_begin(h);
       k_lu_swap<R><<<dim3(max_nts + 1, m.nsub), 256, smem_s, d.stream>>>(a, d.arena);
