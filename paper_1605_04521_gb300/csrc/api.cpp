@@ -180,7 +180,8 @@ static int alloc_factor_space(oras_handle* h, int bits) {
   auto& m = h->mesh;
   auto& d = h->dev;
   size_t el = bits == 64 ? 16 : 8;
-  size_t bytes = (size_t)m.arena_tiles * TB * TB * el;
+  // the factor tiles, then 2 scratch tiles per subdomain (inverted diagonal blocks of a step)
+  size_t bytes = (size_t)(m.arena_tiles + 2 * m.nsub) * TB * TB * el;
   if (d.arena && d.factor_bits == bits && d.arena_bytes == bytes) return ORAS_OK;
   if (d.arena) { cudaFree(d.arena); d.arena = nullptr; }
   cudaError_t e = cudaMalloc(&d.arena, bytes);

@@ -633,24 +633,14 @@ __global__ void k_gidx(int64_t total, const int32_t* perm, const int64_t* np_off
 // row-major planes and Uinv_I = U_II^{-1} stored with column-major planes, so that the in-block
 // substitution steps of the preconditioner apply become tile matrix-vector products like the
 // off-diagonal ones (block substitution with inverted diagonal blocks).
+// Inverts a factored diagonal block held column-major (padded) in D: X[0] gets the columns of
+// L^{-1} (unit lower), X[1] those of U^{-1}.  128 threads: thread t < TB solves column t of
+// L x = e_t, thread TB + j column j of U x = e_j.
 template <typename R>
-__global__ void __launch_bounds__(2 * TB) k_lu_diag_inv(LuArgs a, void* arena, void* inv, const int64_t* inv_off) {
-  extern __shared__ unsigned char smem_raw[];
-  CT<R>* D = (CT<R>*)smem_raw;  // [TB][PS]: D[j*PS+i] = LU(i,j)
-  CT<R>* X = D + TB * PS;       // [2][TB][PS]: columns of L^{-1}, then of U^{-1}
-  const int s = blockIdx.y;
-  const int64_t nts = a.np[s] / TB;
-  const int64_t I = blockIdx.x;
-  if (I >= nts) return;
-  const R* T = tile_base<R>(arena, a, s, I, I);
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int i = e / TB, j = e % TB;
-    D[j * PS + i] = tload<R>(T, true, i, j);
-  }
-  __syncthreads();
+__device__ void invert_block(const CT<R>* D, CT<R>* X) {
   const int t = threadIdx.x;
   const CT<R> zero = {R(0), R(0)}, one = {R(1), R(0)};
-  if (t < TB) {  // column t of L^{-1}: L x = e_t, unit lower
+  if (t < TB) {
     CT<R>* x = X + t * PS;
     for (int i = 0; i < TB; ++i) {
       if (i < t) { x[i] = zero; continue; }
@@ -663,7 +653,7 @@ __global__ void __launch_bounds__(2 * TB) k_lu_diag_inv(LuArgs a, void* arena, v
       }
       x[i] = {-acc.re, -acc.im};
     }
-  } else {  // column j of U^{-1}: U x = e_j
+  } else if (t < 2 * TB) {
     const int j = t - TB;
     CT<R>* x = X + TB * PS + j * PS;
     for (int i = TB - 1; i >= 0; --i) {
@@ -673,9 +663,11 @@ __global__ void __launch_bounds__(2 * TB) k_lu_diag_inv(LuArgs a, void* arena, v
       x[i] = mulc(acc, invc(D[i * PS + i]));
     }
   }
-  __syncthreads();
-  R* Li = (R*)inv + (inv_off[s] + I) * 4 * TILE_PLANE;
-  R* Ui = Li + 2 * TILE_PLANE;
+}
+
+// Stores L^{-1} with row-major planes at Li and U^{-1} with column-major planes at Ui.
+template <typename R>
+__device__ void store_inverses(const CT<R>* X, R* Li, R* Ui) {
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
     const int hi = e / TB, lo = e % TB;
     const CT<R> l = X[lo * PS + hi];                // Linv(i = hi, j = lo): row-major storage
@@ -685,6 +677,56 @@ __global__ void __launch_bounds__(2 * TB) k_lu_diag_inv(LuArgs a, void* arena, v
     Ui[e] = u.re;
     Ui[TILE_PLANE + e] = u.im;
   }
+}
+
+// Inverses of the diagonal blocks of the factors: Linv_I = L_II^{-1} (unit lower) stored with
+// row-major planes and Uinv_I = U_II^{-1} stored with column-major planes, so that the in-block
+// substitution steps of the preconditioner apply become tile matrix-vector products like the
+// off-diagonal ones (block substitution with inverted diagonal blocks).
+template <typename R>
+__global__ void __launch_bounds__(2 * TB) k_lu_diag_inv(LuArgs a, void* arena, void* inv, const int64_t* inv_off) {
+  extern __shared__ unsigned char smem_raw[];
+  CT<R>* D = (CT<R>*)smem_raw;  // [TB][PS]: D[j*PS+i] = LU(i,j)
+  CT<R>* X = D + TB * PS;       // [2][TB][PS]
+  const int s = blockIdx.y;
+  const int64_t nts = a.np[s] / TB;
+  const int64_t I = blockIdx.x;
+  if (I >= nts) return;
+  const R* T = tile_base<R>(arena, a, s, I, I);
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int i = e / TB, j = e % TB;
+    D[j * PS + i] = tload<R>(T, true, i, j);
+  }
+  __syncthreads();
+  invert_block<R>(D, X);
+  __syncthreads();
+  R* Li = (R*)inv + (inv_off[s] + I) * 4 * TILE_PLANE;
+  store_inverses<R>(X, Li, Li + 2 * TILE_PLANE);
+}
+
+// The step's factored diagonal block (from the tournament root): written to tile (k, k) and
+// inverted into the subdomain's two scratch tiles for the tensor-core triangular solves.
+template <typename R>
+__global__ void __launch_bounds__(2 * TB) k_lu_step_inv(LuArgs a, void* arena, int64_t scratch_base) {
+  extern __shared__ unsigned char smem_raw[];
+  CT<R>* D = (CT<R>*)smem_raw;  // [TB][PS]
+  CT<R>* X = D + TB * PS;       // [2][TB][PS]
+  const int s = blockIdx.x;
+  const int64_t nts = a.np[s] / TB;
+  const int k = a.k;
+  if (k >= nts) return;
+  const CT<R>* dg = (const CT<R>*)a.diag + (int64_t)s * TB * TB;  // element (e % TB, e / TB)
+  R* dst = tile_base<R>(arena, a, s, k, k);
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    const CT<R> v = dg[e];
+    D[(e / TB) * PS + (e % TB)] = v;
+    tstore<R>(dst, true, e % TB, e / TB, v);
+  }
+  __syncthreads();
+  invert_block<R>(D, X);
+  __syncthreads();
+  R* Li = (R*)arena + (scratch_base + 2 * s) * 2 * TILE_PLANE;
+  store_inverses<R>(X, Li, Li + 2 * TILE_PLANE);
 }
 
 // number of output tiles of the update regions for the largest subdomain
@@ -730,6 +772,8 @@ static int lu_run(oras_handle* h) {
   cudaFuncSetAttribute(k_lu_swap<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
   cudaFuncSetAttribute(k_lu_trsm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
   cudaFuncSetAttribute(k_lu_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_u);
+  const size_t smem_i = (size_t)3 * TB * PS * sizeof(CT<R>);
+  cudaFuncSetAttribute(k_lu_step_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_i);
   const bool tc = sizeof(R) == 4 && h->opt.lu_engine == ORAS_LU_AUTO && tc_update_available(h);
   auto update = [&](const UpdArgs& u) {
     if (tc) {
@@ -761,8 +805,14 @@ static int lu_run(oras_handle* h) {
       k_lu_swap<R><<<dim3(max_nts + 1, m.nsub), 256, smem_s, d.stream>>>(a, d.arena);
       prof_end(h, KC_LU_SWAP, pb, 1);
       pb = prof_begin(h);
-      k_lu_trsm<R><<<dim3((unsigned)(2 * nrem + 1), m.nsub), TB, smem_r, d.stream>>>(a, d.arena);
-      prof_end(h, KC_LU_TRSM, pb, 1);
+      if (tc) {
+        k_lu_step_inv<R><<<m.nsub, 2 * TB, smem_i, d.stream>>>(a, d.arena, m.arena_tiles);
+        launch_trsm_tc(h, k, max_nts);
+        prof_end(h, KC_LU_TRSM, pb, 2);
+      } else {
+        k_lu_trsm<R><<<dim3((unsigned)(2 * nrem + 1), m.nsub), TB, smem_r, d.stream>>>(a, d.arena);
+        prof_end(h, KC_LU_TRSM, pb, 1);
+      }
       count_launches(3);
       // inner update: the panel's remaining columns below, and the panel's remaining rows
       // to the right of the panel
@@ -784,7 +834,6 @@ static int lu_run(oras_handle* h) {
   k_gidx<<<(unsigned)((total + 255) / 256), 256, 0, d.stream>>>(total, d.perm, d.sub_np_off, d.sub_ns,
                                                               d.sub_ns_off, d.sub_dofs, m.nsub, d.gidx);
   {
-    size_t smem_i = (size_t)3 * TB * PS * sizeof(CT<R>);
     cudaFuncSetAttribute(k_lu_diag_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_i);
     int pb = prof_begin(h);
     k_lu_diag_inv<R><<<dim3(max_nts, m.nsub), 2 * TB, smem_i, d.stream>>>(a, d.arena, d.dinv, d.sub_inv_off);

@@ -31,5 +31,6 @@ __host__ __device__ __forceinline__ void region_clip(const Region& r, int64_t nt
 // uses the CUDA-core kernel)
 bool tc_update_available(const oras_handle* h);
 int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts);
+int launch_trsm_tc(oras_handle* h, int k, int max_nts);
 
 }  // namespace oras

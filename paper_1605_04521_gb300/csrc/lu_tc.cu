@@ -237,6 +237,130 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TC_TMEM_COLS));
 }
 
+// ------------------------------------------------------------------ triangular solves of a step
+// With the step's diagonal block factored as L11 U11 and inverted into two scratch tiles
+// (L11^{-1} row-major, U11^{-1} column-major), the tile solves are products:
+//   below:  L_Ik = A_Ik U11^{-1}            (A_Ik row-major: M = rows of the tile, K-major)
+//   right:  U_kJ^T = A_kJ^T L11^{-T}        (A_kJ column-major: its storage rows are the rows of
+//                                            the transpose, K-major; the result lands in the
+//                                            same storage positions)
+// Each CTA takes two tiles of one side (M = 128), N = 64, K = 64, and overwrites them.
+struct TrsmArgs {
+  const int64_t* np;
+  const int64_t* tile_off;
+  float* arena;
+  int64_t scratch_base;   // first scratch tile: subdomain s uses scratch_base + 2 s (+0 L^-1, +1 U^-1)
+  int k;
+  int32_t* status;
+};
+
+constexpr uint32_t TRSM_CHUNK_BYTES = 6 * TC_BOX_BYTES;  // A_re (2 boxes), A_im (2), B_re, B_im
+
+__device__ __forceinline__ uint32_t idesc_tf32_n64(bool negate_b) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((negate_b ? 1u : 0u) << 14) | ((64u >> 3) << 17) |
+         ((128u >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_lu_trsm_tc(const __grid_constant__ CUtensorMap tmap, TrsmArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ uint64_t full, done;
+  __shared__ uint32_t tmem_base;
+  const int s = blockIdx.y;
+  const int64_t nts = a.np[s] / TB;
+  const int k = a.k;
+  if (k >= nts) return;
+  const int64_t nrem = nts - k - 1, nb = (nrem + 1) / 2;
+  const int64_t b = blockIdx.x;
+  if (b >= 2 * nb) return;
+  const bool lower = b < nb;
+  const int64_t t0 = k + 1 + 2 * (lower ? b : b - nb);
+  const bool two = t0 + 1 < nts;
+  const int64_t t1 = two ? t0 + 1 : t0;
+  const int64_t toff = a.tile_off[s];
+  const int zA0 = (int)(lower ? toff + t0 * nts + k : toff + (int64_t)k * nts + t0);
+  const int zA1 = (int)(lower ? toff + t1 * nts + k : toff + (int64_t)k * nts + t1);
+  const int zB = (int)(a.scratch_base + 2 * s + (lower ? 1 : 0));
+  unsigned char* st = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    mbar_init(&full, 1);
+    mbar_init(&done, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = tmem_base;
+  if (warp == 0 && lane == 0) {
+    mbar_expect_tx(&full, 2 * TRSM_CHUNK_BYTES);
+    for (int h = 0; h < 2; ++h) {
+      unsigned char* sb = st + (size_t)h * TRSM_CHUNK_BYTES;
+      const int x = h * 32;
+      tma_load_3d(sb + 0 * TC_BOX_BYTES, &tmap, x, 0, zA0, &full);
+      tma_load_3d(sb + 1 * TC_BOX_BYTES, &tmap, x, 0, zA1, &full);
+      tma_load_3d(sb + 2 * TC_BOX_BYTES, &tmap, x, 64, zA0, &full);
+      tma_load_3d(sb + 3 * TC_BOX_BYTES, &tmap, x, 64, zA1, &full);
+      tma_load_3d(sb + 4 * TC_BOX_BYTES, &tmap, x, 0, zB, &full);
+      tma_load_3d(sb + 5 * TC_BOX_BYTES, &tmap, x, 64, zB, &full);
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t id_pos = idesc_tf32_n64(false), id_neg = idesc_tf32_n64(true);
+    const uint32_t d_re = tbase, d_im = tbase + 64;
+    if (mbar_wait(&full, 0)) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t sb = smem_u32(st + (size_t)h * TRSM_CHUNK_BYTES);
+        const uint64_t are = sdesc(sb), aim = sdesc(sb + 2 * TC_BOX_BYTES);
+        const uint64_t bre = sdesc(sb + 4 * TC_BOX_BYTES), bim = sdesc(sb + 5 * TC_BOX_BYTES);
+#pragma unroll
+        for (int k8 = 0; k8 < 4; ++k8) {
+          const uint64_t dk = (uint64_t)(k8 * 32) >> 4;
+          const uint32_t first = (h == 0 && k8 == 0) ? 0u : 1u;
+          mma_tf32(d_re, are + dk, bre + dk, id_pos, first);
+          mma_tf32(d_re, aim + dk, bim + dk, id_neg, 1u);
+          mma_tf32(d_im, are + dk, bim + dk, id_pos, first);
+          mma_tf32(d_im, aim + dk, bre + dk, id_pos, 1u);
+        }
+      }
+    } else {
+      atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
+    }
+    mma_commit(&done);
+  }
+  __syncwarp();
+  const bool fin = mbar_wait(&done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (fin) {
+    const int row = warp * 32 + lane, ti = row >> 6, li = row & 63;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    float* T = a.arena + (size_t)(ti ? zA1 : zA0) * 2 * TILE_PLANE;
+#pragma unroll 1
+    for (int cb = 0; cb < 2; ++cb) {
+      float re[32], im[32];
+      tmem_ld32(tbase + lane_off + cb * 32, re);
+      tmem_ld32(tbase + lane_off + 64 + cb * 32, im);
+      if (ti == 1 && !two) continue;
+      float4* cr = (float4*)(T + li * TB + cb * 32);
+      float4* ci = (float4*)(T + TILE_PLANE + li * TB + cb * 32);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        cr[q] = make_float4(re[4 * q], re[4 * q + 1], re[4 * q + 2], re[4 * q + 3]);
+        ci[q] = make_float4(im[4 * q], im[4 * q + 1], im[4 * q + 2], im[4 * q + 3]);
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(128));
+}
+
 // ------------------------------------------------------------------ host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -268,7 +392,7 @@ static std::mutex g_tc_mu;
 static bool make_map(const oras_handle* h, CUtensorMap* map) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
-  const int64_t tiles = h->mesh.arena_tiles;
+  const int64_t tiles = h->mesh.arena_tiles + 2 * h->mesh.nsub;
   if (tiles >= (int64_t(1) << 31)) return false;
   cuuint64_t dims[3] = {64, 128, (cuuint64_t)tiles};
   cuuint64_t strides[2] = {64 * sizeof(float), 128 * 64 * sizeof(float)};
@@ -286,12 +410,38 @@ bool tc_update_available(const oras_handle* h) {
   if (dev < 0 || dev >= 64) return false;
   std::lock_guard<std::mutex> lock(g_tc_mu);
   TcState& st = g_tc_cache[dev];
-  if (st.base != h->dev.arena || st.tiles != h->mesh.arena_tiles) {
+  const int64_t tiles = h->mesh.arena_tiles + 2 * h->mesh.nsub;
+  if (st.base != h->dev.arena || st.tiles != tiles) {
     st.ok = make_map(h, &st.map);
     st.base = h->dev.arena;
-    st.tiles = h->mesh.arena_tiles;
+    st.tiles = tiles;
   }
   return st.ok;
+}
+
+int launch_trsm_tc(oras_handle* h, int k, int max_nts) {
+  const auto& m = h->mesh;
+  const auto& d = h->dev;
+  const int64_t nrem = max_nts - k - 1;
+  if (nrem <= 0) return 0;
+  const int64_t blocks = 2 * ((nrem + 1) / 2);
+  CUtensorMap map;
+  {
+    std::lock_guard<std::mutex> lock(g_tc_mu);
+    map = g_tc_cache[d.device].map;
+  }
+  TrsmArgs a;
+  a.np = d.sub_np;
+  a.tile_off = d.sub_tile_off;
+  a.arena = (float*)d.arena;
+  a.scratch_base = m.arena_tiles;
+  a.k = k;
+  a.status = d.status;
+  const size_t smem = (size_t)2 * TRSM_CHUNK_BYTES + 1024;
+  cudaFuncSetAttribute(k_lu_trsm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_lu_trsm_tc<<<dim3((unsigned)blocks, m.nsub), TC_THREADS, smem, d.stream>>>(map, a);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts) {
