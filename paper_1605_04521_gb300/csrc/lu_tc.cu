@@ -5,15 +5,15 @@
 //   C_re -= L_re U_re - L_im U_im ,   C_im -= L_re U_im + L_im U_re .
 // L tiles (below the diagonal) store row-major planes and U tiles (above it) column-major
 // planes, so both operands are K-major: an L plane is an M x K matrix with K contiguous and a
-// U plane is the N x K transpose of the K x N operand.  Each CTA owns a 128 x 128 complex output
-// block (2 x 2 tiles): D_re and D_im are 128 x 128 FP32 accumulators in 256 tensor-memory
+// U plane is the N x K transpose of the K x N operand.  Each CTA owns a 128 x 256 complex output
+// block (2 x 4 tiles): D_re and D_im are 128 x 256 FP32 accumulators filling the 512 tensor-memory
 // columns.  The -L_im U_im term uses the instruction's negate-B bit.
 //
 // Warp roles (128 threads): warp 0 lane 0 loads operand chunks with TMA (one tensor map over
 // the whole arena, 128-byte swizzle); warp 1 lane 0 issues the MMAs and commits them to the
 // stage's "empty" barrier; after the last commit all four warps read their 32 accumulator rows
 // from tensor memory and subtract them from C.  Stages hold one 32-float K-chunk of all four
-// operand planes (64 KB).  Waits are bounded; a timeout sets the device status flag.
+// operand planes (96 KB).  Waits are bounded; a timeout sets the device status flag.
 #include <cuda.h>
 
 #include <cstdio>
@@ -24,10 +24,12 @@
 namespace oras {
 
 constexpr int TC_THREADS = 128;
-constexpr int TC_STAGES = 3;
-constexpr uint32_t TC_BOX_BYTES = 64 * 32 * 4;          // 64 rows x 32 floats
-constexpr uint32_t TC_STAGE_BYTES = 8 * TC_BOX_BYTES;   // A_re, A_im (2 tiles each), B_re, B_im
-constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr int TC_STAGES = 2;
+constexpr int TC_BN = 4;                                 // output tile columns per CTA (N = 256)
+constexpr int TC_GROUP = 8;                              // block rows per raster group (L2 reuse)
+constexpr uint32_t TC_BOX_BYTES = 64 * 32 * 4;           // 64 rows x 32 floats
+constexpr uint32_t TC_STAGE_BYTES = (4 + 2 * TC_BN) * TC_BOX_BYTES;  // A_re, A_im (2 tiles), B_re, B_im (4)
+constexpr uint32_t TC_TMEM_COLS = 512;
 
 struct TcArgs {
   const int64_t* np;
@@ -49,9 +51,9 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFF) | (1ull << 16) | (64ull << 32) | (1ull << 46) | (2ull << 61);
 }
 
-// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 128.
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 64 TC_BN.
 __device__ __forceinline__ uint32_t idesc_tf32(bool negate_b) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((negate_b ? 1u : 0u) << 14) | ((128u >> 3) << 17) |
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((negate_b ? 1u : 0u) << 14) | (((64u * TC_BN) >> 3) << 17) |
          ((128u >> 4) << 24);
 }
 
@@ -81,18 +83,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-// Map the block index to a 2 x 2-tile output block of one region of subdomain s.
+// Map the block index to a 2 x TC_BN-tile output block of one region of subdomain s.  Blocks
+// are ordered in groups of TC_GROUP block rows, walking down a group before moving right, so
+// that CTAs running at the same time share their L (rows) and U (columns) operands in L2.
+__host__ __device__ __forceinline__ void region_blocks_of(const Region& r, int64_t nts, int64_t& nbi, int64_t& nbj,
+                                                          int64_t& i0, int64_t& i1, int64_t& j0, int64_t& j1) {
+  region_clip(r, nts, i0, i1, j0, j1);
+  nbi = (i1 - i0 + 1) / 2;
+  nbj = (j1 - j0 + TC_BN - 1) / TC_BN;
+}
+
 __device__ __forceinline__ bool tc_block(const UpdArgs& u, int64_t nts, int64_t e, int64_t& I0, int64_t& J0,
                                          int& ni, int& nj) {
   for (int q = 0; q < u.nreg; ++q) {
-    int64_t i0, i1, j0, j1;
-    region_clip(u.reg[q], nts, i0, i1, j0, j1);
-    const int64_t nbi = (i1 - i0 + 1) / 2, nbj = (j1 - j0 + 1) / 2;
+    int64_t nbi, nbj, i0, i1, j0, j1;
+    region_blocks_of(u.reg[q], nts, nbi, nbj, i0, i1, j0, j1);
     if (e < nbi * nbj) {
-      I0 = i0 + 2 * (e / nbj);
-      J0 = j0 + 2 * (e % nbj);
+      const int64_t gsize = (int64_t)TC_GROUP * nbj;
+      const int64_t g = e / gsize, first = g * TC_GROUP;
+      const int64_t gs = nbi - first < TC_GROUP ? nbi - first : TC_GROUP;
+      const int64_t loc = e % gsize;
+      const int64_t bi = first + loc % gs, bj = loc / gs;
+      I0 = i0 + 2 * bi;
+      J0 = j0 + TC_BN * bj;
       ni = (int)((i1 - I0) < 2 ? (i1 - I0) : 2);
-      nj = (int)((j1 - J0) < 2 ? (j1 - J0) : 2);
+      nj = (int)((j1 - J0) < TC_BN ? (j1 - J0) : TC_BN);
       return true;
     }
     e -= nbi * nbj;
@@ -137,7 +152,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
   const uint32_t tbase = tmem_base;
   const int64_t toff = a.tile_off[s];
   // operand tiles (clamped to a valid tile when the block is ragged; results discarded)
-  const int64_t Ia = I0, Ib = ni > 1 ? I0 + 1 : I0, Ja = J0, Jb = nj > 1 ? J0 + 1 : J0;
+  const int64_t Ia = I0, Ib = ni > 1 ? I0 + 1 : I0;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
@@ -152,20 +167,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
       unsigned char* sb = stages + (size_t)st * TC_STAGE_BYTES;
       mbar_expect_tx(&full[st], TC_STAGE_BYTES);
       const int zA0 = (int)(toff + Ia * nts + kk), zA1 = (int)(toff + Ib * nts + kk);
-      const int zB0 = (int)(toff + kk * nts + Ja), zB1 = (int)(toff + kk * nts + Jb);
       tma_load_3d(sb + 0 * TC_BOX_BYTES, &tmap, x, 0, zA0, &full[st]);    // A_re rows 0..63
       tma_load_3d(sb + 1 * TC_BOX_BYTES, &tmap, x, 0, zA1, &full[st]);    // A_re rows 64..127
       tma_load_3d(sb + 2 * TC_BOX_BYTES, &tmap, x, 64, zA0, &full[st]);   // A_im
       tma_load_3d(sb + 3 * TC_BOX_BYTES, &tmap, x, 64, zA1, &full[st]);
-      tma_load_3d(sb + 4 * TC_BOX_BYTES, &tmap, x, 0, zB0, &full[st]);    // B_re cols 0..63
-      tma_load_3d(sb + 5 * TC_BOX_BYTES, &tmap, x, 0, zB1, &full[st]);    // B_re cols 64..127
-      tma_load_3d(sb + 6 * TC_BOX_BYTES, &tmap, x, 64, zB0, &full[st]);   // B_im
-      tma_load_3d(sb + 7 * TC_BOX_BYTES, &tmap, x, 64, zB1, &full[st]);
+#pragma unroll
+      for (int q = 0; q < TC_BN; ++q) {                                   // B_re, B_im: 64 columns per tile
+        const int zB = (int)(toff + kk * nts + J0 + (q < nj ? q : 0));
+        tma_load_3d(sb + (4 + q) * TC_BOX_BYTES, &tmap, x, 0, zB, &full[st]);
+        tma_load_3d(sb + (4 + TC_BN + q) * TC_BOX_BYTES, &tmap, x, 64, zB, &full[st]);
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     const uint32_t id_pos = idesc_tf32(false), id_neg = idesc_tf32(true);
-    const uint32_t d_re = tbase, d_im = tbase + 128;
+    const uint32_t d_re = tbase, d_im = tbase + 64 * TC_BN;
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       const int st = c % TC_STAGES;
@@ -176,7 +192,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sb = smem_u32(stages + (size_t)st * TC_STAGE_BYTES);
       const uint64_t are = sdesc(sb), aim = sdesc(sb + 2 * TC_BOX_BYTES);
-      const uint64_t bre = sdesc(sb + 4 * TC_BOX_BYTES), bim = sdesc(sb + 6 * TC_BOX_BYTES);
+      const uint64_t bre = sdesc(sb + 4 * TC_BOX_BYTES), bim = sdesc(sb + (4 + TC_BN) * TC_BOX_BYTES);
 #pragma unroll
       for (int k8 = 0; k8 < 4; ++k8) {  // K = 8 TF32 = 32 B per instruction
         const uint64_t dk = (uint64_t)(k8 * 32) >> 4;
@@ -202,11 +218,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
     const int ti = row >> 6, li = row & 63;
     const int64_t I = I0 + ti;
 #pragma unroll 1
-    for (int cb = 0; cb < 4; ++cb) {            // 32-column chunks of the 128 complex columns
+    for (int cb = 0; cb < 2 * TC_BN; ++cb) {     // 32-column chunks of the 64 TC_BN complex columns
       float re[32], im[32];
       const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
       tmem_ld32(tbase + lane_off + cb * 32, re);
-      tmem_ld32(tbase + lane_off + 128 + cb * 32, im);
+      tmem_ld32(tbase + lane_off + 64 * TC_BN + cb * 32, im);
       const int tj = cb >> 1, lj0 = (cb & 1) * 32;
       const int64_t J = J0 + tj;
       if (ti >= ni || tj >= nj) continue;
@@ -449,9 +465,9 @@ int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts) {
   const auto& d = h->dev;
   int64_t blocks = 0;
   for (int q = 0; q < u.nreg; ++q) {
-    int64_t i0, i1, j0, j1;
-    region_clip(u.reg[q], max_nts, i0, i1, j0, j1);
-    blocks += ((i1 - i0 + 1) / 2) * ((j1 - j0 + 1) / 2);
+    int64_t nbi, nbj, i0, i1, j0, j1;
+    region_blocks_of(u.reg[q], max_nts, nbi, nbj, i0, i1, j0, j1);
+    blocks += nbi * nbj;
   }
   if (blocks <= 0) return 0;
   CUtensorMap map;
