@@ -23,7 +23,8 @@ int launch_lu(oras_handle* h);
 int lu_max_chunks(int64_t max_np, int factor_bits);
 int launch_apply_f64out(const oras_handle* h, const cplx* v, cplx* z, int k);
 int launch_apply_f32out(const oras_handle* h, const cplx* v, void* z, int k);
-size_t apply_yglob_bytes(const oras_handle* h);
+size_t apply_yglob_bytes_for(const oras_handle* h, int k);
+int apply_passes(const oras_handle* h, int k);
 void launch_spmv_f64(const oras_handle* h, const cplx* x, cplx* y, int k);
 void launch_spmv_f32(const oras_handle* h, const void* x, cplx* y, int k);
 void launch_dot(const oras_handle* h, const cplx* a, const cplx* b, cplx* partials, int k);
@@ -100,15 +101,23 @@ static void prof_clear(oras_handle* h) {
     }                                                                                              \
   } while (0)
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the handle's stream): a
+// free does not synchronise the device, so handles on other streams keep running.
 template <typename T>
-static cudaError_t dalloc(T*& p, size_t n) {
-  if (p) { cudaFree(p); p = nullptr; }
+static cudaError_t dalloc_s(T*& p, size_t n, cudaStream_t s) {
+  if (p) { cudaFreeAsync(p, s); p = nullptr; }
   if (n == 0) n = 1;
-  return cudaMalloc((void**)&p, n * sizeof(T));
+  return cudaMallocAsync((void**)&p, n * sizeof(T), s);
 }
 template <typename T>
+static void dfree_s(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync((void*)p, s);
+  p = nullptr;
+}
+#define dalloc(p, n) dalloc_s(p, n, d.stream)
+template <typename T>
 static cudaError_t dput(T*& p, const std::vector<T>& v, cudaStream_t s) {
-  cudaError_t e = dalloc(p, v.size());
+  cudaError_t e = dalloc_s(p, v.size(), s);
   if (e != cudaSuccess) return e;
   if (!v.empty()) e = cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
   return e;
@@ -122,9 +131,17 @@ static void dfree_all(Device& d) {
                   d.lu_ipiv, d.lu_diag, d.dinv, d.sub_inv_off, d.status, d.V, d.Zf, d.Zd, d.w, d.xk, d.bk, d.tmp, d.H, d.gcs, d.gsn,
                   d.g, d.red, d.scal, d.ybuf, d.io};
   for (void* p : ptrs)
-    if (p) cudaFree(p);
-  if (d.host_pinned) cudaFreeHost(d.host_pinned);
+    if (p) cudaFreeAsync(p, d.stream);
+  cudaStreamSynchronize(d.stream);  // the pool returns the memory at this synchronisation
   d = Device();
+}
+
+// Small pinned host buffer for scalars read back during a solve, one per host thread, kept until
+// the process exits (freeing pinned memory may synchronise the device).
+static double* pinned_scratch() {
+  thread_local double* p = nullptr;
+  if (!p && cudaMallocHost((void**)&p, PINNED_SCRATCH_DOUBLES * sizeof(double)) != cudaSuccess) p = nullptr;
+  return p;
 }
 
 static int upload(oras_handle* h) {
@@ -171,8 +188,21 @@ static int upload(oras_handle* h) {
   CK(dalloc(d.perm, npoff[m.nsub]));
   CK(dalloc(d.gidx, npoff[m.nsub]));
   CK(dalloc(d.status, 8));
-  CK(cudaMallocHost((void**)&d.host_pinned, 4096 * sizeof(double)));
+  d.host_pinned = pinned_scratch();
+  if (!d.host_pinned) { h->err = "pinned host scratch allocation failed"; return ORAS_ERR_OUT_OF_MEMORY; }
   d.uploaded = true;
+  return ORAS_OK;
+}
+
+// Global scratch for the apply's local vectors when k right-hand sides go through it.
+static int ensure_ybuf(oras_handle* h, int k) {
+  auto& d = h->dev;
+  const size_t yb = apply_yglob_bytes_for(h, k);
+  if (yb <= d.ybuf_bytes) return ORAS_OK;
+  dfree_s(d.ybuf, d.stream);
+  d.ybuf_bytes = 0;
+  CK(cudaMallocAsync(&d.ybuf, yb, d.stream));
+  d.ybuf_bytes = yb;
   return ORAS_OK;
 }
 
@@ -183,8 +213,8 @@ static int alloc_factor_space(oras_handle* h, int bits) {
   // the factor tiles, then 2 scratch tiles per subdomain (inverted diagonal blocks of a step)
   size_t bytes = (size_t)(m.arena_tiles + 2 * m.nsub) * TB * TB * el;
   if (d.arena && d.factor_bits == bits && d.arena_bytes == bytes) return ORAS_OK;
-  if (d.arena) { cudaFree(d.arena); d.arena = nullptr; }
-  cudaError_t e = cudaMalloc(&d.arena, bytes);
+  dfree_s(d.arena, d.stream);
+  cudaError_t e = cudaMallocAsync(&d.arena, bytes, d.stream);
   if (e != cudaSuccess) {
     h->err = "local-factor arena of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e);
     d.arena = nullptr;
@@ -198,20 +228,19 @@ static int alloc_factor_space(oras_handle* h, int bits) {
   CK(dalloc(d.lu_cnt, (size_t)m.nsub * slots));
   CK(cudaMemsetAsync(d.lu_cnt, 0, (size_t)m.nsub * slots * sizeof(int32_t), d.stream));
   CK(dalloc(d.lu_ipiv, (size_t)m.nsub * (2 * TB * 2 + 1)));
-  CK(cudaMalloc(&d.lu_diag, (size_t)m.nsub * TB * TB * el));
+  dfree_s(d.lu_diag, d.stream);
+  CK(cudaMallocAsync(&d.lu_diag, (size_t)m.nsub * TB * TB * el, d.stream));
   {
     std::vector<int64_t> inv_off(m.nsub + 1, 0);
     for (int q = 0; q < m.nsub; ++q) inv_off[q + 1] = inv_off[q] + m.sub_np[q] / TB;
     CK(dput(d.sub_inv_off, inv_off, d.stream));
-    if (d.dinv) { cudaFree(d.dinv); d.dinv = nullptr; }
+    dfree_s(d.dinv, d.stream);
     d.dinv_bytes = (size_t)inv_off[m.nsub] * 2 * TB * TB * el;
-    CK(cudaMalloc(&d.dinv, d.dinv_bytes));
+    CK(cudaMallocAsync(&d.dinv, d.dinv_bytes, d.stream));
   }
-  size_t yb = apply_yglob_bytes(h);
-  if (d.ybuf) { cudaFree(d.ybuf); d.ybuf = nullptr; }
-  if (yb) CK(cudaMalloc(&d.ybuf, yb));
-  d.ybuf_bytes = yb;
-  return ORAS_OK;
+  dfree_s(d.ybuf, d.stream);
+  d.ybuf_bytes = 0;
+  return ensure_ybuf(h, 1);
 }
 
 
@@ -324,8 +353,7 @@ int oras_factor(oras_handle* h, const oras_complex* eps_r, const oras_complex* m
     if (!d.mu) CK(dalloc(d.mu, m.nt));
     CK(cudaMemcpyAsync(d.mu, mu_r, sizeof(cplx) * m.nt, kind, d.stream));
   } else if (d.mu) {
-    cudaFree(d.mu);
-    d.mu = nullptr;
+    dfree_s(d.mu, d.stream);
   }
   CK(cudaMemsetAsync(d.status, 0, 8 * sizeof(int32_t), d.stream));
   h->k0 = k0;
@@ -447,6 +475,7 @@ int oras_global_csr(oras_handle* h, int64_t* rowptr, int32_t* cols, oras_complex
 static int ensure_ws(oras_handle* h, int k, int m) {
   auto& d = h->dev;
   const int64_t N = h->mesh.ndof;
+  if (int rc = ensure_ybuf(h, k)) return rc;
   if (d.ws_k >= k && d.ws_m >= m && d.V) return ORAS_OK;
   int kk = std::max(k, d.ws_k), mm = std::max(m, d.ws_m);
   size_t nk = (size_t)N * kk;
@@ -454,9 +483,8 @@ static int ensure_ws(oras_handle* h, int k, int m) {
   if (d.factor_bits == 64) {
     CK(dalloc(d.Zd, nk * mm));
   } else {
-    if (d.Zf) cudaFree(d.Zf);
-    d.Zf = nullptr;
-    CK(cudaMalloc((void**)&d.Zf, nk * mm * 2 * sizeof(float)));
+    dfree_s(d.Zf, d.stream);
+    CK(cudaMallocAsync((void**)&d.Zf, nk * mm * 2 * sizeof(float), d.stream));
   }
   CK(dalloc(d.w, nk));
   CK(dalloc(d.xk, nk));
@@ -505,11 +533,13 @@ static int store_output(oras_handle* h, const cplx* src, int k, int mem, oras_co
   return ORAS_OK;
 }
 
-static void precond_to_z(oras_handle* h, const cplx* v, int k, int j) {
+static int precond_to_z(oras_handle* h, const cplx* v, int k, int j) {
   auto& d = h->dev;
   size_t nk = (size_t)h->mesh.ndof * k;
-  if (d.factor_bits == 64) launch_apply_f64out(h, v, d.Zd + nk * j, k);
-  else launch_apply_f32out(h, v, (char*)d.Zf + nk * j * 2 * sizeof(float), k);
+  int rc = d.factor_bits == 64 ? launch_apply_f64out(h, v, d.Zd + nk * j, k)
+                               : launch_apply_f32out(h, v, (char*)d.Zf + nk * j * 2 * sizeof(float), k);
+  if (rc) h->err = "preconditioner apply launch failed";
+  return rc ? ORAS_ERR_CUDA : ORAS_OK;
 }
 
 static void spmv_z(oras_handle* h, int k, int j, cplx* y) {
@@ -577,8 +607,8 @@ static int fgmres(oras_handle* h, int k, double tol, oras_info* info) {
       cplx* Vj = d.V + nk * j;
       cplx* Vn = d.V + nk * (j + 1);
       int pb = prof_begin(h);
-      precond_to_z(h, Vj, k, j);
-      prof_end(h, KC_APPLY, pb, k);
+      if (precond_to_z(h, Vj, k, j)) return ORAS_ERR_CUDA;
+      prof_end(h, KC_APPLY, pb, apply_passes(h, k));
       pb = prof_begin(h);
       spmv_z(h, k, j, d.w);
       prof_end(h, KC_SPMV, pb, (k + 7) / 8);
@@ -660,8 +690,15 @@ int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t
   if (rc) return rc;
   rc = load_input(h, v, k, mem, h->dev.bk);
   if (rc) return rc;
-  launch_apply_f64out(h, h->dev.bk, h->dev.tmp, k);
-  return store_output(h, h->dev.tmp, k, mem, z);
+  const int pb = prof_begin(h);
+  if (launch_apply_f64out(h, h->dev.bk, h->dev.tmp, k)) {
+    h->err = "oras_precond: apply launch failed";
+    return ORAS_ERR_CUDA;
+  }
+  prof_end(h, KC_APPLY, pb, apply_passes(h, k));
+  rc = store_output(h, h->dev.tmp, k, mem, z);
+  prof_resolve(h);
+  return rc;
 }
 
 int oras_rhs_dipole(oras_handle* h, const double* x0, const double* dir, oras_complex* b, int32_t mem) {
@@ -719,8 +756,8 @@ int oras_rhs_plane_wave(oras_handle* h, const double* dvec, const oras_complex* 
   rc = launch_plane(h, dvec, pvec, h->k0, qs, qw, nq, bface, d.tmp);
   cudaError_t e = cudaMemcpyAsync(b, d.tmp, sizeof(cplx) * h->mesh.ndof,
                                   mem == ORAS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, d.stream);
+  cudaFreeAsync(bface, d.stream);
   cudaStreamSynchronize(d.stream);
-  cudaFree(bface);
   if (rc || e != cudaSuccess) { h->err = "oras_rhs_plane_wave: launch failed"; return ORAS_ERR_CUDA; }
   return ORAS_OK;
 }

@@ -1,37 +1,42 @@
 // ORAS preconditioner apply (Sec. 4):  z = sum_s R_s^T D_s A_s^{-1} R_s v
 // with A_s^{-1} = U_s^{-1} L_s^{-1} P_s from the batched LU.  One cluster of two CTAs per
-// subdomain (body in apply.cuh); the local vector lives in shared memory when it fits next to
-// the tile ring, else in a global scratch slice.  With the Boolean partition of unity every
-// global DOF is written by exactly one subdomain (no atomics); OAS (no D_s) accumulates with
+// subdomain (body in apply.cuh); one launch serves a group of up to KR right-hand sides, so the
+// factor arena is streamed once per group.  The local vectors live in shared memory when they fit
+// next to the tile ring, else in a global scratch slice.  With the Boolean partition of unity
+// every global DOF is written by exactly one subdomain (no atomics); OAS (no D_s) accumulates with
 // atomics.
 #include "apply.cuh"
 
 namespace oras {
 
-template <typename R, typename ZT>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(APPLY_THREADS)
-    k_apply(ApplyGeom a, int k, int r, void* yglob, const cplx* __restrict__ v, ZT* __restrict__ z) {
-  apply_cluster<R, ZT>(a, blockIdx.x / 2, v, k, z, k, r, (CT<R>*)yglob);
+size_t apply_yglob_bytes(const oras_handle* h, int kr);
+
+template <typename R, typename ZT, int KR>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(APPLY_THREADS, 1)
+    k_apply(ApplyGeom a, int k, int r0, int nr, void* yglob, const cplx* __restrict__ v, ZT* __restrict__ z) {
+  apply_cluster<R, ZT, KR>(a, blockIdx.x / 2, v, k, z, k, r0, nr, (CT<R>*)yglob);
 }
 
-constexpr size_t SMEM_LIMIT = 227 * 1024 - 256;  // opt-in dynamic shared memory per block, with margin
+constexpr size_t SMEM_LIMIT = 227 * 1024 - 2048;  // opt-in shared memory per block less the static part
 
-// Ring depth and dynamic shared memory; y in shared memory when `allow_smem_y` and it fits.
-template <typename R>
+// Ring depth and dynamic shared memory for KR right-hand sides per pass; y in shared memory when
+// `allow_smem_y` and it fits next to a ring of at least 3 stages (2 when nothing else fits).
+template <typename R, int KR>
 static void apply_config(const oras_handle* h, bool allow_smem_y, int* S, size_t* smem, bool* y_smem) {
+  using Sm = ApplySmem<R, KR>;
   const int64_t ystrips = (h->mesh.max_np / TB + 1) / 2;
   if (allow_smem_y)
     for (int q = 8; q >= 2; --q)
-      if (ApplySmem<R>::total(q, ystrips) <= SMEM_LIMIT) {
+      if (Sm::total(q, ystrips) <= SMEM_LIMIT) {
         *S = q;
-        *smem = ApplySmem<R>::total(q, ystrips);
+        *smem = Sm::total(q, ystrips);
         *y_smem = true;
         return;
       }
   int q = 8;
-  while (q > 2 && ApplySmem<R>::total(q, 0) > SMEM_LIMIT) --q;
+  while (q > 2 && Sm::total(q, 0) > SMEM_LIMIT) --q;
   *S = q;
-  *smem = ApplySmem<R>::total(q, 0);
+  *smem = Sm::total(q, 0);
   *y_smem = false;
 }
 
@@ -48,19 +53,44 @@ ApplyGeom apply_geom(const oras_handle* h) {
   return a;
 }
 
-template <typename R, typename ZT>
-static int apply_t(const oras_handle* h, const cplx* v, ZT* z, int k) {
+// Right-hand sides per pass for the next group of `rem` (fewest passes, then the smallest KR).
+static int group_kr(int rem, int maxkr) {
+  int kr = 1;
+  while (kr < maxkr && kr < rem) kr *= 2;
+  return kr;
+}
+
+template <typename R, typename ZT, int KR>
+static int apply_group(const oras_handle* h, const cplx* v, ZT* z, int k, int r0, int nr) {
   const auto& m = h->mesh;
   const auto& d = h->dev;
   ApplyGeom a = apply_geom(h);
   size_t smem;
   bool y_smem;
-  apply_config<R>(h, true, &a.stages, &smem, &y_smem);
-  cudaFuncSetAttribute(k_apply<R, ZT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (a.weights != ORAS_WEIGHTS_POU) cudaMemsetAsync(z, 0, sizeof(ZT) * m.ndof * k, d.stream);
-  for (int r = 0; r < k; ++r)
-    k_apply<R, ZT><<<2 * m.nsub, APPLY_THREADS, smem, d.stream>>>(a, k, r, y_smem ? nullptr : d.ybuf, v, z);
-  count_launches(k);
+  apply_config<R, KR>(h, true, &a.stages, &smem, &y_smem);
+  if (!y_smem && (!d.ybuf || d.ybuf_bytes < apply_yglob_bytes(h, KR))) return -1;
+  allow_max_smem((const void*)k_apply<R, ZT, KR>);
+  k_apply<R, ZT, KR><<<2 * m.nsub, APPLY_THREADS, smem, d.stream>>>(a, k, r0, nr, y_smem ? nullptr : d.ybuf, v, z);
+  return 0;
+}
+
+template <typename R, typename ZT>
+static int apply_t(const oras_handle* h, const cplx* v, ZT* z, int k) {
+  const auto& m = h->mesh;
+  const auto& d = h->dev;
+  if (h->opt.weights != ORAS_WEIGHTS_POU) cudaMemsetAsync(z, 0, sizeof(ZT) * m.ndof * k, d.stream);
+  const int maxkr = sizeof(R) == 4 ? APPLY_MAX_KR_F32 : APPLY_MAX_KR_F64;
+  int launches = 0, rc = 0;
+  for (int r0 = 0; r0 < k && rc == 0;) {
+    const int kr = group_kr(k - r0, maxkr), nr = std::min(kr, k - r0);
+    if (kr == 1) rc = apply_group<R, ZT, 1>(h, v, z, k, r0, nr);
+    else if (kr == 2) rc = apply_group<R, ZT, 2>(h, v, z, k, r0, nr);
+    else if constexpr (sizeof(R) == 4) rc = apply_group<R, ZT, 4>(h, v, z, k, r0, nr);
+    r0 += nr;
+    ++launches;
+  }
+  count_launches(launches);
+  if (rc) return rc;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -73,24 +103,51 @@ int launch_apply_f32out(const oras_handle* h, const cplx* v, void* z, int k) {
   return apply_t<float, CT<float>>(h, v, (CT<float>*)z, k);
 }
 
-size_t apply_yglob_bytes(const oras_handle* h) {
+// Number of apply launches (arena passes) for k right-hand sides.
+int apply_passes(const oras_handle* h, int k) {
+  const int maxkr = h->dev.factor_bits == 64 ? APPLY_MAX_KR_F64 : APPLY_MAX_KR_F32;
+  int n = 0;
+  for (int r0 = 0; r0 < k; ++n) r0 += std::min(group_kr(k - r0, maxkr), k - r0);
+  return n;
+}
+
+template <typename R, int KR>
+static size_t yglob_bytes_kr(const oras_handle* h) {
   int S;
   size_t smem;
   bool y_smem;
-  if (h->dev.factor_bits == 64) apply_config<double>(h, true, &S, &smem, &y_smem);
-  else apply_config<float>(h, true, &S, &smem, &y_smem);
+  apply_config<R, KR>(h, true, &S, &smem, &y_smem);
   if (y_smem) return 0;
-  size_t el = h->dev.factor_bits == 64 ? sizeof(CT<double>) : sizeof(CT<float>);
   int64_t total = 0;
   for (int s = 0; s < h->mesh.nsub; ++s) total += h->mesh.sub_np[s];
-  return (size_t)total * el;
+  return (size_t)total * KR * sizeof(CT<R>);
+}
+
+// Global scratch for the local vectors when a group of kr right-hand sides runs (0: shared memory).
+size_t apply_yglob_bytes(const oras_handle* h, int kr) {
+  if (h->dev.factor_bits == 64) return kr <= 1 ? yglob_bytes_kr<double, 1>(h) : yglob_bytes_kr<double, 2>(h);
+  if (kr <= 1) return yglob_bytes_kr<float, 1>(h);
+  if (kr == 2) return yglob_bytes_kr<float, 2>(h);
+  return yglob_bytes_kr<float, 4>(h);
+}
+
+// Largest scratch any group of a k-vector apply needs.
+size_t apply_yglob_bytes_for(const oras_handle* h, int k) {
+  const int maxkr = h->dev.factor_bits == 64 ? APPLY_MAX_KR_F64 : APPLY_MAX_KR_F32;
+  size_t b = 0;
+  for (int r0 = 0; r0 < k;) {
+    const int kr = group_kr(k - r0, maxkr);
+    b = std::max(b, apply_yglob_bytes(h, kr));
+    r0 += std::min(kr, k - r0);
+  }
+  return b;
 }
 
 // Shared-memory configuration for the allocation-free variant (local vectors in global memory).
 void apply_noalloc_config(const oras_handle* h, int* S, size_t* smem) {
   bool y_smem;
-  if (h->dev.factor_bits == 64) apply_config<double>(h, false, S, smem, &y_smem);
-  else apply_config<float>(h, false, S, smem, &y_smem);
+  if (h->dev.factor_bits == 64) apply_config<double, 1>(h, false, S, smem, &y_smem);
+  else apply_config<float, 1>(h, false, S, smem, &y_smem);
 }
 
 }  // namespace oras

@@ -2,17 +2,21 @@
 //   y = P_s R_s v ;  y = L_s^{-1} y ;  y = U_s^{-1} y ;  z += R_s^T D_s y
 // Block substitution over the tiled factor arena (split re/im planes; tiles on/below the block
 // diagonal row-major, above it column-major) with inverted diagonal blocks, so every step is a
-// TB x TB tile times a TB-vector.
+// TB x TB tile times a TB x KR block of KR right-hand sides.  One pass over the arena serves all
+// KR right-hand sides: the factor bytes are read once per group, not once per vector.
 //
 // A cluster of two CTAs works on one subdomain.  CTA c owns the block rows (strips) I with
-// I % 2 == c: it keeps their entries of y in its shared memory and streams the tiles of the
-// block columns J with J % 2 == c.  For every strip both CTAs form partial sums over their own
-// block columns; the non-owner sends its 64 partial sums into the owner's shared memory
-// (distributed shared memory, mbarrier with cluster-scope release/acquire) and the owner
-// applies the inverted diagonal block.  Tiles stream through a ring of shared-memory stages
-// filled by 1-D bulk TMA copies from one producer warp; eight consumer warps compute.
-// Every wait is bounded (about 2 s); a timeout sets the device status flag and the block
-// finishes without further work.
+// I % 2 == c: it keeps their entries of y (shared memory, or a global slice when they do not
+// fit) and streams the tiles of the block columns J with J % 2 == c, which are exactly its own
+// strips.  For every strip both CTAs form partial sums over their own block columns; the
+// non-owner sends its TB x KR partial sums into the owner's shared memory (distributed shared
+// memory, mbarrier with cluster-scope release/acquire) and the owner applies the inverted
+// diagonal block.  Tiles stream through a ring of shared-memory stages filled by 1-D bulk TMA
+// copies from one producer warp; eight consumer warps compute.  When y lives in global memory,
+// every stage also carries the TB x KR slice y_J its tile multiplies: the producer copies it once
+// the consumers have finalised strip J (a shared counter, with a proxy fence on the writer side),
+// so the consumers never wait on a global load.  Every wait is bounded (about
+// 2 s); a timeout sets the device status flag and the block finishes without further work.
 #pragma once
 
 #include "dev.cuh"
@@ -31,6 +35,9 @@ struct ApplyGeom {
 
 constexpr int APPLY_CONSUMERS = 256;            // 8 warps
 constexpr int APPLY_THREADS = APPLY_CONSUMERS + 32;
+constexpr int APPLY_MAX_KR_F32 = 4;             // right-hand sides per arena pass, FP32 factors
+                                                // (9 warps leave 168 registers a thread; 8 spills)
+constexpr int APPLY_MAX_KR_F64 = 2;             // FP64 factors (register budget)
 
 __device__ __forceinline__ void z_store(cplx* z, double re, double im) { *z = {re, im}; }
 __device__ __forceinline__ void z_store(CT<float>* z, double re, double im) { *z = {(float)re, (float)im}; }
@@ -45,45 +52,85 @@ __device__ __forceinline__ void z_add(CT<float>* z, double re, double im) {
 
 template <typename R> __host__ __device__ constexpr uint32_t tile_bytes() { return (uint32_t)(2 * TB * TB * sizeof(R)); }
 
-// Shared-memory layout of one CTA (dynamic part), given the ring depth and the number of
-// owned strips kept in shared memory (0 when y lives in global memory).
-template <typename R>
+// Two adjacent plane entries as one vector load.
+__device__ __forceinline__ void ld_pair(const float* p, float& a, float& b) {
+  const float2 t = *reinterpret_cast<const float2*>(p);
+  a = t.x; b = t.y;
+}
+__device__ __forceinline__ void ld_pair(const double* p, double& a, double& b) {
+  const double2 t = *reinterpret_cast<const double2*>(p);
+  a = t.x; b = t.y;
+}
+
+// Two adjacent complex entries (16 B for FP32, 32 B for FP64) as vector accesses.
+__device__ __forceinline__ void ld_cpair(const CT<float>* p, CT<float>& a, CT<float>& b) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  a = {t.x, t.y}; b = {t.z, t.w};
+}
+__device__ __forceinline__ void ld_cpair(const CT<double>* p, CT<double>& a, CT<double>& b) {
+  const double2 t0 = reinterpret_cast<const double2*>(p)[0], t1 = reinterpret_cast<const double2*>(p)[1];
+  a = {t0.x, t0.y}; b = {t1.x, t1.y};
+}
+__device__ __forceinline__ void st_cpair(CT<float>* p, CT<float> a, CT<float> b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.re, a.im, b.re, b.im);
+}
+__device__ __forceinline__ void st_cpair(CT<double>* p, CT<double> a, CT<double> b) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a.re, a.im);
+  reinterpret_cast<double2*>(p)[1] = make_double2(b.re, b.im);
+}
+
+// Shared-memory layout of one CTA (dynamic part), given the ring depth, the number of
+// right-hand sides per pass and the number of owned strips kept in shared memory (0 when y
+// lives in global memory).  All TB x KR blocks are stored [KR][TB] (one 64-entry column per
+// right-hand side), so a lane's pair of rows is contiguous for every right-hand side.
+template <typename R, int KR>
 struct ApplySmem {
-  static __host__ __device__ size_t ring_off() { return 0; }
-  static __host__ __device__ size_t bar_off(int S) { return (size_t)S * tile_bytes<R>(); }
-  static __host__ __device__ size_t recv_off(int S) { return bar_off(S) + (2 * S + 2) * 8; }
-  static __host__ __device__ size_t red_off(int S) { return recv_off(S) + 2 * TB * sizeof(CT<R>); }
-  static __host__ __device__ size_t rvec_off(int S) { return red_off(S) + 8 * TB * sizeof(CT<R>); }
-  static __host__ __device__ size_t y_off(int S) { return rvec_off(S) + TB * sizeof(CT<R>); }
-  static __host__ __device__ size_t total(int S, int64_t ystrips) {
-    return y_off(S) + (size_t)ystrips * TB * sizeof(CT<R>);
-  }
+  static constexpr size_t C = sizeof(CT<R>);
+  static constexpr uint32_t YB = TB * KR * sizeof(CT<R>);  // y slice staged beside a tile
+  // ystrips > 0: y resident in shared memory; 0: y in global memory, staged through the ring
+  static __host__ __device__ uint32_t slot(int64_t ystrips) { return tile_bytes<R>() + (ystrips ? 0u : YB); }
+  static __host__ __device__ size_t bar_off(int S, int64_t ys) { return (size_t)S * slot(ys); }
+  static __host__ __device__ size_t recv_off(int S, int64_t ys) { return bar_off(S, ys) + (size_t)(2 * S + 2) * 8; }
+  static __host__ __device__ size_t part_off(int S, int64_t ys) { return recv_off(S, ys) + 2 * TB * KR * C; }
+  static __host__ __device__ size_t red_off(int S, int64_t ys) { return part_off(S, ys) + TB * KR * C; }
+  static __host__ __device__ size_t rvec_off(int S, int64_t ys) { return red_off(S, ys) + 8 * TB * KR * C; }
+  static __host__ __device__ size_t y_off(int S, int64_t ys) { return rvec_off(S, ys) + TB * KR * C; }
+  static __host__ __device__ size_t total(int S, int64_t ys) { return y_off(S, ys) + (size_t)ys * TB * KR * C; }
 };
 
-// Strip sequence helpers: the tiles CTA c streams for strip I (forward: J < I, backward: J > I,
-// J % 2 == c), followed by the strip's inverted diagonal block when c owns the strip.
-template <typename R, typename ZT>
+// v and z are [N][vs] / [N][zs] complex arrays; this pass handles right-hand sides off .. off+nr-1
+// (nr <= KR; the unused lanes of the last group carry zeros and are not stored).
+template <typename R, typename ZT, int KR>
 __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict__ v, int64_t vs,
-                              ZT* __restrict__ z, int64_t zs, int64_t off, CT<R>* yglob) {
+                              ZT* __restrict__ z, int64_t zs, int64_t off, int nr, CT<R>* yglob) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
+  using Sm = ApplySmem<R, KR>;
   const int S = a.stages;
-  unsigned char* ring = smem_raw + ApplySmem<R>::ring_off();
-  uint64_t* full = (uint64_t*)(smem_raw + ApplySmem<R>::bar_off(S));
+  const bool ysm = yglob == nullptr;
+  const int64_t ys = ysm ? 1 : 0;                           // layout selector (see ApplySmem)
+  const uint32_t SLOT = Sm::slot(ys);
+  unsigned char* ring = smem_raw;
+  uint64_t* full = (uint64_t*)(smem_raw + Sm::bar_off(S, ys));
   uint64_t* empty = full + S;
-  uint64_t* msg = empty + S;                                     // [2]
-  CT<R>* recv = (CT<R>*)(smem_raw + ApplySmem<R>::recv_off(S));  // [2][TB]
-  CT<R>(*red)[TB] = (CT<R>(*)[TB])(smem_raw + ApplySmem<R>::red_off(S));
-  CT<R>* rvec = (CT<R>*)(smem_raw + ApplySmem<R>::rvec_off(S));
+  uint64_t* msg = empty + S;                                // [2]
+  CT<R>* recv = (CT<R>*)(smem_raw + Sm::recv_off(S, ys));   // [2][TB*KR]
+  CT<R>* part = (CT<R>*)(smem_raw + Sm::part_off(S, ys));   // [TB*KR] this CTA's partial sums
+  CT<R>* red = (CT<R>*)(smem_raw + Sm::red_off(S, ys));     // [8][TB*KR] per-warp partial sums
+  CT<R>* rvec = (CT<R>*)(smem_raw + Sm::rvec_off(S, ys));   // [TB*KR]
   __shared__ int abort_flag;
+  __shared__ int ydone;                                     // strips of y finalised (both passes)
   const int c = (int)cluster_rank();
   const int64_t ns = a.ns[s], np = a.np[s], nts = np / TB;
   const int64_t own0 = (nts + 1) / 2;                   // strips owned by CTA 0
-  CT<R>* y = yglob ? yglob + a.np_off[s] + (c ? own0 * TB : 0)
-                   : (CT<R>*)(smem_raw + ApplySmem<R>::y_off(S));
+  const int64_t nown_s = c ? nts - own0 : own0;         // strips owned by this CTA
+  const int64_t nown = nown_s * TB;                     // owned rows
+  CT<R>* y = ysm ? (CT<R>*)(smem_raw + Sm::y_off(S, ys))
+                 : yglob + (a.np_off[s] + (c ? own0 * TB : 0)) * KR;
   const R* F = (const R*)a.arena + a.tile_off[s] * 2 * TILE_PLANE;
   const R* Dinv = (const R*)a.dinv + a.inv_off[s] * 4 * TILE_PLANE;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr uint32_t TBYTES = tile_bytes<R>();
+  constexpr int NV = TB * KR;               // entries of one strip of y
   if (tid == 0) {
     for (int q = 0; q < S; ++q) {
       mbar_init(&full[q], 1);
@@ -92,6 +139,7 @@ __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
     mbar_init(&msg[0], 1);
     mbar_init(&msg[1], 1);
     abort_flag = 0;
+    ydone = 0;
     fence_mbar_init();
   }
   __syncthreads();
@@ -101,22 +149,37 @@ __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
     // ---------------- producer: one lane issues the bulk copies in consumption order
     if (lane == 0) {
       int64_t n = 0;
-      auto issue = [&](const R* src) -> bool {
-        const int slot = (int)(n % S);
-        if (n >= S && !mbar_wait(&empty[slot], (uint32_t)(((n / S) - 1) & 1))) return false;
-        mbar_expect_tx(&full[slot], TBYTES);
-        bulk_g2s(ring + (size_t)slot * TBYTES, src, TBYTES, &full[slot]);
+      int slot = 0;
+      uint32_t phase = 0;  // parity of the ring round of `slot`
+      // ysrc: the y slice for this tile (global y only); need: finalised strips it requires
+      auto issue = [&](const R* src, const CT<R>* ysrc, int64_t need) -> bool {
+        if (n >= S && !mbar_wait(&empty[slot], phase ^ 1u)) return false;
+        unsigned char* dst = ring + (size_t)slot * SLOT;
+        if (ysrc) {
+          if (!wait_counter(&ydone, (int)need)) return false;
+          fence_proxy_async_global();
+          mbar_expect_tx(&full[slot], TBYTES + Sm::YB);
+          bulk_g2s(dst + TBYTES, ysrc, Sm::YB, &full[slot]);
+        } else {
+          mbar_expect_tx(&full[slot], TBYTES);
+        }
+        bulk_g2s(dst, src, TBYTES, &full[slot]);
         ++n;
+        if (++slot == S) { slot = 0; phase ^= 1u; }
         return true;
       };
       bool ok = true;
+      // forward: own strip J = c + 2 jj is the (jj+1)-th finalised
       for (int64_t I = 0; I < nts && ok; ++I) {
-        for (int64_t J = c; J < I && ok; J += 2) ok = issue(F + (I * nts + J) * 2 * TILE_PLANE);
-        if (ok && (I & 1) == c) ok = issue(Dinv + I * 4 * TILE_PLANE);
+        for (int64_t J = c; J < I && ok; J += 2)
+          ok = issue(F + (I * nts + J) * 2 * TILE_PLANE, ysm ? nullptr : y + (J / 2) * NV, J / 2 + 1);
+        if (ok && (I & 1) == c) ok = issue(Dinv + I * 4 * TILE_PLANE, nullptr, 0);
       }
+      // backward: own strip jj is finalised after the forward ones, from the last strip down
       for (int64_t I = nts - 1; I >= 0 && ok; --I) {
-        for (int64_t J = I + 1 + ((I + 1 + c) & 1); J < nts && ok; J += 2) ok = issue(F + (I * nts + J) * 2 * TILE_PLANE);
-        if (ok && (I & 1) == c) ok = issue(Dinv + I * 4 * TILE_PLANE + 2 * TILE_PLANE);
+        for (int64_t J = I + 1 + ((I + 1 + c) & 1); J < nts && ok; J += 2)
+          ok = issue(F + (I * nts + J) * 2 * TILE_PLANE, ysm ? nullptr : y + (J / 2) * NV, 2 * nown_s - J / 2);
+        if (ok && (I & 1) == c) ok = issue(Dinv + I * 4 * TILE_PLANE + 2 * TILE_PLANE, nullptr, 0);
       }
       if (!ok) {
         atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
@@ -128,25 +191,34 @@ __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
   } else {
     // ---------------- consumers
     const uint32_t partner = (uint32_t)(c ^ 1);
-    int64_t n = 0;
+    int slot = 0;
+    uint32_t phase = 0;  // parity of the ring round of `slot`
     int kr = 0, ks = 0;  // messages received / sent
+    int nfin = 0;        // strips finalised by this CTA (thread 0 publishes it in ydone)
     bool ok = true;
-    auto stage = [&](const R*& T) -> bool {
-      const int slot = (int)(n % S);
-      if (!mbar_wait(&full[slot], (uint32_t)((n / S) & 1))) return false;
-      T = (const R*)(ring + (size_t)slot * TBYTES);
+    // waits for the next stage; T: its tile, Y: its y slice (global y) or nullptr
+    auto stage = [&](const R*& T, const CT<R>*& Y) -> bool {
+      if (!mbar_wait(&full[slot], phase)) return false;
+      T = (const R*)(ring + (size_t)slot * SLOT);
+      Y = ysm ? nullptr : (const CT<R>*)(ring + (size_t)slot * SLOT + TBYTES);
       return true;
     };
     auto release = [&]() {
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[(int)(n % S)]);
-      ++n;
+      if (lane == 0) mbar_arrive(&empty[slot]);
+      if (++slot == S) { slot = 0; phase ^= 1u; }
+    };
+    auto publish = [&]() {  // after the closing barrier of an owned strip
+      ++nfin;
+      if (tid == 0) st_release_cta(&ydone, nfin);
     };
     // gather the owned strips: y(local) = P_s R_s v
-    for (int64_t q = tid; q < (c ? nts - own0 : own0) * TB; q += APPLY_CONSUMERS) {
-      const int64_t I = 2 * (q / TB) + c, pos = I * TB + q % TB;
+    for (int64_t q = tid; q < nown * KR; q += APPLY_CONSUMERS) {  // q = (strip, r, row)
+      const int64_t st = q / NV;
+      const int r = (int)((q % NV) / TB), i = (int)(q % TB);
+      const int64_t pos = (2 * st + c) * TB + i;
       const int32_t g = a.gidx[a.np_off[s] + pos];
-      const cplx val = g >= 0 ? v[(int64_t)g * vs + off] : cplx{0.0, 0.0};
+      const cplx val = (g >= 0 && r < nr) ? v[(int64_t)g * vs + off + r] : cplx{0.0, 0.0};
       y[q] = {R(val.re), R(val.im)};
     }
     named_sync(1, APPLY_CONSUMERS);
@@ -156,74 +228,97 @@ __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
         const int64_t I = fwd ? it : nts - 1 - it;
         const bool owner = (I & 1) == c;
         // partial sums over the owned block columns of strip I
-        CT<R> acc[8];
+        CT<R> acc[8][KR];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = {R(0), R(0)};
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+          for (int r = 0; r < KR; ++r) acc[q][r] = {R(0), R(0)};
         const int64_t J0 = fwd ? c : I + 1 + ((I + 1 + c) & 1), J1 = fwd ? I : nts;
         for (int64_t J = J0; J < J1; J += 2) {
           const R* T = nullptr;
-          if (ok) ok = stage(T);
+          const CT<R>* Y = nullptr;
+          if (ok) ok = stage(T, Y);
           if (!ok) continue;  // keep the barrier sequence uniform; no more work after a timeout
-          const CT<R>* yJ = y + (J / 2) * TB;
+          const CT<R>* yJ = ysm ? y + (J / 2) * NV : Y;
           if (fwd) {  // row-major tile: warp rows 8w..8w+7, lane columns 2l, 2l+1
-            const CT<R> y0 = yJ[2 * lane], y1 = yJ[2 * lane + 1];
+            CT<R> y0[KR], y1[KR];
+#pragma unroll
+            for (int r = 0; r < KR; ++r) ld_cpair(yJ + r * TB + 2 * lane, y0[r], y1[r]);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
               const int e = (warp * 8 + q) * TB + 2 * lane;
-              const R r0 = T[e], r1 = T[e + 1], i0 = T[TILE_PLANE + e], i1 = T[TILE_PLANE + e + 1];
-              acc[q].re += r0 * y0.re - i0 * y0.im + r1 * y1.re - i1 * y1.im;
-              acc[q].im += r0 * y0.im + i0 * y0.re + r1 * y1.im + i1 * y1.re;
+              R r0, r1, i0, i1;
+              ld_pair(T + e, r0, r1);
+              ld_pair(T + TILE_PLANE + e, i0, i1);
+#pragma unroll
+              for (int r = 0; r < KR; ++r) {
+                CT<R>& t = acc[q][r];
+                t.re = fma(r0, y0[r].re, t.re); t.re = fma(-i0, y0[r].im, t.re);
+                t.re = fma(r1, y1[r].re, t.re); t.re = fma(-i1, y1[r].im, t.re);
+                t.im = fma(r0, y0[r].im, t.im); t.im = fma(i0, y0[r].re, t.im);
+                t.im = fma(r1, y1[r].im, t.im); t.im = fma(i1, y1[r].re, t.im);
+              }
             }
           } else {  // column-major tile: warp columns 8w..8w+7, lane rows 2l, 2l+1
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
               const int col = warp * 8 + q;
-              const CT<R> yc = yJ[col];
               const int e = col * TB + 2 * lane;
-              const R r0 = T[e], r1 = T[e + 1], i0 = T[TILE_PLANE + e], i1 = T[TILE_PLANE + e + 1];
-              acc[2 * (q & 3)].re += r0 * yc.re - i0 * yc.im;   // rows 2l (even slots) and 2l+1 (odd)
-              acc[2 * (q & 3)].im += r0 * yc.im + i0 * yc.re;
-              acc[2 * (q & 3) + 1].re += r1 * yc.re - i1 * yc.im;
-              acc[2 * (q & 3) + 1].im += r1 * yc.im + i1 * yc.re;
+              R r0, r1, i0, i1;
+              ld_pair(T + e, r0, r1);
+              ld_pair(T + TILE_PLANE + e, i0, i1);
+#pragma unroll
+              for (int r = 0; r < KR; ++r) {
+                const CT<R> yc = yJ[r * TB + col];
+                CT<R>& a0 = acc[2 * (q & 3)][r];      // row 2l
+                CT<R>& a1 = acc[2 * (q & 3) + 1][r];  // row 2l+1
+                a0.re = fma(r0, yc.re, a0.re); a0.re = fma(-i0, yc.im, a0.re);
+                a0.im = fma(r0, yc.im, a0.im); a0.im = fma(i0, yc.re, a0.im);
+                a1.re = fma(r1, yc.re, a1.re); a1.re = fma(-i1, yc.im, a1.re);
+                a1.im = fma(r1, yc.im, a1.im); a1.im = fma(i1, yc.re, a1.im);
+              }
             }
           }
           release();
         }
-        // reduce to 64 partial sums in red[0][*]
+        // reduce to the TB x KR partial sums of this CTA in part[]
         if (fwd) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            for (int o = 16; o > 0; o >>= 1) {
-              acc[q].re += __shfl_down_sync(0xffffffffu, acc[q].re, o);
-              acc[q].im += __shfl_down_sync(0xffffffffu, acc[q].im, o);
+          for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int r = 0; r < KR; ++r) {
+              CT<R> t = acc[q][r];
+              for (int o = 16; o > 0; o >>= 1) {
+                t.re += __shfl_down_sync(0xffffffffu, t.re, o);
+                t.im += __shfl_down_sync(0xffffffffu, t.im, o);
+              }
+              if (lane == 0) part[r * TB + warp * 8 + q] = t;
             }
-            if (lane == 0) red[0][warp * 8 + q] = acc[q];
-          }
           named_sync(1, APPLY_CONSUMERS);
         } else {
-          CT<R> p0 = {R(0), R(0)}, p1 = {R(0), R(0)};
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            p0.re += acc[2 * q].re; p0.im += acc[2 * q].im;
-            p1.re += acc[2 * q + 1].re; p1.im += acc[2 * q + 1].im;
-          }
-          red[warp][2 * lane] = p0;
-          red[warp][2 * lane + 1] = p1;
-          named_sync(1, APPLY_CONSUMERS);
-          if (tid < TB) {
-            CT<R> t = red[0][tid];
-            for (int w = 1; w < 8; ++w) { t.re += red[w][tid].re; t.im += red[w][tid].im; }
-            rvec[tid] = t;
+          for (int r = 0; r < KR; ++r) {
+            CT<R> p0 = {R(0), R(0)}, p1 = {R(0), R(0)};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              p0.re += acc[2 * q][r].re; p0.im += acc[2 * q][r].im;
+              p1.re += acc[2 * q + 1][r].re; p1.im += acc[2 * q + 1][r].im;
+            }
+            st_cpair(red + warp * NV + r * TB + 2 * lane, p0, p1);
           }
           named_sync(1, APPLY_CONSUMERS);
-          if (tid < TB) red[0][tid] = rvec[tid];
+          for (int q = tid; q < NV; q += APPLY_CONSUMERS) {
+            CT<R> t = red[q];
+            for (int w = 1; w < 8; ++w) { t.re += red[w * NV + q].re; t.im += red[w * NV + q].im; }
+            part[q] = t;
+          }
           named_sync(1, APPLY_CONSUMERS);
         }
         if (!owner) {
           // send the partial sums to the owner's receive buffer, then signal it
-          if (tid < TB) {
-            const uint32_t dst = map_to_rank(&recv[(ks & 1) * TB + tid], partner);
-            st_remote(dst, red[0][tid].re, red[0][tid].im);
+          for (int q = tid; q < NV; q += APPLY_CONSUMERS) {
+            const uint32_t dst = map_to_rank(&recv[(ks & 1) * NV + q], partner);
+            st_remote(dst, part[q].re, part[q].im);
           }
           named_sync(1, APPLY_CONSUMERS);
           if (tid == 0) mbar_arrive_remote(map_to_rank(&msg[ks & 1], partner));
@@ -237,60 +332,80 @@ __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
         }
         named_sync(1, APPLY_CONSUMERS);
         if (abort_flag) ok = false;
-        CT<R>* yI = y + (I / 2) * TB;
-        if (tid < TB) {
-          const CT<R> pr = recv[(kr & 1) * TB + tid];
-          rvec[tid] = {yI[tid].re - red[0][tid].re - pr.re, yI[tid].im - red[0][tid].im - pr.im};
+        CT<R>* yI = y + (I / 2) * NV;
+        for (int q = tid; q < NV; q += APPLY_CONSUMERS) {
+          const CT<R> pr = recv[(kr & 1) * NV + q];
+          rvec[q] = {yI[q].re - part[q].re - pr.re, yI[q].im - part[q].im - pr.im};
         }
         ++kr;
         named_sync(1, APPLY_CONSUMERS);
         // y_I = inv(diag block) r
         const R* T = nullptr;
-        if (ok) ok = stage(T);
+        const CT<R>* Y = nullptr;
+        if (ok) ok = stage(T, Y);
         if (!ok) {
           named_sync(1, APPLY_CONSUMERS);
           if (!fwd) named_sync(1, APPLY_CONSUMERS);
+          publish();
           continue;
         }
         if (fwd) {  // Linv, row-major
-          const CT<R> r0v = rvec[2 * lane], r1v = rvec[2 * lane + 1];
+          CT<R> r0v[KR], r1v[KR];
+#pragma unroll
+          for (int r = 0; r < KR; ++r) ld_cpair(rvec + r * TB + 2 * lane, r0v[r], r1v[r]);
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const int e = (warp * 8 + q) * TB + 2 * lane;
-            const R r0 = T[e], r1 = T[e + 1], i0 = T[TILE_PLANE + e], i1 = T[TILE_PLANE + e + 1];
-            CT<R> t = {r0 * r0v.re - i0 * r0v.im + r1 * r1v.re - i1 * r1v.im,
-                       r0 * r0v.im + i0 * r0v.re + r1 * r1v.im + i1 * r1v.re};
-            for (int o = 16; o > 0; o >>= 1) {
-              t.re += __shfl_down_sync(0xffffffffu, t.re, o);
-              t.im += __shfl_down_sync(0xffffffffu, t.im, o);
+            R r0, r1, i0, i1;
+            ld_pair(T + e, r0, r1);
+            ld_pair(T + TILE_PLANE + e, i0, i1);
+#pragma unroll
+            for (int r = 0; r < KR; ++r) {
+              CT<R> t = {r0 * r0v[r].re - i0 * r0v[r].im + r1 * r1v[r].re - i1 * r1v[r].im,
+                         r0 * r0v[r].im + i0 * r0v[r].re + r1 * r1v[r].im + i1 * r1v[r].re};
+              for (int o = 16; o > 0; o >>= 1) {
+                t.re += __shfl_down_sync(0xffffffffu, t.re, o);
+                t.im += __shfl_down_sync(0xffffffffu, t.im, o);
+              }
+              if (lane == 0) yI[r * TB + warp * 8 + q] = t;
             }
-            if (lane == 0) yI[warp * 8 + q] = t;
           }
           release();
         } else {  // Uinv, column-major
-          CT<R> p0 = {R(0), R(0)}, p1 = {R(0), R(0)};
+          CT<R> p0[KR], p1[KR];
+#pragma unroll
+          for (int r = 0; r < KR; ++r) p0[r] = p1[r] = {R(0), R(0)};
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const int col = warp * 8 + q;
-            const CT<R> rc = rvec[col];
             const int e = col * TB + 2 * lane;
-            const R r0 = T[e], r1 = T[e + 1], i0 = T[TILE_PLANE + e], i1 = T[TILE_PLANE + e + 1];
-            p0.re += r0 * rc.re - i0 * rc.im;
-            p0.im += r0 * rc.im + i0 * rc.re;
-            p1.re += r1 * rc.re - i1 * rc.im;
-            p1.im += r1 * rc.im + i1 * rc.re;
+            R r0, r1, i0, i1;
+            ld_pair(T + e, r0, r1);
+            ld_pair(T + TILE_PLANE + e, i0, i1);
+#pragma unroll
+            for (int r = 0; r < KR; ++r) {
+              const CT<R> rc = rvec[r * TB + col];
+              p0[r].re += r0 * rc.re - i0 * rc.im;
+              p0[r].im += r0 * rc.im + i0 * rc.re;
+              p1[r].re += r1 * rc.re - i1 * rc.im;
+              p1[r].im += r1 * rc.im + i1 * rc.re;
+            }
           }
           release();
-          red[warp][2 * lane] = p0;
-          red[warp][2 * lane + 1] = p1;
+#pragma unroll
+          for (int r = 0; r < KR; ++r) {
+            st_cpair(red + warp * NV + r * TB + 2 * lane, p0[r], p1[r]);
+          }
           named_sync(1, APPLY_CONSUMERS);
-          if (tid < TB) {
-            CT<R> t = red[0][tid];
-            for (int w = 1; w < 8; ++w) { t.re += red[w][tid].re; t.im += red[w][tid].im; }
-            yI[tid] = t;
+          for (int q = tid; q < NV; q += APPLY_CONSUMERS) {
+            CT<R> t = red[q];
+            for (int w = 1; w < 8; ++w) { t.re += red[w * NV + q].re; t.im += red[w * NV + q].im; }
+            yI[q] = t;
           }
         }
+        if (!ysm) fence_proxy_async_global();  // y_I is read next by bulk copies
         named_sync(1, APPLY_CONSUMERS);
+        publish();
       }
     }
     if (!ok) {
@@ -302,11 +417,13 @@ __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
       // scatter the owned strips with the partition of unity
       const int32_t* Ns = a.sub_dofs + a.ns_off[s];
       const uint8_t* Dp = a.pou + a.ns_off[s];
-      for (int64_t q = tid; q < (c ? nts - own0 : own0) * TB; q += APPLY_CONSUMERS) {
-        const int64_t pos = (2 * (q / TB) + c) * TB + q % TB;
-        if (pos >= ns) continue;
+      for (int64_t q = tid; q < nown * KR; q += APPLY_CONSUMERS) {
+        const int64_t st = q / NV;
+        const int r = (int)((q % NV) / TB), i = (int)(q % TB);
+        const int64_t pos = (2 * st + c) * TB + i;
+        if (pos >= ns || r >= nr) continue;
         const CT<R> val = y[q];
-        ZT* dst = z + (int64_t)Ns[pos] * zs + off;
+        ZT* dst = z + (int64_t)Ns[pos] * zs + off + r;
         if (a.weights == ORAS_WEIGHTS_POU) {
           if (Dp[pos]) z_store(dst, (double)val.re, (double)val.im);
         } else {

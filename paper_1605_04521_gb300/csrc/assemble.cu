@@ -435,7 +435,7 @@ int launch_global_rows(const oras_handle* h, double k0) {
   RowArgs A = row_args(h, k0);
   size_t smem = (size_t)ROW_WARPS * m.max_row_nnz * sizeof(cplx);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_global_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem((const void*)k_global_rows);
   int64_t blocks = (m.ndof + ROW_WARPS - 1) / ROW_WARPS;
   k_global_rows<<<(unsigned)blocks, ROW_WARPS * 32, smem, h->dev.stream>>>(A, m.ndof, m.max_row_nnz,
                                                                           h->dev.vals);
@@ -452,7 +452,7 @@ static int launch_local_rows_t(const oras_handle* h, double k0) {
   for (int s = 0; s < m.nsub; ++s) total += m.sub_np[s];
   size_t smem = (size_t)ROW_WARPS * m.max_row_nnz * sizeof(cplx);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_local_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem((const void*)k_local_rows<R>);
   int64_t blocks = (total + ROW_WARPS - 1) / ROW_WARPS;
   k_local_rows<R><<<(unsigned)blocks, ROW_WARPS * 32, smem, d.stream>>>(
       A, m.nsub, total, d.sub_np_off, d.sub_ns, d.sub_np, d.sub_ns_off, d.sub_tile_off, d.sub_dofs,

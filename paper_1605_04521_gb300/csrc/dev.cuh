@@ -111,6 +111,27 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, bool clu
   }
   return false;
 }
+// A counter in shared memory written by one thread and polled by another of the same CTA.
+__device__ __forceinline__ void st_release_cta(int* p, int v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_cta(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+// Bounded wait until *p >= need (about 2 s), false on timeout.
+__device__ __forceinline__ bool wait_counter(const int* p, int need) {
+  if (ld_acquire_cta(p) >= need) return true;
+  const uint64_t t0 = globaltimer();
+  for (long long it = 0; it < ORAS_SPIN_LIMIT; ++it) {
+    if (ld_acquire_cta(p) >= need) return true;
+    if ((it & 255) == 0 && globaltimer() - t0 > 2000000000ull) return false;
+  }
+  return false;
+}
+// Orders this thread's generic-proxy global writes before later async-proxy (bulk copy) reads.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 // 1-D bulk copy global -> shared, completion counted on an mbarrier of this CTA.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"

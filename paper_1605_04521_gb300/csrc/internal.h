@@ -2,7 +2,10 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
+#include <set>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -15,6 +18,7 @@ constexpr int TB = 64;            // tile order of the local-factor arena (TB x 
 constexpr int MAX_NFL = 15;       // face-local DOFs r(r+2) for r <= 3
 constexpr int MAX_NL = 45;        // tet-local DOFs for r <= 3
 constexpr int MAX_RHS = 64;
+constexpr int PINNED_SCRATCH_DOUBLES = 4096;
 
 struct cplx { double re, im; };
 
@@ -155,7 +159,7 @@ struct Device {
   size_t ybuf_bytes = 0;
   cplx* io = nullptr;                           // staging for host I/O [N][k] col-major
   size_t io_elems = 0;
-  double* host_pinned = nullptr;                // small pinned host scalars
+  double* host_pinned = nullptr;                // small pinned host scalars (per host thread)
 };
 
 // ------------------------------------------------------------------ instrumentation
@@ -165,6 +169,25 @@ enum KClass { KC_ELEMENT = 0, KC_GLOBAL_ROWS, KC_LOCAL_ROWS, KC_LU_TOURNAMENT, K
 int prof_begin(const oras_handle* h);                 // -1 when timing is off
 void prof_end(const oras_handle* h, int cls, int begin, int launches);
 void count_launches(int n);                           // process-wide launch counter
+
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in maximum, once per
+// (device, kernel).  A fixed maximum (instead of the size of the next launch) keeps launches of
+// the same kernel from different host threads from lowering each other's limit.
+inline void allow_max_smem(const void* fn) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({dev, fn})) return;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, fn);
+  if (optin > (int)fa.sharedSizeBytes &&
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes) == cudaSuccess)
+    done.insert({dev, fn});
+}
 
 }  // namespace oras
 

@@ -768,12 +768,12 @@ static int lu_run(oras_handle* h) {
   size_t smem_s = (size_t)2 * TB * TB * sizeof(CT<R>);
   size_t smem_r = (size_t)2 * TB * PS * sizeof(CT<R>);
   size_t smem_u = (size_t)2 * TB * TB * sizeof(CT<R>);
-  cudaFuncSetAttribute(k_lu_tournament<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
-  cudaFuncSetAttribute(k_lu_swap<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
-  cudaFuncSetAttribute(k_lu_trsm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
-  cudaFuncSetAttribute(k_lu_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_u);
+  allow_max_smem((const void*)k_lu_tournament<R>);
+  allow_max_smem((const void*)k_lu_swap<R>);
+  allow_max_smem((const void*)k_lu_trsm<R>);
+  allow_max_smem((const void*)k_lu_update<R>);
   const size_t smem_i = (size_t)3 * TB * PS * sizeof(CT<R>);
-  cudaFuncSetAttribute(k_lu_step_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_i);
+  allow_max_smem((const void*)k_lu_step_inv<R>);
   const bool tc = sizeof(R) == 4 && h->opt.lu_engine == ORAS_LU_AUTO && tc_update_available(h);
   auto update = [&](const UpdArgs& u) {
     if (tc) {
@@ -834,7 +834,7 @@ static int lu_run(oras_handle* h) {
   k_gidx<<<(unsigned)((total + 255) / 256), 256, 0, d.stream>>>(total, d.perm, d.sub_np_off, d.sub_ns,
                                                               d.sub_ns_off, d.sub_dofs, m.nsub, d.gidx);
   {
-    cudaFuncSetAttribute(k_lu_diag_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_i);
+    allow_max_smem((const void*)k_lu_diag_inv<R>);
     int pb = prof_begin(h);
     k_lu_diag_inv<R><<<dim3(max_nts, m.nsub), 2 * TB, smem_i, d.stream>>>(a, d.arena, d.dinv, d.sub_inv_off);
     prof_end(h, KC_LU_TRSM, pb, 1);

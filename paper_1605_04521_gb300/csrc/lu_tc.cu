@@ -454,7 +454,7 @@ int launch_trsm_tc(oras_handle* h, int k, int max_nts) {
   a.k = k;
   a.status = d.status;
   const size_t smem = (size_t)2 * TRSM_CHUNK_BYTES + 1024;
-  cudaFuncSetAttribute(k_lu_trsm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_max_smem((const void*)k_lu_trsm_tc);
   k_lu_trsm_tc<<<dim3((unsigned)blocks, m.nsub), TC_THREADS, smem, d.stream>>>(map, a);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -482,7 +482,7 @@ int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts) {
   a.u = u;
   a.status = d.status;
   const size_t smem = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
-  cudaFuncSetAttribute(k_lu_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_max_smem((const void*)k_lu_update_tc);
   int pb = prof_begin(h);
   k_lu_update_tc<<<dim3((unsigned)blocks, m.nsub), TC_THREADS, smem, d.stream>>>(map, a);
   prof_end(h, KC_LU_UPDATE, pb, 1);

@@ -24,7 +24,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(APPLY_THREADS)
     k_apply_noalloc(ApplyGeom a, int64_t n, int k, void* scratch, const cplx* __restrict__ v,
                     cplx* __restrict__ z) {
   for (int r = 0; r < k; ++r)  // columns one after the other: the scratch slices are reused
-    apply_cluster<R, cplx>(a, blockIdx.x / 2, v, 1, z, 1, (int64_t)r * n, (CT<R>*)scratch);
+    apply_cluster<R, cplx, 1>(a, blockIdx.x / 2, v, 1, z, 1, (int64_t)r * n, 1, (CT<R>*)scratch);
 }
 
 ApplyGeom apply_geom(const oras_handle* h);
@@ -82,11 +82,11 @@ extern "C" int oras_precond_noalloc(oras_handle* h, const oras_complex* v, oras_
     if (e != cudaSuccess) { h->err = std::string("oras_precond_noalloc: ") + cudaGetErrorString(e); return ORAS_ERR_CUDA; }
   }
   if (d.factor_bits == 64) {
-    cudaFuncSetAttribute(k_apply_noalloc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem((const void*)k_apply_noalloc<double>);
     k_apply_noalloc<double><<<2 * m.nsub, APPLY_THREADS, smem, d.stream>>>(a, m.ndof, k, scratch, (const cplx*)v,
                                                                            (cplx*)z);
   } else {
-    cudaFuncSetAttribute(k_apply_noalloc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem((const void*)k_apply_noalloc<float>);
     k_apply_noalloc<float><<<2 * m.nsub, APPLY_THREADS, smem, d.stream>>>(a, m.ndof, k, scratch, (const cplx*)v,
                                                                          (cplx*)z);
   }
