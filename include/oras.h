@@ -48,6 +48,7 @@ typedef struct oras_handle oras_handle;
 enum {
   ORAS_OK = 0,
   ORAS_NOT_CONVERGED = 1,        /* x holds the best iterate of the last cycle           */
+  ORAS_PENDING = 2,              /* serving: the request has not finished yet            */
   ORAS_ERR_INVALID_ARG = -1,
   ORAS_ERR_BAD_MESH = -2,        /* index out of range, repeated vertex, zero volume     */
   ORAS_ERR_OUT_OF_MEMORY = -3,
@@ -219,6 +220,91 @@ int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t
  * GPU (other streams, other threads) race on the array.  Nothing is allocated or freed.
  * Errors: STATE (no oras_factor yet), INVALID_ARG, CUDA. */
 int oras_precond_noalloc(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k);
+
+/* Device bytes that oras_factor followed by an oras_solve of k right-hand sides allocate for
+ * this handle (factor arena, inverted diagonal blocks, A, element matrices, Krylov basis of
+ * restart+1 FP64 and restart FP32/FP64 vectors per right-hand side, staging), including the
+ * allocator's rounding.  Host-only: valid right after oras_create.  Errors: INVALID_ARG. */
+int oras_footprint(const oras_handle* h, int32_t k, int64_t* bytes);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of solve requests on one GPU (the imaging loop of Sec. 6 needs one
+ * Maxwell solve per antenna and per permittivity update).  Requests of different meshes,
+ * degrees and right-hand-side counts are accepted at any time.  Host threads run the mesh
+ * set-up of each request (as oras_create), which fixes its device footprint (oras_footprint);
+ * the oldest planned request is admitted as soon as a worker slot is free and its footprint
+ * fits in the HBM budget beside the requests already on the GPU.  Each admitted request runs
+ * assembly, batched LU and FGMRES on its slot's own CUDA stream, so the work of concurrent
+ * requests overlaps on the device; its factors and Krylov basis stay resident until it
+ * finishes.  Every result equals what oras_setup + oras_solve give for that request alone.
+ * The paper has no serving interface; this is the library's. */
+typedef struct oras_server oras_server;
+
+typedef struct {
+  int64_t hbm_budget;         /* device bytes the admitted requests may hold together;     */
+                              /*   0: 90% of the device's free memory at creation          */
+  int32_t device;             /* CUDA device ordinal [0]                                   */
+  int32_t max_active;         /* requests on the GPU at once: worker threads, one CUDA     */
+                              /*   stream each [4], at most 64                             */
+  int32_t planners;           /* host threads for the set-up of queued requests [2]        */
+  int32_t reserved[5];
+} oras_server_config;
+
+/* Life of one request; times in seconds since oras_server_create. */
+typedef struct {
+  double submit_s;            /* oras_submit returned                                      */
+  double planned_s;           /* host set-up done, footprint known                         */
+  double admitted_s;          /* admitted onto the GPU (0 if never)                        */
+  double done_s;              /* result ready                                              */
+  int64_t footprint;          /* device bytes reserved for it                              */
+  int64_t ndof;               /* N of its problem (0 if set-up failed)                     */
+  int32_t k;                  /* right-hand sides                                          */
+  int32_t status;             /* its return code; ORAS_PENDING while unfinished            */
+} oras_ticket;
+
+typedef struct {
+  int64_t hbm_budget, hbm_in_use, hbm_peak;   /* bytes                                     */
+  int32_t queued;             /* submitted, not yet admitted                               */
+  int32_t active;             /* on the GPU now                                            */
+  int32_t peak_active;        /* most requests on the GPU at once so far                   */
+  int32_t completed;          /* finished (any status but REJECTED)                        */
+  int32_t rejected;           /* footprint above the whole budget                          */
+  int32_t pad;
+} oras_server_counters;
+
+/* Starts the planner and worker threads (no GPU work until a request is admitted).
+ * cfg may be NULL (defaults).  Errors: INVALID_ARG, CUDA (budget 0 and no device),
+ * OUT_OF_MEMORY. */
+int oras_server_create(const oras_server_config* cfg, oras_server** out);
+/* Queues one solve: problem p and options o (NULL: defaults) as for oras_setup, and k
+ * right-hand sides given either as rhs (host, n x k column-major, n = N of the problem) or
+ * as dipoles (host, [k][6]: position x0 and direction of each point dipole, as
+ * oras_rhs_dipole) -- exactly one of the two.  All inputs are copied before the call returns.
+ * Returns a ticket > 0, or INVALID_ARG / OUT_OF_MEMORY / STATE (server shutting down).
+ * Problems found later (bad mesh, n != N, footprint above the budget: REJECTED) are the
+ * ticket's status. */
+int64_t oras_submit(oras_server* srv, const oras_problem* p, const oras_options* o, const oras_complex* rhs,
+                    int64_t n, const double* dipoles, int32_t k, double tol);
+/* Waits up to timeout_ms (< 0: no limit) for the ticket.  Returns ORAS_PENDING if it is still
+ * running (call again), else the request's status (as oras_solve's, or the error that stopped
+ * it), copies the solution into x (host, n x k column-major, n = N; NULL: discard) and the
+ * per-column outcome into info ([k] or NULL), and retires the ticket (oras_ticket_info keeps
+ * its record).  Errors of the call itself: INVALID_ARG (unknown ticket; n != N for a solved
+ * request, ticket kept), STATE (ticket already retired). */
+int oras_wait(oras_server* srv, int64_t ticket, oras_complex* x, int64_t n, oras_info* info, int32_t timeout_ms);
+/* Waits up to timeout_ms (< 0: no limit) until the ticket has finished, without retiring it
+ * (then oras_ticket_info gives N and the status).  Returns ORAS_OK (finished or retired),
+ * ORAS_PENDING, or INVALID_ARG (unknown ticket). */
+int oras_ticket_wait(oras_server* srv, int64_t ticket, int32_t timeout_ms);
+/* Record of a ticket, pending or retired.  Errors: INVALID_ARG (unknown ticket). */
+int oras_ticket_info(oras_server* srv, int64_t ticket, oras_ticket* out);
+/* Message of a failed ticket ("" if none); ticket <= 0: the last failing server call. */
+const char* oras_server_error(oras_server* srv, int64_t ticket);
+/* Budget, occupancy and counters. */
+int oras_server_stats(oras_server* srv, oras_server_counters* out);
+/* Cancels queued requests (status STATE), lets running ones finish, joins the threads and
+ * frees everything, including tickets nobody collected. */
+void oras_server_destroy(oras_server* srv);
 
 /* ---------------------------------------------------------------- instrumentation */
 

@@ -245,6 +245,64 @@ static int alloc_factor_space(oras_handle* h, int bits) {
 
 
 
+// Device bytes that oras_factor plus an oras_solve of k right-hand sides allocate for this
+// handle (the sizes of upload, alloc_factor_space, ensure_ybuf, ensure_ws and ensure_io), plus the
+// stream-ordered pool's rounding (2 MiB per allocation).
+int64_t footprint_bytes(const oras_handle* h, int k) {
+  const auto& m = h->mesh;
+  const auto& T = h->tab;
+  const int bits = h->opt.factor_bits;
+  const size_t el = bits == 64 ? 16 : 8;
+  const int64_t N = m.ndof, mm = std::max(h->opt.restart, 1);
+  auto vb = [](const auto& v) { return (int64_t)(v.size() * sizeof(v[0])); };
+  int64_t total_np = 0, blocks = 0;
+  for (int s = 0; s < m.nsub; ++s) {
+    total_np += m.sub_np[s];
+    blocks += m.sub_np[s] / TB;
+  }
+  int64_t b = 0;
+  int nalloc = 0;
+  auto add = [&](int64_t x) { b += std::max<int64_t>(x, 1); ++nalloc; };
+  // upload
+  for (int64_t x : {vb(m.xyz), vb(m.st), vb(m.dofmap), vb(m.tinc_ptr), vb(m.tinc), vb(m.if_tet0), vb(m.if_lf0),
+                    vb(m.if_tet1), vb(m.if_dofs), vb(m.finc_ptr), vb(m.finc), vb(m.rowptr), vb(m.cols),
+                    vb(m.sub_ns), vb(m.sub_np), vb(m.sub_ns_off), vb(m.sub_tile_off), vb(m.sub_dofs),
+                    vb(m.sub_pou), vb(m.member), (int64_t)(m.nsub + 1) * 8, vb(T.cm), vb(T.ck), vb(T.cs),
+                    (int64_t)T.fl.size() * 4, vb(T.tc), (int64_t)T.ta.size() * 4, (int64_t)T.tm.size() * 4})
+    add(x);
+  add(m.nt * 16);                                                   // eps
+  add(m.nt * 16);                                                   // mu (when given)
+  add(m.nt * m.nl * m.nl * 16);                                     // element matrices
+  add(std::max<int64_t>(1, m.nif) * m.nfl * m.nfl * 8);            // face matrices
+  add((int64_t)m.cols.size() * 16);                                 // values of A
+  add(total_np * 4);                                                // perm
+  add(total_np * 4);                                                // gidx
+  add(8 * 4);                                                       // status
+  // factor space
+  const int slots = 2 * lu_max_chunks(m.max_np, bits) + 16;
+  add((m.arena_tiles + 2 * m.nsub) * TB * TB * (int64_t)el);
+  add((int64_t)m.nsub * slots * TB * 4);
+  add((int64_t)m.nsub * slots * 4);
+  add((int64_t)m.nsub * (2 * TB * 2 + 1) * 4);
+  add((int64_t)m.nsub * TB * TB * (int64_t)el);
+  add((int64_t)(m.nsub + 1) * 8);
+  add(blocks * 2 * TB * TB * (int64_t)el);                          // inverted diagonal blocks
+  add((int64_t)apply_yglob_bytes_for(h, std::max(k, 1)));
+  // Krylov workspace and I/O staging
+  const int64_t nk = N * std::max(k, 1), kk = std::max(k, 1);
+  add(nk * (mm + 1) * 16);                                          // V
+  add(nk * mm * (bits == 64 ? 16 : 8));                             // Z
+  for (int q = 0; q < 4; ++q) add(nk * 16);                         // w, xk, bk, tmp
+  add(kk * (mm + 1) * mm * 16);                                     // H
+  add(kk * mm * 8);
+  add(kk * mm * 16);
+  add(kk * (mm + 1) * 16);
+  add((int64_t)2 * red_blocks() * kk * 2 * 8);
+  add((kk * 8 + kk * mm * 2 + 64) * 8);
+  add(nk * 16);                                                     // io
+  return b + (int64_t)nalloc * (2 << 20);
+}
+
 static int sync_status(oras_handle* h) {
   auto& d = h->dev;
   int32_t st[8];
@@ -401,6 +459,12 @@ void oras_destroy(oras_handle* h) {
     dfree_all(h->dev);
   }
   delete h;
+}
+
+int oras_footprint(const oras_handle* h, int32_t k, int64_t* bytes) {
+  if (!h || !bytes || k < 1 || k > MAX_RHS) return ORAS_ERR_INVALID_ARG;
+  *bytes = footprint_bytes(h, k);
+  return ORAS_OK;
 }
 
 int64_t oras_ndof(const oras_handle* h) { return h ? h->mesh.ndof : -1; }

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "liboras_gb300.so")
 
 ORAS_OK = 0
 ORAS_NOT_CONVERGED = 1
+ORAS_PENDING = 2
 ORAS_ERR_INVALID_ARG = -1
 ORAS_ERR_BAD_MESH = -2
 ORAS_ERR_OUT_OF_MEMORY = -3
@@ -57,6 +58,23 @@ class oras_info(C.Structure):
                 ("pad", C.c_int32), ("relres", C.c_double)]
 
 
+class oras_server_config(C.Structure):
+    _fields_ = [("hbm_budget", C.c_int64), ("device", C.c_int32), ("max_active", C.c_int32),
+                ("planners", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+
+class oras_ticket(C.Structure):
+    _fields_ = [("submit_s", C.c_double), ("planned_s", C.c_double), ("admitted_s", C.c_double),
+                ("done_s", C.c_double), ("footprint", C.c_int64), ("ndof", C.c_int64), ("k", C.c_int32),
+                ("status", C.c_int32)]
+
+
+class oras_server_counters(C.Structure):
+    _fields_ = [("hbm_budget", C.c_int64), ("hbm_in_use", C.c_int64), ("hbm_peak", C.c_int64),
+                ("queued", C.c_int32), ("active", C.c_int32), ("peak_active", C.c_int32),
+                ("completed", C.c_int32), ("rejected", C.c_int32), ("pad", C.c_int32)]
+
+
 EXPORTS = {
     "oras_last_error": (C.c_char_p, [C.c_void_p]),
     "oras_abi_version": (C.c_int32, []),
@@ -88,6 +106,16 @@ EXPORTS = {
     "oras_reset_timings": (C.c_int, [C.c_void_p]),
     "oras_launch_count": (C.c_int64, []),
     "oras_precond_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "oras_footprint": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
+    "oras_server_create": (C.c_int, [C.POINTER(oras_server_config), C.POINTER(C.c_void_p)]),
+    "oras_submit": (C.c_int64, [C.c_void_p, C.POINTER(oras_problem), C.POINTER(oras_options), C.c_void_p,
+                                C.c_int64, C.c_void_p, C.c_int32, C.c_double]),
+    "oras_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.POINTER(oras_info), C.c_int32]),
+    "oras_ticket_info": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(oras_ticket)]),
+    "oras_ticket_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32]),
+    "oras_server_error": (C.c_char_p, [C.c_void_p, C.c_int64]),
+    "oras_server_stats": (C.c_int, [C.c_void_p, C.POINTER(oras_server_counters)]),
+    "oras_server_destroy": (None, [C.c_void_p]),
 }
 
 
@@ -346,3 +374,99 @@ def oras_precond_noalloc(h, v, z, k=1):
     """z = M^{-1} v without any device allocation; v, z: torch CUDA complex128 tensors holding
     N x k column-major data (shape (k, N) contiguous, or (N,) for k = 1)."""
     return _check(h, lib.oras_precond_noalloc(h, _ptr(v), _ptr(z), int(k)))
+
+
+def oras_footprint(h, k=1):
+    """Device bytes oras_factor + an oras_solve of k right-hand sides allocate."""
+    b = C.c_int64()
+    _check(h, lib.oras_footprint(h, int(k), C.byref(b)))
+    return b.value
+
+
+# ------------------------------------------------------------------ serving
+class ServerError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"oras server error {code}: {msg}")
+        self.code = code
+
+
+def _scheck(srv, rc, ticket=0, allow=(ORAS_OK,)):
+    if rc in allow:
+        return rc
+    msg = lib.oras_server_error(srv, ticket)
+    raise ServerError(rc, msg.decode() if msg else "")
+
+
+def oras_server_create(hbm_budget=0, device=0, max_active=4, planners=2):
+    cfg = oras_server_config()
+    cfg.hbm_budget, cfg.device, cfg.max_active, cfg.planners = int(hbm_budget), int(device), int(max_active), int(planners)
+    srv = C.c_void_p()
+    _scheck(None, lib.oras_server_create(C.byref(cfg), C.byref(srv)))
+    return srv
+
+
+def oras_submit(srv, xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part=None, rhs=None, dipoles=None,
+                tol=1e-8, **opts):
+    """Queues one solve; rhs: host (N,) or (N, k) complex, or dipoles: (k, 6) positions and
+    directions.  Returns the ticket."""
+    p, keep = _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part)
+    o = _options(**opts)
+    if rhs is not None:
+        b = np.asfortranarray(np.asarray(rhs, dtype=np.complex128))
+        if b.ndim == 1:
+            b = b.reshape(-1, 1, order="F")
+        n, k = b.shape
+        t = lib.oras_submit(srv, C.byref(p), C.byref(o), _ptr(b), n, None, k, float(tol))
+    else:
+        d = np.ascontiguousarray(dipoles, dtype=np.float64).reshape(-1, 6)
+        t = lib.oras_submit(srv, C.byref(p), C.byref(o), None, 0, _ptr(d), d.shape[0], float(tol))
+    del keep
+    if t < 0:
+        _scheck(srv, int(t))
+    return int(t)
+
+
+def oras_ticket_info(srv, ticket):
+    rec = oras_ticket()
+    _scheck(srv, lib.oras_ticket_info(srv, int(ticket), C.byref(rec)))
+    return {f: getattr(rec, f) for f, _ in oras_ticket._fields_}
+
+
+def oras_ticket_wait(srv, ticket, timeout_ms=-1):
+    return _scheck(srv, lib.oras_ticket_wait(srv, int(ticket), int(timeout_ms)), allow=(ORAS_OK, ORAS_PENDING))
+
+
+def oras_wait(srv, ticket, timeout_ms=-1):
+    """Returns (x, infos, rc): x (N, k) complex (or (N,) for k = 1), None when the request
+    failed; rc is the request's status, ORAS_PENDING (x None) if it is still running.  Raises
+    ServerError for an unknown or already collected ticket."""
+    if oras_ticket_wait(srv, ticket, timeout_ms) == ORAS_PENDING:
+        return None, None, ORAS_PENDING
+    rec = oras_ticket_info(srv, ticket)
+    n, k = rec["ndof"], rec["k"]
+    x = np.empty((max(n, 1), k), dtype=np.complex128, order="F")
+    info = (oras_info * k)()
+    live = rec["status"] != ORAS_PENDING
+    rc = lib.oras_wait(srv, int(ticket), _ptr(x), n, info, 0)
+    if rc == ORAS_ERR_STATE or (rc == ORAS_ERR_INVALID_ARG and not live):
+        _scheck(srv, rc)
+    if rc not in (ORAS_OK, ORAS_NOT_CONVERGED):
+        return None, None, rc
+    infos = [dict(iterations=i.iterations, restarts=i.restarts, converged=bool(i.converged),
+                  relres=i.relres) for i in info]
+    return (x if k > 1 else x[:, 0]), infos, rc
+
+
+def oras_server_error(srv, ticket=0):
+    msg = lib.oras_server_error(srv, int(ticket))
+    return msg.decode() if msg else ""
+
+
+def oras_server_stats(srv):
+    c = oras_server_counters()
+    _scheck(srv, lib.oras_server_stats(srv, C.byref(c)))
+    return {f: getattr(c, f) for f, _ in oras_server_counters._fields_ if f != "pad"}
+
+
+def oras_server_destroy(srv):
+    lib.oras_server_destroy(srv)
