@@ -55,6 +55,11 @@ def parse():
                          "head8: 8^3 r=2 8 subdomains (1.9 GB arena, for kernel profiles)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--serve-count", type=int, default=12,
+                    help="requests of the serving stream replayed after the main measurement (0: none)")
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-max-iter", type=int, default=60,
+                    help="FGMRES iteration cap per served request (requests above it report not converged)")
     return ap.parse_args()
 
 
@@ -195,7 +200,7 @@ def roofline(timings, upd_flops_per_factor, apply_bytes, factors, hbm, bf16_burs
         peak = bf16_burst * TF32_OVER_BF16
         return dom, {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_lu_update (complex FP32 trailing update)",
+                     "kernel": "k_lu_update_tc (tcgen05 kind::tf32 complex trailing update)",
                      "peak_note": "TF32 dense = measured bf16 burst x nominal tf32/bf16 ratio"}
     if dom == "apply":
         achieved = apply_bytes * launches / (ms / 1e3) / 1e9
@@ -255,6 +260,75 @@ def oracle_estimate(w, iterations, budget_s=20.0):
                        f"{w.nsub} subdomains (n_s {int(smp.min())}-{int(smp.max())}), scaled by sum n_s^3 / "
                        f"sum n_s^2; {iterations} iterations (GPU count) of SpMV + {w.restart // 2} MGS steps"),
             "seconds_per_solve_estimate": per_solve}
+
+
+# ------------------------------------------------------------------ serving replay
+def serving_replay(O, count, slots, device=0, max_iter=60):
+    """Replays the first `count` requests of the seeded serving stream (Poisson arrivals at
+    5/s; grids 8^3-24^3, degree 1-3, 1/8/32 dipole right-hand sides, perturbation radius and
+    permittivity drawn per request) through the serving runtime with `slots` worker slots,
+    then again with one slot (sequential), and reports solves/s and latency percentiles.
+    Meshes and materials are generated before the clock starts; each request's latency runs
+    from its submission (at its arrival time) to its result.  Every request is capped at
+    `max_iter` FGMRES iterations: the degree-3 requests with 256 subdomains converge far more
+    slowly under the zeroth-order impedance transmission condition, and only right-hand sides
+    that reach the tolerance count as solves."""
+    reqs = synth.serving_requests()[:count]
+    prepared = []
+    for w in reqs:
+        xyz, tets = w.mesh()
+        eps, mu = w.materials(xyz, tets)
+        dip = np.concatenate([synth.dipole_ring(w.nrhs), np.tile([0.0, 0.0, 1.0], (w.nrhs, 1))], axis=1)
+        prepared.append((w, xyz, tets, eps, mu, dip))
+
+    def replay(nslots):
+        srv = O.oras_server_create(max_active=nslots, device=device)
+        try:
+            t0 = time.perf_counter()
+            tickets = []
+            for w, xyz, tets, eps, mu, dip in prepared:
+                delay = t0 + w.arrival_s - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append(O.oras_submit(srv, xyz, tets, eps, mu, w.k0, w.r, w.nsub, w.overlap, dipoles=dip,
+                                             tol=w.tol, restart=w.restart, factor_bits=w.factor_bits,
+                                             max_iter=max_iter))
+            outs = []
+            for t, (w, *_rest) in zip(tickets, prepared):
+                x, info, rc = O.oras_wait(srv, t)
+                rec = O.oras_ticket_info(srv, t)
+                outs.append((w, rc, info, rec))
+            wall = time.perf_counter() - t0
+            st = O.oras_server_stats(srv)
+        finally:
+            O.oras_server_destroy(srv)
+        done = [(w, rc, info, rec) for w, rc, info, rec in outs if rc in (O.ORAS_OK, O.ORAS_NOT_CONVERGED)]
+        lat = sorted(rec["done_s"] - rec["submit_s"] for _, _, _, rec in done)
+        solves = sum(sum(1 for i in info if i["converged"]) for _, _, info, _ in done)
+        worst = max((i["relres"] for _, _, info, _ in done for i in info if i["converged"]), default=None)
+        first = min(rec["submit_s"] for _, _, _, rec in outs)
+        last = max(rec["done_s"] for _, _, _, rec in outs)
+
+        def pct(q):
+            return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))] if lat else None
+        return {"slots": nslots, "solves_per_s": solves / (last - first) if last > first else None,
+                "requests_per_s": len(done) / (last - first) if last > first else None,
+                "solves": solves, "requests_completed": len(done),
+                "rejected": sum(1 for _, rc, _, _ in outs if rc == O.ORAS_ERR_REJECTED),
+                "failed": sum(1 for _, rc, _, _ in outs if rc not in (O.ORAS_OK, O.ORAS_NOT_CONVERGED,
+                                                                      O.ORAS_ERR_REJECTED)),
+                "not_converged_requests": sum(1 for _, rc, _, _ in outs if rc == O.ORAS_NOT_CONVERGED),
+                "p50_latency_s": pct(0.5), "p99_latency_s": pct(0.99), "makespan_s": last - first,
+                "wall_s": wall, "peak_active": st["peak_active"], "hbm_peak_gb": st["hbm_peak"] / 1e9,
+                "hbm_budget_gb": st["hbm_budget"] / 1e9, "worst_true_relres": worst}
+
+    mix = replay(slots)
+    seq = replay(1)
+    return {"stream": f"first {count} of the seeded serving stream (Poisson 5/s; n 8-24, r 1-3, k 1/8/32 dipoles, "
+                      "N_sub = 2^ceil(log2(N/2500)), 1 vertex overlap layer, FGMRES(50), FP32 factors, "
+                      f"at most {max_iter} iterations per request)",
+            "requests": [dict(n=w.n, r=w.r, k=w.nrhs, nsub=w.nsub, arrival_s=round(w.arrival_s, 3)) for w, *_ in prepared],
+            "continuous_batching": mix, "sequential_one_slot": seq}
 
 
 # ------------------------------------------------------------------ our arm
@@ -349,6 +423,9 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(time.perf_counter() - e0, world)
     e2e_val = world * e2e_steps / e2e_s
+    serving = None
+    if rank == 0 and args.serve_count > 0:
+        serving = serving_replay(O, args.serve_count, args.serve_slots, device=local, max_iter=args.serve_max_iter)
     out = None
     if rank == 0:
         cpu = None
@@ -372,6 +449,7 @@ def run_ours(args, world, rank, local):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "path": "oras_setup (host mesh + materials) + oras_solve (host rhs -> host x) + oras_destroy"},
             "gpu_launches": int(launches),
+            "serving": serving,
             "clocks": clk,
             "peaks": {"hbm_gbs": hbm, "bf16_tflops": bf16, "source": src},
             "wall_s_timed": wall,
