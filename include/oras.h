@@ -201,6 +201,12 @@ int oras_element_matrices(oras_handle* h, const int32_t* tets, int64_t count, or
 int oras_global_csr(oras_handle* h, int64_t* rowptr, int32_t* cols, oras_complex* vals);
 /* y = A x for k columns (N x k column-major, `mem`). */
 int oras_matvec(oras_handle* h, const oras_complex* x, oras_complex* y, int32_t k, int32_t mem);
+/* y = A x for k columns of complex FP32 x (N x k column-major pairs of floats, `mem`) into
+ * complex FP64 y (N x k column-major): the product FGMRES forms with the preconditioned vectors
+ * of FP32 factors.  Computed on the FP32 pipes with error-free transformations (A split into
+ * FP32 hi + lo parts, exact product and sum errors carried), about 2^-48 relative error per
+ * entry.  Requires oras_factor.  Errors: INVALID_ARG, STATE, CUDA. */
+int oras_matvec_c64(oras_handle* h, const void* x, oras_complex* y, int32_t k, int32_t mem);
 /* z = M^{-1}_ORAS v for k columns (N x k column-major, `mem`), Sec. 4. */
 int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k, int32_t mem);
 

@@ -27,6 +27,8 @@ size_t apply_yglob_bytes_for(const oras_handle* h, int k);
 int apply_passes(const oras_handle* h, int k);
 void launch_spmv_f64(const oras_handle* h, const cplx* x, cplx* y, int k);
 void launch_spmv_f32(const oras_handle* h, const void* x, cplx* y, int k);
+void launch_split_vals(const oras_handle* h);
+void launch_to_internal_c64(const oras_handle* h, int k, const void* src, void* dst);
 void launch_dot(const oras_handle* h, const cplx* a, const cplx* b, cplx* partials, int k);
 void launch_mgs_step(const oras_handle* h, int k, int m, int i, int j, const cplx* Vi, const cplx* Vn, cplx* w,
                      const cplx* pin, cplx* pout, cplx* H);
@@ -127,7 +129,7 @@ static void dfree_all(Device& d) {
   void* ptrs[] = {d.xyz, d.st, d.dofmap, d.tinc_ptr, d.tinc, d.if_tet0, d.if_lf0, d.if_tet1, d.if_dofs,
                   d.finc_ptr, d.finc, d.rowptr, d.cols, d.sub_ns, d.sub_np, d.sub_ns_off, d.sub_tile_off,
                   d.sub_dofs, d.sub_pou, d.member, d.cm, d.ck, d.cs, d.fl, d.tc, d.ta, d.tm, d.eps, d.mu,
-                  d.elem, d.fmat, d.vals, d.arena, d.perm, d.gidx, d.sub_np_off, d.lu_cand, d.lu_cnt,
+                  d.elem, d.fmat, d.vals, d.vals_df, d.arena, d.perm, d.gidx, d.sub_np_off, d.lu_cand, d.lu_cnt,
                   d.lu_ipiv, d.lu_diag, d.dinv, d.sub_inv_off, d.status, d.V, d.Zf, d.Zd, d.w, d.xk, d.bk, d.tmp, d.H, d.gcs, d.gsn,
                   d.g, d.red, d.scal, d.ybuf, d.io};
   for (void* p : ptrs)
@@ -185,6 +187,7 @@ static int upload(oras_handle* h) {
   CK(dalloc(d.elem, (size_t)m.nt * m.nl * m.nl));
   CK(dalloc(d.fmat, (size_t)std::max<int64_t>(1, m.nif) * m.nfl * m.nfl));
   CK(dalloc(d.vals, m.cols.size()));
+  CK(dalloc(d.vals_df, m.cols.size()));
   CK(dalloc(d.perm, npoff[m.nsub]));
   CK(dalloc(d.gidx, npoff[m.nsub]));
   CK(dalloc(d.status, 8));
@@ -275,6 +278,7 @@ int64_t footprint_bytes(const oras_handle* h, int k) {
   add(m.nt * m.nl * m.nl * 16);                                     // element matrices
   add(std::max<int64_t>(1, m.nif) * m.nfl * m.nfl * 8);            // face matrices
   add((int64_t)m.cols.size() * 16);                                 // values of A
+  add((int64_t)m.cols.size() * 16);                                 // values of A as FP32 pairs
   add(total_np * 4);                                                // perm
   add(total_np * 4);                                                // gidx
   add(8 * 4);                                                       // status
@@ -423,7 +427,8 @@ int oras_factor(oras_handle* h, const oras_complex* eps_r, const oras_complex* m
   {
     int b = prof_begin(h);
     if (launch_global_rows(h, k0)) CK(cudaGetLastError());
-    prof_end(h, KC_GLOBAL_ROWS, b, 1);
+    launch_split_vals(h);
+    prof_end(h, KC_GLOBAL_ROWS, b, 2);
   }
   {
     int b = prof_begin(h);
@@ -745,6 +750,23 @@ int oras_matvec(oras_handle* h, const oras_complex* x, oras_complex* y, int32_t 
   if (rc) return rc;
   launch_spmv_f64(h, h->dev.bk, h->dev.tmp, k);
   return store_output(h, h->dev.tmp, k, mem, y);
+}
+
+int oras_matvec_c64(oras_handle* h, const void* x, oras_complex* y, int32_t k, int32_t mem) {
+  if (!h || !x || !y || k < 1 || k > MAX_RHS) return ORAS_ERR_INVALID_ARG;
+  if (!h->factored) { h->err = "oras_matvec_c64: call oras_factor first"; return ORAS_ERR_STATE; }
+  int rc = ensure_ws(h, k, h->opt.restart);
+  if (rc) return rc;
+  rc = ensure_io(h, (size_t)h->mesh.ndof * k);
+  if (rc) return rc;
+  auto& d = h->dev;
+  const size_t bytes = (size_t)h->mesh.ndof * k * 2 * sizeof(float);
+  // staging: the first half of io holds the column-major copy, the internal [N][k] copy goes to w
+  CK(cudaMemcpyAsync(d.io, x, bytes, mem == ORAS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     d.stream));
+  launch_to_internal_c64(h, k, d.io, d.w);
+  launch_spmv_f32(h, d.w, d.tmp, k);
+  return store_output(h, d.tmp, k, mem, y);
 }
 
 int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k, int32_t mem) {

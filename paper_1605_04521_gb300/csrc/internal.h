@@ -128,6 +128,7 @@ struct Device {
   cplx* elem = nullptr;                         // [nt][nl][nl]
   double* fmat = nullptr;                       // [nif][nfl][nfl]
   cplx* vals = nullptr;                         // [nnz]
+  float4* vals_df = nullptr;                    // [nnz] A = hi + lo in FP32 pairs (FP32-pipe SpMV)
   void* arena = nullptr;                        // tiles, complex float or double
   size_t arena_bytes = 0;
   int factor_bits = 0;

@@ -47,6 +47,90 @@ __global__ void k_spmv(int64_t n, const int64_t* __restrict__ rowptr, const int3
   }
 }
 
+// ------------------------------------------------------------------ FP32-pipe SpMV, FP64 accuracy
+// GB300 executes FP64 on a narrow pipe (about 1/64 of the FP32 rate), which caps the FP64 CSR
+// SpMV far below the HBM bound.  The Arnoldi SpMV multiplies the FP64 matrix by preconditioned
+// vectors that are exactly FP32 (z = M^-1 v with FP32 factors), so it is done on the FP32 pipes
+// with error-free transformations: A = A_hi + A_lo with A_hi = fl32(A) and A_lo = fl32(A - A_hi)
+// (the same 16 bytes per entry as FP64 complex), each product A_hi x split exactly into
+// p + e by one FMA (two-product), each running sum kept as an unevaluated pair hi + lo with the
+// rounding error of every addition recovered exactly (two-sum, Knuth).  The result carries
+// about 2^-48 relative error per entry, the accuracy class of FP64, and is stored in FP64.
+
+// hi + lo += a * x with a = a_hi + a_lo
+__device__ __forceinline__ void df_mac(float& hi, float& lo, float a_hi, float a_lo, float x) {
+  const float p = a_hi * x;
+  const float ep = fmaf(a_hi, x, -p);           // a_hi * x - p, exactly
+  const float t = hi + p;
+  const float bp = t - hi;
+  const float es = (hi - (t - bp)) + (p - bp);   // hi + p - t, exactly
+  hi = t;
+  lo += (ep + es) + a_lo * x;
+}
+// (h1 + l1) += (h2 + l2)
+__device__ __forceinline__ void df_add(float& h1, float& l1, float h2, float l2) {
+  const float t = h1 + h2;
+  const float bp = t - h1;
+  const float es = (h1 - (t - bp)) + (h2 - bp);
+  h1 = t;
+  l1 += es + l2;
+}
+
+// vals_df[p] = {re_hi, im_hi, re_lo, im_lo}
+__global__ void k_split_vals(int64_t nnz, const cplx* __restrict__ vals, float4* __restrict__ out) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nnz) return;
+  const cplx v = vals[p];
+  const float rh = (float)v.re, ih = (float)v.im;
+  out[p] = make_float4(rh, ih, (float)(v.re - (double)rh), (float)(v.im - (double)ih));
+}
+
+// y = A x with x complex FP32 ([N][k]), y FP64 ([N][k]).  Sixteen lanes per row (two rows per
+// warp); KC right-hand sides per pass (kc <= KC of them live), so the single-vector product keeps
+// few registers and many rows in flight.
+template <int KC>
+__global__ void __launch_bounds__(256) k_spmv_df(int64_t n, const int64_t* __restrict__ rowptr,
+                                                 const int32_t* __restrict__ cols, const float4* __restrict__ vals,
+                                                 const CT<float>* __restrict__ x, cplx* __restrict__ y, int k,
+                                                 int r0, int kc) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int sl = threadIdx.x & 15;
+  const bool live = row < n;
+  float rh[KC], rl[KC], ih[KC], il[KC];
+#pragma unroll
+  for (int q = 0; q < KC; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.0f;
+  if (live) {
+    const int64_t p1 = rowptr[row + 1];
+#pragma unroll 2
+    for (int64_t p = rowptr[row] + sl; p < p1; p += 16) {
+      const float4 a = vals[p];
+      const int64_t c = cols[p];
+      const CT<float>* xc = x + c * k + r0;
+#pragma unroll
+      for (int q = 0; q < KC; ++q)
+        if (q < kc) {
+          const CT<float> xv = xc[q];
+          df_mac(rh[q], rl[q], a.x, a.z, xv.re);    // + a_re x_re
+          df_mac(rh[q], rl[q], -a.y, -a.w, xv.im);  // - a_im x_im
+          df_mac(ih[q], il[q], a.x, a.z, xv.im);    // + a_re x_im
+          df_mac(ih[q], il[q], a.y, a.w, xv.re);    // + a_im x_re
+        }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < KC; ++q) {
+    if (q >= kc) break;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      const float h2 = __shfl_down_sync(0xffffffffu, rh[q], o, 16), l2 = __shfl_down_sync(0xffffffffu, rl[q], o, 16);
+      const float h3 = __shfl_down_sync(0xffffffffu, ih[q], o, 16), l3 = __shfl_down_sync(0xffffffffu, il[q], o, 16);
+      df_add(rh[q], rl[q], h2, l2);
+      df_add(ih[q], il[q], h3, l3);
+    }
+    if (live && sl == 0) y[row * k + r0 + q] = {(double)rh[q] + (double)rl[q], (double)ih[q] + (double)il[q]};
+  }
+}
+
 // partials[b][r] = sum over this block's slice of conj(a) * b  (complex), or |a|^2 if b == nullptr
 __device__ void block_reduce_store(cplx* vals, int k, cplx* partials) {
   // vals: per-thread accumulators for r in 0..k-1 are reduced across the block
@@ -249,6 +333,11 @@ __global__ void k_to_internal(int64_t n, int k, const cplx* __restrict__ src, cp
   int r = (int)(e % k);
   dst[e] = src[(int64_t)r * n + g];
 }
+__global__ void k_to_internal_c64(int64_t n, int k, const CT<float>* __restrict__ src, CT<float>* __restrict__ dst) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * k) return;
+  dst[e] = src[(int64_t)(e % k) * n + e / k];
+}
 __global__ void k_to_external(int64_t n, int k, const cplx* __restrict__ src, cplx* __restrict__ dst) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * k) return;
@@ -270,7 +359,26 @@ static void spmv_t(const oras_handle* h, const XT* x, cplx* y, int k) {
   }
 }
 void launch_spmv_f64(const oras_handle* h, const cplx* x, cplx* y, int k) { spmv_t<cplx>(h, x, y, k); }
-void launch_spmv_f32(const oras_handle* h, const void* x, cplx* y, int k) { spmv_t<CT<float>>(h, (const CT<float>*)x, y, k); }
+// complex FP32 x: FP32-pipe kernel with FP64-class accuracy (k_spmv_df)
+void launch_spmv_f32(const oras_handle* h, const void* x, cplx* y, int k) {
+  const auto& m = h->mesh;
+  const auto& d = h->dev;
+  const int64_t blocks = (m.ndof * 16 + 255) / 256;
+  for (int r0 = 0; r0 < k; r0 += 8) {
+    const int kc = k - r0 < 8 ? k - r0 : 8;
+    const CT<float>* xx = (const CT<float>*)x;
+    if (kc == 1) k_spmv_df<1><<<(unsigned)blocks, 256, 0, d.stream>>>(m.ndof, d.rowptr, d.cols, d.vals_df, xx, y, k, r0, kc);
+    else if (kc == 2) k_spmv_df<2><<<(unsigned)blocks, 256, 0, d.stream>>>(m.ndof, d.rowptr, d.cols, d.vals_df, xx, y, k, r0, kc);
+    else if (kc <= 4) k_spmv_df<4><<<(unsigned)blocks, 256, 0, d.stream>>>(m.ndof, d.rowptr, d.cols, d.vals_df, xx, y, k, r0, kc);
+    else k_spmv_df<8><<<(unsigned)blocks, 256, 0, d.stream>>>(m.ndof, d.rowptr, d.cols, d.vals_df, xx, y, k, r0, kc);
+    count_launches(1);
+  }
+}
+void launch_split_vals(const oras_handle* h) {
+  const int64_t nnz = (int64_t)h->mesh.cols.size();
+  k_split_vals<<<(unsigned)((nnz + 255) / 256), 256, 0, h->dev.stream>>>(nnz, h->dev.vals, h->dev.vals_df);
+  count_launches(1);
+}
 
 void launch_dot(const oras_handle* h, const cplx* a, const cplx* b, cplx* partials, int k) {
   k_dot<<<RED_BLOCKS, RED_THREADS, 0, h->dev.stream>>>(h->mesh.ndof * k, k, a, b, partials);
@@ -313,6 +421,12 @@ void launch_restart(const oras_handle* h, int k, int m, const cplx* rv, const do
                     cplx* V0, cplx* g) {
   int64_t nk = h->mesh.ndof * k;
   k_restart<<<(unsigned)((nk + 255) / 256), 256, 0, h->dev.stream>>>(nk, k, m, rv, beta, active, V0, g);
+  count_launches(1);
+}
+void launch_to_internal_c64(const oras_handle* h, int k, const void* src, void* dst) {
+  const int64_t nk = h->mesh.ndof * k;
+  k_to_internal_c64<<<(unsigned)((nk + 255) / 256), 256, 0, h->dev.stream>>>(h->mesh.ndof, k, (const CT<float>*)src,
+                                                                            (CT<float>*)dst);
   count_launches(1);
 }
 void launch_to_internal(const oras_handle* h, int k, const cplx* src, cplx* dst) {

@@ -253,8 +253,15 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_tournament(LuArgs a, void* ar
 // candidate row t (64 complex values in registers).  No row is moved: the chosen pivot row is
 // marked and broadcast through shared memory for the rank-1 update of the rows not yet chosen.
 // Pivot choice: max |Re| + |Im| over unchosen rows, ties to the lowest candidate position.
+//
+// The 64 columns are eliminated in 8 blocks of 8 by a runtime loop: within a block the column
+// indices are compile-time (registers stay registers), and after each block every row is
+// rotated left by 8 so the next block's columns come to positions 0..7 (after the 8th rotation
+// the rows are back in their original order).  The loop body stays small enough for the
+// instruction cache; positions >= 64 - 8*block hold already eliminated columns and are skipped
+// block by block.
 struct RegGepp {
-  float pr[2][TB], pi[2][TB];   // pivot row broadcast, double buffered by column parity
+  float2 prow[8][TB];           // pivot rows of the current block (rotated like the rows)
   float wv[2][8];
   int wi[2][8];
   int order[TB];                // pivot rank -> candidate position
@@ -268,46 +275,71 @@ __device__ __forceinline__ void gepp_regs(float (&xr)[TB], float (&xi)[TB], bool
   mypiv = 0.0f;
   if (t < TB) g.order[t] = -1;
   __syncthreads();
+#pragma unroll 1
+  for (int cb = 0; cb < TB / 8; ++cb) {
+    const int lim = TB - 8 * cb;  // rotated positions >= lim: columns eliminated in earlier blocks
 #pragma unroll
-  for (int c = 0; c < TB; ++c) {
-    const int b = c & 1;
-    float v = (valid && !chosen) ? fabsf(xr[c]) + fabsf(xi[c]) : -1.0f;
-    if (v != v) v = 0.0f;  // a non-finite entry still lets a row be chosen
-    int key = t;
+    for (int c8 = 0; c8 < 8; ++c8) {
+      const int c = 8 * cb + c8;
+      const int b = c8 & 1;
+      float v = (valid && !chosen) ? fabsf(xr[c8]) + fabsf(xi[c8]) : -1.0f;
+      if (v != v) v = 0.0f;  // a non-finite entry still lets a row be chosen
+      int key = t;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ov = __shfl_down_sync(0xffffffffu, v, o);
-      const int ok = __shfl_down_sync(0xffffffffu, key, o);
-      if (ov > v || (ov == v && ok < key)) { v = ov; key = ok; }
-    }
-    if (lane == 0) { g.wv[b][warp] = v; g.wi[b][warp] = key; }
-    __syncthreads();
-    float bv = g.wv[b][0];
-    int bk = g.wi[b][0];
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_down_sync(0xffffffffu, v, o);
+        const int ok = __shfl_down_sync(0xffffffffu, key, o);
+        if (ov > v || (ov == v && ok < key)) { v = ov; key = ok; }
+      }
+      if (lane == 0) { g.wv[b][warp] = v; g.wi[b][warp] = key; }
+      __syncthreads();
+      float bv = g.wv[b][0];
+      int bk = g.wi[b][0];
 #pragma unroll
-    for (int w = 1; w < LU_THREADS / 32; ++w)
-      if (g.wv[b][w] > bv || (g.wv[b][w] == bv && g.wi[b][w] < bk)) { bv = g.wv[b][w]; bk = g.wi[b][w]; }
-    if (t == bk && bv >= 0.0f) {
-      chosen = true;
-      myrank = c;
-      mypiv = bv;
-      g.order[c] = t;
+      for (int w = 1; w < LU_THREADS / 32; ++w)
+        if (g.wv[b][w] > bv || (g.wv[b][w] == bv && g.wi[b][w] < bk)) { bv = g.wv[b][w]; bk = g.wi[b][w]; }
+      if (t == bk && bv >= 0.0f) {
+        chosen = true;
+        myrank = c;
+        mypiv = bv;
+        g.order[c] = t;
 #pragma unroll
-      for (int j = c; j < TB; ++j) { g.pr[b][j] = xr[j]; g.pi[b][j] = xi[j]; }
-    }
-    __syncthreads();
-    if (bv > 0.0f && valid && !chosen) {
-      const float dr = g.pr[b][c], di = g.pi[b][c], den = dr * dr + di * di;
-      const float lr = (xr[c] * dr + xi[c] * di) / den, li = (xi[c] * dr - xr[c] * di) / den;
-      xr[c] = lr;
-      xi[c] = li;
+        for (int j = 0; j < TB; ++j) g.prow[c8][j] = make_float2(xr[j], xi[j]);
+      }
+      __syncthreads();
+      if (bv > 0.0f && valid && !chosen) {
+        const float2 p = g.prow[c8][c8];
+        const float den = p.x * p.x + p.y * p.y;
+        const float lr = (xr[c8] * p.x + xi[c8] * p.y) / den, li = (xi[c8] * p.x - xr[c8] * p.y) / den;
+        xr[c8] = lr;
+        xi[c8] = li;
 #pragma unroll
-      for (int j = c + 1; j < TB; ++j) {
-        const float ur = g.pr[b][j], ui = g.pi[b][j];
-        xr[j] -= lr * ur - li * ui;
-        xi[j] -= lr * ui + li * ur;
+        for (int j = c8 + 1; j < 8; ++j) {
+          const float2 u = g.prow[c8][j];
+          xr[j] -= lr * u.x - li * u.y;
+          xi[j] -= lr * u.y + li * u.x;
+        }
+#pragma unroll
+        for (int jb = 1; jb < TB / 8; ++jb) {
+          if (8 * jb < lim) {  // the same for the whole block: no divergence
+#pragma unroll
+            for (int j = 8 * jb; j < 8 * jb + 8; ++j) {
+              const float2 u = g.prow[c8][j];
+              xr[j] -= lr * u.x - li * u.y;
+              xi[j] -= lr * u.y + li * u.x;
+            }
+          }
+        }
       }
     }
+    // rotate left by 8: the next block's columns move to positions 0..7
+    float tr[8], ti[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { tr[j] = xr[j]; ti[j] = xi[j]; }
+#pragma unroll
+    for (int j = 0; j < TB - 8; ++j) { xr[j] = xr[j + 8]; xi[j] = xi[j + 8]; }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { xr[TB - 8 + j] = tr[j]; xi[TB - 8 + j] = ti[j]; }
   }
 }
 
@@ -361,42 +393,47 @@ __global__ void __launch_bounds__(LU_THREADS, 1) k_lu_tournament_rg(LuArgs a, vo
   int myrank;
   float mypiv;
   ids[t] = t < m ? (int32_t)(R0 + (int64_t)c * CH + t) : -1;
-  if (t < m) load_row_regs(arena, a, s, ids[t], xr, xi);
-  __syncthreads();
-  gepp_regs(xr, xi, t < m, g, myrank, mypiv);
-  if (t < TB) nids[t] = pick_checked(a, s, ids, g.order[t], R0, np, 1);
+  bool okrow = t < m;
+  if (okrow) load_row_regs(arena, a, s, ids[t], xr, xi);
   __syncthreads();
   int32_t* cand = a.cand + (int64_t)s * a.slots * TB;
   int32_t* cnt = a.cnt + (int64_t)s * a.slots;
-  int level_off = 0, n_l = nch, j = c;
-  if (n_l > 1 && t < TB) cand[(level_off + j) * TB + t] = nids[t];
-  while (n_l > 1) {
-    const int n_next = (n_l + 1) >> 1;
-    const int parent = j >> 1, sib = j ^ 1;
-    const int next_off = level_off + n_l;
-    if (sib >= n_l) {  // odd one out: pass the candidates up unchanged
-      if (t < TB) cand[(next_off + parent) * TB + t] = nids[t];
-      level_off = next_off; n_l = n_next; j = parent;
-      continue;
-    }
-    __threadfence();
-    __syncthreads();
-    if (t == 0) s_old = atomicAdd(&cnt[next_off + parent], 1);
-    __syncthreads();
-    if (s_old == 0) return;  // the sibling will merge
-    if (t == 0) cnt[next_off + parent] = 0;
-    __threadfence();
-    const int left = j & ~1;
-    ids[t] = t < 2 * TB ? ((volatile int32_t*)cand)[(level_off + left + (t >= TB)) * TB + (t % TB)] : -1;
-    __syncthreads();
-    bool okrow = t < 2 * TB && ids[t] >= R0 && ids[t] < np;
-    if (t < 2 * TB && !okrow) flag_bad(a, s, 2);
-    if (okrow) load_row_regs(arena, a, s, ids[t], xr, xi);
+  int level_off = 0, n_l = nch, j = c, code = 1;
+  // leaf elimination, then one merge per level while this block arrives second at its parent
+  for (;;) {
     gepp_regs(xr, xi, okrow, g, myrank, mypiv);
-    if (t < TB) nids[t] = pick_checked(a, s, ids, g.order[t], R0, np, 3);
+    if (t < TB) nids[t] = pick_checked(a, s, ids, g.order[t], R0, np, code);
     __syncthreads();
-    level_off = next_off; n_l = n_next; j = parent;
     if (n_l > 1 && t < TB) cand[(level_off + j) * TB + t] = nids[t];
+    bool merge = false;
+    while (n_l > 1) {
+      const int n_next = (n_l + 1) >> 1;
+      const int parent = j >> 1, sib = j ^ 1;
+      const int next_off = level_off + n_l;
+      if (sib >= n_l) {  // odd one out: pass the candidates up unchanged
+        if (t < TB) cand[(next_off + parent) * TB + t] = nids[t];
+        level_off = next_off; n_l = n_next; j = parent;
+        continue;
+      }
+      __threadfence();
+      __syncthreads();
+      if (t == 0) s_old = atomicAdd(&cnt[next_off + parent], 1);
+      __syncthreads();
+      if (s_old == 0) return;  // the sibling will merge
+      if (t == 0) cnt[next_off + parent] = 0;
+      __threadfence();
+      const int left = j & ~1;
+      ids[t] = t < 2 * TB ? ((volatile int32_t*)cand)[(level_off + left + (t >= TB)) * TB + (t % TB)] : -1;
+      __syncthreads();
+      okrow = t < 2 * TB && ids[t] >= R0 && ids[t] < np;
+      if (t < 2 * TB && !okrow) flag_bad(a, s, 2);
+      if (okrow) load_row_regs(arena, a, s, ids[t], xr, xi);
+      level_off = next_off; n_l = n_next; j = parent;
+      code = 3;
+      merge = true;
+      break;
+    }
+    if (!merge) break;  // this block holds the root's result
   }
   // root: the chosen rows, in pivot order, are L11\U11 of the step
   CT<float>* dg = (CT<float>*)a.diag + (int64_t)s * TB * TB;

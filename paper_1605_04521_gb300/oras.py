@@ -101,6 +101,7 @@ EXPORTS = {
     "oras_global_csr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "oras_matvec": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "oras_precond": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
+    "oras_matvec_c64": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "oras_timings": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "oras_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "oras_reset_timings": (C.c_int, [C.c_void_p]),
@@ -326,6 +327,19 @@ def _vec_call(fn, h, x, k, mem, out=None):
 
 def oras_matvec(h, x, k=1, mem=ORAS_MEM_HOST, out=None):
     return _vec_call(lib.oras_matvec, h, x, k, mem, out)
+
+
+def oras_matvec_c64(h, x, k=1, mem=ORAS_MEM_HOST, out=None):
+    """y = A x for complex64 x (host: (N,) or (N, k); device: torch complex64, N x k column-major);
+    y complex128."""
+    n = oras_ndof(h)
+    if mem == ORAS_MEM_HOST:
+        xx = np.asfortranarray(np.asarray(x, dtype=np.complex64).reshape(n, k))
+        y = np.empty((n, k), dtype=np.complex128, order="F")
+        _check(h, lib.oras_matvec_c64(h, _ptr(xx), _ptr(y), k, mem))
+        return y if k > 1 else y[:, 0]
+    _check(h, lib.oras_matvec_c64(h, _ptr(x), _ptr(out), k, mem))
+    return out
 
 
 def oras_precond(h, v, k=1, mem=ORAS_MEM_HOST, out=None):

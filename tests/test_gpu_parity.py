@@ -72,6 +72,24 @@ def test_global_matrix_and_matvec(O, r, n):
         O.oras_destroy(h)
 
 
+@pytest.mark.parametrize("r,n,k", [(1, 4, 1), (2, 3, 3), (3, 2, 9)])
+def test_fp32_input_matvec_keeps_fp64_accuracy(O, r, n, k):
+    """A z for complex FP32 z on the FP32 pipes (split A, exact product and sum errors) against the
+    oracle's FP64 A @ z: every column within 1e-13 relative, no worse than the FP64 kernel's bar."""
+    w = synth.small(n=n, r=r, nsub=4, overlap=1)
+    h = gpu_handle(O, w)
+    try:
+        p = problem.from_workload(w, with_oras=False)
+        rng = np.random.default_rng(13)
+        Z = (rng.normal(size=(p.A.shape[0], k)) + 1j * rng.normal(size=(p.A.shape[0], k))).astype(np.complex64)
+        Y = np.asarray(O.oras_matvec_c64(h, Z, k=k)).reshape(-1, k)
+        ref = p.A @ Z.astype(np.complex128)
+        for j in range(k):
+            assert rel(Y[:, j], ref[:, j]) <= 1e-13
+    finally:
+        O.oras_destroy(h)
+
+
 def test_right_hand_sides(O):
     w = synth.config(0)
     h = gpu_handle(O, w, factor_bits=64)
