@@ -351,6 +351,7 @@ def run_ours(args, world, rank, local):
     eps_d = torch.from_numpy(eps).to(dev)
     mu_d = torch.from_numpy(mu).to(dev)
     O.oras_factor(h, eps_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
+    panel, tune_ms = O.oras_autotune(h)   # LU panel width for this problem (set-up, untimed)
     n = O.oras_ndof(h)
     if w.source == "plane":
         b_d = O.oras_rhs_plane_wave(h, src_pt, direction.astype(np.complex128), mem=O.ORAS_MEM_DEVICE,
@@ -414,7 +415,7 @@ def run_ours(args, world, rank, local):
     e0 = time.perf_counter()
     for _ in range(e2e_steps):
         he = O.oras_setup(xyz, tets, eps, mu, w.k0, w.r, w.nsub, w.overlap, factor_bits=w.factor_bits,
-                          restart=w.restart)
+                          restart=w.restart, lu_panel=panel)
         xe, info_e, rc = O.oras_solve(he, b_host, w.tol)
         x_host[:] = xe
         O.oras_destroy(he)
@@ -441,7 +442,8 @@ def run_ours(args, world, rank, local):
                        "l2": "512 MiB buffer written between timed steps; the step itself streams the "
                              f"{arena / 1e9:.1f} GB factor arena",
                        "step": "oras_factor (element matrices, A, A_s, batched LU) + oras_solve, device buffers",
-                       "mesh_setup_s_untimed": t_mesh, "parallelism": f"replicas x{world}"},
+                       "mesh_setup_s_untimed": t_mesh, "parallelism": f"replicas x{world}",
+                       "lu_panel": panel, "lu_panel_autotune_ms": {str(k_): round(v_, 1) for k_, v_ in tune_ms.items()}},
             "iterations": iters, "true_relres": infos[-1][0]["relres"],
             "phase_ms_per_step": {c: v[0] / args.steps for c, v in timings.items() if v[1] > 0},
             "roofline": roof,

@@ -227,6 +227,17 @@ int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t
  * Errors: STATE (no oras_factor yet), INVALID_ARG, CUDA. */
 int oras_precond_noalloc(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k);
 
+/* Autotuner of the batched LU's outer panel width (tiles of 64 columns per trailing update;
+ * trades the inner panel updates against the passes over the trailing matrix).  Factorises the
+ * handle's current problem (materials of the last oras_factor, on the handle's stream) once per
+ * candidate width 4, 6, 8, 12, 16, keeps the fastest in the handle's options (lu_panel) and leaves
+ * the factors of that width.  The choice is cached for the process under the problem's shape
+ * (factor precision, LU engine, padded subdomain orders): a later handle of the same shape takes
+ * it without timing.  panel: chosen width (or NULL); ms[0..nms): the candidates' factorisation
+ * times in milliseconds (-1 when taken from the cache; NULL allowed).
+ * Errors: INVALID_ARG, STATE (no oras_factor yet), and those of oras_factor. */
+int oras_autotune(oras_handle* h, int32_t* panel, double* ms, int32_t nms);
+
 /* Device bytes that oras_factor followed by an oras_solve of k right-hand sides allocate for
  * this handle (factor arena, inverted diagonal blocks, A, element matrices, Krylov basis of
  * restart+1 FP64 and restart FP32/FP64 vectors per right-hand side, staging), including the

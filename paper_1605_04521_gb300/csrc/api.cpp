@@ -8,6 +8,9 @@
 #include <string>
 #include <vector>
 
+#include <map>
+#include <mutex>
+
 #include "internal.h"
 
 namespace oras {
@@ -307,6 +310,36 @@ int64_t footprint_bytes(const oras_handle* h, int k) {
   return b + (int64_t)nalloc * (2 << 20);
 }
 
+static int sync_status(oras_handle* h);
+
+// Element matrices, A, local matrices and batched LU from the materials already on the device.
+static int factor_device(oras_handle* h) {
+  auto& d = h->dev;
+  const double k0 = h->k0;
+  CK(cudaMemsetAsync(d.status, 0, 8 * sizeof(int32_t), d.stream));
+  {
+    int b = prof_begin(h);
+    if (launch_element(h, k0) || launch_faces(h)) CK(cudaGetLastError());
+    prof_end(h, KC_ELEMENT, b, 2);
+  }
+  {
+    int b = prof_begin(h);
+    if (launch_global_rows(h, k0)) CK(cudaGetLastError());
+    launch_split_vals(h);
+    prof_end(h, KC_GLOBAL_ROWS, b, 2);
+  }
+  {
+    int b = prof_begin(h);
+    CK(cudaMemsetAsync(d.arena, 0, d.arena_bytes, d.stream));
+    if (launch_local_rows(h, k0)) CK(cudaGetLastError());
+    prof_end(h, KC_LOCAL_ROWS, b, 1);
+  }
+  if (launch_lu(h)) CK(cudaGetLastError());
+  prof_resolve(h);
+  return sync_status(h);
+}
+
+
 static int sync_status(oras_handle* h) {
   auto& d = h->dev;
   int32_t st[8];
@@ -417,32 +450,66 @@ int oras_factor(oras_handle* h, const oras_complex* eps_r, const oras_complex* m
   } else if (d.mu) {
     dfree_s(d.mu, d.stream);
   }
-  CK(cudaMemsetAsync(d.status, 0, 8 * sizeof(int32_t), d.stream));
   h->k0 = k0;
-  {
-    int b = prof_begin(h);
-    if (launch_element(h, k0) || launch_faces(h)) CK(cudaGetLastError());
-    prof_end(h, KC_ELEMENT, b, 2);
-  }
-  {
-    int b = prof_begin(h);
-    if (launch_global_rows(h, k0)) CK(cudaGetLastError());
-    launch_split_vals(h);
-    prof_end(h, KC_GLOBAL_ROWS, b, 2);
-  }
-  {
-    int b = prof_begin(h);
-    CK(cudaMemsetAsync(d.arena, 0, d.arena_bytes, d.stream));
-    if (launch_local_rows(h, k0)) CK(cudaGetLastError());
-    prof_end(h, KC_LOCAL_ROWS, b, 1);
-  }
-  if (launch_lu(h)) CK(cudaGetLastError());
-  prof_resolve(h);
-  rc = sync_status(h);
+  rc = factor_device(h);
   if (rc) return rc;
   h->factored = true;
   return ORAS_OK;
 }
+
+// Autotuner of the LU panel width: each candidate factorises the handle's current problem once
+// (CUDA events on the handle's stream); the fastest is kept in the handle's options and cached
+// for the process under the problem's shape, so later handles of the same shape reuse it.
+static std::mutex g_tune_mu;
+static std::map<std::vector<int64_t>, int> g_tune_cache;
+
+int oras_autotune(oras_handle* h, int32_t* panel, double* ms, int32_t nms) {
+  if (!h) return ORAS_ERR_INVALID_ARG;
+  if (!h->factored) { h->err = "oras_autotune: call oras_factor first"; return ORAS_ERR_STATE; }
+  static const int cand[] = {4, 6, 8, 12, 16};
+  constexpr int NC = sizeof(cand) / sizeof(cand[0]);
+  std::vector<int64_t> key = {h->opt.factor_bits, h->opt.lu_engine, h->mesh.nsub};
+  key.insert(key.end(), h->mesh.sub_np.begin(), h->mesh.sub_np.end());
+  int best = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) best = it->second;
+  }
+  for (int q = 0; q < nms && ms; ++q) ms[q] = -1.0;
+  if (best < 0) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double tbest = 1e300;
+    const int keep = h->opt.lu_panel;
+    for (int c = 0; c < NC; ++c) {
+      h->opt.lu_panel = cand[c];
+      cudaEventRecord(e0, h->dev.stream);
+      int rc = factor_device(h);
+      cudaEventRecord(e1, h->dev.stream);
+      cudaEventSynchronize(e1);
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rc) {
+        h->opt.lu_panel = keep;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+      }
+      if (ms && c < nms) ms[c] = t;
+      if (t < tbest) { tbest = t; best = cand[c]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  h->opt.lu_panel = best;
+  if (panel) *panel = best;
+  return factor_device(h);  // leave the factors of the chosen width
+}
+
 
 int oras_setup(const oras_problem* p, const oras_options* o, oras_handle** out) {
   int rc = oras_create(p, o, out);

@@ -207,4 +207,10 @@ struct oras_handle {
   mutable std::vector<int> marks;                    // (class, begin event, end event, launches)*
   double cls_ms[oras::KC_COUNT] = {0};
   double cls_n[oras::KC_COUNT] = {0};
+  // tcgen05 operand tensor map over this handle's factor arena (a CUtensorMap, 128 bytes),
+  // rebuilt when the arena moves; per handle, so concurrent handles never share one
+  alignas(64) unsigned char tc_map[128] = {0};
+  const void* tc_map_base = nullptr;
+  int64_t tc_map_tiles = 0;
+  bool tc_map_ok = false;
 };

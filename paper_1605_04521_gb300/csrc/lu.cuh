@@ -29,7 +29,7 @@ __host__ __device__ __forceinline__ void region_clip(const Region& r, int64_t nt
 
 // tensor-core trailing update (lu_tc.cu): returns false when it cannot run (then the caller
 // uses the CUDA-core kernel)
-bool tc_update_available(const oras_handle* h);
+bool tc_update_available(oras_handle* h);
 int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts);
 int launch_trsm_tc(oras_handle* h, int k, int max_nts);
 

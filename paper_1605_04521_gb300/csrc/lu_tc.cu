@@ -17,6 +17,7 @@
 #include <cuda.h>
 
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "lu.cuh"
@@ -395,14 +396,7 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-struct TcState {
-  CUtensorMap map;
-  void* base = nullptr;
-  int64_t tiles = 0;
-  bool ok = false;
-};
-static TcState g_tc_cache[64];
-static std::mutex g_tc_mu;
+static_assert(sizeof(CUtensorMap) == sizeof(((oras_handle*)nullptr)->tc_map), "tensor map storage");
 
 // Tensor map over the arena viewed as [tiles][2 planes x 64 rows][64 floats].
 static bool make_map(const oras_handle* h, CUtensorMap* map) {
@@ -420,19 +414,17 @@ static bool make_map(const oras_handle* h, CUtensorMap* map) {
   return r == CUDA_SUCCESS;
 }
 
-bool tc_update_available(const oras_handle* h) {
+bool tc_update_available(oras_handle* h) {
   if (h->dev.factor_bits != 32 || !h->dev.arena) return false;
-  int dev = h->dev.device;
-  if (dev < 0 || dev >= 64) return false;
-  std::lock_guard<std::mutex> lock(g_tc_mu);
-  TcState& st = g_tc_cache[dev];
   const int64_t tiles = h->mesh.arena_tiles + 2 * h->mesh.nsub;
-  if (st.base != h->dev.arena || st.tiles != tiles) {
-    st.ok = make_map(h, &st.map);
-    st.base = h->dev.arena;
-    st.tiles = tiles;
+  if (h->tc_map_base != h->dev.arena || h->tc_map_tiles != tiles) {
+    CUtensorMap map;
+    h->tc_map_ok = make_map(h, &map);
+    std::memcpy(h->tc_map, &map, sizeof(map));
+    h->tc_map_base = h->dev.arena;
+    h->tc_map_tiles = tiles;
   }
-  return st.ok;
+  return h->tc_map_ok;
 }
 
 int launch_trsm_tc(oras_handle* h, int k, int max_nts) {
@@ -442,10 +434,7 @@ int launch_trsm_tc(oras_handle* h, int k, int max_nts) {
   if (nrem <= 0) return 0;
   const int64_t blocks = 2 * ((nrem + 1) / 2);
   CUtensorMap map;
-  {
-    std::lock_guard<std::mutex> lock(g_tc_mu);
-    map = g_tc_cache[d.device].map;
-  }
+  std::memcpy(&map, h->tc_map, sizeof(map));
   TrsmArgs a;
   a.np = d.sub_np;
   a.tile_off = d.sub_tile_off;
@@ -471,10 +460,7 @@ int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts) {
   }
   if (blocks <= 0) return 0;
   CUtensorMap map;
-  {
-    std::lock_guard<std::mutex> lock(g_tc_mu);
-    map = g_tc_cache[d.device].map;
-  }
+  std::memcpy(&map, h->tc_map, sizeof(map));
   TcArgs a;
   a.np = d.sub_np;
   a.tile_off = d.sub_tile_off;

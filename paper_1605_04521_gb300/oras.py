@@ -108,6 +108,7 @@ EXPORTS = {
     "oras_launch_count": (C.c_int64, []),
     "oras_precond_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "oras_footprint": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
+    "oras_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_int32]),
     "oras_server_create": (C.c_int, [C.POINTER(oras_server_config), C.POINTER(C.c_void_p)]),
     "oras_submit": (C.c_int64, [C.c_void_p, C.POINTER(oras_problem), C.POINTER(oras_options), C.c_void_p,
                                 C.c_int64, C.c_void_p, C.c_int32, C.c_double]),
@@ -388,6 +389,15 @@ def oras_precond_noalloc(h, v, z, k=1):
     """z = M^{-1} v without any device allocation; v, z: torch CUDA complex128 tensors holding
     N x k column-major data (shape (k, N) contiguous, or (N,) for k = 1)."""
     return _check(h, lib.oras_precond_noalloc(h, _ptr(v), _ptr(z), int(k)))
+
+
+def oras_autotune(h):
+    """Returns (panel width chosen, {width: factorisation ms} (empty when cached))."""
+    panel = C.c_int32()
+    ms = np.full(5, -1.0)
+    _check(h, lib.oras_autotune(h, C.byref(panel), _ptr(ms), 5))
+    times = {w: t for w, t in zip((4, 6, 8, 12, 16), ms) if t >= 0}
+    return panel.value, times
 
 
 def oras_footprint(h, k=1):

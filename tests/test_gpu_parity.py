@@ -310,3 +310,26 @@ def test_tensor_core_lu_matches_cuda_core_lu(O, n, r, nsub, delta):
     finally:
         O.oras_destroy(ht)
         O.oras_destroy(hc)
+
+
+def test_autotuned_panel_width(O):
+    """The autotuner times every candidate panel width once per problem shape, keeps the
+    fastest, and the factors it leaves solve to the oracle's field."""
+    w = synth.small(n=5, r=2, nsub=4, overlap=1)
+    p = problem.from_workload(w)
+    h = gpu_handle(O, w)
+    try:
+        panel, times = O.oras_autotune(h)
+        assert set(times) == {4, 6, 8, 12, 16} and panel == min(times, key=times.get)
+        x, info, rc = O.oras_solve(h, p.B[:, 0], w.tol)
+        assert rc == O.ORAS_OK
+        assert np.linalg.norm(p.B[:, 0] - p.A @ x) / np.linalg.norm(p.B[:, 0]) <= 1e-8
+        assert rel(x, spla.spsolve(p.A.tocsc(), p.B[:, 0])) <= 1e-6
+    finally:
+        O.oras_destroy(h)
+    h2 = gpu_handle(O, w)      # same shape: the cached choice, no timing
+    try:
+        panel2, times2 = O.oras_autotune(h2)
+        assert panel2 == panel and times2 == {}
+    finally:
+        O.oras_destroy(h2)

@@ -112,5 +112,11 @@ def test_error_codes(O):
         with pytest.raises(O.OrasError) as e:
             O.oras_matvec(h, np.ones(O.oras_ndof(h)))
         assert e.value.code == O.ORAS_ERR_STATE
+        with pytest.raises(O.OrasError) as e:
+            O.oras_matvec_c64(h, np.ones(O.oras_ndof(h)))
+        assert e.value.code == O.ORAS_ERR_STATE
+        with pytest.raises(O.OrasError) as e:
+            O.oras_autotune(h)
+        assert e.value.code == O.ORAS_ERR_STATE
     finally:
         O.oras_destroy(h)

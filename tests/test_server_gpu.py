@@ -31,6 +31,10 @@ REQUESTS = [
     synth.small(n=6, r=1, nsub=8, overlap=2, nrhs=2),
     synth.small(n=5, r=2, nsub=4, overlap=1, nrhs=5),
     synth.small(n=4, r=1, nsub=2, overlap=0, head=False, source="plane"),
+    # three of the same shape with long tensor-core factorisations that overlap in time
+    synth.small(n=8, r=2, nsub=8, overlap=1, nrhs=1),
+    synth.small(n=8, r=2, nsub=8, overlap=1, nrhs=2),
+    synth.small(n=8, r=2, nsub=8, overlap=1, nrhs=4),
 ]
 
 
@@ -58,7 +62,7 @@ def test_alone_and_in_the_mix(O):
     finally:
         O.oras_server_destroy(srv)
     # the mix: everything submitted at once, three slots
-    srv = O.oras_server_create(max_active=3)
+    srv = O.oras_server_create(max_active=4)
     try:
         tickets = [submit(O, srv, w, p) for w, p in zip(REQUESTS, probs)]
         mix = []
@@ -78,6 +82,7 @@ def test_alone_and_in_the_mix(O):
     for w, p, xa, xm in zip(REQUESTS, probs, alone, mix):
         for j in range(xa.shape[1]):
             assert rel(xm[:, j], xa[:, j]) <= 1e-6                     # alone == in the mix
+            assert np.array_equal(xm[:, j], xa[:, j])                  # (deterministic kernels)
             b = p.B[:, j]
             assert np.linalg.norm(b - p.A @ xm[:, j]) / np.linalg.norm(b) <= 1e-8 * 1.01
 
