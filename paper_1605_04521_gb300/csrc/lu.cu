@@ -11,12 +11,15 @@
 //     LU, Grigori, Demmel, Xiang 2011);
 //  2. the row interchanges of the step, applied to every column (one permutation of at most
 //     2 TB rows);
-//  3. L21 = A21 U11^{-1} below and U12 = L11^{-1} A12 along the whole tile row;
-//  4. the inner update: tiles of the panel's remaining columns, and of the panel's remaining
-//     rows right of the panel, get -= L_Ik U_kJ.
+//  3. the pivot tile row, right of the panel, receives the updates of the panel's earlier
+//     steps (C_kJ -= sum_{k0 <= j < k} L_kj U_jJ, left-looking);
+//  4. L21 = A21 U11^{-1} below and U12 = L11^{-1} A12 along the whole tile row;
+//  5. the inner update: the panel's remaining columns, every row below, get -= L_Ik U_kJ.
 // After the W columns of a panel, the trailing matrix gets one update with a W-tile-deep
 // contraction, C_IJ -= sum_k L_Ik U_kJ, which reads and writes every trailing tile once per
-// panel instead of once per column.
+// panel instead of once per column.  Right of the panel, every row not yet a pivot row stays
+// in the state of the panel's start until then, so a row interchange never mixes rows that
+// have received different updates.
 // The tree merge uses "last arriver continues" counters, so no block ever waits for another.
 #include <algorithm>
 #include <climits>
@@ -841,6 +844,17 @@ static int lu_run(oras_handle* h) {
       pb = prof_begin(h);
       k_lu_swap<R><<<dim3(max_nts + 1, m.nsub), 256, smem_s, d.stream>>>(a, d.arena);
       prof_end(h, KC_LU_SWAP, pb, 1);
+      if (k > k0) {
+        // the pivot row's columns right of the panel, from the panel's earlier steps (left-looking:
+        // every row below the panel keeps those updates deferred until the outer update, so a
+        // pivot row swapped up from there must receive them now, and no row may get them early)
+        UpdArgs u;
+        u.kk0 = k0;
+        u.kk1 = k;
+        u.nreg = 1;
+        u.reg[0] = {k, k + 1, kend, INT_MAX};
+        update(u);
+      }
       pb = prof_begin(h);
       if (tc) {
         k_lu_step_inv<R><<<m.nsub, 2 * TB, smem_i, d.stream>>>(a, d.arena, m.arena_tiles);
@@ -851,14 +865,13 @@ static int lu_run(oras_handle* h) {
         prof_end(h, KC_LU_TRSM, pb, 1);
       }
       count_launches(3);
-      // inner update: the panel's remaining columns below, and the panel's remaining rows
-      // to the right of the panel
+      // inner update: the panel's remaining columns, every row below (all rows stay in the same
+      // state there, so later row interchanges stay consistent)
       UpdArgs u;
       u.kk0 = k;
       u.kk1 = k + 1;
-      u.nreg = 2;
+      u.nreg = 1;
       u.reg[0] = {k + 1, INT_MAX, k + 1, kend};
-      u.reg[1] = {k + 1, kend, kend, INT_MAX};
       update(u);
     }
     UpdArgs u;  // outer update of the trailing matrix

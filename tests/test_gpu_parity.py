@@ -113,6 +113,8 @@ def test_right_hand_sides(O):
 # FP32 factors: the trailing updates round their operands to TF32 (unit roundoff 2^-11), so the
 # apply of the FP32 factors differs from the FP64 oracle's by a small multiple of that.
 TOL_APPLY_F32 = 10 * 2.0 ** -11
+# Degree-3 local matrices are worse conditioned (observed up to 5.5e-3 on 4^3 x 6, 8 subdomains).
+TOL_APPLY_F32_R3 = 20 * 2.0 ** -11
 
 
 @pytest.mark.parametrize("bits,tol", [(64, 1e-9), (32, TOL_APPLY_F32)])
@@ -126,6 +128,26 @@ def test_preconditioner_apply(O, bits, tol):
         v = rng.normal(size=p.topo.ndof) + 1j * rng.normal(size=p.topo.ndof)
         z = O.oras_precond(h, v)
         assert rel(z, p.oras.apply(v)) <= tol
+    finally:
+        O.oras_destroy(h)
+
+
+@pytest.mark.parametrize("n,nsub,overlap,bits,panel", [
+    (3, 1, 0, 64, 0), (3, 1, 0, 64, 2), (3, 1, 0, 32, 3), (4, 8, 1, 64, 0), (4, 8, 1, 32, 0), (4, 8, 1, 32, 2)])
+def test_preconditioner_apply_degree3(O, n, nsub, overlap, bits, panel):
+    """Degree 3: the local matrices need row interchanges across panel boundaries of the batched
+    LU.  With one subdomain M^-1 = A^-1 (the FGMRES converges in one step)."""
+    w = synth.small(n=n, r=3, nsub=nsub, overlap=overlap)
+    h = gpu_handle(O, w, factor_bits=bits, lu_panel=panel)
+    try:
+        p = problem.from_workload(w)
+        rng = np.random.default_rng(31)
+        v = rng.normal(size=p.topo.ndof) + 1j * rng.normal(size=p.topo.ndof)
+        z = O.oras_precond(h, v)
+        assert rel(z, p.oras.apply(v)) <= (1e-9 if bits == 64 else TOL_APPLY_F32_R3)
+        if nsub == 1 and bits == 64:
+            x, info, rc = O.oras_solve(h, p.B[:, 0], 1e-8)
+            assert rc == O.ORAS_OK and info[0]["iterations"] == 1
     finally:
         O.oras_destroy(h)
 
