@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--serve-count", type=int, default=12,
                     help="requests of the serving stream replayed after the main measurement (0: none)")
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--lu-panel", type=int, default=0,
+                    help="LU outer panel width in tiles (0: picked by oras_autotune at set-up)")
     ap.add_argument("--serve-max-iter", type=int, default=60,
                     help="FGMRES iteration cap per served request (requests above it report not converged)")
     return ap.parse_args()
@@ -351,7 +353,15 @@ def run_ours(args, world, rank, local):
     eps_d = torch.from_numpy(eps).to(dev)
     mu_d = torch.from_numpy(mu).to(dev)
     O.oras_factor(h, eps_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
-    panel, tune_ms = O.oras_autotune(h)   # LU panel width for this problem (set-up, untimed)
+    if args.lu_panel > 0:
+        panel, tune_ms = args.lu_panel, {}
+        O.oras_destroy(h)
+        h = O.oras_create(xyz, tets, w.r, w.nsub, w.overlap, factor_bits=w.factor_bits, restart=w.restart,
+                          lu_panel=panel)
+        O.oras_set_stream(h, stream.cuda_stream)
+        O.oras_factor(h, eps_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
+    else:
+        panel, tune_ms = O.oras_autotune(h)   # LU panel width for this problem (set-up, untimed)
     n = O.oras_ndof(h)
     if w.source == "plane":
         b_d = O.oras_rhs_plane_wave(h, src_pt, direction.astype(np.complex128), mem=O.ORAS_MEM_DEVICE,
