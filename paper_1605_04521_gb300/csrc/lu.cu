@@ -5,8 +5,8 @@
 // Two-level right-looking blocked LU.  Outer panels are W tile columns wide; inside a panel,
 // every tile column k is processed for all subdomains at once by
 //  1. tournament pivoting of the tall panel column: chunks of rows are reduced with partial
-//     pivoting (pivot = max |Re| + |Im|, first on ties) to TB candidate rows each; pairs of
-//     candidate sets are merged the same way up a binary tree; the root's choice is the pivot
+//     pivoting (pivot = max |Re| + |Im|, first on ties) to TB candidate rows each; candidate
+//     sets are merged the same way up a tree (4-way for FP32, 2-way for FP64); the root's choice is the pivot
 //     sequence of the step and its factored TB x TB block is L11\U11 (communication-avoiding
 //     LU, Grigori, Demmel, Xiang 2011);
 //  2. the row interchanges of the step, applied to every column (one permutation of at most
@@ -402,18 +402,19 @@ __global__ void __launch_bounds__(LU_THREADS, 1) k_lu_tournament_rg(LuArgs a, vo
   int32_t* cand = a.cand + (int64_t)s * a.slots * TB;
   int32_t* cnt = a.cnt + (int64_t)s * a.slots;
   int level_off = 0, n_l = nch, j = c, code = 1;
-  // leaf elimination, then one merge per level while this block arrives second at its parent
+  // leaf elimination, then one merge per level while this block arrives last at its parent
   for (;;) {
     gepp_regs(xr, xi, okrow, g, myrank, mypiv);
     if (t < TB) nids[t] = pick_checked(a, s, ids, g.order[t], R0, np, code);
     __syncthreads();
     if (n_l > 1 && t < TB) cand[(level_off + j) * TB + t] = nids[t];
     bool merge = false;
-    while (n_l > 1) {
-      const int n_next = (n_l + 1) >> 1;
-      const int parent = j >> 1, sib = j ^ 1;
+    while (n_l > 1) {  // 4-way tree: the last of up to four siblings to arrive merges them
+      const int n_next = (n_l + 3) >> 2;
+      const int parent = j >> 2, first = parent << 2;
+      const int nsib = n_l - first < 4 ? n_l - first : 4;
       const int next_off = level_off + n_l;
-      if (sib >= n_l) {  // odd one out: pass the candidates up unchanged
+      if (nsib == 1) {  // only child: pass the candidates up unchanged
         if (t < TB) cand[(next_off + parent) * TB + t] = nids[t];
         level_off = next_off; n_l = n_next; j = parent;
         continue;
@@ -422,14 +423,13 @@ __global__ void __launch_bounds__(LU_THREADS, 1) k_lu_tournament_rg(LuArgs a, vo
       __syncthreads();
       if (t == 0) s_old = atomicAdd(&cnt[next_off + parent], 1);
       __syncthreads();
-      if (s_old == 0) return;  // the sibling will merge
+      if (s_old != nsib - 1) return;  // a sibling still to arrive will merge
       if (t == 0) cnt[next_off + parent] = 0;
       __threadfence();
-      const int left = j & ~1;
-      ids[t] = t < 2 * TB ? ((volatile int32_t*)cand)[(level_off + left + (t >= TB)) * TB + (t % TB)] : -1;
+      ids[t] = t < nsib * TB ? ((volatile int32_t*)cand)[(level_off + first + t / TB) * TB + (t % TB)] : -1;
       __syncthreads();
-      okrow = t < 2 * TB && ids[t] >= R0 && ids[t] < np;
-      if (t < 2 * TB && !okrow) flag_bad(a, s, 2);
+      okrow = t < nsib * TB && ids[t] >= R0 && ids[t] < np;
+      if (t < nsib * TB && !okrow) flag_bad(a, s, 2);
       if (okrow) load_row_regs(arena, a, s, ids[t], xr, xi);
       level_off = next_off; n_l = n_next; j = parent;
       code = 3;
