@@ -50,9 +50,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="head16", choices=["head16", "cube8", "head8"],
+    ap.add_argument("--workload", default="head16",
+                    choices=["head16", "cube8", "head8", "krylov24", "batch32", "head32r3"],
                     help="head16: the benchmark workload; cube8: 8^3 r=1 plane wave (FP64 factors); "
-                         "head8: 8^3 r=2 8 subdomains (1.9 GB arena, for kernel profiles)")
+                         "head8: 8^3 r=2 8 subdomains (1.9 GB arena, for kernel profiles); krylov24: "
+                         "24^3 r=2 512 subdomains without overlap (464 MB matrix, small arena, for Krylov "
+                         "kernel profiles); batch32: 24^3 r=2 256 subdomains, 32 dipoles solved together; "
+                         "head32r3: 32^3 r=3 4096 subdomains without overlap (3.7 M DOFs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--serve-count", type=int, default=12,
@@ -72,6 +76,14 @@ def workload(name):
         w = synth.small(n=8, r=2, nsub=8, overlap=1, restart=100)
         w.name = "head8_r2_s8_d1_profile"
         return w
+    if name == "krylov24":
+        w = synth.small(n=24, r=2, nsub=512, overlap=0, restart=50)
+        w.name = "head24_r2_s512_d0_krylov_profile"
+        return w
+    if name == "batch32":
+        return synth.config(2)
+    if name == "head32r3":
+        return synth.config(4)
     return synth.config(0)
 
 
@@ -192,6 +204,22 @@ def work_model(O, h, nsub, k):
     return upd, apply_bytes
 
 
+TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+
+
+def measured_traffic(kernel, workload, panel):
+    """DRAM bytes per launch from the committed ncu capture of this kernel on this workload and
+    panel width (None when there is none)."""
+    try:
+        with open(TRAFFIC) as f:
+            t = json.load(f)[kernel]
+        if t["workload"] == workload and int(t["lu_panel"]) == int(panel):
+            return float(t["bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
 def roofline(timings, upd_flops_per_factor, apply_bytes, factors, hbm, bf16_burst):
     cls = {c: v for c, v in timings.items() if v[1] > 0}
     dom = max(cls, key=lambda c: cls[c][0])
@@ -213,7 +241,7 @@ def roofline(timings, upd_flops_per_factor, apply_bytes, factors, hbm, bf16_burs
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
-def oracle_estimate(w, iterations, budget_s=20.0):
+def oracle_estimate(w, iterations, budget_s=20.0, k=1):
     """Time the oracle (as it stands) on a bounded sample of the workload and extrapolate to
     one solve: full global assembly, then local assembly + dense LU + one local solve on the
     smallest subdomains until ~budget_s of CPU work, scaled by sum n_s^3 (LU) and sum n_s^2
@@ -256,7 +284,7 @@ def oracle_estimate(w, iterations, budget_s=20.0):
         h_ = np.vdot(v, y)
         y = y - h_ * v
     t_kry = time.perf_counter() - t4
-    per_solve = t_asm + lu_total + iterations * (apply_total + t_kry)
+    per_solve = (t_asm + lu_total) / k + iterations * (apply_total + t_kry)  # k right-hand sides share A and LU
     return {"value": 1.0 / per_solve, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": (f"global assembly in full; local assembly + LU + 1 solve of the {len(sample)} smallest of "
                        f"{w.nsub} subdomains (n_s {int(smp.min())}-{int(smp.max())}), scaled by sum n_s^3 / "
@@ -343,7 +371,6 @@ def run_ours(args, world, rank, local):
     hbm, bf16, bf16_sus, src = peaks()
     xyz, tets = w.mesh()
     eps, mu = w.materials(xyz, tets)
-    src_pt, direction = w.sources()[0][1], w.sources()[0][2]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     t_mesh0 = time.perf_counter()
@@ -363,19 +390,21 @@ def run_ours(args, world, rank, local):
     else:
         panel, tune_ms = O.oras_autotune(h)   # LU panel width for this problem (set-up, untimed)
     n = O.oras_ndof(h)
-    if w.source == "plane":
-        b_d = O.oras_rhs_plane_wave(h, src_pt, direction.astype(np.complex128), mem=O.ORAS_MEM_DEVICE,
-                                    out=torch.empty(n, dtype=torch.complex128, device=dev))
-    else:
-        b_d = O.oras_rhs_dipole(h, src_pt, direction, mem=O.ORAS_MEM_DEVICE,
-                                out=torch.empty(n, dtype=torch.complex128, device=dev))
+    srcs = w.sources()
+    krhs = len(srcs)
+    b_d = torch.empty(krhs, n, dtype=torch.complex128, device=dev)  # N x k column-major
+    for j, (kind, pt, direction) in enumerate(srcs):
+        if kind == "plane":
+            O.oras_rhs_plane_wave(h, pt, direction.astype(np.complex128), mem=O.ORAS_MEM_DEVICE, out=b_d[j])
+        else:
+            O.oras_rhs_dipole(h, pt, direction, mem=O.ORAS_MEM_DEVICE, out=b_d[j])
     x_d = torch.empty_like(b_d)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def step():
         O.oras_factor(h, eps_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
-        _, info, rc = O.oras_solve(h, b_d, w.tol, mem=O.ORAS_MEM_DEVICE, out=x_d)
-        if rc != O.ORAS_OK or not info[0]["converged"]:
+        _, info, rc = O.oras_solve(h, b_d, w.tol, k=krhs, mem=O.ORAS_MEM_DEVICE, out=x_d)
+        if rc != O.ORAS_OK or not all(i["converged"] for i in info):
             raise RuntimeError(f"solve did not converge: {info}")
         return info
 
@@ -406,18 +435,22 @@ def run_ours(args, world, rank, local):
     O.oras_set_timing(h, 0)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), world)
-    value = aggregate(total_ms, args.steps * 1, world)
+    value = aggregate(total_ms, args.steps * krhs, world)
     # true residual of the last field, FP64, on the host with the library's own A (sanity)
     x_last = x_d.cpu().numpy()
-    iters = infos[-1][0]["iterations"]
+    iters = max(i["iterations"] for i in infos[-1])
     upd_flops, apply_bytes = work_model(O, h, w.nsub, 1)
     dom, roof = roofline(timings, upd_flops, apply_bytes, args.steps, hbm, bf16)
+    if dom == "lu_update":
+        roof["traffic"] = measured_traffic("k_lu_update_tc", w.name, panel)
+        roof["traffic_note"] = ("DRAM read+write bytes per launch, averaged over every trailing-update launch of a "
+                                "factorisation, from the ncu capture recorded in profiles/roofline_traffic.json")
     arena = O.oras_arena_bytes(h)
     O.oras_destroy(h)
     # ---------------- end to end through the public API with host buffers
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, args.steps)
-    b_host = torch.from_numpy(b_d.cpu().numpy()).pin_memory().numpy()
-    x_host = torch.empty(n, dtype=torch.complex128).pin_memory().numpy()
+    b_host = torch.from_numpy(b_d.cpu().numpy().T.copy()).pin_memory().numpy()   # (N, k)
+    x_host = torch.empty(n, krhs, dtype=torch.complex128).pin_memory().numpy()
     h2d = xyz.nbytes + tets.nbytes + eps.nbytes + mu.nbytes + b_host.nbytes
     d2h = x_host.nbytes
     barrier(world)
@@ -426,14 +459,14 @@ def run_ours(args, world, rank, local):
     for _ in range(e2e_steps):
         he = O.oras_setup(xyz, tets, eps, mu, w.k0, w.r, w.nsub, w.overlap, factor_bits=w.factor_bits,
                           restart=w.restart, lu_panel=panel)
-        xe, info_e, rc = O.oras_solve(he, b_host, w.tol)
-        x_host[:] = xe
+        xe, info_e, rc = O.oras_solve(he, b_host, w.tol, k=krhs)
+        x_host[:] = np.asarray(xe).reshape(n, krhs)
         O.oras_destroy(he)
         if rc != O.ORAS_OK:
             raise RuntimeError("e2e solve did not converge")
     torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(time.perf_counter() - e0, world)
-    e2e_val = world * e2e_steps / e2e_s
+    e2e_val = world * e2e_steps * krhs / e2e_s
     serving = None
     if rank == 0 and args.serve_count > 0:
         serving = serving_replay(O, args.serve_count, args.serve_slots, device=local, max_iter=args.serve_max_iter)
@@ -441,20 +474,20 @@ def run_ours(args, world, rank, local):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = oracle_estimate(w, iters)
+            cpu = oracle_estimate(w, iters, k=krhs)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 factors / c128 Krylov", "data": "synthetic",
             "config": {"workload": w.name, "mesh": f"{w.n}^3 x 6 tets (Kuhn)", "degree": w.r, "ndof": n,
                        "nsub": w.nsub, "overlap_layers": w.overlap, "restart": w.restart, "tol": w.tol,
-                       "rhs_per_solve": 1, "factor_arena_bytes": arena,
+                       "rhs_per_step": krhs, "factor_arena_bytes": arena,
                        "l2": "512 MiB buffer written between timed steps; the step itself streams the "
                              f"{arena / 1e9:.1f} GB factor arena",
                        "step": "oras_factor (element matrices, A, A_s, batched LU) + oras_solve, device buffers",
                        "mesh_setup_s_untimed": t_mesh, "parallelism": f"replicas x{world}",
                        "lu_panel": panel, "lu_panel_autotune_ms": {str(k_): round(v_, 1) for k_, v_ in tune_ms.items()}},
-            "iterations": iters, "true_relres": infos[-1][0]["relres"],
+            "iterations": iters, "true_relres": max(i["relres"] for i in infos[-1]),
             "phase_ms_per_step": {c: v[0] / args.steps for c, v in timings.items() if v[1] > 0},
             "roofline": roof,
             "cpu_baseline": cpu,

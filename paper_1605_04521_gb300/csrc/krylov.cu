@@ -76,6 +76,17 @@ __device__ __forceinline__ void df_add(float& h1, float& l1, float h2, float l2)
   l1 += es + l2;
 }
 
+// Exact float -> double by bit construction on the integer pipes (the conversion instruction runs
+// on the FP64 pipe, which GB300 keeps narrow).  Subnormal floats become zero.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ex = (u >> 23) & 0xFFu;
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  if (ex == 0) return __longlong_as_double((long long)sign);
+  const uint64_t e64 = ex == 0xFFu ? 0x7FFull : (uint64_t)ex + 896u;  // rebias 127 -> 1023
+  return __longlong_as_double((long long)(sign | (e64 << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
+}
+
 // vals_df[p] = {re_hi, im_hi, re_lo, im_lo}
 __global__ void k_split_vals(int64_t nnz, const cplx* __restrict__ vals, float4* __restrict__ out) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,7 +138,7 @@ __global__ void __launch_bounds__(256) k_spmv_df(int64_t n, const int64_t* __res
       df_add(rh[q], rl[q], h2, l2);
       df_add(ih[q], il[q], h3, l3);
     }
-    if (live && sl == 0) y[row * k + r0 + q] = {(double)rh[q] + (double)rl[q], (double)ih[q] + (double)il[q]};
+    if (live && sl == 0) y[row * k + r0 + q] = {f2d_bits(rh[q]) + f2d_bits(rl[q]), f2d_bits(ih[q]) + f2d_bits(il[q])};
   }
 }
 
