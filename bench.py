@@ -388,7 +388,8 @@ def run_ours(args, world, rank, local):
         O.oras_set_stream(h, stream.cuda_stream)
         O.oras_factor(h, eps_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
     else:
-        panel, tune_ms = O.oras_autotune(h)   # LU panel width for this problem (set-up, untimed)
+        panel, tune_ms = O.oras_autotune(h)   # LU tile shapes for this problem (set-up, untimed)
+    group = O.oras_lu_group(h)
     n = O.oras_ndof(h)
     srcs = w.sources()
     krhs = len(srcs)
@@ -458,7 +459,7 @@ def run_ours(args, world, rank, local):
     e0 = time.perf_counter()
     for _ in range(e2e_steps):
         he = O.oras_setup(xyz, tets, eps, mu, w.k0, w.r, w.nsub, w.overlap, factor_bits=w.factor_bits,
-                          restart=w.restart, lu_panel=panel)
+                          restart=w.restart, lu_panel=panel, lu_group=group)
         xe, info_e, rc = O.oras_solve(he, b_host, w.tol, k=krhs)
         x_host[:] = np.asarray(xe).reshape(n, krhs)
         O.oras_destroy(he)
@@ -486,7 +487,8 @@ def run_ours(args, world, rank, local):
                              f"{arena / 1e9:.1f} GB factor arena",
                        "step": "oras_factor (element matrices, A, A_s, batched LU) + oras_solve, device buffers",
                        "mesh_setup_s_untimed": t_mesh, "parallelism": f"replicas x{world}",
-                       "lu_panel": panel, "lu_panel_autotune_ms": {str(k_): round(v_, 1) for k_, v_ in tune_ms.items()}},
+                       "lu_panel": panel, "lu_group": group,
+                       "lu_autotune_ms": {str(k_): round(v_, 1) for k_, v_ in tune_ms.items()}},
             "iterations": iters, "true_relres": max(i["relres"] for i in infos[-1]),
             "phase_ms_per_step": {c: v[0] / args.steps for c, v in timings.items() if v[1] > 0},
             "roofline": roof,

@@ -94,7 +94,9 @@ typedef struct {
                               /*   ORAS_LU_CUDA_CORES: FP32 CUDA-core updates             */
   int32_t lu_panel;           /* outer LU panel width in 64-column tiles [8]: the trailing */
                               /*   matrix is updated once per panel                        */
-  int32_t reserved[9];
+  int32_t lu_group;           /* tensor-core update: 128-row output blocks per raster group  */
+                              /*   (operand reuse in L2) [8]                                 */
+  int32_t reserved[8];
 } oras_options;
 
 /* Per right-hand-side outcome of oras_solve. */
@@ -227,16 +229,21 @@ int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t
  * Errors: STATE (no oras_factor yet), INVALID_ARG, CUDA. */
 int oras_precond_noalloc(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k);
 
-/* Autotuner of the batched LU's outer panel width (tiles of 64 columns per trailing update;
- * trades the inner panel updates against the passes over the trailing matrix).  Factorises the
- * handle's current problem (materials of the last oras_factor, on the handle's stream) once per
- * candidate width 4, 6, 8, 12, 16, keeps the fastest in the handle's options (lu_panel) and leaves
- * the factors of that width.  The choice is cached for the process under the problem's shape
+/* Autotuner of the batched LU's tile shapes: the outer panel width (tiles of 64 columns per
+ * trailing update; trades the inner panel updates against the passes over the trailing matrix)
+ * and the raster group of the tensor-core update (output blocks that share operands in L2).
+ * Factorises the handle's current problem (materials of the last oras_factor, on the handle's
+ * stream) once per candidate width 4, 6, 8, 12, 16 (group 8), then once per group 16, 32, 64 at
+ * the best width, keeps the fastest pair in the handle's options (lu_panel, lu_group) and leaves
+ * the factors of that pair.  The choice is cached for the process under the problem's shape
  * (factor precision, LU engine, padded subdomain orders): a later handle of the same shape takes
  * it without timing.  panel: chosen width (or NULL); ms[0..nms): the candidates' factorisation
- * times in milliseconds (-1 when taken from the cache; NULL allowed).
+ * times in milliseconds, widths then groups (8 entries; -1 when taken from the cache; NULL
+ * allowed).
  * Errors: INVALID_ARG, STATE (no oras_factor yet), and those of oras_factor. */
 int oras_autotune(oras_handle* h, int32_t* panel, double* ms, int32_t nms);
+/* The raster group oras_autotune chose for the handle (0 before tuning: the default). */
+int32_t oras_lu_group(const oras_handle* h);
 
 /* Device bytes that oras_factor followed by an oras_solve of k right-hand sides allocate for
  * this handle (factor arena, inverted diagonal blocks, A, element matrices, Krylov basis of

@@ -461,54 +461,63 @@ int oras_factor(oras_handle* h, const oras_complex* eps_r, const oras_complex* m
 // (CUDA events on the handle's stream); the fastest is kept in the handle's options and cached
 // for the process under the problem's shape, so later handles of the same shape reuse it.
 static std::mutex g_tune_mu;
-static std::map<std::vector<int64_t>, int> g_tune_cache;
+static std::map<std::vector<int64_t>, std::pair<int, int>> g_tune_cache;  // shape -> (panel, group)
 
 int oras_autotune(oras_handle* h, int32_t* panel, double* ms, int32_t nms) {
   if (!h) return ORAS_ERR_INVALID_ARG;
   if (!h->factored) { h->err = "oras_autotune: call oras_factor first"; return ORAS_ERR_STATE; }
-  static const int cand[] = {4, 6, 8, 12, 16};
-  constexpr int NC = sizeof(cand) / sizeof(cand[0]);
+  static const int widths[] = {4, 6, 8, 12, 16};
+  static const int groups[] = {16, 32, 64};  // after the widths, which run with the default group 8
+  constexpr int NW = sizeof(widths) / sizeof(widths[0]), NG = sizeof(groups) / sizeof(groups[0]);
   std::vector<int64_t> key = {h->opt.factor_bits, h->opt.lu_engine, h->mesh.nsub};
   key.insert(key.end(), h->mesh.sub_np.begin(), h->mesh.sub_np.end());
-  int best = -1;
+  std::pair<int, int> best(-1, -1);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) best = it->second;
   }
   for (int q = 0; q < nms && ms; ++q) ms[q] = -1.0;
-  if (best < 0) {
+  if (best.first < 0) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    const oras_options keep = h->opt;
     double tbest = 1e300;
-    const int keep = h->opt.lu_panel;
-    for (int c = 0; c < NC; ++c) {
-      h->opt.lu_panel = cand[c];
+    auto time_one = [&](int w, int g, int slot) -> int {
+      h->opt.lu_panel = w;
+      h->opt.lu_group = g;
       cudaEventRecord(e0, h->dev.stream);
       int rc = factor_device(h);
       cudaEventRecord(e1, h->dev.stream);
       cudaEventSynchronize(e1);
       float t = 0.0f;
       cudaEventElapsedTime(&t, e0, e1);
-      if (rc) {
-        h->opt.lu_panel = keep;
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return rc;
-      }
-      if (ms && c < nms) ms[c] = t;
-      if (t < tbest) { tbest = t; best = cand[c]; }
-    }
+      if (rc) return rc;
+      if (ms && slot < nms) ms[slot] = t;
+      if (t < tbest) { tbest = t; best = {w, g}; }
+      return ORAS_OK;
+    };
+    int rc = ORAS_OK;
+    for (int c = 0; c < NW && rc == ORAS_OK; ++c) rc = time_one(widths[c], 8, c);
+    const int w = best.first;
+    for (int c = 0; c < NG && rc == ORAS_OK; ++c) rc = time_one(w, groups[c], NW + c);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (rc) {
+      h->opt = keep;
+      return rc;
+    }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;
   }
-  h->opt.lu_panel = best;
-  if (panel) *panel = best;
-  return factor_device(h);  // leave the factors of the chosen width
+  h->opt.lu_panel = best.first;
+  h->opt.lu_group = best.second;
+  if (panel) *panel = best.first;
+  return factor_device(h);  // leave the factors of the chosen shape
 }
+
+int32_t oras_lu_group(const oras_handle* h) { return h ? h->opt.lu_group : -1; }
 
 
 int oras_setup(const oras_problem* p, const oras_options* o, oras_handle** out) {

@@ -27,7 +27,7 @@ namespace oras {
 constexpr int TC_THREADS = 128;
 constexpr int TC_STAGES = 2;
 constexpr int TC_BN = 4;                                 // output tile columns per CTA (N = 256)
-constexpr int TC_GROUP = 8;                              // block rows per raster group (L2 reuse)
+constexpr int TC_GROUP = 8;                              // default block rows per raster group (L2 reuse)
 constexpr uint32_t TC_BOX_BYTES = 64 * 32 * 4;           // 64 rows x 32 floats
 constexpr uint32_t TC_STAGE_BYTES = (4 + 2 * TC_BN) * TC_BOX_BYTES;  // A_re, A_im (2 tiles), B_re, B_im (4)
 constexpr uint32_t TC_TMEM_COLS = 512;
@@ -38,6 +38,7 @@ struct TcArgs {
   float* arena;
   UpdArgs u;
   int32_t* status;
+  int group;                 // block rows per raster group
 };
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
@@ -94,15 +95,15 @@ __host__ __device__ __forceinline__ void region_blocks_of(const Region& r, int64
   nbj = (j1 - j0 + TC_BN - 1) / TC_BN;
 }
 
-__device__ __forceinline__ bool tc_block(const UpdArgs& u, int64_t nts, int64_t e, int64_t& I0, int64_t& J0,
-                                         int& ni, int& nj) {
+__device__ __forceinline__ bool tc_block(const UpdArgs& u, int64_t nts, int64_t e, int group, int64_t& I0,
+                                         int64_t& J0, int& ni, int& nj) {
   for (int q = 0; q < u.nreg; ++q) {
     int64_t nbi, nbj, i0, i1, j0, j1;
     region_blocks_of(u.reg[q], nts, nbi, nbj, i0, i1, j0, j1);
     if (e < nbi * nbj) {
-      const int64_t gsize = (int64_t)TC_GROUP * nbj;
-      const int64_t g = e / gsize, first = g * TC_GROUP;
-      const int64_t gs = nbi - first < TC_GROUP ? nbi - first : TC_GROUP;
+      const int64_t gsize = (int64_t)group * nbj;
+      const int64_t g = e / gsize, first = g * group;
+      const int64_t gs = nbi - first < group ? nbi - first : group;
       const int64_t loc = e % gsize;
       const int64_t bi = first + loc % gs, bj = loc / gs;
       I0 = i0 + 2 * bi;
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
   const int64_t nts = a.np[s] / TB;
   int64_t I0, J0;
   int ni, nj;
-  if (!tc_block(a.u, nts, blockIdx.x, I0, J0, ni, nj)) return;
+  if (!tc_block(a.u, nts, blockIdx.x, a.group, I0, J0, ni, nj)) return;
   int64_t kk1 = a.u.kk1 < nts ? a.u.kk1 : nts;
   const int64_t kk0 = a.u.kk0;
   if (kk1 <= kk0) return;
@@ -467,6 +468,7 @@ int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts) {
   a.arena = (float*)d.arena;
   a.u = u;
   a.status = d.status;
+  a.group = h->opt.lu_group > 0 ? h->opt.lu_group : TC_GROUP;
   const size_t smem = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
   allow_max_smem((const void*)k_lu_update_tc);
   int pb = prof_begin(h);

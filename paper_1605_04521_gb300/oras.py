@@ -50,7 +50,7 @@ class oras_problem(C.Structure):
 class oras_options(C.Structure):
     _fields_ = [("restart", C.c_int32), ("max_iter", C.c_int32), ("factor_bits", C.c_int32),
                 ("weights", C.c_int32), ("overlap_kind", C.c_int32), ("lu_engine", C.c_int32),
-                ("lu_panel", C.c_int32), ("reserved", C.c_int32 * 9)]
+                ("lu_panel", C.c_int32), ("lu_group", C.c_int32), ("reserved", C.c_int32 * 8)]
 
 
 class oras_info(C.Structure):
@@ -109,6 +109,7 @@ EXPORTS = {
     "oras_precond_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "oras_footprint": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
     "oras_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_int32]),
+    "oras_lu_group": (C.c_int32, [C.c_void_p]),
     "oras_server_create": (C.c_int, [C.POINTER(oras_server_config), C.POINTER(C.c_void_p)]),
     "oras_submit": (C.c_int64, [C.c_void_p, C.POINTER(oras_problem), C.POINTER(oras_options), C.c_void_p,
                                 C.c_int64, C.c_void_p, C.c_int32, C.c_double]),
@@ -183,11 +184,12 @@ def _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part):
     return p, keep
 
 
-def _options(restart=0, max_iter=0, factor_bits=0, weights=0, overlap_kind=0, lu_engine=0, lu_panel=0):
+def _options(restart=0, max_iter=0, factor_bits=0, weights=0, overlap_kind=0, lu_engine=0, lu_panel=0, lu_group=0):
     o = oras_options()
     o.restart, o.max_iter, o.factor_bits, o.weights, o.overlap_kind = restart, max_iter, factor_bits, weights, overlap_kind
     o.lu_engine = lu_engine
     o.lu_panel = lu_panel
+    o.lu_group = lu_group
     return o
 
 
@@ -392,12 +394,20 @@ def oras_precond_noalloc(h, v, z, k=1):
 
 
 def oras_autotune(h):
-    """Returns (panel width chosen, {width: factorisation ms} (empty when cached))."""
+    """Returns (panel width chosen, {(width, group): factorisation ms} (empty when cached)).
+    The chosen raster group is oras_lu_group(h)."""
     panel = C.c_int32()
-    ms = np.full(5, -1.0)
-    _check(h, lib.oras_autotune(h, C.byref(panel), _ptr(ms), 5))
-    times = {w: t for w, t in zip((4, 6, 8, 12, 16), ms) if t >= 0}
+    ms = np.full(8, -1.0)
+    _check(h, lib.oras_autotune(h, C.byref(panel), _ptr(ms), 8))
+    cands = [(w, 8) for w in (4, 6, 8, 12, 16)]
+    best_w = max(((w, t) for (w, _), t in zip(cands, ms[:5]) if t >= 0), key=lambda x: -x[1], default=(panel.value, 0))[0]
+    cands += [(best_w, g) for g in (16, 32, 64)]
+    times = {c: t for c, t in zip(cands, ms) if t >= 0}
     return panel.value, times
+
+
+def oras_lu_group(h):
+    return lib.oras_lu_group(h)
 
 
 def oras_footprint(h, k=1):

@@ -342,7 +342,9 @@ def test_autotuned_panel_width(O):
     h = gpu_handle(O, w)
     try:
         panel, times = O.oras_autotune(h)
-        assert set(times) == {4, 6, 8, 12, 16} and panel == min(times, key=times.get)
+        assert {w for w, g in times if g == 8} == {4, 6, 8, 12, 16} and len(times) == 8
+        best = min(times, key=times.get)
+        assert panel == best[0] and O.oras_lu_group(h) == best[1]
         x, info, rc = O.oras_solve(h, p.B[:, 0], w.tol)
         assert rc == O.ORAS_OK
         assert np.linalg.norm(p.B[:, 0] - p.A @ x) / np.linalg.norm(p.B[:, 0]) <= 1e-8
@@ -352,6 +354,24 @@ def test_autotuned_panel_width(O):
     h2 = gpu_handle(O, w)      # same shape: the cached choice, no timing
     try:
         panel2, times2 = O.oras_autotune(h2)
-        assert panel2 == panel and times2 == {}
+        assert panel2 == panel and times2 == {} and O.oras_lu_group(h2) == best[1]
     finally:
         O.oras_destroy(h2)
+
+
+def test_raster_group_does_not_change_factors(O):
+    """The raster group only orders the tensor-core update's output blocks: every group gives
+    bit-identical factors, so the same preconditioned vector."""
+    w = synth.small(n=6, r=2, nsub=4, overlap=1)
+    rng = np.random.default_rng(41)
+    zs = []
+    for group in (8, 3, 64):
+        h = gpu_handle(O, w, lu_panel=4, lu_group=group)
+        try:
+            n = O.oras_ndof(h)
+            if not zs:
+                v = rng.normal(size=n) + 1j * rng.normal(size=n)
+            zs.append(O.oras_precond(h, v))
+        finally:
+            O.oras_destroy(h)
+    assert np.array_equal(zs[0], zs[1]) and np.array_equal(zs[0], zs[2])
