@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--serve-count", type=int, default=12,
                     help="requests of the serving stream replayed after the main measurement (0: none)")
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--factor-bits", type=int, default=0, choices=[0, 32, 64],
+                    help="local factor precision (0: the workload's; 64: the plain FP64 path)")
     ap.add_argument("--lu-panel", type=int, default=0,
                     help="LU outer panel width in tiles (0: picked by oras_autotune at set-up)")
     ap.add_argument("--serve-max-iter", type=int, default=60,
@@ -220,10 +222,19 @@ def measured_traffic(kernel, workload, panel):
     return None
 
 
-def roofline(timings, upd_flops_per_factor, apply_bytes, factors, hbm, bf16_burst):
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64, nominal (no measured figure in the peaks file)
+
+
+def roofline(timings, upd_flops_per_factor, apply_bytes, factors, hbm, bf16_burst, factor_bits=32):
     cls = {c: v for c, v in timings.items() if v[1] > 0}
     dom = max(cls, key=lambda c: cls[c][0])
     ms, launches = cls[dom]
+    if dom == "lu_update" and factor_bits == 64:
+        achieved = upd_flops_per_factor * factors / (ms / 1e3) / 1e12
+        return dom, {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                     "kernel": "k_lu_update<double> (FP64 CUDA-core trailing update)",
+                     "peak_note": "nominal GB300 dense FP64 (not measured)"}
     if dom == "lu_update":
         flops = upd_flops_per_factor * factors
         achieved = flops / (ms / 1e3) / 1e12
@@ -368,6 +379,9 @@ def run_ours(args, world, rank, local):
     build.build()
     from paper_1605_04521_gb300 import oras as O
     w = workload(args.workload)
+    if args.factor_bits:
+        w.factor_bits = args.factor_bits
+        w.name += f"_factors{args.factor_bits}"
     hbm, bf16, bf16_sus, src = peaks()
     xyz, tets = w.mesh()
     eps, mu = w.materials(xyz, tets)
@@ -441,8 +455,8 @@ def run_ours(args, world, rank, local):
     x_last = x_d.cpu().numpy()
     iters = max(i["iterations"] for i in infos[-1])
     upd_flops, apply_bytes = work_model(O, h, w.nsub, 1)
-    dom, roof = roofline(timings, upd_flops, apply_bytes, args.steps, hbm, bf16)
-    if dom == "lu_update":
+    dom, roof = roofline(timings, upd_flops, apply_bytes, args.steps, hbm, bf16, w.factor_bits)
+    if dom == "lu_update" and w.factor_bits == 32:
         roof["traffic"] = measured_traffic("k_lu_update_tc", w.name, panel)
         roof["traffic_note"] = ("DRAM read+write bytes per launch, averaged over every trailing-update launch of a "
                                 "factorisation, from the ncu capture recorded in profiles/roofline_traffic.json")
@@ -479,7 +493,8 @@ def run_ours(args, world, rank, local):
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64 factors / c128 Krylov", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("c128 factors / c128 Krylov" if w.factor_bits == 64 else "c64 factors / c128 Krylov"), "data": "synthetic",
             "config": {"workload": w.name, "mesh": f"{w.n}^3 x 6 tets (Kuhn)", "degree": w.r, "ndof": n,
                        "nsub": w.nsub, "overlap_layers": w.overlap, "restart": w.restart, "tol": w.tol,
                        "rhs_per_step": krhs, "factor_arena_bytes": arena,
