@@ -64,6 +64,10 @@ enum { ORAS_MEM_HOST = 0, ORAS_MEM_DEVICE = 1 };
 enum { ORAS_WEIGHTS_POU = 0 /* ORAS: R_s^T D_s */, ORAS_WEIGHTS_NONE = 1 /* OAS, Sec. 4 */ };
 enum { ORAS_OVERLAP_VERTEX = 0, ORAS_OVERLAP_FACE = 1 };
 enum { ORAS_LU_AUTO = 0 /* tensor cores for FP32 factors */, ORAS_LU_CUDA_CORES = 1 };
+/* Transmission condition of the local problems (Sec. 4): impedance (ORAS: A_s = sum of the
+ * element matrices of Omega_s^delta + i w~ S on its boundary faces) or Dirichlet (RAS:
+ * A_s = R_s A R_s^T, the rows and columns N_s of the global matrix). */
+enum { ORAS_TRANSMISSION_IMPEDANCE = 0, ORAS_TRANSMISSION_DIRICHLET = 1 };
 
 /* Problem statement (Sec. 2-4).  All pointers are host pointers, read during the call. */
 typedef struct {
@@ -96,7 +100,8 @@ typedef struct {
                               /*   matrix is updated once per panel                        */
   int32_t lu_group;           /* tensor-core update: 128-row output blocks per raster group  */
                               /*   (operand reuse in L2) [8]                                 */
-  int32_t reserved[8];
+  int32_t transmission;       /* ORAS_TRANSMISSION_IMPEDANCE [default] or _DIRICHLET (RAS) */
+  int32_t reserved[7];
 } oras_options;
 
 /* Per right-hand-side outcome of oras_solve. */

@@ -153,15 +153,29 @@ def local_matrix(topo: Topology, xyz, eps_r, mu_r, k0, dec: Decomposition, s):
     return A
 
 
-class ORAS:
-    """M^{-1} v = sum_s R_s^T D_s A_s^{-1} R_s v with LU-factored dense A_s."""
+def restricted_matrix(A_global, dec: Decomposition, s):
+    """Dense R_s A R_s^T: the rows and columns N_s of the global matrix (restricted additive
+    Schwarz with Dirichlet transmission, the variant the paper compares ORAS against, Sec. 4)."""
+    Ns = dec.dofs[s]
+    return A_global[Ns][:, Ns].toarray()
 
-    def __init__(self, topo, xyz, eps_r, mu_r, k0, dec: Decomposition, weights="pou"):
+
+class ORAS:
+    """M^{-1} v = sum_s R_s^T D_s A_s^{-1} R_s v with LU-factored dense A_s.
+
+    transmission "impedance": A_s of local_matrix (ORAS, Sec. 4); "dirichlet": A_s = R_s A R_s^T
+    (RAS), which needs the global matrix A_global."""
+
+    def __init__(self, topo, xyz, eps_r, mu_r, k0, dec: Decomposition, weights="pou",
+                 transmission="impedance", A_global=None):
         self.dec = dec
         self.n = topo.ndof
         self.lu = []
         for s in range(len(dec.dofs)):
-            A = local_matrix(topo, xyz, eps_r, mu_r, k0, dec, s)
+            if transmission == "dirichlet":
+                A = restricted_matrix(A_global, dec, s)
+            else:
+                A = local_matrix(topo, xyz, eps_r, mu_r, k0, dec, s)
             self.lu.append(sla.lu_factor(A, check_finite=False))
         self.weights = weights
 

@@ -386,6 +386,11 @@ int oras_create(const oras_problem* p, const oras_options* o, oras_handle** out)
     delete h;
     return ORAS_ERR_INVALID_ARG;
   }
+  if (h->opt.transmission != ORAS_TRANSMISSION_IMPEDANCE && h->opt.transmission != ORAS_TRANSMISSION_DIRICHLET) {
+    g_err = "oras_create: unknown transmission condition";
+    delete h;
+    return ORAS_ERR_INVALID_ARG;
+  }
   int rc;
   try {
     rc = host_setup(p, h->opt.overlap_kind, h->mesh, g_err);

@@ -120,6 +120,7 @@ struct RowArgs {
   const cplx* elem; const double* fmat;
   const cplx* eps; const cplx* mu;
   const uint32_t* member; int64_t member_words;
+  int dirichlet;             // local rows: 1 = rows of the global matrix (RAS), 0 = ORAS local problem
 };
 
 __device__ __forceinline__ int bsearch32(const int32_t* a, int n, int32_t key) {
@@ -234,7 +235,8 @@ __global__ void k_local_rows(RowArgs A, int nsub, int64_t total_rows, const int6
   int64_t r0 = A.rowptr[g];
   int rn = (int)(A.rowptr[g + 1] - r0);
   const int32_t* rc = A.cols + r0;
-  accumulate_row<true>(A, g, s, acc, rn, rc);
+  if (A.dirichlet) accumulate_row<false>(A, g, s, acc, rn, rc);  // R_s A R_s^T: the global row
+  else accumulate_row<true>(A, g, s, acc, rn, rc);
   for (int p = lane; p < rn; p += 32) {
     int lj = bsearch32(Ns, (int)ns, rc[p]);
     if (lj >= 0) put(li, lj, R(acc[p].re), R(acc[p].im));
@@ -427,6 +429,7 @@ static RowArgs row_args(const oras_handle* h, double k0) {
   A.rowptr = d.rowptr; A.cols = d.cols;
   A.elem = d.elem; A.fmat = d.fmat; A.eps = d.eps; A.mu = d.mu;
   A.member = d.member; A.member_words = m.member_words;
+  A.dirichlet = h->opt.transmission == ORAS_TRANSMISSION_DIRICHLET ? 1 : 0;
   return A;
 }
 

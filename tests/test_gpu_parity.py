@@ -375,3 +375,28 @@ def test_raster_group_does_not_change_factors(O):
         finally:
             O.oras_destroy(h)
     assert np.array_equal(zs[0], zs[1]) and np.array_equal(zs[0], zs[2])
+
+
+@pytest.mark.parametrize("bits,tol", [(64, 1e-9), (32, TOL_APPLY_F32)])
+def test_ras_dirichlet_transmission(O, bits, tol):
+    """RAS (A_s = R_s A R_s^T) against the oracle's RAS, and the paper's comparison: the ORAS
+    impedance transmission needs fewer FGMRES iterations than the Dirichlet one."""
+    from oracle import dd
+    w = synth.small(n=4, r=2, nsub=8, overlap=1)
+    p = problem.from_workload(w)
+    ras = dd.ORAS(p.topo, p.xyz, p.eps_r, p.mu_r, p.k0, p.dec, transmission="dirichlet", A_global=p.A.tocsr())
+    h = gpu_handle(O, w, factor_bits=bits, transmission=O.ORAS_TRANSMISSION_DIRICHLET)
+    h2 = gpu_handle(O, w, factor_bits=bits)
+    try:
+        rng = np.random.default_rng(51)
+        v = rng.normal(size=p.topo.ndof) + 1j * rng.normal(size=p.topo.ndof)
+        assert rel(O.oras_precond(h, v), ras.apply(v)) <= tol
+        b = p.B[:, 0]
+        x, info, rc = O.oras_solve(h, b, w.tol)
+        assert rc == O.ORAS_OK
+        assert np.linalg.norm(b - p.A @ x) / np.linalg.norm(b) <= 1e-8
+        _, info2, _ = O.oras_solve(h2, b, w.tol)
+        assert info2[0]["iterations"] < info[0]["iterations"]
+    finally:
+        O.oras_destroy(h)
+        O.oras_destroy(h2)

@@ -103,6 +103,9 @@ def test_error_codes(O):
     with pytest.raises(O.OrasError) as e:
         O.oras_create(xyz, tets, 1, 2, 0, factor_bits=16)
     assert e.value.code == O.ORAS_ERR_INVALID_ARG
+    with pytest.raises(O.OrasError) as e:
+        O.oras_create(xyz, tets, 1, 2, 0, transmission=2)
+    assert e.value.code == O.ORAS_ERR_INVALID_ARG
     # numeric calls before the numeric set-up report a state error without touching a GPU
     h = O.oras_create(xyz, tets, 1, 2, 0)
     try:

@@ -459,3 +459,45 @@ def test_quadrature_rules_exactness():
     for alpha in [(0, 0, 0), (3, 2, 2), (0, 7, 0)]:
         exact = np.prod([factorial(a) for a in alpha]) / factorial(sum(alpha) + 2)
         assert abs(np.sum(w * np.prod(lam ** np.array(alpha), axis=1)) - exact) < 1e-15
+
+
+def test_ras_and_oras_local_rows_agree_inside_the_subdomain():
+    """RAS (Dirichlet transmission, A_s = R_s A R_s^T) and ORAS (impedance transmission, element
+    sums over Omega_s^delta plus i w~ S on its boundary faces, Sec. 4) differ only through the
+    subdomain boundary: the row of a DOF whose every incident tetrahedron lies in Omega_s^delta is
+    the same in both, and boundary rows differ."""
+    from oracle import dd
+    w = synth.small(n=4, r=2, nsub=8, overlap=1)
+    P = problem.from_workload(w, with_oras=False)
+    dec = dd.decompose(P.topo, P.xyz, w.nsub, w.overlap)
+    A = P.A.tocsr()
+    nt, nl = P.topo.dofmap.shape
+    g_all = P.topo.dofmap.ravel()
+    t_all = np.repeat(np.arange(nt), nl)
+    for s in (0, 3, 7):
+        member = np.zeros(nt, dtype=bool)
+        member[dec.tets[s]] = True
+        outside = np.zeros(P.topo.ndof, dtype=bool)
+        outside[g_all[~member[t_all]]] = True          # DOF touched by a tet outside Omega_s^delta
+        Ns = dec.dofs[s]
+        inside = ~outside[Ns]
+        Ar = dd.restricted_matrix(A, dec, s)
+        Ao = dd.local_matrix(P.topo, P.xyz, P.eps_r, P.mu_r, P.k0, dec, s)
+        scale = np.abs(Ar).max()
+        assert inside.any() and (~inside).any()
+        assert np.abs(Ar[inside] - Ao[inside]).max() <= 1e-13 * scale
+        assert np.abs(Ar[~inside] - Ao[~inside]).max(axis=1).min() > 1e-6 * scale
+
+
+@pytest.mark.parametrize("n,r,nsub", [(4, 2, 8), (5, 1, 16)])
+def test_oras_converges_faster_than_ras(n, r, nsub):
+    """The paper's comparison (Sec. 4-5): impedance transmission (ORAS) needs fewer FGMRES
+    iterations than Dirichlet transmission (RAS) with the same subdomains."""
+    from oracle import dd, fgmres
+    w = synth.small(n=n, r=r, nsub=nsub, overlap=1)
+    P = problem.from_workload(w)
+    ras = dd.ORAS(P.topo, P.xyz, P.eps_r, P.mu_r, P.k0, P.dec, transmission="dirichlet", A_global=P.A.tocsr())
+    b = P.B[:, 0]
+    it_o = fgmres.fgmres(lambda v: P.A @ v, P.oras.apply, b, 1e-8, 50, 5000).iterations
+    it_r = fgmres.fgmres(lambda v: P.A @ v, ras.apply, b, 1e-8, 50, 5000).iterations
+    assert it_o < it_r
