@@ -101,7 +101,11 @@ typedef struct {
   int32_t lu_group;           /* tensor-core update: 128-row output blocks per raster group  */
                               /*   (operand reuse in L2) [8]                                 */
   int32_t transmission;       /* ORAS_TRANSMISSION_IMPEDANCE [default] or _DIRICHLET (RAS) */
-  int32_t reserved[7];
+  int32_t graphs;             /* 1: run each Arnoldi step (apply, SpMV, orthogonalisation) as */
+                              /*   a captured CUDA graph, captured on its second use and      */
+                              /*   replayed afterwards; needs a non-default stream            */
+                              /*   (oras_set_stream) and timing off [0]                       */
+  int32_t reserved[6];
 } oras_options;
 
 /* Per right-hand-side outcome of oras_solve. */

@@ -540,6 +540,8 @@ int oras_setup(const oras_problem* p, const oras_options* o, oras_handle** out) 
 void oras_destroy(oras_handle* h) {
   if (!h) return;
   for (auto e : h->evpool) cudaEventDestroy(e);
+  for (auto g : h->step_graph)
+    if (g) cudaGraphExecDestroy(g);
   if (h->dev.uploaded) {
     cudaStreamSynchronize(h->dev.stream);
     dfree_all(h->dev);
@@ -699,6 +701,65 @@ static void spmv_z(oras_handle* h, int k, int j, cplx* y) {
   else launch_spmv_f32(h, (char*)d.Zf + nk * j * 2 * sizeof(float), y, k);
 }
 
+// Drops every captured Arnoldi step and sizes the cache for restart length m.
+static void reset_step_graphs(oras_handle* h, int m) {
+  for (auto g : h->step_graph)
+    if (g) cudaGraphExecDestroy(g);
+  h->step_graph.assign(m, nullptr);
+  h->step_seen.assign(m, 0);
+  h->step_kernels.assign(m, 0);
+}
+
+// Runs Arnoldi step j through `body` (which launches its kernels on the handle's stream): directly
+// on its first use, captured into an executable graph on its second, replayed from then on.  A
+// capture that fails falls back to direct launches.
+template <typename Body>
+static int run_step(oras_handle* h, int j, int k, int m, Body&& body) {
+  auto& d = h->dev;
+  const void* Z = d.factor_bits == 64 ? (const void*)d.Zd : (const void*)d.Zf;
+  if (h->graph_stream != d.stream || h->graph_k != k || h->graph_m != m || h->graph_V != d.V || h->graph_Z != Z ||
+      h->graph_arena != d.arena || h->graph_ybuf != d.ybuf || (int)h->step_graph.size() != m) {
+    reset_step_graphs(h, m);
+    h->graph_stream = d.stream;
+    h->graph_k = k;
+    h->graph_m = m;
+    h->graph_V = d.V;
+    h->graph_Z = Z;
+    h->graph_arena = d.arena;
+    h->graph_ybuf = d.ybuf;
+  }
+  if (h->step_graph[j]) {
+    if (cudaGraphLaunch(h->step_graph[j], d.stream) != cudaSuccess) return ORAS_ERR_CUDA;
+    count_launches(h->step_kernels[j]);
+    return ORAS_OK;
+  }
+  if (h->step_seen[j] == 0) {
+    ++h->step_seen[j];
+    return body();
+  }
+  // second use: capture (the captured launches do not run), instantiate, then launch
+  const int64_t l0 = g_launches.load();
+  if (cudaStreamBeginCapture(d.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return body();
+  const int rc = body();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(d.stream, &graph);
+  const int kernels = (int)(g_launches.load() - l0);
+  count_launches(-kernels);  // captured, not yet run
+  cudaGraphExec_t exec = nullptr;
+  if (rc == ORAS_OK && e == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+    h->step_graph[j] = exec;
+    h->step_kernels[j] = kernels;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();  // a failed capture leaves its error here; the step runs below either way
+  if (h->step_graph[j]) {
+    if (cudaGraphLaunch(h->step_graph[j], d.stream) != cudaSuccess) return ORAS_ERR_CUDA;
+    count_launches(kernels);
+    return ORAS_OK;
+  }
+  return body();
+}
+
 // FGMRES(m) on internal [N][k] vectors: b = d.bk, solution in d.xk.
 static int fgmres(oras_handle* h, int k, double tol, oras_info* info) {
   auto& d = h->dev;
@@ -753,25 +814,31 @@ static int fgmres(oras_handle* h, int k, double tol, oras_info* info) {
     CK(cudaMemcpyAsync(active_d, active.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, d.stream));
     launch_restart(h, k, m, d.tmp, beta_d, active_d, d.V, d.g);
     int kk = 0;
+    const bool graphs = h->opt.graphs && d.stream != nullptr && !h->timing;
     for (int j = 0; j < m; ++j) {
       cplx* Vj = d.V + nk * j;
       cplx* Vn = d.V + nk * (j + 1);
-      int pb = prof_begin(h);
-      if (precond_to_z(h, Vj, k, j)) return ORAS_ERR_CUDA;
-      prof_end(h, KC_APPLY, pb, apply_passes(h, k));
-      pb = prof_begin(h);
-      spmv_z(h, k, j, d.w);
-      prof_end(h, KC_SPMV, pb, (k + 7) / 8);
-      pb = prof_begin(h);
-      launch_dot(h, d.V, d.w, pA, k);
-      cplx* pin = pA;
-      cplx* pout = pB;
-      for (int i = 0; i <= j; ++i) {
-        launch_mgs_step(h, k, m, i, j, d.V + nk * i, i < j ? d.V + nk * (i + 1) : nullptr, d.w, pin, pout, d.H);
-        std::swap(pin, pout);
-      }
-      launch_mgs_finish(h, k, m, j, d.w, Vn, pin, d.H, d.gcs, d.gsn, d.g, res_d);
-      prof_end(h, KC_ORTH, pb, j + 3);
+      // z_j = M^-1 v_j ; w = A z_j ; modified Gram-Schmidt against v_0..v_j ; Givens
+      auto step = [&]() -> int {
+        int pb = prof_begin(h);
+        if (precond_to_z(h, Vj, k, j)) return ORAS_ERR_CUDA;
+        prof_end(h, KC_APPLY, pb, apply_passes(h, k));
+        pb = prof_begin(h);
+        spmv_z(h, k, j, d.w);
+        prof_end(h, KC_SPMV, pb, (k + 7) / 8);
+        pb = prof_begin(h);
+        launch_dot(h, d.V, d.w, pA, k);
+        cplx* pin = pA;
+        cplx* pout = pB;
+        for (int i = 0; i <= j; ++i) {
+          launch_mgs_step(h, k, m, i, j, d.V + nk * i, i < j ? d.V + nk * (i + 1) : nullptr, d.w, pin, pout, d.H);
+          std::swap(pin, pout);
+        }
+        launch_mgs_finish(h, k, m, j, d.w, Vn, pin, d.H, d.gcs, d.gsn, d.g, res_d);
+        prof_end(h, KC_ORTH, pb, j + 3);
+        return ORAS_OK;
+      };
+      if ((graphs ? run_step(h, j, k, m, step) : step()) != ORAS_OK) return ORAS_ERR_CUDA;
       kk = j + 1;
       for (int r = 0; r < k; ++r)
         if (active[r]) ++iters[r];

@@ -213,4 +213,15 @@ struct oras_handle {
   const void* tc_map_base = nullptr;
   int64_t tc_map_tiles = 0;
   bool tc_map_ok = false;
+  // captured Arnoldi steps (oras_options.graphs): one executable graph per inner index j, valid
+  // for the stream, k, restart length and workspace it was captured with
+  std::vector<cudaGraphExec_t> step_graph;
+  std::vector<int> step_seen;                // direct executions of step j since the cache was built
+  std::vector<int> step_kernels;             // kernels in graph j (launch accounting)
+  cudaStream_t graph_stream = nullptr;
+  int graph_k = 0, graph_m = 0;
+  const void* graph_V = nullptr;
+  const void* graph_Z = nullptr;
+  const void* graph_arena = nullptr;
+  const void* graph_ybuf = nullptr;
 };

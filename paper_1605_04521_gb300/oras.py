@@ -53,7 +53,7 @@ class oras_options(C.Structure):
     _fields_ = [("restart", C.c_int32), ("max_iter", C.c_int32), ("factor_bits", C.c_int32),
                 ("weights", C.c_int32), ("overlap_kind", C.c_int32), ("lu_engine", C.c_int32),
                 ("lu_panel", C.c_int32), ("lu_group", C.c_int32), ("transmission", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("graphs", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class oras_info(C.Structure):
@@ -188,13 +188,14 @@ def _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part):
 
 
 def _options(restart=0, max_iter=0, factor_bits=0, weights=0, overlap_kind=0, lu_engine=0, lu_panel=0, lu_group=0,
-             transmission=0):
+             transmission=0, graphs=0):
     o = oras_options()
     o.restart, o.max_iter, o.factor_bits, o.weights, o.overlap_kind = restart, max_iter, factor_bits, weights, overlap_kind
     o.lu_engine = lu_engine
     o.lu_panel = lu_panel
     o.lu_group = lu_group
     o.transmission = transmission
+    o.graphs = graphs
     return o
 
 

@@ -400,3 +400,33 @@ def test_ras_dirichlet_transmission(O, bits, tol):
     finally:
         O.oras_destroy(h)
         O.oras_destroy(h2)
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_captured_arnoldi_steps_replay_identically(O, k):
+    """With oras_options.graphs every Arnoldi step is captured into a CUDA graph on its second use
+    and replayed afterwards (restart 4: later cycles and the second solve replay); the fields are
+    bit-identical to direct launches."""
+    import torch
+    w = synth.small(n=4, r=2, nsub=8, overlap=1, nrhs=k, restart=4)
+    p = problem.from_workload(w, with_oras=False)
+    stream = torch.cuda.Stream()
+    xs = {}
+    for graphs in (0, 1):
+        h = gpu_handle(O, w, graphs=graphs)
+        try:
+            O.oras_set_stream(h, stream.cuda_stream)
+            l0 = O.oras_launch_count()
+            x1, info1, rc1 = O.oras_solve(h, p.B, w.tol, k=k)
+            x2, info2, rc2 = O.oras_solve(h, p.B, w.tol, k=k)
+            assert rc1 == rc2 == O.ORAS_OK
+            assert np.array_equal(x1, x2)
+            assert all(i["iterations"] > 4 for i in info1)  # several restart cycles
+            xs[graphs] = (x1, O.oras_launch_count() - l0)
+        finally:
+            O.oras_destroy(h)
+    assert np.array_equal(xs[0][0], xs[1][0])
+    assert xs[0][1] == xs[1][1]  # the same kernels ran, counted once each
+    X = np.asarray(xs[1][0]).reshape(-1, k)
+    for j in range(k):
+        assert np.linalg.norm(p.B[:, j] - p.A @ X[:, j]) / np.linalg.norm(p.B[:, j]) <= 1e-8
