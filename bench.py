@@ -207,15 +207,18 @@ def work_model(O, h, nsub, k):
 
 
 TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+# the LU schedule and update kernel the committed counters must have been taken on
+UPDATE_VERSION = "tcgen05 update with 128x256 and 128x64 blocks, left-looking panel steps"
 
 
 def measured_traffic(kernel, workload, panel):
     """DRAM bytes per launch from the committed ncu capture of this kernel on this workload and
-    panel width (None when there is none)."""
+    panel width, taken on the current kernel version (None when there is none)."""
     try:
         with open(TRAFFIC) as f:
             t = json.load(f)[kernel]
-        if t["workload"] == workload and int(t["lu_panel"]) == int(panel):
+        if (t["workload"] == workload and int(t["lu_panel"]) == int(panel)
+                and t.get("source_version") == UPDATE_VERSION):
             return float(t["bytes_per_launch"])
     except Exception:
         pass

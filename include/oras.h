@@ -242,7 +242,7 @@ int oras_precond_noalloc(oras_handle* h, const oras_complex* v, oras_complex* z,
  * trailing update; trades the inner panel updates against the passes over the trailing matrix)
  * and the raster group of the tensor-core update (output blocks that share operands in L2).
  * Factorises the handle's current problem (materials of the last oras_factor, on the handle's
- * stream) once per candidate width 4, 6, 8, 12, 16 (group 8), then once per group 16, 32, 64 at
+ * stream) once per candidate width 4, 8, 12, 16, 24 (group 8), then once per group 16, 32, 64 at
  * the best width, keeps the fastest pair in the handle's options (lu_panel, lu_group) and leaves
  * the factors of that pair.  The choice is cached for the process under the problem's shape
  * (factor precision, LU engine, padded subdomain orders): a later handle of the same shape takes

@@ -2,8 +2,12 @@
 // P_s A_s = L_s U_s, over the tiled arena (TB x TB complex tiles, split re/im planes, row-major
 // on and below the block diagonal, column-major above it).
 //
-// Two-level right-looking blocked LU.  Outer panels are W tile columns wide; inside a panel,
-// every tile column k is processed for all subdomains at once by
+// Two-level blocked LU: right-looking across outer panels W tile columns wide, left-looking
+// inside a panel.  Every tile column k of a panel is processed for all subdomains at once by
+//  0. bringing column k, on and below the diagonal, up to date with the panel's earlier steps
+//     (C_Ik -= sum_{k0 <= j < k} L_Ij U_jk: one tile column written per step, where updating
+//     all the panel's remaining columns after every step would rewrite each of them up to W
+//     times);
 //  1. tournament pivoting of the tall panel column: chunks of rows are reduced with partial
 //     pivoting (pivot = max |Re| + |Im|, first on ties) to TB candidate rows each; candidate
 //     sets are merged the same way up a tree (4-way for FP32, 2-way for FP64); the root's choice is the pivot
@@ -11,13 +15,12 @@
 //     LU, Grigori, Demmel, Xiang 2011);
 //  2. the row interchanges of the step, applied to every column (one permutation of at most
 //     2 TB rows);
-//  3. the pivot tile row, right of the panel, receives the updates of the panel's earlier
-//     steps (C_kJ -= sum_{k0 <= j < k} L_kj U_jJ, left-looking);
-//  4. L21 = A21 U11^{-1} below and U12 = L11^{-1} A12 along the whole tile row;
-//  5. the inner update: the panel's remaining columns, every row below, get -= L_Ik U_kJ.
+//  3. the pivot tile row, right of column k, receives the updates of the panel's earlier
+//     steps (C_kJ -= sum_{k0 <= j < k} L_kj U_jJ);
+//  4. L21 = A21 U11^{-1} below and U12 = L11^{-1} A12 along the whole tile row.
 // After the W columns of a panel, the trailing matrix gets one update with a W-tile-deep
 // contraction, C_IJ -= sum_k L_Ik U_kJ, which reads and writes every trailing tile once per
-// panel instead of once per column.  Right of the panel, every row not yet a pivot row stays
+// panel instead of once per column.  Right of column k, every row not yet a pivot row stays
 // in the state of the panel's start until then, so a row interchange never mixes rows that
 // have received different updates.
 // The tree merge uses "last arriver continues" counters, so no block ever waits for another.
@@ -835,6 +838,17 @@ static int lu_run(oras_handle* h) {
       int64_t rows_max = m.max_np - (int64_t)k * TB;
       int nch = (int)((rows_max + CH - 1) / CH);
       int64_t nrem = max_nts - k - 1;
+      if (k > k0) {
+        // left-looking panel step: column k, on and below the diagonal, receives the updates of
+        // the panel's earlier steps just before its pivot search (every row there is in the same
+        // state, so the row interchanges stay consistent)
+        UpdArgs u;
+        u.kk0 = k0;
+        u.kk1 = k;
+        u.nreg = 1;
+        u.reg[0] = {k, INT_MAX, k, k + 1};
+        update(u);
+      }
       int pb = prof_begin(h);
       if (sizeof(R) == 4)
         k_lu_tournament_rg<<<dim3(nch, m.nsub), LU_THREADS, 0, d.stream>>>(a, d.arena);
@@ -845,14 +859,14 @@ static int lu_run(oras_handle* h) {
       k_lu_swap<R><<<dim3(max_nts + 1, m.nsub), 256, smem_s, d.stream>>>(a, d.arena);
       prof_end(h, KC_LU_SWAP, pb, 1);
       if (k > k0) {
-        // the pivot row's columns right of the panel, from the panel's earlier steps (left-looking:
-        // every row below the panel keeps those updates deferred until the outer update, so a
-        // pivot row swapped up from there must receive them now, and no row may get them early)
+        // the pivot tile row right of column k, from the panel's earlier steps: the rows below
+        // keep those updates deferred (panel columns until their own step, the rest until the
+        // outer update), so a pivot row swapped up from there receives them now
         UpdArgs u;
         u.kk0 = k0;
         u.kk1 = k;
         u.nreg = 1;
-        u.reg[0] = {k, k + 1, kend, INT_MAX};
+        u.reg[0] = {k, k + 1, k + 1, INT_MAX};
         update(u);
       }
       pb = prof_begin(h);
@@ -865,14 +879,6 @@ static int lu_run(oras_handle* h) {
         prof_end(h, KC_LU_TRSM, pb, 1);
       }
       count_launches(3);
-      // inner update: the panel's remaining columns, every row below (all rows stay in the same
-      // state there, so later row interchanges stay consistent)
-      UpdArgs u;
-      u.kk0 = k;
-      u.kk1 = k + 1;
-      u.nreg = 1;
-      u.reg[0] = {k + 1, INT_MAX, k + 1, kend};
-      update(u);
     }
     UpdArgs u;  // outer update of the trailing matrix
     u.kk0 = k0;

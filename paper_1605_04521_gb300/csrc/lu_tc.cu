@@ -5,15 +5,18 @@
 //   C_re -= L_re U_re - L_im U_im ,   C_im -= L_re U_im + L_im U_re .
 // L tiles (below the diagonal) store row-major planes and U tiles (above it) column-major
 // planes, so both operands are K-major: an L plane is an M x K matrix with K contiguous and a
-// U plane is the N x K transpose of the K x N operand.  Each CTA owns a 128 x 256 complex output
-// block (2 x 4 tiles): D_re and D_im are 128 x 256 FP32 accumulators filling the 512 tensor-memory
-// columns.  The -L_im U_im term uses the instruction's negate-B bit.
+// U plane is the N x K transpose of the K x N operand.  Each CTA owns a 128 x 64*BN complex
+// output block (2 x BN tiles): D_re and D_im are 128 x 64*BN FP32 accumulators in tensor memory
+// (BN = 4: all 512 columns, for wide regions; BN = 1: 128 columns, for the single tile column
+// that a left-looking panel step updates).  The -L_im U_im term uses the instruction's negate-B
+// bit.
 //
 // Warp roles (128 threads): warp 0 lane 0 loads operand chunks with TMA (one tensor map over
 // the whole arena, 128-byte swizzle); warp 1 lane 0 issues the MMAs and commits them to the
 // stage's "empty" barrier; after the last commit all four warps read their 32 accumulator rows
 // from tensor memory and subtract them from C.  Stages hold one 32-float K-chunk of all four
-// operand planes (96 KB).  Waits are bounded; a timeout sets the device status flag.
+// operand planes (96 KB for BN = 4, two stages; 48 KB for BN = 1, four stages).  Waits are
+// bounded; a timeout sets the device status flag.
 #include <cuda.h>
 
 #include <cstdio>
@@ -25,12 +28,18 @@
 namespace oras {
 
 constexpr int TC_THREADS = 128;
-constexpr int TC_STAGES = 2;
-constexpr int TC_BN = 4;                                 // output tile columns per CTA (N = 256)
 constexpr int TC_GROUP = 8;                              // default block rows per raster group (L2 reuse)
 constexpr uint32_t TC_BOX_BYTES = 64 * 32 * 4;           // 64 rows x 32 floats
-constexpr uint32_t TC_STAGE_BYTES = (4 + 2 * TC_BN) * TC_BOX_BYTES;  // A_re, A_im (2 tiles), B_re, B_im (4)
-constexpr uint32_t TC_TMEM_COLS = 512;
+
+// Shape of one output block: BN tile columns (N = 64 BN).
+template <int BN>
+struct TcShape {
+  static_assert(BN == 1 || BN == 4, "output block widths");
+  static constexpr int STAGES = BN == 4 ? 2 : 4;
+  static constexpr uint32_t STAGE_BYTES = (4 + 2 * BN) * TC_BOX_BYTES;  // A_re, A_im (2 tiles), B_re, B_im (BN)
+  static constexpr uint32_t TMEM_COLS = 2 * 64 * BN;                    // D_re, D_im
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
+};
 
 struct TcArgs {
   const int64_t* np;
@@ -53,9 +62,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFF) | (1ull << 16) | (64ull << 32) | (1ull << 46) | (2ull << 61);
 }
 
-// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 64 TC_BN.
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 64 BN.
+template <int BN>
 __device__ __forceinline__ uint32_t idesc_tf32(bool negate_b) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((negate_b ? 1u : 0u) << 14) | (((64u * TC_BN) >> 3) << 17) |
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((negate_b ? 1u : 0u) << 14) | (((64u * BN) >> 3) << 17) |
          ((128u >> 4) << 24);
 }
 
@@ -85,21 +95,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-// Map the block index to a 2 x TC_BN-tile output block of one region of subdomain s.  Blocks
+// Map the block index to a 2 x BN-tile output block of one region of subdomain s.  Blocks
 // are ordered in groups of TC_GROUP block rows, walking down a group before moving right, so
 // that CTAs running at the same time share their L (rows) and U (columns) operands in L2.
+template <int BN>
 __host__ __device__ __forceinline__ void region_blocks_of(const Region& r, int64_t nts, int64_t& nbi, int64_t& nbj,
                                                           int64_t& i0, int64_t& i1, int64_t& j0, int64_t& j1) {
   region_clip(r, nts, i0, i1, j0, j1);
   nbi = (i1 - i0 + 1) / 2;
-  nbj = (j1 - j0 + TC_BN - 1) / TC_BN;
+  nbj = (j1 - j0 + BN - 1) / BN;
 }
 
+template <int BN>
 __device__ __forceinline__ bool tc_block(const UpdArgs& u, int64_t nts, int64_t e, int group, int64_t& I0,
                                          int64_t& J0, int& ni, int& nj) {
   for (int q = 0; q < u.nreg; ++q) {
     int64_t nbi, nbj, i0, i1, j0, j1;
-    region_blocks_of(u.reg[q], nts, nbi, nbj, i0, i1, j0, j1);
+    region_blocks_of<BN>(u.reg[q], nts, nbi, nbj, i0, i1, j0, j1);
     if (e < nbi * nbj) {
       const int64_t gsize = (int64_t)group * nbj;
       const int64_t g = e / gsize, first = g * group;
@@ -107,9 +119,9 @@ __device__ __forceinline__ bool tc_block(const UpdArgs& u, int64_t nts, int64_t 
       const int64_t loc = e % gsize;
       const int64_t bi = first + loc % gs, bj = loc / gs;
       I0 = i0 + 2 * bi;
-      J0 = j0 + TC_BN * bj;
+      J0 = j0 + BN * bj;
       ni = (int)((i1 - I0) < 2 ? (i1 - I0) : 2);
-      nj = (int)((j1 - J0) < TC_BN ? (j1 - J0) : TC_BN);
+      nj = (int)((j1 - J0) < BN ? (j1 - J0) : BN);
       return true;
     }
     e -= nbi * nbj;
@@ -117,7 +129,11 @@ __device__ __forceinline__ bool tc_block(const UpdArgs& u, int64_t nts, int64_t 
   return false;
 }
 
+template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+  using S = TcShape<BN>;
+  constexpr int TC_STAGES = S::STAGES;
+  constexpr uint32_t TC_STAGE_BYTES = S::STAGE_BYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ uint64_t full[TC_STAGES], empty[TC_STAGES], done;
   __shared__ uint32_t tmem_base;
@@ -126,7 +142,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
   const int64_t nts = a.np[s] / TB;
   int64_t I0, J0;
   int ni, nj;
-  if (!tc_block(a.u, nts, blockIdx.x, a.group, I0, J0, ni, nj)) return;
+  if (!tc_block<BN>(a.u, nts, blockIdx.x, a.group, I0, J0, ni, nj)) return;
   int64_t kk1 = a.u.kk1 < nts ? a.u.kk1 : nts;
   const int64_t kk0 = a.u.kk0;
   if (kk1 <= kk0) return;
@@ -145,7 +161,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(TC_TMEM_COLS));
+                 "r"(S::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -174,16 +190,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
       tma_load_3d(sb + 2 * TC_BOX_BYTES, &tmap, x, 64, zA0, &full[st]);   // A_im
       tma_load_3d(sb + 3 * TC_BOX_BYTES, &tmap, x, 64, zA1, &full[st]);
 #pragma unroll
-      for (int q = 0; q < TC_BN; ++q) {                                   // B_re, B_im: 64 columns per tile
+      for (int q = 0; q < BN; ++q) {                                      // B_re, B_im: 64 columns per tile
         const int zB = (int)(toff + kk * nts + J0 + (q < nj ? q : 0));
         tma_load_3d(sb + (4 + q) * TC_BOX_BYTES, &tmap, x, 0, zB, &full[st]);
-        tma_load_3d(sb + (4 + TC_BN + q) * TC_BOX_BYTES, &tmap, x, 64, zB, &full[st]);
+        tma_load_3d(sb + (4 + BN + q) * TC_BOX_BYTES, &tmap, x, 64, zB, &full[st]);
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    const uint32_t id_pos = idesc_tf32(false), id_neg = idesc_tf32(true);
-    const uint32_t d_re = tbase, d_im = tbase + 64 * TC_BN;
+    const uint32_t id_pos = idesc_tf32<BN>(false), id_neg = idesc_tf32<BN>(true);
+    const uint32_t d_re = tbase, d_im = tbase + 64 * BN;
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       const int st = c % TC_STAGES;
@@ -194,7 +210,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sb = smem_u32(stages + (size_t)st * TC_STAGE_BYTES);
       const uint64_t are = sdesc(sb), aim = sdesc(sb + 2 * TC_BOX_BYTES);
-      const uint64_t bre = sdesc(sb + 4 * TC_BOX_BYTES), bim = sdesc(sb + (4 + TC_BN) * TC_BOX_BYTES);
+      const uint64_t bre = sdesc(sb + 4 * TC_BOX_BYTES), bim = sdesc(sb + (4 + BN) * TC_BOX_BYTES);
 #pragma unroll
       for (int k8 = 0; k8 < 4; ++k8) {  // K = 8 TF32 = 32 B per instruction
         const uint64_t dk = (uint64_t)(k8 * 32) >> 4;
@@ -220,11 +236,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
     const int ti = row >> 6, li = row & 63;
     const int64_t I = I0 + ti;
 #pragma unroll 1
-    for (int cb = 0; cb < 2 * TC_BN; ++cb) {     // 32-column chunks of the 64 TC_BN complex columns
+    for (int cb = 0; cb < 2 * BN; ++cb) {        // 32-column chunks of the 64 BN complex columns
       float re[32], im[32];
       const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
       tmem_ld32(tbase + lane_off + cb * 32, re);
-      tmem_ld32(tbase + lane_off + 64 * TC_BN + cb * 32, im);
+      tmem_ld32(tbase + lane_off + 64 * BN + cb * 32, im);
       const int tj = cb >> 1, lj0 = (cb & 1) * 32;
       const int64_t J = J0 + tj;
       if (ti >= ni || tj >= nj) continue;
@@ -252,7 +268,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TC_TMEM_COLS));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(S::TMEM_COLS));
 }
 
 // ------------------------------------------------------------------ triangular solves of a step
@@ -273,11 +289,6 @@ struct TrsmArgs {
 };
 
 constexpr uint32_t TRSM_CHUNK_BYTES = 6 * TC_BOX_BYTES;  // A_re (2 boxes), A_im (2), B_re, B_im
-
-__device__ __forceinline__ uint32_t idesc_tf32_n64(bool negate_b) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((negate_b ? 1u : 0u) << 14) | ((64u >> 3) << 17) |
-         ((128u >> 4) << 24);
-}
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_trsm_tc(const __grid_constant__ CUtensorMap tmap, TrsmArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -327,7 +338,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_trsm_tc(const __grid_const
       tma_load_3d(sb + 5 * TC_BOX_BYTES, &tmap, x, 64, zB, &full);
     }
   } else if (warp == 1 && lane == 0) {
-    const uint32_t id_pos = idesc_tf32_n64(false), id_neg = idesc_tf32_n64(true);
+    const uint32_t id_pos = idesc_tf32<1>(false), id_neg = idesc_tf32<1>(true);
     const uint32_t d_re = tbase, d_im = tbase + 64;
     if (mbar_wait(&full, 0)) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -450,16 +461,20 @@ int launch_trsm_tc(oras_handle* h, int k, int max_nts) {
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts) {
-  const auto& m = h->mesh;
-  const auto& d = h->dev;
+template <int BN>
+static int64_t update_blocks(const UpdArgs& u, int max_nts) {
   int64_t blocks = 0;
   for (int q = 0; q < u.nreg; ++q) {
     int64_t nbi, nbj, i0, i1, j0, j1;
-    region_blocks_of(u.reg[q], max_nts, nbi, nbj, i0, i1, j0, j1);
+    region_blocks_of<BN>(u.reg[q], max_nts, nbi, nbj, i0, i1, j0, j1);
     blocks += nbi * nbj;
   }
-  if (blocks <= 0) return 0;
+  return blocks;
+}
+
+template <int BN>
+static void launch_update_shape(oras_handle* h, const UpdArgs& u, int64_t blocks) {
+  const auto& d = h->dev;
   CUtensorMap map;
   std::memcpy(&map, h->tc_map, sizeof(map));
   TcArgs a;
@@ -469,12 +484,29 @@ int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts) {
   a.u = u;
   a.status = d.status;
   a.group = h->opt.lu_group > 0 ? h->opt.lu_group : TC_GROUP;
-  const size_t smem = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
-  allow_max_smem((const void*)k_lu_update_tc);
+  allow_max_smem((const void*)k_lu_update_tc<BN>);
   int pb = prof_begin(h);
-  k_lu_update_tc<<<dim3((unsigned)blocks, m.nsub), TC_THREADS, smem, d.stream>>>(map, a);
+  k_lu_update_tc<BN><<<dim3((unsigned)blocks, h->mesh.nsub), TC_THREADS, TcShape<BN>::SMEM, d.stream>>>(map, a);
   prof_end(h, KC_LU_UPDATE, pb, 1);
   count_launches(1);
+}
+
+// Regions one tile column wide (the column a left-looking panel step brings up to date) take
+// the 128 x 64 output blocks; wider ones the 128 x 256 blocks.
+int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts) {
+  int64_t width = 0;
+  for (int q = 0; q < u.nreg; ++q) {
+    int64_t i0, i1, j0, j1;
+    region_clip(u.reg[q], max_nts, i0, i1, j0, j1);
+    if (j1 - j0 > width) width = j1 - j0;
+  }
+  if (width <= 1) {
+    const int64_t blocks = update_blocks<1>(u, max_nts);
+    if (blocks > 0) launch_update_shape<1>(h, u, blocks);
+  } else {
+    const int64_t blocks = update_blocks<4>(u, max_nts);
+    if (blocks > 0) launch_update_shape<4>(h, u, blocks);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
