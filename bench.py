@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -62,6 +63,8 @@ def parse():
     ap.add_argument("--serve-count", type=int, default=12,
                     help="requests of the serving stream replayed after the main measurement (0: none)")
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--clocks-dir", default=None,
+                    help="where the nvidia-smi clock samples of the timed region are written (default: the temp dir)")
     ap.add_argument("--factor-bits", type=int, default=0, choices=[0, 32, 64],
                     help="local factor precision (0: the workload's; 64: the plain FP64 path)")
     ap.add_argument("--lu-panel", type=int, default=0,
@@ -142,9 +145,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, directory=None):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(directory or tempfile.gettempdir(), f"clocks_rank{gpu_index}.csv")
         self.gpu = gpu_index
 
     def start(self):
@@ -432,7 +435,7 @@ def run_ours(args, world, rank, local):
     O.oras_set_timing(h, 1)
     O.oras_reset_timings(h)
     launches0 = O.oras_launch_count()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_dir)
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier(world)
