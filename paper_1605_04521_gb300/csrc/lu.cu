@@ -48,6 +48,7 @@ template <> struct LuCfg<double> { static constexpr int CH = 128; };
 
 constexpr int PS = TB + 1;  // padded row stride of the panel in shared memory
 constexpr int LU_THREADS = 256;
+constexpr int INV_THREADS = 512;  // diagonal-block inversion: 16 warps over the 2 TB columns
 
 struct LuArgs {
   int nsub;
@@ -677,33 +678,41 @@ __global__ void k_gidx(int64_t total, const int32_t* perm, const int64_t* np_off
 // substitution steps of the preconditioner apply become tile matrix-vector products like the
 // off-diagonal ones (block substitution with inverted diagonal blocks).
 // Inverts a factored diagonal block held column-major (padded) in D: X[0] gets the columns of
-// L^{-1} (unit lower), X[1] those of U^{-1}.  128 threads: thread t < TB solves column t of
-// L x = e_t, thread TB + j column j of U x = e_j.
+// L^{-1} (unit lower), X[1] those of U^{-1}.  One warp per column (warps take the 2 TB columns
+// in turn), lanes own rows lane and lane + 32; column-oriented substitution, the pivot entry
+// broadcast by shuffle at each step:
+//   L x = e_t:  x = e_t; for l = t .. TB-2:  x_i -= L(i,l) x_l  (i > l)
+//   U x = e_j:  b = e_j; for l = j .. 0:     x_l = b_l / U(l,l);  b_i -= U(i,l) x_l  (i < l)
 template <typename R>
 __device__ void invert_block(const CT<R>* D, CT<R>* X) {
-  const int t = threadIdx.x;
-  const CT<R> zero = {R(0), R(0)}, one = {R(1), R(0)};
-  if (t < TB) {
-    CT<R>* x = X + t * PS;
-    for (int i = 0; i < TB; ++i) {
-      if (i < t) { x[i] = zero; continue; }
-      if (i == t) { x[i] = one; continue; }
-      CT<R> acc = zero;
-      for (int l = t; l < i; ++l) {
-        CT<R> p = mulc(D[l * PS + i], x[l]);
-        acc.re += p.re;
-        acc.im += p.im;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int i0 = lane, i1 = lane + 32;
+  for (int task = warp; task < 2 * TB; task += nw) {
+    if (task < TB) {
+      const int t = task;
+      CT<R> x0 = {R(i0 == t ? 1 : 0), R(0)}, x1 = {R(i1 == t ? 1 : 0), R(0)};
+      for (int l = t; l < TB - 1; ++l) {
+        const CT<R> own = l < 32 ? x0 : x1;
+        const CT<R> xl = {__shfl_sync(0xffffffffu, own.re, l & 31), __shfl_sync(0xffffffffu, own.im, l & 31)};
+        if (i0 > l) x0 = subc(x0, mulc(D[l * PS + i0], xl));
+        if (i1 > l) x1 = subc(x1, mulc(D[l * PS + i1], xl));
       }
-      x[i] = {-acc.re, -acc.im};
-    }
-  } else if (t < 2 * TB) {
-    const int j = t - TB;
-    CT<R>* x = X + TB * PS + j * PS;
-    for (int i = TB - 1; i >= 0; --i) {
-      if (i > j) { x[i] = zero; continue; }
-      CT<R> acc = i == j ? one : zero;
-      for (int l = i + 1; l <= j; ++l) acc = subc(acc, mulc(D[l * PS + i], x[l]));
-      x[i] = mulc(acc, invc(D[i * PS + i]));
+      X[t * PS + i0] = x0;
+      X[t * PS + i1] = x1;
+    } else {
+      const int j = task - TB;
+      CT<R> b0 = {R(i0 == j ? 1 : 0), R(0)}, b1 = {R(i1 == j ? 1 : 0), R(0)};
+      for (int l = j; l >= 0; --l) {
+        const CT<R> own = l < 32 ? b0 : b1;
+        const CT<R> bl = {__shfl_sync(0xffffffffu, own.re, l & 31), __shfl_sync(0xffffffffu, own.im, l & 31)};
+        const CT<R> xl = mulc(bl, invc(D[l * PS + l]));
+        if (i0 < l) b0 = subc(b0, mulc(D[l * PS + i0], xl));
+        else if (i0 == l) b0 = xl;
+        if (i1 < l) b1 = subc(b1, mulc(D[l * PS + i1], xl));
+        else if (i1 == l) b1 = xl;
+      }
+      X[TB * PS + j * PS + i0] = b0;
+      X[TB * PS + j * PS + i1] = b1;
     }
   }
 }
@@ -727,7 +736,7 @@ __device__ void store_inverses(const CT<R>* X, R* Li, R* Ui) {
 // substitution steps of the preconditioner apply become tile matrix-vector products like the
 // off-diagonal ones (block substitution with inverted diagonal blocks).
 template <typename R>
-__global__ void __launch_bounds__(2 * TB) k_lu_diag_inv(LuArgs a, void* arena, void* inv, const int64_t* inv_off) {
+__global__ void __launch_bounds__(INV_THREADS) k_lu_diag_inv(LuArgs a, void* arena, void* inv, const int64_t* inv_off) {
   extern __shared__ unsigned char smem_raw[];
   CT<R>* D = (CT<R>*)smem_raw;  // [TB][PS]: D[j*PS+i] = LU(i,j)
   CT<R>* X = D + TB * PS;       // [2][TB][PS]
@@ -750,7 +759,7 @@ __global__ void __launch_bounds__(2 * TB) k_lu_diag_inv(LuArgs a, void* arena, v
 // The step's factored diagonal block (from the tournament root): written to tile (k, k) and
 // inverted into the subdomain's two scratch tiles for the tensor-core triangular solves.
 template <typename R>
-__global__ void __launch_bounds__(2 * TB) k_lu_step_inv(LuArgs a, void* arena, int64_t scratch_base) {
+__global__ void __launch_bounds__(INV_THREADS) k_lu_step_inv(LuArgs a, void* arena, int64_t scratch_base) {
   extern __shared__ unsigned char smem_raw[];
   CT<R>* D = (CT<R>*)smem_raw;  // [TB][PS]
   CT<R>* X = D + TB * PS;       // [2][TB][PS]
@@ -871,7 +880,7 @@ static int lu_run(oras_handle* h) {
       }
       pb = prof_begin(h);
       if (tc) {
-        k_lu_step_inv<R><<<m.nsub, 2 * TB, smem_i, d.stream>>>(a, d.arena, m.arena_tiles);
+        k_lu_step_inv<R><<<m.nsub, INV_THREADS, smem_i, d.stream>>>(a, d.arena, m.arena_tiles);
         launch_trsm_tc(h, k, max_nts);
         prof_end(h, KC_LU_TRSM, pb, 2);
       } else {
@@ -892,7 +901,7 @@ static int lu_run(oras_handle* h) {
   {
     allow_max_smem((const void*)k_lu_diag_inv<R>);
     int pb = prof_begin(h);
-    k_lu_diag_inv<R><<<dim3(max_nts, m.nsub), 2 * TB, smem_i, d.stream>>>(a, d.arena, d.dinv, d.sub_inv_off);
+    k_lu_diag_inv<R><<<dim3(max_nts, m.nsub), INV_THREADS, smem_i, d.stream>>>(a, d.arena, d.dinv, d.sub_inv_off);
     prof_end(h, KC_LU_TRSM, pb, 1);
   }
   count_launches(3);
