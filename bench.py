@@ -464,8 +464,12 @@ def run_ours(args, world, rank, local):
     dom, roof = roofline(timings, upd_flops, apply_bytes, args.steps, hbm, bf16, w.factor_bits)
     if dom == "lu_update" and w.factor_bits == 32:
         roof["traffic"] = measured_traffic("k_lu_update_tc", w.name, panel)
-        roof["traffic_note"] = ("DRAM read+write bytes per launch, averaged over every trailing-update launch of a "
-                                "factorisation, from the ncu capture recorded in profiles/roofline_traffic.json")
+        if roof["traffic"] is not None:
+            roof["traffic_note"] = ("DRAM read+write bytes per launch, averaged over every trailing-update launch of "
+                                    "a factorisation, from the ncu capture recorded in profiles/roofline_traffic.json")
+        else:
+            roof["traffic_note"] = ("null: profiles/roofline_traffic.json holds no ncu capture of this workload and "
+                                    "panel width on the current update kernel (" + UPDATE_VERSION + ")")
     arena = O.oras_arena_bytes(h)
     O.oras_destroy(h)
     # ---------------- end to end through the public API with host buffers
