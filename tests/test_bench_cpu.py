@@ -1,0 +1,88 @@
+"""Host logic of bench.py on CPU: whole-job throughput, the roofline object of the dominant kernel
+class, the version gate on stored ncu traffic, and the parsing of the nvidia-smi clock record
+that decides whether a run was throttled."""
+import json
+
+import pytest
+
+import bench
+
+
+def test_whole_job_throughput():
+    assert bench.aggregate(2000.0, 3, 2) == pytest.approx(3.0)      # 6 solves in 2 s
+    assert bench.aggregate(500.0, 1, 1) == pytest.approx(2.0)
+
+
+def test_peak_ratio_is_the_nominal_tf32_over_bf16():
+    assert bench.TF32_OVER_BF16 == pytest.approx(1.1 / 2.25)
+
+
+def test_roofline_of_a_tensor_bound_factorisation():
+    timings = {"lu_update": (800.0, 400), "apply": (300.0, 17), "spmv": (2.0, 17), "orth": (0.0, 0)}
+    flops = 4.0e14
+    dom, r = bench.roofline(timings, flops, 8.0e10, 2, 6779.4, 1890.3)
+    assert dom == "lu_update" and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(flops * 2 / 0.8 / 1e12)
+    assert r["peak"] == pytest.approx(1890.3 * 1.1 / 2.25)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+
+
+def test_roofline_of_an_hbm_bound_apply():
+    timings = {"lu_update": (100.0, 50), "apply": (300.0, 20)}
+    dom, r = bench.roofline(timings, 1e13, 5.0e10, 1, 6779.4, 1890.3)
+    assert dom == "apply" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(5.0e10 * 20 / 0.3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6779.4)
+
+
+def test_roofline_of_fp64_factors_is_alu_bound():
+    dom, r = bench.roofline({"lu_update": (1000.0, 10)}, 1e12, 1.0, 1, 6779.4, 1890.3, factor_bits=64)
+    assert dom == "lu_update" and r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(1.0) and r["peak"] == bench.FP64_NOMINAL_TFLOPS
+
+
+def test_stored_traffic_needs_the_current_kernel_version(tmp_path, monkeypatch):
+    path = tmp_path / "traffic.json"
+    entry = {"workload": "w", "lu_panel": 24, "bytes_per_launch": 123.0, "source_version": "old"}
+    path.write_text(json.dumps({"k_lu_update_tc": entry}))
+    monkeypatch.setattr(bench, "TRAFFIC", str(path))
+    assert bench.measured_traffic("k_lu_update_tc", "w", 24) is None
+    entry["source_version"] = bench.UPDATE_VERSION
+    path.write_text(json.dumps({"k_lu_update_tc": entry}))
+    assert bench.measured_traffic("k_lu_update_tc", "w", 24) == 123.0
+    assert bench.measured_traffic("k_lu_update_tc", "w", 16) is None
+    assert bench.measured_traffic("k_lu_update_tc", "other", 24) is None
+
+
+class _DoneProcess:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _clock_summary(tmp_path, lines):
+    s = bench.ClockSampler(0, str(tmp_path))
+    with open(s.path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    s.proc = _DoneProcess()
+    s.f = open(s.path)
+    return s.stop()
+
+
+def test_clock_record_without_throttling(tmp_path):
+    rows = [f"0, {mhz}, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+            for mhz in (2070, 2055, 2070, 1980, 2070)]
+    c = _clock_summary(tmp_path, rows)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 5}
+
+
+def test_clock_record_flags_every_throttle_reason(tmp_path):
+    rows = ["0, 1800, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 1500, 2070, 1400.0, 0x48, Active, Not Active, Active, Not Active",
+            "garbage line",
+            "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    c = _clock_summary(tmp_path, rows)
+    assert c["samples"] == 2 and c["sm_mhz"] == 1650.0
+    assert c["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
