@@ -11,14 +11,68 @@
 //  * N_s: every DOF on an entity of a tetrahedron of Omega_s^delta, ascending;
 //  * D_s: a DOF belongs to the subdomain of the lowest-index tetrahedron carrying it.
 #include <algorithm>
+#include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <exception>
+#include <mutex>
 #include <numeric>
+#include <system_error>
+#include <thread>
 
 #include "internal.h"
 
 namespace oras {
+
+// Runs fn(i, worker) for i in [0, n) on up to min(hardware_concurrency(), 16) threads (chunks from a
+// shared counter).  Every i writes only its own outputs, so results do not depend on the thread
+// count or the schedule.  An exception in any worker is rethrown here after all workers joined.
+template <typename F>
+static void parallel_for(int64_t n, int64_t grain, F fn) {
+  unsigned hw = std::thread::hardware_concurrency();
+  int64_t nw = std::min<int64_t>(hw ? hw : 1, 16);
+  nw = std::min<int64_t>(nw, (n + grain - 1) / grain);
+  if (nw <= 1) {
+    for (int64_t i = 0; i < n; ++i) fn(i, 0);
+    return;
+  }
+  std::atomic<int64_t> next(0);
+  std::exception_ptr err;
+  std::mutex err_mu;
+  auto work = [&](int w) {
+    try {
+      for (;;) {
+        const int64_t i0 = next.fetch_add(grain);
+        if (i0 >= n) return;
+        const int64_t i1 = std::min(n, i0 + grain);
+        for (int64_t i = i0; i < i1; ++i) fn(i, w);
+      }
+    } catch (...) {  // keep the first error for the caller; no further chunks are taken
+      std::lock_guard<std::mutex> lk(err_mu);
+      if (!err) err = std::current_exception();
+      next.store(n);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < nw; ++w) {
+    try {
+      th.emplace_back(work, w);
+    } catch (const std::system_error&) {  // no more threads: the started ones take the rest
+      break;
+    }
+  }
+  work(0);
+  for (auto& x : th) x.join();
+  if (err) std::rethrow_exception(err);
+}
+
+static int workers_for(int64_t n, int64_t grain) {
+  unsigned hw = std::thread::hardware_concurrency();
+  int64_t nw = std::min<int64_t>(hw ? hw : 1, 16);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(nw, (n + grain - 1) / grain));
+}
 
 static const int EDGES[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
 static const int FACES[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
@@ -65,14 +119,16 @@ static void rcb(const HostMesh& m, int nsub, std::vector<int32_t>& part) {
     double best = hi[0] - lo[0];
     for (int d = 1; d < 3; ++d)
       if (hi[d] - lo[d] > best) { best = hi[d] - lo[d]; axis = d; }
-    std::sort(s.ids.begin(), s.ids.end(), [&](int32_t a, int32_t b) {
+    int p0 = s.p / 2;
+    int64_t h = ((int64_t)s.ids.size() * p0) / s.p;
+    // the first h tets in (coordinate, id) order: a strict total order, so the selected set is
+    // the same as after a full sort (the order inside each child is not used)
+    std::nth_element(s.ids.begin(), s.ids.begin() + h, s.ids.end(), [&](int32_t a, int32_t b) {
       double ca = cen[(size_t)a * 3 + axis], cb = cen[(size_t)b * 3 + axis];
       if (ca < cb) return true;
       if (cb < ca) return false;
       return a < b;
     });
-    int p0 = s.p / 2;
-    int64_t h = ((int64_t)s.ids.size() * p0) / s.p;
     Seg c0, c1;
     c0.ids.assign(s.ids.begin(), s.ids.begin() + h);
     c1.ids.assign(s.ids.begin() + h, s.ids.end());
@@ -135,8 +191,9 @@ int host_setup(const oras_problem* p, int overlap_kind, HostMesh& m, std::string
   ue.erase(std::unique(ue.begin(), ue.end()), ue.end());
   m.ne = (int64_t)ue.size();
   std::vector<int32_t> tet_edges(T * 6);
-  for (int64_t i = 0; i < T * 6; ++i)
+  parallel_for(T * 6, 1 << 14, [&](int64_t i, int) {
     tet_edges[i] = (int32_t)(std::lower_bound(ue.begin(), ue.end(), ek[i]) - ue.begin());
+  });
   std::vector<uint64_t> fk(T * 4);
   for (int64_t t = 0; t < T; ++t)
     for (int f = 0; f < 4; ++f)
@@ -148,10 +205,12 @@ int host_setup(const oras_problem* p, int overlap_kind, HostMesh& m, std::string
   m.nf = (int64_t)uf.size();
   m.tet_faces.resize(T * 4);
   m.face_tets.assign(m.nf * 2, -1);
+  parallel_for(T * 4, 1 << 14, [&](int64_t i, int) {
+    m.tet_faces[i] = (int32_t)(std::lower_bound(uf.begin(), uf.end(), fk[i]) - uf.begin());
+  });
   for (int64_t t = 0; t < T; ++t)
     for (int f = 0; f < 4; ++f) {
-      int32_t id = (int32_t)(std::lower_bound(uf.begin(), uf.end(), fk[t * 4 + f]) - uf.begin());
-      m.tet_faces[t * 4 + f] = id;
+      const int32_t id = m.tet_faces[t * 4 + f];
       if (m.face_tets[id * 2] < 0) m.face_tets[id * 2] = (int32_t)t;
       else if (m.face_tets[id * 2 + 1] < 0) m.face_tets[id * 2 + 1] = (int32_t)t;
       else { err = "oras_create: a face is shared by more than two tets"; return ORAS_ERR_BAD_MESH; }
@@ -191,39 +250,73 @@ int host_setup(const oras_problem* p, int overlap_kind, HostMesh& m, std::string
     rcb(m, m.nsub, m.part);
   }
   // ---------------- overlap and membership
+  // Omega_s^delta grown layer by layer from the tets of part s: a layer adds every tet sharing a
+  // vertex (or a face) with the current set.  Only the tets added by the previous layer can
+  // bring new neighbours, so each layer walks that frontier through the vertex -> tet (or face)
+  // adjacency instead of sweeping the whole mesh.
   m.member_words = (T + 31) / 32;
   m.member.assign((size_t)m.nsub * m.member_words, 0u);
+  std::vector<std::vector<int32_t>> omega(m.nsub);  // Omega_s^delta, ascending
   {
-    std::vector<uint8_t> tmark(T), vmark(nv);
-    for (int s = 0; s < m.nsub; ++s) {
-      for (int64_t t = 0; t < T; ++t) tmark[t] = m.part[t] == s;
+    std::vector<int64_t> part_ptr(m.nsub + 1, 0);
+    for (int64_t t = 0; t < T; ++t) part_ptr[m.part[t] + 1]++;
+    for (int s = 0; s < m.nsub; ++s) part_ptr[s + 1] += part_ptr[s];
+    std::vector<int32_t> part_tets(T);
+    {
+      std::vector<int64_t> pos(part_ptr.begin(), part_ptr.end() - 1);
+      for (int64_t t = 0; t < T; ++t) part_tets[pos[m.part[t]]++] = (int32_t)t;
+    }
+    std::vector<int64_t> v2t_ptr(nv + 1, 0);
+    std::vector<int32_t> v2t;
+    if (m.overlap > 0 && overlap_kind != ORAS_OVERLAP_FACE) {
+      for (int64_t i = 0; i < T * 4; ++i) v2t_ptr[m.st[i] + 1]++;
+      for (int64_t v = 0; v < nv; ++v) v2t_ptr[v + 1] += v2t_ptr[v];
+      v2t.resize(T * 4);
+      std::vector<int64_t> pos(v2t_ptr.begin(), v2t_ptr.end() - 1);
+      for (int64_t i = 0; i < T * 4; ++i) v2t[pos[m.st[i]]++] = (int32_t)(i / 4);
+    }
+    const int nw = workers_for(m.nsub, 1);
+    std::vector<std::vector<int32_t>> tstamp(nw), vstamp(nw);
+    parallel_for(m.nsub, 1, [&](int64_t s64, int w) {
+      const int s = (int)s64;
+      auto& ts = tstamp[w];
+      auto& vs = vstamp[w];
+      if (ts.empty()) ts.assign(T, -1);
+      if (vs.empty() && !v2t.empty()) vs.assign(nv, -1);
+      std::vector<int32_t>& list = omega[s];
+      list.assign(part_tets.begin() + part_ptr[s], part_tets.begin() + part_ptr[s + 1]);
+      for (int32_t t : list) ts[t] = s;
+      size_t begin = 0;
       for (int layer = 0; layer < m.overlap; ++layer) {
-        if (overlap_kind == ORAS_OVERLAP_FACE) {
-          std::vector<uint8_t> next(tmark);
-          for (int64_t t = 0; t < T; ++t)
-            if (tmark[t])
-              for (int f = 0; f < 4; ++f) {
-                int32_t fid = m.tet_faces[t * 4 + f];
-                for (int q = 0; q < 2; ++q) {
-                  int32_t o = m.face_tets[fid * 2 + q];
-                  if (o >= 0) next[o] = 1;
-                }
+        const size_t end = list.size();
+        for (size_t i = begin; i < end; ++i) {
+          const int32_t t = list[i];
+          if (overlap_kind == ORAS_OVERLAP_FACE) {
+            for (int f = 0; f < 4; ++f) {
+              const int32_t fid = m.tet_faces[(int64_t)t * 4 + f];
+              for (int q = 0; q < 2; ++q) {
+                const int32_t o = m.face_tets[(int64_t)fid * 2 + q];
+                if (o >= 0 && ts[o] != s) { ts[o] = s; list.push_back(o); }
               }
-          tmark.swap(next);
-        } else {
-          std::fill(vmark.begin(), vmark.end(), 0);
-          for (int64_t t = 0; t < T; ++t)
-            if (tmark[t])
-              for (int q = 0; q < 4; ++q) vmark[m.st[t * 4 + q]] = 1;
-          for (int64_t t = 0; t < T; ++t) {
-            const int32_t* v = &m.st[t * 4];
-            tmark[t] = vmark[v[0]] | vmark[v[1]] | vmark[v[2]] | vmark[v[3]];
+            }
+          } else {
+            for (int q = 0; q < 4; ++q) {
+              const int32_t v = m.st[(int64_t)t * 4 + q];
+              if (vs[v] == s) continue;
+              vs[v] = s;
+              for (int64_t k = v2t_ptr[v]; k < v2t_ptr[v + 1]; ++k) {
+                const int32_t o = v2t[k];
+                if (ts[o] != s) { ts[o] = s; list.push_back(o); }
+              }
+            }
           }
         }
+        begin = end;
       }
-      for (int64_t t = 0; t < T; ++t)
-        if (tmark[t]) m.member[(size_t)s * m.member_words + (t >> 5)] |= 1u << (t & 31);
-    }
+      std::sort(list.begin(), list.end());
+      uint32_t* row = m.member.data() + (size_t)s * m.member_words;
+      for (int32_t t : list) row[t >> 5] |= 1u << (t & 31);
+    });
   }
   // ---------------- owners (lowest tet carrying the DOF) and N_s / D_s
   std::vector<int32_t> owner(ndof, -1);
@@ -245,23 +338,35 @@ int host_setup(const oras_problem* p, int overlap_kind, HostMesh& m, std::string
   m.sub_tets.clear();
   m.max_np = 0;
   std::vector<uint8_t> iface_mark(m.nf, 0);
-  std::vector<int32_t> buf;
+  // N_s of every subdomain (ascending DOFs of the tets of Omega_s^delta), in parallel
+  std::vector<std::vector<int32_t>> ndofs(m.nsub);
+  {
+    const int nw = workers_for(m.nsub, 1);
+    std::vector<std::vector<int32_t>> stamp(nw);
+    parallel_for(m.nsub, 1, [&](int64_t s64, int w) {
+      const int s = (int)s64;
+      auto& st = stamp[w];
+      if (st.empty()) st.assign(ndof, -1);
+      auto& buf = ndofs[s];
+      for (int32_t t : omega[s])
+        for (int a = 0; a < nl; ++a) {
+          const int32_t g = m.dofmap[(int64_t)t * nl + a];
+          if (st[g] != s) { st[g] = s; buf.push_back(g); }
+        }
+      std::sort(buf.begin(), buf.end());
+    });
+  }
   for (int s = 0; s < m.nsub; ++s) {
-    buf.clear();
-    int64_t nts = 0;
-    for (int64_t t = 0; t < T; ++t) {
-      if (!member_of(m, s, t)) continue;
-      m.sub_tets.push_back((int32_t)t);
-      ++nts;
-      for (int a = 0; a < nl; ++a) buf.push_back(m.dofmap[t * nl + a]);
+    const int64_t nts = (int64_t)omega[s].size();
+    for (int32_t t : omega[s]) {
+      m.sub_tets.push_back(t);
       for (int f = 0; f < 4; ++f) {
-        int32_t fid = m.tet_faces[t * 4 + f];
+        int32_t fid = m.tet_faces[(int64_t)t * 4 + f];
         int32_t o = m.face_tets[fid * 2] == t ? m.face_tets[fid * 2 + 1] : m.face_tets[fid * 2];
         if (o >= 0 && !member_of(m, s, o)) iface_mark[fid] = 1;
       }
     }
-    std::sort(buf.begin(), buf.end());
-    buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+    const std::vector<int32_t>& buf = ndofs[s];
     int64_t ns = (int64_t)buf.size();
     m.sub_ns[s] = ns;
     m.sub_np[s] = (ns + TB - 1) / TB * TB;
@@ -274,6 +379,7 @@ int host_setup(const oras_problem* p, int overlap_kind, HostMesh& m, std::string
     m.sub_nt_off[s + 1] = m.sub_nt_off[s] + nts;
     int64_t tt = m.sub_np[s] / TB;
     m.sub_tile_off[s + 1] = m.sub_tile_off[s] + tt * tt;
+    std::vector<int32_t>().swap(ndofs[s]);
   }
   m.arena_tiles = m.sub_tile_off[m.nsub];
   // ---------------- impedance faces: outer boundary + interface faces of some subdomain
@@ -306,26 +412,58 @@ int host_setup(const oras_problem* p, int overlap_kind, HostMesh& m, std::string
       for (int af = 0; af < nfl; ++af) m.finc[pos[m.if_dofs[i * nfl + af]]++] = (int32_t)(i * nfl + af);
   }
   // ---------------- CSR pattern: union of the DOFs of the tets carrying each row
+  // All DOFs of one entity (edge, face, volume) are carried by the same tets, so they share
+  // one column set: it is built once per entity, in parallel over entities, in two passes
+  // (count the distinct columns with a per-worker stamp array, then fill and sort).
   m.rowptr.assign(ndof + 1, 0);
-  std::vector<std::vector<int32_t>> rows;
-  const int64_t CH = 1 << 16;
-  std::vector<int32_t> colbuf;
-  m.cols.clear();
-  m.max_row_nnz = 0;
-  std::vector<int32_t> row;
-  for (int64_t g = 0; g < ndof; ++g) {
-    row.clear();
-    for (int64_t q = m.tinc_ptr[g]; q < m.tinc_ptr[g + 1]; ++q) {
-      int64_t t = m.tinc[q] / nl;
-      for (int b = 0; b < nl; ++b) row.push_back(m.dofmap[t * nl + b]);
+  {
+    const int64_t n_e = m.ne, n_f = nfd ? m.nf : 0, n_v = nvd ? T : 0;
+    const int64_t ngroups = n_e + n_f + n_v;
+    auto group = [&](int64_t q, int64_t& g0, int64_t& len) {
+      if (q < n_e) { g0 = q * ned; len = ned; }
+      else if (q < n_e + n_f) { g0 = m.ne * ned + (q - n_e) * nfd; len = nfd; }
+      else { g0 = m.ne * ned + m.nf * nfd + (q - n_e - n_f) * nvd; len = nvd; }
+    };
+    const int64_t grain = 2048;
+    const int nw = workers_for(ngroups, grain);
+    std::vector<std::vector<int32_t>> stamp(nw);
+    auto each_col = [&](int64_t g, int w, auto&& emit) {
+      auto& st = stamp[w];
+      if (st.empty()) st.assign(ndof, -1);
+      for (int64_t q = m.tinc_ptr[g]; q < m.tinc_ptr[g + 1]; ++q) {
+        const int64_t t = m.tinc[q] / nl;
+        for (int b = 0; b < nl; ++b) {
+          const int32_t c = m.dofmap[t * nl + b];
+          if (st[c] != (int32_t)g) { st[c] = (int32_t)g; emit(c); }
+        }
+      }
+    };
+    parallel_for(ngroups, grain, [&](int64_t q, int w) {
+      int64_t g0, len;
+      group(q, g0, len);
+      int64_t n = 0;
+      each_col(g0, w, [&](int32_t) { ++n; });
+      for (int64_t g = g0; g < g0 + len; ++g) m.rowptr[g + 1] = n;
+    });
+    // a row stamped in the counting pass must count again in the filling pass
+    for (auto& st : stamp) std::fill(st.begin(), st.end(), -1);
+    int max_nnz = 0;
+    for (int64_t g = 0; g < ndof; ++g) {
+      max_nnz = std::max<int>(max_nnz, (int)m.rowptr[g + 1]);
+      m.rowptr[g + 1] += m.rowptr[g];
     }
-    std::sort(row.begin(), row.end());
-    row.erase(std::unique(row.begin(), row.end()), row.end());
-    m.cols.insert(m.cols.end(), row.begin(), row.end());
-    m.rowptr[g + 1] = (int64_t)m.cols.size();
-    m.max_row_nnz = std::max<int>(m.max_row_nnz, (int)row.size());
+    m.max_row_nnz = max_nnz;
+    m.cols.resize(m.rowptr[ndof]);
+    parallel_for(ngroups, grain, [&](int64_t q, int w) {
+      int64_t g0, len;
+      group(q, g0, len);
+      int32_t* out = m.cols.data() + m.rowptr[g0];
+      int64_t n = 0;
+      each_col(g0, w, [&](int32_t c) { out[n++] = c; });
+      std::sort(out, out + n);
+      for (int64_t g = g0 + 1; g < g0 + len; ++g) std::memcpy(m.cols.data() + m.rowptr[g], out, n * sizeof(int32_t));
+    });
   }
-  (void)CH;
   return ORAS_OK;
 }
 
