@@ -21,7 +21,10 @@
  *     memory) or ORAS_MEM_DEVICE (device memory of the current CUDA device, e.g. a torch
  *     tensor's data_ptr()).  Device pointers are read/written on the handle's stream.
  *   - The caller owns every buffer it passes; the library copies what it keeps.  The
- *     library owns all device memory it allocates and frees it in oras_destroy().
+ *     library owns all device memory it allocates and frees it in oras_destroy().  Device
+ *     memory comes from the current device's default stream-ordered memory pool, whose
+ *     release threshold the library sets to unlimited: freed memory stays in the pool and
+ *     serves the next handle without mapping new pages.  oras_release_memory() returns it.
  *   - Return codes: 0 = ORAS_OK, > 0 = warning, < 0 = error.  Nothing throws across the
  *     ABI.  oras_last_error(h) (or oras_last_error(NULL) before a handle exists) gives a
  *     message for the last failing call on this thread.
@@ -150,8 +153,14 @@ int oras_factor(oras_handle* h, const oras_complex* eps_r, const oras_complex* m
 /* oras_create followed by oras_factor(p->eps_r, p->mu_r, p->k0, ORAS_MEM_HOST). */
 int oras_setup(const oras_problem* p, const oras_options* o, oras_handle** out);
 
-/* Frees host and device memory of h (NULL is ignored). */
+/* Frees host and device memory of h (NULL is ignored).  The device memory goes back to the
+ * device's memory pool (see the conventions above). */
 void oras_destroy(oras_handle* h);
+
+/* Returns to the driver the device memory that the default memory pool of `device` holds
+ * unused (after oras_destroy), after synchronising that device.  No counterpart in the paper:
+ * memory management of the single-GPU library.  Errors: INVALID_ARG (no such device), CUDA. */
+int oras_release_memory(int32_t device);
 
 /* Stream for all device work of h (a cudaStream_t; NULL = legacy default stream). */
 int oras_set_stream(oras_handle* h, void* stream);

@@ -107,12 +107,13 @@ static void prof_clear(oras_handle* h) {
   } while (0)
 
 // Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the handle's stream): a
-// free does not synchronise the device, so handles on other streams keep running.
+// free does not synchronise the device, so handles on other streams keep running.  Freed memory
+// stays in the device's pool for the next handle (pool_malloc).
 template <typename T>
 static cudaError_t dalloc_s(T*& p, size_t n, cudaStream_t s) {
   if (p) { cudaFreeAsync(p, s); p = nullptr; }
   if (n == 0) n = 1;
-  return cudaMallocAsync((void**)&p, n * sizeof(T), s);
+  return pool_malloc((void**)&p, n * sizeof(T), s);
 }
 template <typename T>
 static void dfree_s(T*& p, cudaStream_t s) {
@@ -137,7 +138,7 @@ static void dfree_all(Device& d) {
                   d.g, d.red, d.scal, d.ybuf, d.io};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, d.stream);
-  cudaStreamSynchronize(d.stream);  // the pool returns the memory at this synchronisation
+  cudaStreamSynchronize(d.stream);  // the frees have run: the memory is back in the pool
   d = Device();
 }
 
@@ -207,7 +208,7 @@ static int ensure_ybuf(oras_handle* h, int k) {
   if (yb <= d.ybuf_bytes) return ORAS_OK;
   dfree_s(d.ybuf, d.stream);
   d.ybuf_bytes = 0;
-  CK(cudaMallocAsync(&d.ybuf, yb, d.stream));
+  CK(pool_malloc(&d.ybuf, yb, d.stream));
   d.ybuf_bytes = yb;
   return ORAS_OK;
 }
@@ -220,7 +221,7 @@ static int alloc_factor_space(oras_handle* h, int bits) {
   size_t bytes = (size_t)(m.arena_tiles + 2 * m.nsub) * TB * TB * el;
   if (d.arena && d.factor_bits == bits && d.arena_bytes == bytes) return ORAS_OK;
   dfree_s(d.arena, d.stream);
-  cudaError_t e = cudaMallocAsync(&d.arena, bytes, d.stream);
+  cudaError_t e = pool_malloc(&d.arena, bytes, d.stream);
   if (e != cudaSuccess) {
     h->err = "local-factor arena of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e);
     d.arena = nullptr;
@@ -235,14 +236,14 @@ static int alloc_factor_space(oras_handle* h, int bits) {
   CK(cudaMemsetAsync(d.lu_cnt, 0, (size_t)m.nsub * slots * sizeof(int32_t), d.stream));
   CK(dalloc(d.lu_ipiv, (size_t)m.nsub * (2 * TB * 2 + 1)));
   dfree_s(d.lu_diag, d.stream);
-  CK(cudaMallocAsync(&d.lu_diag, (size_t)m.nsub * TB * TB * el, d.stream));
+  CK(pool_malloc(&d.lu_diag, (size_t)m.nsub * TB * TB * el, d.stream));
   {
     std::vector<int64_t> inv_off(m.nsub + 1, 0);
     for (int q = 0; q < m.nsub; ++q) inv_off[q + 1] = inv_off[q] + m.sub_np[q] / TB;
     CK(dput(d.sub_inv_off, inv_off, d.stream));
     dfree_s(d.dinv, d.stream);
     d.dinv_bytes = (size_t)inv_off[m.nsub] * 2 * TB * TB * el;
-    CK(cudaMallocAsync(&d.dinv, d.dinv_bytes, d.stream));
+    CK(pool_malloc(&d.dinv, d.dinv_bytes, d.stream));
   }
   dfree_s(d.ybuf, d.stream);
   d.ybuf_bytes = 0;
@@ -549,6 +550,17 @@ void oras_destroy(oras_handle* h) {
   delete h;
 }
 
+int oras_release_memory(int32_t device) {
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) return ORAS_ERR_CUDA;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = pool_trim(device);
+  cudaSetDevice(prev);
+  if (e == cudaErrorInvalidDevice) return ORAS_ERR_INVALID_ARG;
+  return e == cudaSuccess ? ORAS_OK : ORAS_ERR_CUDA;
+}
+
 int oras_footprint(const oras_handle* h, int32_t k, int64_t* bytes) {
   if (!h || !bytes || k < 1 || k > MAX_RHS) return ORAS_ERR_INVALID_ARG;
   *bytes = footprint_bytes(h, k);
@@ -636,7 +648,7 @@ static int ensure_ws(oras_handle* h, int k, int m) {
     CK(dalloc(d.Zd, nk * mm));
   } else {
     dfree_s(d.Zf, d.stream);
-    CK(cudaMallocAsync((void**)&d.Zf, nk * mm * 2 * sizeof(float), d.stream));
+    CK(pool_malloc((void**)&d.Zf, nk * mm * 2 * sizeof(float), d.stream));
   }
   CK(dalloc(d.w, nk));
   CK(dalloc(d.xk, nk));

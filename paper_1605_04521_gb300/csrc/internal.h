@@ -171,6 +171,38 @@ int prof_begin(const oras_handle* h);                 // -1 when timing is off
 void prof_end(const oras_handle* h, int cls, int begin, int launches);
 void count_launches(int n);                           // process-wide launch counter
 
+// Stream-ordered allocation from the current device's default memory pool.  The pool keeps
+// memory freed by cudaFreeAsync for reuse (release threshold unlimited, set once per device), so
+// a set-up after a destroy does not map the pages again.  If an allocation fails for lack of
+// memory, the pool's unused memory is returned to the driver and the allocation retried once.
+inline cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s) {
+  static std::mutex mu;
+  static std::set<int> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done.count(dev) && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess) done.insert(dev);
+    }
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e != cudaErrorMemoryAllocation) return e;
+  cudaGetLastError();
+  if (!pool && cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return e;
+  cudaMemPoolTrimTo(pool, 0);
+  return cudaMallocAsync(p, bytes, s);
+}
+
+// Returns the unused memory of a device's default pool to the driver.
+inline cudaError_t pool_trim(int dev) {
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = cudaDeviceGetDefaultMemPool(&pool, dev);
+  return e == cudaSuccess ? cudaMemPoolTrimTo(pool, 0) : e;
+}
+
 // Raises a kernel's dynamic shared-memory limit to the device's opt-in maximum, once per
 // (device, kernel).  A fixed maximum (instead of the size of the next launch) keeps launches of
 // the same kernel from different host threads from lowering each other's limit.

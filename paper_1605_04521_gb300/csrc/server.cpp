@@ -159,8 +159,8 @@ int run_request(Request* q, cudaStream_t stream, std::string& err) {
       oras_complex* b = nullptr;
       oras_complex* xd = nullptr;
       const size_t bytes = (size_t)N * q->k * sizeof(oras_complex);
-      cudaError_t e = cudaMallocAsync((void**)&b, bytes, stream);
-      if (e == cudaSuccess) e = cudaMallocAsync((void**)&xd, bytes, stream);
+      cudaError_t e = pool_malloc((void**)&b, bytes, stream);
+      if (e == cudaSuccess) e = pool_malloc((void**)&xd, bytes, stream);
       if (e != cudaSuccess) {
         rc = e == cudaErrorMemoryAllocation ? ORAS_ERR_OUT_OF_MEMORY : ORAS_ERR_CUDA;
         err = std::string("right-hand side buffers: ") + cudaGetErrorString(e);
@@ -252,6 +252,7 @@ int oras_server_create(const oras_server_config* cfg, oras_server** out) {
     size_t fr = 0, tot = 0;
     cudaGetDevice(&prev);
     cudaError_t e = cudaSetDevice(c.device);
+    if (e == cudaSuccess) e = pool_trim(c.device);  // the pool's unused memory counts as free
     if (e == cudaSuccess) e = cudaMemGetInfo(&fr, &tot);
     cudaSetDevice(prev);
     if (e != cudaSuccess) return ORAS_ERR_CUDA;

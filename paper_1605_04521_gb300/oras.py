@@ -111,6 +111,7 @@ EXPORTS = {
     "oras_launch_count": (C.c_int64, []),
     "oras_precond_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "oras_footprint": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
+    "oras_release_memory": (C.c_int, [C.c_int32]),
     "oras_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_int32]),
     "oras_lu_group": (C.c_int32, [C.c_void_p]),
     "oras_server_create": (C.c_int, [C.POINTER(oras_server_config), C.POINTER(C.c_void_p)]),
@@ -414,6 +415,13 @@ def oras_autotune(h):
 
 def oras_lu_group(h):
     return lib.oras_lu_group(h)
+
+
+def oras_release_memory(device=0):
+    """Returns the unused memory of the device's memory pool to the driver."""
+    rc = lib.oras_release_memory(int(device))
+    if rc != ORAS_OK:
+        raise OrasError(rc, f"oras_release_memory({device}) failed")
 
 
 def oras_footprint(h, k=1):

@@ -278,6 +278,27 @@ def test_refactor_equals_fresh_setup(O):
         O.oras_destroy(h2)
 
 
+def test_pool_memory_reused_and_released(O):
+    """A handle set up on memory that an earlier handle freed into the device's pool solves
+    bit-identically; oras_release_memory then hands the pool's unused memory back."""
+    import torch
+    w = synth.small(n=5, r=2, nsub=8, overlap=1)
+    xs = []
+    for _ in range(2):
+        h = gpu_handle(O, w)
+        try:
+            b = O.oras_rhs_dipole(h, synth.dipole_ring(1)[0], [0, 0, 1.0])
+            x, info, rc = O.oras_solve(h, b, 1e-8)
+            assert rc == O.ORAS_OK
+            xs.append(x)
+        finally:
+            O.oras_destroy(h)
+    assert np.array_equal(xs[0], xs[1])
+    free0 = torch.cuda.mem_get_info(0)[0]
+    O.oras_release_memory(0)
+    assert torch.cuda.mem_get_info(0)[0] >= free0
+
+
 def test_full_size_head16_r2_workload(O):
     """The 16^3 x 6, r = 2, 64-subdomain, 2-layer workload (163,424 DOFs): integer arrays
     bit-exact, sampled element matrices and the whole A within 1e-12, dipole load within

@@ -123,3 +123,10 @@ def test_error_codes(O):
         assert e.value.code == O.ORAS_ERR_STATE
     finally:
         O.oras_destroy(h)
+
+
+def test_release_memory_of_a_missing_device_is_an_error(O):
+    """Device 9999 does not exist: INVALID_ARG on a GPU machine, CUDA (no device) here."""
+    with pytest.raises(O.OrasError) as e:
+        O.oras_release_memory(9999)
+    assert e.value.code in (O.ORAS_ERR_INVALID_ARG, O.ORAS_ERR_CUDA)
