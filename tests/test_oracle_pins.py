@@ -501,3 +501,30 @@ def test_oras_converges_faster_than_ras(n, r, nsub):
     it_o = fgmres.fgmres(lambda v: P.A @ v, P.oras.apply, b, 1e-8, 50, 5000).iterations
     it_r = fgmres.fgmres(lambda v: P.A @ v, ras.apply, b, 1e-8, 50, 5000).iterations
     assert it_o < it_r
+
+
+def test_oas_is_symmetric_and_oras_is_not():
+    """Sec. 4: without the partition of unity, M_OAS = sum_s R_s^T A_s^-1 R_s is symmetric for a
+    symmetric problem (here complex symmetric: A = A^T and every A_s = A_s^T); the D_s of ORAS
+    break that symmetry.  Dense M from the oracle's apply on the unit vectors."""
+    w = synth.small(n=3, r=1, nsub=4, overlap=1)
+    P = problem.from_workload(w)
+    n = P.topo.ndof
+    E = np.eye(n)
+    for weights, symmetric in (("none", True), ("pou", False)):
+        M = dd.ORAS(P.topo, P.xyz, P.eps_r, P.mu_r, P.k0, P.dec, weights=weights)
+        D = np.stack([M.apply(E[:, j]) for j in range(n)], axis=1)
+        asym = np.abs(D - D.T).max() / np.abs(D).max()
+        assert (asym <= 1e-12) if symmetric else (asym >= 1e-3), (weights, asym)
+
+
+@pytest.mark.parametrize("n,r,nsub", [(4, 2, 8), (5, 1, 16)])
+def test_oras_converges_faster_than_oas(n, r, nsub):
+    """Sec. 4: in practice OAS (no partition of unity) converges more slowly than ORAS."""
+    w = synth.small(n=n, r=r, nsub=nsub, overlap=1)
+    P = problem.from_workload(w)
+    oas = dd.ORAS(P.topo, P.xyz, P.eps_r, P.mu_r, P.k0, P.dec, weights="none")
+    b = P.B[:, 0]
+    it_oras = fgmres.fgmres(lambda v: P.A @ v, P.oras.apply, b, 1e-8, 50, 5000).iterations
+    it_oas = fgmres.fgmres(lambda v: P.A @ v, oas.apply, b, 1e-8, 50, 5000).iterations
+    assert it_oras < it_oas
