@@ -26,14 +26,21 @@
 
 namespace oras {
 
-// Runs fn(i, worker) for i in [0, n) on up to min(hardware_concurrency(), 16) threads (chunks from a
-// shared counter).  Every i writes only its own outputs, so results do not depend on the thread
-// count or the schedule.  An exception in any worker is rethrown here after all workers joined.
-template <typename F>
-static void parallel_for(int64_t n, int64_t grain, F fn) {
+// Number of workers parallel_for(n, grain, ...) uses (at most min(hardware_concurrency(), 16));
+// per-worker buffers are sized with it.
+static int workers_for(int64_t n, int64_t grain) {
   unsigned hw = std::thread::hardware_concurrency();
   int64_t nw = std::min<int64_t>(hw ? hw : 1, 16);
-  nw = std::min<int64_t>(nw, (n + grain - 1) / grain);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(nw, (n + grain - 1) / grain));
+}
+
+// Runs fn(i, worker) for i in [0, n), worker in [0, workers_for(n, grain)), chunks of `grain`
+// taken from a shared counter.  Every i writes only its own outputs, so results do not depend on
+// the thread count or the schedule.  An exception in any worker is rethrown here after all
+// workers joined.
+template <typename F>
+static void parallel_for(int64_t n, int64_t grain, F fn) {
+  const int nw = workers_for(n, grain);
   if (nw <= 1) {
     for (int64_t i = 0; i < n; ++i) fn(i, 0);
     return;
@@ -66,12 +73,6 @@ static void parallel_for(int64_t n, int64_t grain, F fn) {
   work(0);
   for (auto& x : th) x.join();
   if (err) std::rethrow_exception(err);
-}
-
-static int workers_for(int64_t n, int64_t grain) {
-  unsigned hw = std::thread::hardware_concurrency();
-  int64_t nw = std::min<int64_t>(hw ? hw : 1, 16);
-  return (int)std::max<int64_t>(1, std::min<int64_t>(nw, (n + grain - 1) / grain));
 }
 
 static const int EDGES[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
