@@ -86,3 +86,29 @@ def test_clock_record_flags_every_throttle_reason(tmp_path):
     c = _clock_summary(tmp_path, rows)
     assert c["samples"] == 2 and c["sm_mhz"] == 1650.0
     assert c["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+
+
+class _FakeLib:
+    """Subdomain sizes only: (n_s, tets, padded order)."""
+
+    def __init__(self, sizes):
+        self.sizes = sizes
+
+    def oras_subdomain_size(self, h, s):
+        n = self.sizes[s]
+        return n, 0, -(-n // bench.TB) * bench.TB
+
+
+def test_work_model_closed_forms():
+    sizes = [12749, 1000, 64, 8370]
+    upd, apply_bytes = bench.work_model(_FakeLib(sizes), None, len(sizes), 3)
+    tb = bench.TB
+    closed = 0.0
+    for n in sizes:
+        nts = -(-n // tb)
+        closed += 8.0 * tb ** 3 * (nts - 1) * nts * (2 * nts - 1) / 6.0   # 8 TB^3 sum_j j^2
+    assert upd == pytest.approx(closed, rel=1e-12)
+    # the trailing updates of a dense LU are (8/3) n^3 real flops to leading order
+    big = bench.work_model(_FakeLib([12749]), None, 1, 1)[0]
+    assert big == pytest.approx(8.0 / 3.0 * 12749 ** 3, rel=0.01)
+    assert apply_bytes == pytest.approx(8.0 * sum(n * n for n in sizes) + 3 * 36.0 * sum(sizes))
