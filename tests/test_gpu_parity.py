@@ -278,6 +278,26 @@ def test_refactor_equals_fresh_setup(O):
         O.oras_destroy(h2)
 
 
+@pytest.mark.parametrize("bits,tol", [(64, 1e-9), (32, TOL_APPLY_F32)])
+def test_oas_weights(O, bits, tol):
+    """OAS (ORAS_WEIGHTS_NONE, Sec. 4): z = sum_s R_s^T A_s^-1 R_s v against the oracle's OAS,
+    and an OAS-preconditioned solve reaching the FP64 residual bar."""
+    w = synth.small(n=4, r=2, nsub=8, overlap=1)
+    p = problem.from_workload(w)
+    oas = dd.ORAS(p.topo, p.xyz, p.eps_r, p.mu_r, p.k0, p.dec, weights="none")
+    rng = np.random.default_rng(12)
+    v = rng.normal(size=p.topo.ndof) + 1j * rng.normal(size=p.topo.ndof)
+    h = gpu_handle(O, w, factor_bits=bits, weights=O.ORAS_WEIGHTS_NONE)
+    try:
+        assert rel(O.oras_precond(h, v), oas.apply(v)) <= tol
+        b = p.B[:, 0]
+        x, info, rc = O.oras_solve(h, b, 1e-8)
+        assert rc == O.ORAS_OK
+        assert np.linalg.norm(b - p.A @ x) / np.linalg.norm(b) <= 1e-8
+    finally:
+        O.oras_destroy(h)
+
+
 def test_pool_memory_reused_and_released(O):
     """A handle set up on memory that an earlier handle freed into the device's pool solves
     bit-identically; oras_release_memory then hands the pool's unused memory back."""
