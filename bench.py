@@ -494,7 +494,13 @@ def run_ours(args, world, rank, local):
     e2e_val = world * e2e_steps * krhs / e2e_s
     serving = None
     if rank == 0 and args.serve_count > 0:
-        serving = serving_replay(O, args.serve_count, args.serve_slots, device=local, max_iter=args.serve_max_iter)
+        # the serving replay is reported beside the main measurement: a failure there is recorded
+        # in the line instead of losing the measurement taken above
+        try:
+            serving = serving_replay(O, args.serve_count, args.serve_slots, device=local,
+                                     max_iter=args.serve_max_iter)
+        except Exception as e:  # noqa: BLE001
+            serving = {"error": f"{type(e).__name__}: {e}"}
     out = None
     if rank == 0:
         cpu = None
