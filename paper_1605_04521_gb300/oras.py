@@ -211,6 +211,9 @@ def oras_create(xyz, tets, r, nsub, overlap, part=None, **opts):
 
 
 def oras_setup(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part=None, **opts):
+    """oras_create + oras_factor: host mesh xyz (nv, 3), tets (nt, 4), per-tet complex eps_r and
+    mu_r (None: 1), wave number k0, degree r, nsub subdomains (RCB unless part is given),
+    overlap layers; opts are oras_options fields.  Returns the handle."""
     p, keep = _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part)
     o = _options(**opts)
     h = C.c_void_p()
@@ -220,6 +223,8 @@ def oras_setup(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part=None, **opts):
 
 
 def oras_factor(h, eps_r, mu_r, k0, mem=ORAS_MEM_HOST):
+    """(Re)assembles A and the local matrices for new materials on the handle's mesh and factors
+    them (batched LU)."""
     if mem == ORAS_MEM_HOST:
         eps_r = _c128(eps_r)
         mu_r = None if mu_r is None else _c128(mu_r)
@@ -227,10 +232,12 @@ def oras_factor(h, eps_r, mu_r, k0, mem=ORAS_MEM_HOST):
 
 
 def oras_destroy(h):
+    """Frees the handle; its device memory returns to the device's memory pool."""
     lib.oras_destroy(h)
 
 
 def oras_set_stream(h, stream_ptr):
+    """Runs the handle's work on a caller's CUDA stream (e.g. torch.cuda.Stream().cuda_stream)."""
     return _check(h, lib.oras_set_stream(h, C.c_void_p(stream_ptr)))
 
 
@@ -336,6 +343,7 @@ def _vec_call(fn, h, x, k, mem, out=None):
 
 
 def oras_matvec(h, x, k=1, mem=ORAS_MEM_HOST, out=None):
+    """y = A x (host: (N,) or (N, k) complex128; device: torch tensors, N x k column-major)."""
     return _vec_call(lib.oras_matvec, h, x, k, mem, out)
 
 
@@ -353,6 +361,8 @@ def oras_matvec_c64(h, x, k=1, mem=ORAS_MEM_HOST, out=None):
 
 
 def oras_precond(h, v, k=1, mem=ORAS_MEM_HOST, out=None):
+    """z = M^-1 v, the ORAS preconditioner (OAS with weights=ORAS_WEIGHTS_NONE); layouts as in
+    oras_matvec."""
     return _vec_call(lib.oras_precond, h, v, k, mem, out)
 
 
@@ -377,6 +387,7 @@ def oras_solve(h, rhs, tol, k=1, mem=ORAS_MEM_HOST, out=None):
 
 
 def oras_rhs_dipole(h, x0, direction, mem=ORAS_MEM_HOST, out=None):
+    """Point-dipole load b_a = w_a(x0) . direction (complex128, length N)."""
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
     d = np.ascontiguousarray(direction, dtype=np.float64)
     if mem == ORAS_MEM_HOST:
@@ -386,6 +397,7 @@ def oras_rhs_dipole(h, x0, direction, mem=ORAS_MEM_HOST, out=None):
 
 
 def oras_rhs_plane_wave(h, d, p, mem=ORAS_MEM_HOST, out=None):
+    """Impedance data of the plane wave p exp(-i gamma d.x) on the outer boundary, as a load."""
     d = np.ascontiguousarray(d, dtype=np.float64)
     p = _c128(p)
     if mem == ORAS_MEM_HOST:
@@ -446,6 +458,8 @@ def _scheck(srv, rc, ticket=0, allow=(ORAS_OK,)):
 
 
 def oras_server_create(hbm_budget=0, device=0, max_active=4, planners=2):
+    """Serving runtime: `max_active` worker slots (one CUDA stream each), `planners` host set-up
+    threads, admission by device footprint within hbm_budget bytes (0: 0.9 of free memory)."""
     cfg = oras_server_config()
     cfg.hbm_budget, cfg.device, cfg.max_active, cfg.planners = int(hbm_budget), int(device), int(max_active), int(planners)
     srv = C.c_void_p()
