@@ -39,6 +39,14 @@ struct TcShape {
   static constexpr uint32_t STAGE_BYTES = (4 + 2 * BN) * TC_BOX_BYTES;  // A_re, A_im (2 tiles), B_re, B_im (BN)
   static constexpr uint32_t TMEM_COLS = 2 * 64 * BN;                    // D_re, D_im
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
+  // stage bases stay on the 1024-byte boundary of the 128-byte swizzle atoms
+  static_assert(TC_BOX_BYTES % 1024 == 0 && STAGE_BYTES % 1024 == 0, "swizzle-atom alignment");
+  // dynamic (+ alignment slack) and static shared memory within the 227 KB opt-in limit
+  static_assert(SMEM + 1024 <= 227 * 1024, "shared memory per CTA");
+  // tcgen05.alloc takes a power of two from 32 to 512 columns
+  static_assert(TMEM_COLS >= 32 && TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM columns");
+  // kind::tf32 with M = 128: N a multiple of 16, at most 256
+  static_assert((64 * BN) % 16 == 0 && 64 * BN <= 256, "MMA N");
 };
 
 struct TcArgs {
@@ -289,6 +297,7 @@ struct TrsmArgs {
 };
 
 constexpr uint32_t TRSM_CHUNK_BYTES = 6 * TC_BOX_BYTES;  // A_re (2 boxes), A_im (2), B_re, B_im
+static_assert(TRSM_CHUNK_BYTES % 1024 == 0 && 2 * TRSM_CHUNK_BYTES + 2048 <= 227 * 1024, "trsm staging");
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_trsm_tc(const __grid_constant__ CUtensorMap tmap, TrsmArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
