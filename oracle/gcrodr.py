@@ -16,7 +16,7 @@ Maiti (SIAM J. Sci. Comput. 28, 2006), written from its description:
 * for the next system the same U is kept and C recomputed from A_hat_new U by a QR
   factorisation.
 
-With k = 0 it is restarted GMRES(m).  Counts are matrix-vector products with A_hat.
+With k = 0 it is restarted GMRES(m).
 Dense NumPy/SciPy only: library eigen-, QR and least-squares routines serve as steps.
 """
 from __future__ import annotations
@@ -30,7 +30,8 @@ import scipy.linalg as sla
 @dataclass
 class GcroResult:
     y: np.ndarray            # solution of A_hat y = b
-    matvecs: int             # products with A_hat (including the recycled subspace's k)
+    matvecs: int             # products with A_hat in Arnoldi steps and for C = A_hat U (the true
+                             # residual at each cycle end is not counted, as in fgmres)
     relres: float            # true ||b - A_hat y|| / ||b||
     converged: bool
     U: np.ndarray            # recycled subspace for the next system (n x k), or None
