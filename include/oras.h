@@ -120,10 +120,12 @@ typedef struct {
   double relres;              /* true FP64 ||b - A x|| / ||b|| of the returned x        */
 } oras_info;
 
-/* Message of the last failing call on this thread for h (NULL: calls without a handle). */
+/* Message of the last failing call on this thread for h (NULL: calls without a handle).  No
+ * counterpart in the paper (error reporting).  Never fails; the string stays valid until the
+ * next failing call on h or its destruction. */
 const char* oras_last_error(const oras_handle* h);
 
-/* Version of the ABI described here. */
+/* Version of the ABI described here.  No counterpart in the paper.  Never fails. */
 int32_t oras_abi_version(void);
 
 /* ---------------------------------------------------------------- set-up */
@@ -150,11 +152,13 @@ int oras_create(const oras_problem* p, const oras_options* o, oras_handle** out)
 int oras_factor(oras_handle* h, const oras_complex* eps_r, const oras_complex* mu_r, double k0,
                 int32_t mem);
 
-/* oras_create followed by oras_factor(p->eps_r, p->mu_r, p->k0, ORAS_MEM_HOST). */
+/* oras_create followed by oras_factor(p->eps_r, p->mu_r, p->k0, ORAS_MEM_HOST) (Sec. 2-4).
+ * Errors: those of oras_create and oras_factor; on failure nothing is kept and *out is
+ * not set. */
 int oras_setup(const oras_problem* p, const oras_options* o, oras_handle** out);
 
 /* Frees host and device memory of h (NULL is ignored).  The device memory goes back to the
- * device's memory pool (see the conventions above). */
+ * device's memory pool (see the conventions above).  No counterpart in the paper. */
 void oras_destroy(oras_handle* h);
 
 /* Returns to the driver the device memory that the default memory pool of `device` holds
@@ -162,7 +166,8 @@ void oras_destroy(oras_handle* h);
  * memory management of the single-GPU library.  Errors: INVALID_ARG (no such device), CUDA. */
 int oras_release_memory(int32_t device);
 
-/* Stream for all device work of h (a cudaStream_t; NULL = legacy default stream). */
+/* Stream for all device work of h (a cudaStream_t; NULL = legacy default stream).  No
+ * counterpart in the paper.  Errors: INVALID_ARG (h NULL). */
 int oras_set_stream(oras_handle* h, void* stream);
 
 /* ---------------------------------------------------------------- solve (Sec. 5) */
@@ -182,17 +187,23 @@ int oras_solve(oras_handle* h, const oras_complex* rhs, int32_t k, double tol, o
 /* Impedance data of Sec. 2 for the plane wave E = p exp(-i gamma d.x),
  * gamma = k0 sqrt(mu_r eps_r) (principal root), on every outer face:
  * g = mu_r^{-1} (curl E) x n + i beta n x (E x n),  b_a = int_boundary g . w_a.
- * d: unit direction [3], p: polarisation [3] (host).  b: N values in `mem`. */
+ * d: unit direction [3], p: polarisation [3] (host).  b: N values in `mem`.
+ * Errors: INVALID_ARG (NULL arguments), STATE (no oras_factor yet), CUDA. */
 int oras_rhs_plane_wave(oras_handle* h, const double* d, const oras_complex* p, oras_complex* b,
                         int32_t mem);
 
 /* Point dipole: b_a = w_a(x0) . dir in the lowest-index tetrahedron whose barycentric
- * coordinates of x0 are all >= -1e-12.  x0, dir: [3] host.  b: N values in `mem`.
- * Error INVALID_ARG if x0 lies in no tetrahedron. */
+ * coordinates of x0 are all >= -1e-12.  x0, dir: [3] host.  b: N values in `mem`.  The
+ * paper's sources are waveguide ports (Sec. 2); the point dipole is the synthetic source that
+ * stands in for them.  Errors: INVALID_ARG (NULL arguments, or x0 in no tetrahedron), STATE
+ * (no oras_factor yet), CUDA. */
 int oras_rhs_dipole(oras_handle* h, const double* x0, const double* dir, oras_complex* b,
                     int32_t mem);
 
-/* ---------------------------------------------------------------- queries (host data) */
+/* ---------------------------------------------------------------- queries (host data)
+ * The mesh, numbering and subdomain data of oras_create (Sec. 3-4), copied to the caller's
+ * host arrays.  Counts return -1 for a NULL handle; the int-returning calls return
+ * INVALID_ARG for a NULL handle or output, or s out of range. */
 
 int64_t oras_ndof(const oras_handle* h);            /* N, or -1                          */
 int32_t oras_nlocal(const oras_handle* h);          /* n_loc = r(r+2)(r+3)/2, or -1      */
@@ -214,12 +225,16 @@ int64_t oras_arena_bytes(const oras_handle* h);
 
 /* ---------------------------------------------------------------- operator access */
 
-/* Element matrices A_T (without boundary-face terms) of `count` tetrahedra `tets` (host),
- * copied from the device into out[count][n_loc][n_loc] (host). Requires oras_factor. */
+/* Element matrices A_T (without boundary-face terms, Sec. 2-3) of `count` tetrahedra `tets`
+ * (host), copied from the device into out[count][n_loc][n_loc] (host).  Errors: INVALID_ARG
+ * (NULL arrays, tetrahedron id out of range), STATE (no oras_factor yet), CUDA. */
 int oras_element_matrices(oras_handle* h, const int32_t* tets, int64_t count, oras_complex* out);
-/* CSR of A (host arrays): rowptr [N+1], cols [nnz], vals [nnz]; any may be NULL. */
+/* CSR of the global matrix A (Sec. 2-3; host arrays): rowptr [N+1], cols [nnz], vals [nnz];
+ * any may be NULL.  Errors: INVALID_ARG (h NULL), STATE (vals before oras_factor), CUDA. */
 int oras_global_csr(oras_handle* h, int64_t* rowptr, int32_t* cols, oras_complex* vals);
-/* y = A x for k columns (N x k column-major, `mem`). */
+/* y = A x for k columns (N x k column-major, `mem`), the product of Sec. 5's GMRES.
+ * Errors: INVALID_ARG (NULL vectors, k < 1 or > 64), STATE (no oras_factor yet),
+ * OUT_OF_MEMORY, CUDA. */
 int oras_matvec(oras_handle* h, const oras_complex* x, oras_complex* y, int32_t k, int32_t mem);
 /* y = A x for k columns of complex FP32 x (N x k column-major pairs of floats, `mem`) into
  * complex FP64 y (N x k column-major): the product FGMRES forms with the preconditioned vectors
@@ -227,7 +242,10 @@ int oras_matvec(oras_handle* h, const oras_complex* x, oras_complex* y, int32_t 
  * FP32 hi + lo parts, exact product and sum errors carried), about 2^-48 relative error per
  * entry.  Requires oras_factor.  Errors: INVALID_ARG, STATE, CUDA. */
 int oras_matvec_c64(oras_handle* h, const void* x, oras_complex* y, int32_t k, int32_t mem);
-/* z = M^{-1}_ORAS v for k columns (N x k column-major, `mem`), Sec. 4. */
+/* z = M^{-1}_ORAS v for k columns (N x k column-major, `mem`), Sec. 4 (M^{-1}_OAS with
+ * weights ORAS_WEIGHTS_NONE).  Errors: INVALID_ARG (NULL vectors, k < 1 or > 64), STATE (no
+ * oras_factor yet), OUT_OF_MEMORY, CUDA.  A bounded device wait that gives up inside this
+ * call is not reported yet (oras_factor reports its own). */
 int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k, int32_t mem);
 
 /* Allocation-free preconditioner apply: z = M^{-1}_ORAS v for k columns, the same result as
@@ -260,7 +278,8 @@ int oras_precond_noalloc(oras_handle* h, const oras_complex* v, oras_complex* z,
  * allowed).
  * Errors: INVALID_ARG, STATE (no oras_factor yet), and those of oras_factor. */
 int oras_autotune(oras_handle* h, int32_t* panel, double* ms, int32_t nms);
-/* The raster group oras_autotune chose for the handle (0 before tuning: the default). */
+/* The raster group oras_autotune chose for the handle (0 before tuning: the default); -1 for
+ * a NULL handle.  No counterpart in the paper (a tile shape of the batched LU). */
 int32_t oras_lu_group(const oras_handle* h);
 
 /* Device bytes that oras_factor followed by an oras_solve of k right-hand sides allocate for
@@ -342,7 +361,7 @@ int oras_ticket_wait(oras_server* srv, int64_t ticket, int32_t timeout_ms);
 int oras_ticket_info(oras_server* srv, int64_t ticket, oras_ticket* out);
 /* Message of a failed ticket ("" if none); ticket <= 0: the last failing server call. */
 const char* oras_server_error(oras_server* srv, int64_t ticket);
-/* Budget, occupancy and counters. */
+/* Budget, occupancy and counters.  Errors: INVALID_ARG (NULL server or output). */
 int oras_server_stats(oras_server* srv, oras_server_counters* out);
 /* Cancels queued requests (status STATE), lets running ones finish, joins the threads and
  * frees everything, including tickets nobody collected. */
