@@ -240,7 +240,8 @@ int oras_matvec(oras_handle* h, const oras_complex* x, oras_complex* y, int32_t 
  * complex FP64 y (N x k column-major): the product FGMRES forms with the preconditioned vectors
  * of FP32 factors.  Computed on the FP32 pipes with error-free transformations (A split into
  * FP32 hi + lo parts, exact product and sum errors carried), about 2^-48 relative error per
- * entry.  Requires oras_factor.  Errors: INVALID_ARG, STATE, CUDA. */
+ * entry: the SpMV of Sec. 5's GMRES, formed on the FP32 pipes because GB300's FP64 pipe is
+ * narrow.  Requires oras_factor.  Errors: INVALID_ARG, STATE, CUDA. */
 int oras_matvec_c64(oras_handle* h, const void* x, oras_complex* y, int32_t k, int32_t mem);
 /* z = M^{-1}_ORAS v for k columns (N x k column-major, `mem`), Sec. 4 (M^{-1}_OAS with
  * weights ORAS_WEIGHTS_NONE).  Errors: INVALID_ARG (NULL vectors, k < 1 or > 64), STATE (no
@@ -265,7 +266,7 @@ int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t
  * Errors: STATE (no oras_factor yet), INVALID_ARG, CUDA. */
 int oras_precond_noalloc(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k);
 
-/* Autotuner of the batched LU's tile shapes: the outer panel width (tiles of 64 columns per
+/* Autotuner of the batched LU's tile shapes (no counterpart in the paper): the outer panel width (tiles of 64 columns per
  * trailing update; trades the inner panel updates against the passes over the trailing matrix)
  * and the raster group of the tensor-core update (output blocks that share operands in L2).
  * Factorises the handle's current problem (materials of the last oras_factor, on the handle's
@@ -285,7 +286,8 @@ int32_t oras_lu_group(const oras_handle* h);
 /* Device bytes that oras_factor followed by an oras_solve of k right-hand sides allocate for
  * this handle (factor arena, inverted diagonal blocks, A, element matrices, Krylov basis of
  * restart+1 FP64 and restart FP32/FP64 vectors per right-hand side, staging), including the
- * allocator's rounding.  Host-only: valid right after oras_create.  Errors: INVALID_ARG. */
+ * allocator's rounding.  Host-only: valid right after oras_create.  No counterpart in the
+ * paper (admission control of the serving runtime).  Errors: INVALID_ARG. */
 int oras_footprint(const oras_handle* h, int32_t k, int64_t* bytes);
 
 /* ---------------------------------------------------------------- serving
@@ -359,15 +361,18 @@ int oras_wait(oras_server* srv, int64_t ticket, oras_complex* x, int64_t n, oras
 int oras_ticket_wait(oras_server* srv, int64_t ticket, int32_t timeout_ms);
 /* Record of a ticket, pending or retired.  Errors: INVALID_ARG (unknown ticket). */
 int oras_ticket_info(oras_server* srv, int64_t ticket, oras_ticket* out);
-/* Message of a failed ticket ("" if none); ticket <= 0: the last failing server call. */
+/* Message of a failed ticket ("" if none); ticket <= 0: the last failing server call.  Never
+ * fails ("" for a NULL server or an unknown ticket). */
 const char* oras_server_error(oras_server* srv, int64_t ticket);
 /* Budget, occupancy and counters.  Errors: INVALID_ARG (NULL server or output). */
 int oras_server_stats(oras_server* srv, oras_server_counters* out);
 /* Cancels queued requests (status STATE), lets running ones finish, joins the threads and
- * frees everything, including tickets nobody collected. */
+ * frees everything, including tickets nobody collected.  NULL is ignored. */
 void oras_server_destroy(oras_server* srv);
 
-/* ---------------------------------------------------------------- instrumentation */
+/* ---------------------------------------------------------------- instrumentation
+ * No counterpart in the paper: measurement of the library's own kernels.  The int-returning
+ * calls return INVALID_ARG for a NULL handle or output. */
 
 /* Device time accumulated by kernel class since the last oras_reset_timings, measured with
  * CUDA event pairs on the handle's stream while timing is on: t[2c] = milliseconds and
