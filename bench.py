@@ -60,16 +60,19 @@ def parse():
                          "head32r3: 32^3 r=3 4096 subdomains without overlap (3.7 M DOFs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--serve-count", type=int, default=12,
+    ap.add_argument("--serve-count", type=int, default=50,
                     help="requests of the serving stream replayed after the main measurement (0: none)")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--clocks-dir", default=None,
                     help="where the nvidia-smi clock samples of the timed region are written (default: the temp dir)")
     ap.add_argument("--factor-bits", type=int, default=0, choices=[0, 32, 64],
                     help="local factor precision (0: the workload's; 64: the plain FP64 path)")
+    ap.add_argument("--fp64-path", type=int, default=1,
+                    help="1: also time the plain FP64 single-RHS path against the FP32-factor path on the "
+                         "workloads where the FP64 factorisation finishes (head8, cube8)")
     ap.add_argument("--lu-panel", type=int, default=0,
                     help="LU outer panel width in tiles (0: picked by oras_autotune at set-up)")
-    ap.add_argument("--serve-max-iter", type=int, default=60,
+    ap.add_argument("--serve-max-iter", type=int, default=150,
                     help="FGMRES iteration cap per served request (requests above it report not converged)")
     return ap.parse_args()
 
@@ -189,13 +192,14 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ algorithmic work
-def work_model(O, h, nsub, k):
+def work_model(O, h, nsub, k, factor_bytes=8):
     """Algorithmic work of the kernels whose roofline is reported.
 
     LU trailing update: 8 real flops per complex multiply-add; a step of panel k updates
     (nts-k-1)^2 tiles of TB x TB with TB complex MACs each.
-    ORAS apply: reads every stored factor entry once (8 B per complex FP32 entry, n_s^2 per
-    subdomain), plus per RHS a 4 B index, a 16 B gather and a 16 B scatter per local DOF."""
+    ORAS apply: one pass reads every stored factor entry once (8 B per complex FP32 entry, 16 B
+    per FP64 entry, n_s^2 per subdomain), plus per right-hand side of the pass a 4 B index, a 16 B
+    gather and a 16 B scatter per local DOF; k = right-hand sides per pass."""
     upd = 0.0
     ns_sq = 0
     ns_sum = 0
@@ -205,8 +209,27 @@ def work_model(O, h, nsub, k):
         upd += sum((nts - q - 1) ** 2 for q in range(nts)) * 8.0 * TB ** 3
         ns_sq += n * n
         ns_sum += n
-    apply_bytes = 8.0 * ns_sq + ns_sum * (4 + 16 * 2) * k
+    apply_bytes = float(factor_bytes) * ns_sq + ns_sum * (4 + 16 * 2) * k
     return upd, apply_bytes
+
+
+def rhs_groups(k, per_pass):
+    """Right-hand sides in each launch when k columns go through a kernel per_pass at a time."""
+    return [min(per_pass, k - r0) for r0 in range(0, k, per_pass)]
+
+
+def apply_group_sizes(k, factor_bits):
+    """Right-hand sides of each apply pass: groups of up to 4 (FP32 factors) or 2 (FP64), the
+    last one rounded up to a power of two (its unused lanes carry zeros)."""
+    maxkr = 4 if factor_bits == 32 else 2
+    out, r0 = [], 0
+    while r0 < k:
+        kr = 1
+        while kr < maxkr and kr < k - r0:
+            kr *= 2
+        out.append(min(kr, k - r0))
+        r0 += min(kr, k - r0)
+    return out
 
 
 TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.json")
@@ -231,30 +254,50 @@ def measured_traffic(kernel, workload, panel):
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64, nominal (no measured figure in the peaks file)
 
 
-def roofline(timings, upd_flops_per_factor, apply_bytes, factors, hbm, bf16_burst, factor_bits=32):
+def spmv_bytes(n, nnz, k, fp32_input):
+    """Algorithmic bytes of one SpMV launch over k right-hand sides: the CSR matrix once (16 B of
+    values + 4 B column per entry, 8 B row pointer per row), the input vector entries (8 B complex
+    FP32 or 16 B complex FP64) and the FP64 output entries (16 B) per right-hand side."""
+    return 20.0 * nnz + 8.0 * (n + 1) + (8.0 if fp32_input else 16.0) * n * k + 16.0 * n * k
+
+
+def roofline(timings, upd_flops_per_factor, apply_bytes, factors, hbm, bf16_sus, factor_bits=32, spmv=None):
+    """Roofline objects of the kernel classes timed with CUDA events inside the step: the
+    dominant class (largest device time) first, then the others that have a work model.  The
+    TF32 peak is the measured sustained bf16 rate (the update runs inside a seconds-long step)
+    times the nominal tf32/bf16 ratio.  spmv = (bytes of all SpMV launches of the timed steps)."""
     cls = {c: v for c, v in timings.items() if v[1] > 0}
     dom = max(cls, key=lambda c: cls[c][0])
-    ms, launches = cls[dom]
-    if dom == "lu_update" and factor_bits == 64:
+    out = {}
+    if "lu_update" in cls:
+        ms, _ = cls["lu_update"]
         achieved = upd_flops_per_factor * factors / (ms / 1e3) / 1e12
-        return dom, {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
-                     "kernel": "k_lu_update<double> (FP64 CUDA-core trailing update)",
-                     "peak_note": "nominal GB300 dense FP64 (not measured)"}
-    if dom == "lu_update":
-        flops = upd_flops_per_factor * factors
-        achieved = flops / (ms / 1e3) / 1e12
-        peak = bf16_burst * TF32_OVER_BF16
-        return dom, {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_lu_update_tc (tcgen05 kind::tf32 complex trailing update)",
-                     "peak_note": "TF32 dense = measured bf16 burst x nominal tf32/bf16 ratio"}
-    if dom == "apply":
+        if factor_bits == 64:
+            out["lu_update"] = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                                "kernel": "k_lu_update<double> (FP64 CUDA-core trailing update)",
+                                "peak_note": "nominal GB300 dense FP64 (not measured)"}
+        else:
+            peak = bf16_sus * TF32_OVER_BF16
+            out["lu_update"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                "frac": achieved / peak, "traffic": None,
+                                "kernel": "k_lu_update_tc (tcgen05 kind::tf32 complex trailing update)",
+                                "peak_note": "TF32 dense = measured bf16 sustained (of measured) x nominal "
+                                             "tf32/bf16 ratio 1.1/2.25"}
+    if "apply" in cls:
+        ms, launches = cls["apply"]
         achieved = apply_bytes * launches / (ms / 1e3) / 1e9
-        return dom, {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": "k_apply (ORAS preconditioner)"}
-    return dom, {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
-                 "traffic": None, "kernel": dom}
+        out["apply"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        "traffic": None, "kernel": "k_apply (ORAS preconditioner, one arena pass per launch)"}
+    if "spmv" in cls and spmv:
+        ms, _ = cls["spmv"]
+        achieved = spmv / (ms / 1e3) / 1e9
+        out["spmv"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                       "traffic": None, "kernel": "k_spmv_df (Arnoldi) + k_spmv (true residual)"}
+    if dom not in out:
+        out[dom] = {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                    "traffic": None, "kernel": dom}
+    return dom, out
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
@@ -358,7 +401,12 @@ def serving_replay(O, count, slots, device=0, max_iter=60):
 
         def pct(q):
             return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))] if lat else None
+        rejections = [dict(index=q, n=w.n, r=w.r, k=w.nrhs, nsub=w.nsub, footprint_gb=rec["footprint"] / 1e9,
+                           budget_gb=st["hbm_budget"] / 1e9, reason="footprint (arena + A + Krylov basis) above the "
+                                                                      "whole HBM budget")
+                      for q, (w, rc, _, rec) in enumerate(outs) if rc == O.ORAS_ERR_REJECTED]
         return {"slots": nslots, "solves_per_s": solves / (last - first) if last > first else None,
+                "rejections": rejections,
                 "requests_per_s": len(done) / (last - first) if last > first else None,
                 "solves": solves, "requests_completed": len(done),
                 "rejected": sum(1 for _, rc, _, _ in outs if rc == O.ORAS_ERR_REJECTED),
@@ -376,6 +424,66 @@ def serving_replay(O, count, slots, device=0, max_iter=60):
                       f"at most {max_iter} iterations per request)",
             "requests": [dict(n=w.n, r=w.r, k=w.nrhs, nsub=w.nsub, arrival_s=round(w.arrival_s, 3)) for w, *_ in prepared],
             "continuous_batching": mix, "sequential_one_slot": seq}
+
+
+# ------------------------------------------------------------------ plain FP64 path
+def fp64_path(O, dev, stream, steps=2, warmup=1):
+    """The plain FP64 single-right-hand-side GPU path (FP64 local factors, CUDA-core FP64 LU,
+    FP64 apply; the same FGMRES) against the FP32-factor path, one step = oras_factor +
+    oras_solve of one right-hand side on device buffers, CUDA events on the handle's stream.
+    Run on the workloads where the FP64 factorisation finishes in seconds (8^3 x 6 meshes): on
+    the 16^3 benchmark it takes more than 12 minutes per factorisation (GB300's FP64 rate is
+    about 1/64 of its FP32 rate)."""
+    import torch
+    out = {}
+    for name in ("head8", "cube8"):
+        w = workload(name)
+        xyz, tets = w.mesh()
+        eps, mu = w.materials(xyz, tets)
+        eps_d = torch.from_numpy(eps).to(dev)
+        mu_d = torch.from_numpy(mu).to(dev)
+        row = {"ndof": None}
+        for bits in (32, 64):
+            h = O.oras_create(xyz, tets, w.r, w.nsub, w.overlap, factor_bits=bits, restart=w.restart)
+            try:
+                O.oras_set_stream(h, stream.cuda_stream)
+                O.oras_factor(h, eps_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
+                n = O.oras_ndof(h)
+                kind, pt, direction = w.sources()[0]
+                b = torch.empty(n, dtype=torch.complex128, device=dev)
+                if kind == "plane":
+                    O.oras_rhs_plane_wave(h, pt, direction.astype(np.complex128), mem=O.ORAS_MEM_DEVICE, out=b)
+                else:
+                    O.oras_rhs_dipole(h, pt, direction, mem=O.ORAS_MEM_DEVICE, out=b)
+                x = torch.empty_like(b)
+                info = None
+
+                def one():
+                    O.oras_factor(h, eps_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
+                    _, inf, rc = O.oras_solve(h, b, w.tol, mem=O.ORAS_MEM_DEVICE, out=x)
+                    if rc != O.ORAS_OK:
+                        raise RuntimeError(f"{name} factor_bits={bits}: solve did not converge")
+                    return inf
+                for _ in range(warmup):
+                    one()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                e0.record(stream)
+                for _ in range(steps):
+                    info = one()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms = e0.elapsed_time(e1) / steps
+                row["ndof"] = n
+                row[f"factors{bits}"] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms,
+                                         "iterations": info[0]["iterations"], "true_relres": info[0]["relres"]}
+            finally:
+                O.oras_destroy(h)
+        row["speedup_fp32_factors_over_fp64"] = row["factors32"]["solves_per_s"] / row["factors64"]["solves_per_s"]
+        out[w.name] = row
+    out["note"] = ("one step = oras_factor + oras_solve of one right-hand side to true rel-res 1e-8; factors64 = "
+                   "the plain FP64 single-RHS GPU path, factors32 = this library's FP32-factor path")
+    return out
 
 
 # ------------------------------------------------------------------ our arm
@@ -460,16 +568,29 @@ def run_ours(args, world, rank, local):
     # true residual of the last field, FP64, on the host with the library's own A (sanity)
     x_last = x_d.cpu().numpy()
     iters = max(i["iterations"] for i in infos[-1])
-    upd_flops, apply_bytes = work_model(O, h, w.nsub, 1)
-    dom, roof = roofline(timings, upd_flops, apply_bytes, args.steps, hbm, bf16, w.factor_bits)
-    if dom == "lu_update" and w.factor_bits == 32:
-        roof["traffic"] = measured_traffic("k_lu_update_tc", w.name, panel)
-        if roof["traffic"] is not None:
-            roof["traffic_note"] = ("DRAM read+write bytes per launch, averaged over every trailing-update launch of "
-                                    "a factorisation, from the ncu capture recorded in profiles/roofline_traffic.json")
+    fb = 16 if w.factor_bits == 64 else 8
+    groups = apply_group_sizes(krhs, w.factor_bits)
+    upd_flops, _ = work_model(O, h, w.nsub, 1, fb)
+    # bytes of one apply launch, averaged over the launches of a step (groups of right-hand sides)
+    apply_bytes = sum(work_model(O, h, w.nsub, g, fb)[1] for g in groups) / len(groups)
+    nnz = O.oras_nnz(h)
+    spmv_total = 0.0
+    for info in infos:
+        it = max(i["iterations"] for i in info)
+        cyc = max(i["restarts"] for i in info)
+        spmv_total += it * sum(spmv_bytes(n, nnz, g, w.factor_bits == 32) for g in rhs_groups(krhs, 8))
+        spmv_total += cyc * sum(spmv_bytes(n, nnz, g, False) for g in rhs_groups(krhs, 8))
+    dom, roofs = roofline(timings, upd_flops, apply_bytes, args.steps, hbm, bf16_sus, w.factor_bits, spmv_total)
+    if "lu_update" in roofs and w.factor_bits == 32:
+        ru = roofs["lu_update"]
+        ru["traffic"] = measured_traffic("k_lu_update_tc", w.name, panel)
+        if ru["traffic"] is not None:
+            ru["traffic_note"] = ("DRAM read+write bytes per launch, averaged over every trailing-update launch of "
+                                  "a factorisation, from the ncu capture recorded in profiles/roofline_traffic.json")
         else:
-            roof["traffic_note"] = ("null: profiles/roofline_traffic.json holds no ncu capture of this workload and "
-                                    "panel width on the current update kernel (" + UPDATE_VERSION + ")")
+            ru["traffic_note"] = ("null: profiles/roofline_traffic.json holds no ncu capture of this workload and "
+                                  "panel width on the current update kernel (" + UPDATE_VERSION + ")")
+    roof = roofs[dom]
     arena = O.oras_arena_bytes(h)
     O.oras_destroy(h)
     # ---------------- end to end through the public API with host buffers
@@ -492,6 +613,12 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(time.perf_counter() - e0, world)
     e2e_val = world * e2e_steps * krhs / e2e_s
+    fp64 = None
+    if rank == 0 and args.fp64_path:
+        try:
+            fp64 = fp64_path(O, dev, stream)
+        except Exception as e:  # noqa: BLE001
+            fp64 = {"error": f"{type(e).__name__}: {e}"}
     serving = None
     if rank == 0 and args.serve_count > 0:
         # the serving replay is reported beside the main measurement: a failure there is recorded
@@ -523,13 +650,15 @@ def run_ours(args, world, rank, local):
             "iterations": iters, "true_relres": max(i["relres"] for i in infos[-1]),
             "phase_ms_per_step": {c: v[0] / args.steps for c, v in timings.items() if v[1] > 0},
             "roofline": roof,
+            "roofline_kernels": roofs,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "path": "oras_setup (host mesh + materials) + oras_solve (host rhs -> host x) + oras_destroy"},
             "gpu_launches": int(launches),
+            "fp64_path": fp64,
             "serving": serving,
             "clocks": clk,
-            "peaks": {"hbm_gbs": hbm, "bf16_tflops": bf16, "source": src},
+            "peaks": {"hbm_gbs": hbm, "bf16_tflops": bf16, "bf16_tflops_sustained": bf16_sus, "source": src},
             "wall_s_timed": wall,
         }
         print(json.dumps(out))

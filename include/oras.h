@@ -87,6 +87,13 @@ typedef struct {
   int32_t overlap;            /* overlap layers delta >= 0                              */
   const int32_t* part;        /* [nt] subdomain of each tetrahedron, or NULL for        */
                               /*      recursive coordinate bisection into nsub parts    */
+  const double* beta_face;    /* [nt][4] impedance coefficient beta > 0 of Sec. 2 on the   */
+                              /*   face of tetrahedron t opposite its vertex tets[4t+q]    */
+                              /*   (the caller's vertex order); read for outer boundary    */
+                              /*   faces only (other entries are ignored), kept for every  */
+                              /*   later oras_factor of the handle.  NULL: beta = k0       */
+                              /*   sqrt(Re mu_r Re eps_r) of the adjacent tetrahedron,     */
+                              /*   from the materials of each oras_factor                  */
 } oras_problem;
 
 /* Solver options.  Zero-initialised fields take the defaults given in brackets. */
@@ -108,7 +115,12 @@ typedef struct {
                               /*   a captured CUDA graph, captured on its second use and      */
                               /*   replayed afterwards; needs a non-default stream            */
                               /*   (oras_set_stream) and timing off [0]                       */
-  int32_t reserved[6];
+  int32_t wait_ms;            /* limit of every bounded device-side wait, in milliseconds: a  */
+                              /*   wait on another warp or CTA that lasts longer gives up, the */
+                              /*   kernel returns and the call reports ORAS_ERR_DEVICE_TIMEOUT */
+                              /*   [2000]; waits of a CTA for its own copies in flight before  */
+                              /*   it exits never use less than 2000                           */
+  int32_t reserved[5];
 } oras_options;
 
 /* Per right-hand-side outcome of oras_solve. */
@@ -126,7 +138,7 @@ typedef struct {
 const char* oras_last_error(const oras_handle* h);
 
 /* Version of the ABI described here.  No counterpart in the paper.  Never fails. */
-int32_t oras_abi_version(void);
+int32_t oras_abi_version(void);  /* 2: oras_problem.beta_face, oras_options.wait_ms */
 
 /* ---------------------------------------------------------------- set-up */
 
@@ -135,15 +147,16 @@ int32_t oras_abi_version(void);
  * coordinate bisection), overlapping sets Omega_s^delta, ordered unknown sets N_s (Sec. 4,
  * R_s), Boolean partition of unity D_s (sum_s R_s^T D_s R_s = I), interface faces and the
  * CSR pattern of A.  p->eps_r, p->mu_r, p->k0 are ignored here.
- * Errors: INVALID_ARG (r not in 1..3, nsub < 1 or > nt, overlap < 0, NULL arrays),
+ * Errors: INVALID_ARG (r not in 1..3, nsub < 1 or > nt, overlap < 0, NULL arrays, a
+ * beta_face entry of an outer face that is not finite and > 0),
  * BAD_MESH (vertex id out of range, repeated vertex, zero-volume tetrahedron, part entry
  * out of range), UNSUPPORTED (more than 2^31-1 DOFs or 2^21 vertices). */
 int oras_create(const oras_problem* p, const oras_options* o, oras_handle** out);
 
 /* Numeric set-up on the GPU for one material set (Sec. 2-4): element matrices
  *   A_T = mu_r^{-1} int curl w_a . curl w_b - k0^2 eps_r int w_a . w_b      (FP64, exact)
- * plus i beta int (w_a x n).(w_b x n) on outer faces, beta = k0 sqrt(Re mu_r Re eps_r) of
- * the adjacent tetrahedron; global CSR matrix A; dense local matrices A_s with impedance
+ * plus i beta int (w_a x n).(w_b x n) on outer faces, beta from oras_problem.beta_face or else
+ * k0 sqrt(Re mu_r Re eps_r) of the adjacent tetrahedron; global CSR matrix A; dense local matrices A_s with impedance
  * transmission i omega~ on interface faces (omega~ from the tetrahedron inside Omega_s);
  * batched LU with pivoting of every A_s in the factor precision.  eps_r, mu_r: [nt] arrays
  * in `mem` (mu_r may be NULL -> 1).  May be called again with new materials (the mesh,
@@ -178,7 +191,9 @@ int oras_set_stream(oras_handle* h, void* stream);
  * block, Sec. 5).  rhs, x: N x k column-major in `mem`; info: k host structs or NULL.
  * Returns ORAS_OK when every column reached ||b - A x|| / ||b|| <= tol,
  * ORAS_NOT_CONVERGED when max_iter ran out for some column.  Errors: STATE (no
- * oras_factor yet), INVALID_ARG (k < 1 or > 64, tol <= 0), CUDA, OUT_OF_MEMORY. */
+ * oras_factor yet), INVALID_ARG (k < 1 or > 64, tol <= 0), CUDA, OUT_OF_MEMORY,
+ * DEVICE_TIMEOUT (a bounded device wait gave up during an Arnoldi step: the device status is
+ * read after every step, and the solve stops there; x is not written). */
 int oras_solve(oras_handle* h, const oras_complex* rhs, int32_t k, double tol, oras_complex* x,
                oras_info* info, int32_t mem);
 
@@ -186,7 +201,8 @@ int oras_solve(oras_handle* h, const oras_complex* rhs, int32_t k, double tol, o
 
 /* Impedance data of Sec. 2 for the plane wave E = p exp(-i gamma d.x),
  * gamma = k0 sqrt(mu_r eps_r) (principal root), on every outer face:
- * g = mu_r^{-1} (curl E) x n + i beta n x (E x n),  b_a = int_boundary g . w_a.
+ * g = mu_r^{-1} (curl E) x n + i beta n x (E x n),  b_a = int_boundary g . w_a, with the
+ * face's beta of oras_factor (oras_problem.beta_face or the derived one).
  * d: unit direction [3], p: polarisation [3] (host).  b: N values in `mem`.
  * Errors: INVALID_ARG (NULL arguments), STATE (no oras_factor yet), CUDA. */
 int oras_rhs_plane_wave(oras_handle* h, const double* d, const oras_complex* p, oras_complex* b,
@@ -244,9 +260,9 @@ int oras_matvec(oras_handle* h, const oras_complex* x, oras_complex* y, int32_t 
  * narrow.  Requires oras_factor.  Errors: INVALID_ARG, STATE, CUDA. */
 int oras_matvec_c64(oras_handle* h, const void* x, oras_complex* y, int32_t k, int32_t mem);
 /* z = M^{-1}_ORAS v for k columns (N x k column-major, `mem`), Sec. 4 (M^{-1}_OAS with
- * weights ORAS_WEIGHTS_NONE).  Errors: INVALID_ARG (NULL vectors, k < 1 or > 64), STATE (no
- * oras_factor yet), OUT_OF_MEMORY, CUDA.  A bounded device wait that gives up inside this
- * call is not reported yet (oras_factor reports its own). */
+ * weights ORAS_WEIGHTS_NONE).  Synchronises the handle's stream before it returns.  Errors:
+ * INVALID_ARG (NULL vectors, k < 1 or > 64), STATE (no oras_factor yet), OUT_OF_MEMORY, CUDA,
+ * DEVICE_TIMEOUT (a bounded device wait of the apply gave up; z is not valid). */
 int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k, int32_t mem);
 
 /* Allocation-free preconditioner apply: z = M^{-1}_ORAS v for k columns, the same result as
@@ -262,9 +278,26 @@ int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t
  * The first call on a device resolves the array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture.  Every call shares the array and leaves its last
  * contents there; each call writes every entry before reading it.  Calls that overlap on the
- * GPU (other streams, other threads) race on the array.  Nothing is allocated or freed.
- * Errors: STATE (no oras_factor yet), INVALID_ARG, CUDA. */
+ * GPU (other streams, other threads) race on the array.  Nothing is allocated or freed.  Cost:
+ * the k columns go through the apply one after the other, so the factor arena is streamed k
+ * times (oras_precond streams it once per group of up to 4 columns with FP32 factors).  The call
+ * does not wait for the GPU, so a bounded device wait that gives up inside it is not reported
+ * (the kernel stops the affected subdomain and returns; z is then not valid).
+ * Errors: INVALID_ARG (NULL vector, k < 1 or > 64, or the scratch need above 16 MiB: checked
+ * from the host set-up alone, before the STATE check), STATE (no oras_factor yet), CUDA. */
 int oras_precond_noalloc(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k);
+
+/* Self-test of failure detection (no counterpart in the paper): runs, on the handle's stream,
+ * one kernel that waits with each bounded-wait primitive of the library's kernels (a CTA-scope
+ * mbarrier phase, a cluster-scope acquire on an mbarrier, a shared-memory counter) on a
+ * condition that nothing ever satisfies, with the handle's limit oras_options.wait_ms.  Each
+ * wait gives up, records the timeout in the handle's device status, and the kernel returns;
+ * the call reads the status like oras_solve does and returns ORAS_ERR_DEVICE_TIMEOUT, with
+ * detail (or NULL) = bit mask of the primitives that gave up (1 CTA mbarrier, 2 cluster
+ * mbarrier, 4 counter; 7 when all behave).  The status is cleared again before returning, so the
+ * handle stays usable.  Takes about 3 x wait_ms.  Errors: INVALID_ARG, STATE (no oras_factor
+ * yet), CUDA. */
+int oras_wait_selftest(oras_handle* h, int32_t* detail);
 
 /* Autotuner of the batched LU's tile shapes (no counterpart in the paper): the outer panel width (tiles of 64 columns per
  * trailing update; trades the inner panel updates against the passes over the trailing matrix)

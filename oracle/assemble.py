@@ -26,6 +26,29 @@ def impedance_beta(k0, eps_r, mu_r):
     return k0 * np.sqrt(np.real(mu_r) * np.real(eps_r))
 
 
+def face_beta_table(tets, beta_face):
+    """beta[t, lf] on the sorted local face lf of every tetrahedron from a caller's table
+    beta_face[t, q] given on the face opposite the caller's vertex tets[t, q] (Sec. 2: beta is
+    the caller's per-port wave number).  The sorted local face lf (basis.LOCAL_FACES) is the
+    face opposite the sorted vertex FACE_OPPOSITE[lf]."""
+    tets = np.asarray(tets)
+    beta_face = np.asarray(beta_face, dtype=np.float64).reshape(-1, 4)
+    st = np.sort(tets, axis=1)
+    out = np.empty((len(tets), 4))
+    for lf in range(4):
+        opp = st[:, basis.FACE_OPPOSITE[lf]]
+        q = np.argmax(tets == opp[:, None], axis=1)
+        out[:, lf] = beta_face[np.arange(len(tets)), q]
+    return out
+
+
+def outer_beta(k0, eps_r, mu_r, t, lf, beta_lf=None):
+    """beta of outer faces (t, lf): the caller's table when given, else k0 sqrt(Re mu Re eps)."""
+    if beta_lf is not None:
+        return np.asarray(beta_lf)[t, lf]
+    return impedance_beta(k0, eps_r[t], mu_r[t])
+
+
 def boundary_face_list(topo: Topology):
     """(face ids, adjacent tet, local face index) of all outer faces."""
     bf = topo.boundary_faces()
@@ -34,12 +57,13 @@ def boundary_face_list(topo: Topology):
     return bf, t, lf
 
 
-def global_matrix(topo: Topology, xyz, eps_r, mu_r, k0):
+def global_matrix(topo: Topology, xyz, eps_r, mu_r, k0, beta_lf=None):
+    """beta_lf: [T, 4] beta per sorted local face (face_beta_table) or None (derived)."""
     AT = elements.element_matrices(xyz, topo.st, topo.r, eps_r, mu_r, k0)
     bf, bt, blf = boundary_face_list(topo)
     if len(bf):
         S = elements.face_matrices(xyz, topo.st, bt, blf, topo.r)
-        beta = impedance_beta(k0, eps_r[bt], mu_r[bt])
+        beta = outer_beta(k0, eps_r, mu_r, bt, blf, beta_lf)
         np.add.at(AT, bt, 1j * beta[:, None, None] * S)
     nl = AT.shape[1]
     rows = np.repeat(topo.dofmap, nl, axis=1).ravel()
@@ -62,7 +86,7 @@ def _basis_on_points(r, lam, grads):
     return out
 
 
-def plane_wave_load(topo: Topology, xyz, eps_r, mu_r, k0, d, p, nq=8):
+def plane_wave_load(topo: Topology, xyz, eps_r, mu_r, k0, d, p, nq=8, beta_lf=None):
     d = np.asarray(d, dtype=np.float64)
     p = np.asarray(p, dtype=np.complex128)
     b = np.zeros(topo.ndof, dtype=np.complex128)
@@ -86,7 +110,7 @@ def plane_wave_load(topo: Topology, xyz, eps_r, mu_r, k0, d, p, nq=8):
         verts = xyz[topo.st[t]]                       # [F,4,3]
         x = np.einsum("pv,fvi->fpi", lam, verts)      # [F,P,3]
         gamma = k0 * np.sqrt(mu_r[t] * eps_r[t])
-        beta = impedance_beta(k0, eps_r[t], mu_r[t])
+        beta = outer_beta(k0, eps_r, mu_r, t, np.full(len(t), lf), beta_lf)
         phase = np.exp(-1j * gamma[:, None] * (x @ d))  # [F,P]
         E = phase[:, :, None] * p[None, None, :]
         curlE = (-1j * gamma)[:, None, None] * phase[:, :, None] * np.cross(d, p)[None, None, :]

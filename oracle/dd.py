@@ -30,7 +30,7 @@ import numpy as np
 import scipy.linalg as sla
 
 from . import elements
-from .assemble import impedance_beta
+from .assemble import impedance_beta, outer_beta
 from .topology import Topology, dof_min_tet
 
 
@@ -122,8 +122,9 @@ def decompose(topo: Topology, xyz, nsub, delta, part=None, kind="vertex") -> Dec
     return Decomposition(part=part, tets=tets, dofs=dofs, pou=pou, owner=owner, iface=iface)
 
 
-def local_matrix(topo: Topology, xyz, eps_r, mu_r, k0, dec: Decomposition, s):
-    """Dense A_s: element terms of Omega_s^delta + outer impedance + interface impedance."""
+def local_matrix(topo: Topology, xyz, eps_r, mu_r, k0, dec: Decomposition, s, beta_lf=None):
+    """Dense A_s: element terms of Omega_s^delta + outer impedance (beta of the caller's table
+    beta_lf [T, 4] when given) + interface impedance (omega~ of the inside tetrahedron)."""
     Ns = dec.dofs[s]
     ts = dec.tets[s]
     n = len(Ns)
@@ -140,7 +141,7 @@ def local_matrix(topo: Topology, xyz, eps_r, mu_r, k0, dec: Decomposition, s):
             if topo.face_tets[f, 1] < 0:
                 ft_t.append(t)
                 ft_f.append(lf)
-                coef.append(impedance_beta(k0, eps_r[t], mu_r[t]))
+                coef.append(outer_beta(k0, eps_r, mu_r, t, lf, beta_lf))
     it, il = dec.iface[s]
     ft_t += list(it)
     ft_f += list(il)
@@ -167,7 +168,7 @@ class ORAS:
     (RAS), which needs the global matrix A_global."""
 
     def __init__(self, topo, xyz, eps_r, mu_r, k0, dec: Decomposition, weights="pou",
-                 transmission="impedance", A_global=None):
+                 transmission="impedance", A_global=None, beta_lf=None):
         self.dec = dec
         self.n = topo.ndof
         self.lu = []
@@ -175,7 +176,7 @@ class ORAS:
             if transmission == "dirichlet":
                 A = restricted_matrix(A_global, dec, s)
             else:
-                A = local_matrix(topo, xyz, eps_r, mu_r, k0, dec, s)
+                A = local_matrix(topo, xyz, eps_r, mu_r, k0, dec, s, beta_lf)
             self.lu.append(sla.lu_factor(A, check_finite=False))
         self.weights = weights
 

@@ -25,20 +25,23 @@ class OracleProblem:
 
 
 def build(xyz, tets, eps_r, mu_r, k0, r, sources, nsub=None, delta=None, part=None,
-          with_oras=True):
+          with_oras=True, beta_face=None):
+    """beta_face: [T, 4] impedance coefficients on the face opposite the caller's vertex
+    tets[t, q] (outer faces only), or None (derived from the materials)."""
     topo = topology.build(tets, xyz.shape[0], r)
-    A = assemble.global_matrix(topo, xyz, eps_r, mu_r, k0)
+    beta_lf = None if beta_face is None else assemble.face_beta_table(tets, beta_face)
+    A = assemble.global_matrix(topo, xyz, eps_r, mu_r, k0, beta_lf)
     cols = []
     for kind, a, b in sources:
         if kind == "plane":
-            cols.append(assemble.plane_wave_load(topo, xyz, eps_r, mu_r, k0, a, b))
+            cols.append(assemble.plane_wave_load(topo, xyz, eps_r, mu_r, k0, a, b, beta_lf=beta_lf))
         else:
             cols.append(assemble.dipole_load(topo, xyz, a, b))
     B = np.stack(cols, axis=1) if cols else np.zeros((topo.ndof, 0), dtype=np.complex128)
     prob = OracleProblem(xyz, tets, eps_r, mu_r, k0, r, topo, A, B)
     if with_oras and nsub is not None:
         prob.dec = dd.decompose(topo, xyz, nsub, delta, part)
-        prob.oras = dd.ORAS(topo, xyz, eps_r, mu_r, k0, prob.dec)
+        prob.oras = dd.ORAS(topo, xyz, eps_r, mu_r, k0, prob.dec, beta_lf=beta_lf)
     return prob
 
 

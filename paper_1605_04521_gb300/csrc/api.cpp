@@ -48,6 +48,7 @@ void launch_restart(const oras_handle* h, int k, int m, const cplx* rv, const do
 void launch_to_internal(const oras_handle* h, int k, const cplx* src, cplx* dst);
 void launch_to_external(const oras_handle* h, int k, const cplx* src, cplx* dst);
 int red_blocks();
+int launch_wait_selftest(const oras_handle* h);
 }  // namespace oras
 
 using namespace oras;
@@ -57,6 +58,10 @@ static std::atomic<int64_t> g_launches{0};
 
 namespace oras {
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+uint64_t wait_limit_ns(const oras_handle* h) {
+  return h->opt.wait_ms > 0 ? (uint64_t)h->opt.wait_ms * 1000000ull : 2000000000ull;
+}
 
 int prof_begin(const oras_handle* h) {
   if (!h->timing) return -1;
@@ -130,7 +135,7 @@ static cudaError_t dput(T*& p, const std::vector<T>& v, cudaStream_t s) {
 }
 
 static void dfree_all(Device& d) {
-  void* ptrs[] = {d.xyz, d.st, d.dofmap, d.tinc_ptr, d.tinc, d.if_tet0, d.if_lf0, d.if_tet1, d.if_dofs,
+  void* ptrs[] = {d.xyz, d.st, d.dofmap, d.tinc_ptr, d.tinc, d.if_tet0, d.if_lf0, d.if_tet1, d.if_dofs, d.if_beta,
                   d.finc_ptr, d.finc, d.rowptr, d.cols, d.sub_ns, d.sub_np, d.sub_ns_off, d.sub_tile_off,
                   d.sub_dofs, d.sub_pou, d.member, d.cm, d.ck, d.cs, d.fl, d.tc, d.ta, d.tm, d.eps, d.mu,
                   d.elem, d.fmat, d.vals, d.vals_df, d.arena, d.perm, d.gidx, d.sub_np_off, d.lu_cand, d.lu_cnt,
@@ -165,6 +170,7 @@ static int upload(oras_handle* h) {
   CK(dput(d.if_lf0, m.if_lf0, s));
   CK(dput(d.if_tet1, m.if_tet1, s));
   CK(dput(d.if_dofs, m.if_dofs, s));
+  if (!m.if_beta.empty()) CK(dput(d.if_beta, m.if_beta, s));
   CK(dput(d.finc_ptr, m.finc_ptr, s));
   CK(dput(d.finc, m.finc, s));
   CK(dput(d.rowptr, m.rowptr, s));
@@ -272,7 +278,7 @@ int64_t footprint_bytes(const oras_handle* h, int k) {
   auto add = [&](int64_t x) { b += std::max<int64_t>(x, 1); ++nalloc; };
   // upload
   for (int64_t x : {vb(m.xyz), vb(m.st), vb(m.dofmap), vb(m.tinc_ptr), vb(m.tinc), vb(m.if_tet0), vb(m.if_lf0),
-                    vb(m.if_tet1), vb(m.if_dofs), vb(m.finc_ptr), vb(m.finc), vb(m.rowptr), vb(m.cols),
+                    vb(m.if_tet1), vb(m.if_dofs), vb(m.if_beta), vb(m.finc_ptr), vb(m.finc), vb(m.rowptr), vb(m.cols),
                     vb(m.sub_ns), vb(m.sub_np), vb(m.sub_ns_off), vb(m.sub_tile_off), vb(m.sub_dofs),
                     vb(m.sub_pou), vb(m.member), (int64_t)(m.nsub + 1) * 8, vb(T.cm), vb(T.ck), vb(T.cs),
                     (int64_t)T.fl.size() * 4, vb(T.tc), (int64_t)T.ta.size() * 4, (int64_t)T.tm.size() * 4})
@@ -341,11 +347,8 @@ static int factor_device(oras_handle* h) {
 }
 
 
-static int sync_status(oras_handle* h) {
-  auto& d = h->dev;
-  int32_t st[8];
-  CK(cudaMemcpyAsync(st, d.status, sizeof(st), cudaMemcpyDeviceToHost, d.stream));
-  CK(cudaStreamSynchronize(d.stream));
+// Return code for the device status flags st[8] (read back from Device::status).
+static int status_code(oras_handle* h, const int32_t* st) {
   if (st[ST_ERR] == DEV_SINGULAR) {
     h->err = "local matrix of subdomain " + std::to_string(st[ST_SUB]) + " has a zero pivot column";
     return ORAS_ERR_SINGULAR_LOCAL;
@@ -362,9 +365,17 @@ static int sync_status(oras_handle* h) {
   return ORAS_OK;
 }
 
+static int sync_status(oras_handle* h) {
+  auto& d = h->dev;
+  int32_t* st = (int32_t*)(d.host_pinned + PINNED_STATUS_OFF);
+  CK(cudaMemcpyAsync(st, d.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, d.stream));
+  CK(cudaStreamSynchronize(d.stream));
+  return status_code(h, st);
+}
+
 extern "C" {
 
-int32_t oras_abi_version(void) { return 1; }
+int32_t oras_abi_version(void) { return 2; }
 
 const char* oras_last_error(const oras_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
 
@@ -548,6 +559,21 @@ void oras_destroy(oras_handle* h) {
     dfree_all(h->dev);
   }
   delete h;
+}
+
+int oras_wait_selftest(oras_handle* h, int32_t* detail) {
+  if (!h) return ORAS_ERR_INVALID_ARG;
+  if (!h->dev.uploaded) { h->err = "oras_wait_selftest: call oras_factor first"; return ORAS_ERR_STATE; }
+  auto& d = h->dev;
+  CK(cudaMemsetAsync(d.status, 0, 8 * sizeof(int32_t), d.stream));
+  if (launch_wait_selftest(h)) CK(cudaGetLastError());
+  int32_t* st = (int32_t*)(d.host_pinned + PINNED_STATUS_OFF);
+  CK(cudaMemcpyAsync(st, d.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, d.stream));
+  CK(cudaStreamSynchronize(d.stream));
+  if (detail) *detail = st[ST_DETAIL];
+  const int rc = status_code(h, st);
+  CK(cudaMemsetAsync(d.status, 0, 8 * sizeof(int32_t), d.stream));  // the handle stays usable
+  return rc;
 }
 
 int oras_release_memory(int32_t device) {
@@ -789,6 +815,8 @@ static int fgmres(oras_handle* h, int k, double tol, oras_info* info) {
   double* hp = d.host_pinned;                  // [0,k): norms; [k,2k): res
   std::vector<double> bnorm(k), relres(k);
   std::vector<int32_t> active(k, 1), iters(k, 0), cycles(k, 0), conv(k, 0);
+  int32_t* st_h = (int32_t*)(hp + PINNED_STATUS_OFF);  // device status flags, read with every step
+  CK(cudaMemsetAsync(d.status, 0, 8 * sizeof(int32_t), d.stream));
   // ||b||
   CK(cudaMemsetAsync(d.xk, 0, nk * sizeof(cplx), d.stream));
   CK(cudaMemsetAsync(d.tmp, 0, nk * sizeof(cplx), d.stream));
@@ -855,7 +883,10 @@ static int fgmres(oras_handle* h, int k, double tol, oras_info* info) {
       for (int r = 0; r < k; ++r)
         if (active[r]) ++iters[r];
       CK(cudaMemcpyAsync(hp + k, res_d, k * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
+      CK(cudaMemcpyAsync(st_h, d.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, d.stream));
       CK(cudaStreamSynchronize(d.stream));
+      // a bounded wait that gave up in this step's apply: the step's vectors are not valid
+      if (int sc = status_code(h, st_h)) return sc;
       bool more = false;
       for (int r = 0; r < k; ++r)
         if (active[r] && hp[k + r] / bnorm[r] > tol && iters[r] < max_iter) more = true;
@@ -936,6 +967,7 @@ int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t
   if (rc) return rc;
   rc = load_input(h, v, k, mem, h->dev.bk);
   if (rc) return rc;
+  CK(cudaMemsetAsync(h->dev.status, 0, 8 * sizeof(int32_t), h->dev.stream));
   const int pb = prof_begin(h);
   if (launch_apply_f64out(h, h->dev.bk, h->dev.tmp, k)) {
     h->err = "oras_precond: apply launch failed";
@@ -944,7 +976,8 @@ int oras_precond(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t
   prof_end(h, KC_APPLY, pb, apply_passes(h, k));
   rc = store_output(h, h->dev.tmp, k, mem, z);
   prof_resolve(h);
-  return rc;
+  if (rc) return rc;
+  return sync_status(h);  // a bounded wait that gave up inside the apply
 }
 
 int oras_rhs_dipole(oras_handle* h, const double* x0, const double* dir, oras_complex* b, int32_t mem) {

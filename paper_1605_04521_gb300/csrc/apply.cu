@@ -50,6 +50,7 @@ ApplyGeom apply_geom(const oras_handle* h) {
   a.weights = h->opt.weights;
   a.stages = 2;
   a.status = d.status;
+  a.wait_ns = wait_limit_ns(h);
   return a;
 }
 

@@ -15,8 +15,10 @@
 // copies from one producer warp; eight consumer warps compute.  When y lives in global memory,
 // every stage also carries the TB x KR slice y_J its tile multiplies: the producer copies it once
 // the consumers have finalised strip J (a shared counter, with a proxy fence on the writer side),
-// so the consumers never wait on a global load.  Every wait is bounded (about
-// 2 s); a timeout sets the device status flag and the block finishes without further work.
+// so the consumers never wait on a global load.  Every wait is bounded (ApplyGeom::wait_ns, 2 s
+// by default); a timeout sets the device status flag and the block finishes without further
+// work, after waiting (at least 2 s) for its own bulk copies still in flight.  apply_cluster
+// returns whether either CTA of the cluster gave up, the same value in both.
 #pragma once
 
 #include "dev.cuh"
@@ -31,6 +33,7 @@ struct ApplyGeom {
   int weights;
   int stages;               // ring depth
   int32_t* status;
+  uint64_t wait_ns;         // limit of every bounded wait
 };
 
 constexpr int APPLY_CONSUMERS = 256;            // 8 warps
@@ -101,7 +104,7 @@ struct ApplySmem {
 // v and z are [N][vs] / [N][zs] complex arrays; this pass handles right-hand sides off .. off+nr-1
 // (nr <= KR; the unused lanes of the last group carry zeros and are not stored).
 template <typename R, typename ZT, int KR>
-__device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict__ v, int64_t vs,
+__device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict__ v, int64_t vs,
                               ZT* __restrict__ z, int64_t zs, int64_t off, int nr, CT<R>* yglob) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   using Sm = ApplySmem<R, KR>;
@@ -118,6 +121,7 @@ __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
   CT<R>* red = (CT<R>*)(smem_raw + Sm::red_off(S, ys));     // [8][TB*KR] per-warp partial sums
   CT<R>* rvec = (CT<R>*)(smem_raw + Sm::rvec_off(S, ys));   // [TB*KR]
   __shared__ int abort_flag;
+  __shared__ int peer_abort;                                // set by the partner CTA at the end
   __shared__ int ydone;                                     // strips of y finalised (both passes)
   const int c = (int)cluster_rank();
   const int64_t ns = a.ns[s], np = a.np[s], nts = np / TB;
@@ -139,6 +143,7 @@ __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
     mbar_init(&msg[0], 1);
     mbar_init(&msg[1], 1);
     abort_flag = 0;
+    peer_abort = 0;
     ydone = 0;
     fence_mbar_init();
   }
@@ -153,10 +158,10 @@ __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
       uint32_t phase = 0;  // parity of the ring round of `slot`
       // ysrc: the y slice for this tile (global y only); need: finalised strips it requires
       auto issue = [&](const R* src, const CT<R>* ysrc, int64_t need) -> bool {
-        if (n >= S && !mbar_wait(&empty[slot], phase ^ 1u)) return false;
+        if (n >= S && !mbar_wait(&empty[slot], phase ^ 1u, false, a.wait_ns)) return false;
         unsigned char* dst = ring + (size_t)slot * SLOT;
         if (ysrc) {
-          if (!wait_counter(&ydone, (int)need)) return false;
+          if (!wait_counter(&ydone, (int)need, a.wait_ns)) return false;
           fence_proxy_async_global();
           mbar_expect_tx(&full[slot], TBYTES + Sm::YB);
           bulk_g2s(dst + TBYTES, ysrc, Sm::YB, &full[slot]);
@@ -186,7 +191,8 @@ __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
         abort_flag = 1;
       }
       // drain: every issued copy must land before the block may exit
-      for (int64_t q = n > S ? n - S : 0; q < n; ++q) mbar_wait(&full[q % S], (uint32_t)((q / S) & 1));
+      for (int64_t q = n > S ? n - S : 0; q < n; ++q)
+        mbar_wait(&full[q % S], (uint32_t)((q / S) & 1), false, drain_limit(a.wait_ns));
     }
   } else {
     // ---------------- consumers
@@ -198,7 +204,7 @@ __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
     bool ok = true;
     // waits for the next stage; T: its tile, Y: its y slice (global y) or nullptr
     auto stage = [&](const R*& T, const CT<R>*& Y) -> bool {
-      if (!mbar_wait(&full[slot], phase)) return false;
+      if (!mbar_wait(&full[slot], phase, false, a.wait_ns)) return false;
       T = (const R*)(ring + (size_t)slot * SLOT);
       Y = ysm ? nullptr : (const CT<R>*)(ring + (size_t)slot * SLOT + TBYTES);
       return true;
@@ -326,7 +332,7 @@ __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
           continue;
         }
         // owner: r = b_I - own partial - partner partial
-        if (tid == 0 && !mbar_wait(&msg[kr & 1], (uint32_t)((kr >> 1) & 1), true)) {
+        if (tid == 0 && !mbar_wait(&msg[kr & 1], (uint32_t)((kr >> 1) & 1), true, a.wait_ns)) {
           atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
           abort_flag = 1;
         }
@@ -433,7 +439,11 @@ __device__ void apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
     }
   }
   __syncthreads();
+  // tell the partner whether this CTA gave up; the closing cluster barrier (release/acquire)
+  // makes the flag visible, so both CTAs return the same result
+  if (threadIdx.x == 0 && abort_flag) st_remote_u32(map_to_rank(&peer_abort, (uint32_t)(c ^ 1)), 1u);
   cluster_sync_all();  // the partner must not touch our shared memory after we exit
+  return abort_flag != 0 || peer_abort != 0;
 }
 
 }  // namespace oras

@@ -119,6 +119,7 @@ struct RowArgs {
   const int64_t* rowptr; const int32_t* cols;
   const cplx* elem; const double* fmat;
   const cplx* eps; const cplx* mu;
+  const double* if_beta;     // [nif] caller's beta of outer faces, or nullptr (derived)
   const uint32_t* member; int64_t member_words;
   int dirichlet;             // local rows: 1 = rows of the global matrix (RAS), 0 = ORAS local problem
 };
@@ -176,7 +177,8 @@ __device__ void accumulate_row(const RowArgs& A, int64_t g, int s, cplx* acc, in
       if (m0 == m1) continue;
       tin = m0 ? t0 : t1;
     }
-    double w = omega_t(A, tin);
+    // outer faces: the caller's beta when given; interfaces: omega~ of the inside tet
+    double w = (t1 < 0 && A.if_beta) ? A.if_beta[slot] : omega_t(A, tin);
     const double* fr = A.fmat + (slot * A.nfl + af) * A.nfl;
     for (int bf = lane; bf < A.nfl; bf += 32) {
       int p = bsearch32(rc, rn, A.if_dofs[slot * A.nfl + bf]);
@@ -310,8 +312,9 @@ __global__ void k_plane_faces(int64_t nif, int nfl, const double* __restrict__ x
                               const int32_t* __restrict__ st, const int32_t* __restrict__ tet0,
                               const int32_t* __restrict__ lf0, const int32_t* __restrict__ tet1,
                               const int32_t* __restrict__ fl, const cplx* __restrict__ eps,
-                              const cplx* __restrict__ mu, const double* tc, const int32_t* ta,
-                              const int32_t* tm, PlaneArgs P, cplx* __restrict__ bface) {
+                              const cplx* __restrict__ mu, const double* __restrict__ if_beta,
+                              const double* tc, const int32_t* ta, const int32_t* tm, PlaneArgs P,
+                              cplx* __restrict__ bface) {
   int64_t f = blockIdx.x;
   int af = threadIdx.x;
   if (f >= nif || af >= nfl) return;
@@ -335,7 +338,7 @@ __global__ void k_plane_faces(int64_t nif, int nfl, const double* __restrict__ x
   double sr = sqrt(0.5 * (mod + me.re));
   double si = copysign(sqrt(fmax(0.0, 0.5 * (mod - me.re))), me.im);
   cplx gam = {P.k0 * sr, P.k0 * si};
-  double beta = P.k0 * sqrt(m.re * e.re);
+  double beta = if_beta ? if_beta[f] : P.k0 * sqrt(m.re * e.re);
   double mden = m.re * m.re + m.im * m.im;
   cplx imu = {m.re / mden, -m.im / mden};
   // d x p
@@ -428,6 +431,7 @@ static RowArgs row_args(const oras_handle* h, double k0) {
   A.if_tet0 = d.if_tet0; A.if_tet1 = d.if_tet1; A.if_dofs = d.if_dofs;
   A.rowptr = d.rowptr; A.cols = d.cols;
   A.elem = d.elem; A.fmat = d.fmat; A.eps = d.eps; A.mu = d.mu;
+  A.if_beta = d.if_beta;
   A.member = d.member; A.member_words = m.member_words;
   A.dirichlet = h->opt.transmission == ORAS_TRANSMISSION_DIRICHLET ? 1 : 0;
   return A;
@@ -496,8 +500,8 @@ int launch_plane(const oras_handle* h, const double* dvec, const oras_complex* p
   for (int i = 0; i < nq; ++i) { P.qs[i] = qs[i]; P.qw[i] = qw[i]; }
   if (m.nif > 0)
     k_plane_faces<<<(unsigned)m.nif, 32, 0, d.stream>>>(m.nif, m.nfl, d.xyz, d.st, d.if_tet0, d.if_lf0,
-                                                        d.if_tet1, d.fl, d.eps, d.mu, d.tc, d.ta, d.tm,
-                                                        P, bface);
+                                                        d.if_tet1, d.fl, d.eps, d.mu, d.if_beta, d.tc, d.ta,
+                                                        d.tm, P, bface);
   count_launches(1);
   k_gather_faces<<<(unsigned)((m.ndof + 255) / 256), 256, 0, d.stream>>>(m.ndof, m.nfl, d.finc_ptr, d.finc,
                                                                         bface, b);

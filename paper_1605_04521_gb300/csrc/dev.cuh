@@ -101,13 +101,18 @@ __device__ __forceinline__ bool mbar_test_cluster(uint64_t* b, uint32_t parity) 
       : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
   return ok != 0;
 }
-// Waits for the phase with the given parity; gives up after ~2 s and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, bool cluster_scope = false) {
+// Default limit of a bounded device wait (oras_options.wait_ms = 0): 2 s of %globaltimer.
+constexpr uint64_t WAIT_NS_DEFAULT = 2000000000ull;
+
+// Waits for the phase with the given parity; gives up after limit_ns of %globaltimer (or 2^26
+// polls) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, bool cluster_scope = false,
+                                          uint64_t limit_ns = WAIT_NS_DEFAULT) {
   if (cluster_scope ? mbar_test_cluster(b, parity) : mbar_test(b, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (long long it = 0; it < ORAS_SPIN_LIMIT; ++it) {
     if (cluster_scope ? mbar_test_cluster(b, parity) : mbar_test(b, parity)) return true;
-    if ((it & 255) == 0 && globaltimer() - t0 > 2000000000ull) return false;
+    if ((it & 255) == 0 && globaltimer() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -120,15 +125,24 @@ __device__ __forceinline__ int ld_acquire_cta(const int* p) {
   asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
   return v;
 }
-// Bounded wait until *p >= need (about 2 s), false on timeout.
-__device__ __forceinline__ bool wait_counter(const int* p, int need) {
+// Bounded wait until *p >= need (limit_ns of %globaltimer), false on timeout.
+__device__ __forceinline__ bool wait_counter(const int* p, int need, uint64_t limit_ns = WAIT_NS_DEFAULT) {
   if (ld_acquire_cta(p) >= need) return true;
   const uint64_t t0 = globaltimer();
   for (long long it = 0; it < ORAS_SPIN_LIMIT; ++it) {
     if (ld_acquire_cta(p) >= need) return true;
-    if ((it & 255) == 0 && globaltimer() - t0 > 2000000000ull) return false;
+    if ((it & 255) == 0 && globaltimer() - t0 > limit_ns) return false;
   }
   return false;
+}
+// Limit of the waits for a CTA's own bulk copies still in flight before it exits: never below
+// the default, so a short user limit cannot let a CTA leave while copies land in its memory.
+__device__ __forceinline__ uint64_t drain_limit(uint64_t limit_ns) {
+  return limit_ns > WAIT_NS_DEFAULT ? limit_ns : WAIT_NS_DEFAULT;
+}
+// st.shared::cluster of one 32-bit word into a partner CTA's shared memory.
+__device__ __forceinline__ void st_remote_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 // Orders this thread's generic-proxy global writes before later async-proxy (bulk copy) reads.
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }

@@ -397,6 +397,26 @@ int host_setup(const oras_problem* p, int overlap_kind, HostMesh& m, std::string
     m.if_tet1.push_back(m.face_tets[f * 2 + 1]);
   }
   m.nif = (int64_t)m.if_face.size();
+  // caller's impedance coefficients: face (t, q) of the caller is the one opposite the caller's
+  // vertex tets[4t+q]; the sorted local face lf is opposite the sorted vertex 3 - lf
+  m.if_beta.clear();
+  if (p->beta_face) {
+    m.if_beta.assign(m.nif, 0.0);
+    for (int64_t i = 0; i < m.nif; ++i) {
+      if (m.if_tet1[i] >= 0) continue;
+      const int64_t t = m.if_tet0[i];
+      const int32_t vo = m.st[t * 4 + (3 - m.if_lf0[i])];
+      int q = 0;
+      while (q < 4 && p->tets[t * 4 + q] != vo) ++q;
+      const double b = q < 4 ? p->beta_face[t * 4 + q] : NAN;
+      if (!(std::isfinite(b) && b > 0.0)) {
+        err = "oras_create: beta_face of the outer face " + std::to_string(q) + " of tetrahedron " +
+              std::to_string(t) + " is not finite and positive";
+        return ORAS_ERR_INVALID_ARG;
+      }
+      m.if_beta[i] = b;
+    }
+  }
   m.if_dofs.resize(m.nif * nfl);
   std::vector<std::vector<int>> fld(4);
   for (int lf = 0; lf < 4; ++lf) fld[lf] = face_local_dofs(r, lf);

@@ -19,6 +19,7 @@ constexpr int MAX_NFL = 15;       // face-local DOFs r(r+2) for r <= 3
 constexpr int MAX_NL = 45;        // tet-local DOFs for r <= 3
 constexpr int MAX_RHS = 64;
 constexpr int PINNED_SCRATCH_DOUBLES = 4096;
+constexpr int PINNED_STATUS_OFF = 2048;   // pinned scratch: doubles [2048, 2052) hold the status flags
 
 struct cplx { double re, im; };
 
@@ -73,6 +74,7 @@ struct HostMesh {
   int64_t nif = 0;
   std::vector<int32_t> if_face, if_tet0, if_lf0, if_tet1;  // tet1 = -1 on the outer boundary
   std::vector<int32_t> if_dofs;   // [nif][nfl] global DOFs, intrinsic face order
+  std::vector<double> if_beta;    // [nif] caller's beta of outer faces (empty: derived per factor)
   std::vector<int64_t> finc_ptr;  // [ndof+1]
   std::vector<int32_t> finc;      // slot*nfl + a_f
   // CSR pattern of A
@@ -111,6 +113,7 @@ struct Device {
   int32_t* tinc = nullptr;
   int32_t* if_tet0 = nullptr; int32_t* if_lf0 = nullptr; int32_t* if_tet1 = nullptr;
   int32_t* if_dofs = nullptr;
+  double* if_beta = nullptr;                    // [nif] or nullptr (beta derived from the materials)
   int64_t* finc_ptr = nullptr;
   int32_t* finc = nullptr;
   int64_t* rowptr = nullptr;
@@ -170,6 +173,8 @@ enum KClass { KC_ELEMENT = 0, KC_GLOBAL_ROWS, KC_LOCAL_ROWS, KC_LU_TOURNAMENT, K
 int prof_begin(const oras_handle* h);                 // -1 when timing is off
 void prof_end(const oras_handle* h, int cls, int begin, int launches);
 void count_launches(int n);                           // process-wide launch counter
+// Limit of the bounded device waits of a handle's kernels (oras_options.wait_ms; 0 -> 2 s).
+uint64_t wait_limit_ns(const oras_handle* h);
 
 // Stream-ordered allocation from the current device's default memory pool.  The pool keeps
 // memory freed by cudaFreeAsync for reuse (release threshold unlimited, set once per device), so

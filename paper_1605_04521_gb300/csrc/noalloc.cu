@@ -23,8 +23,11 @@ template <typename R>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(APPLY_THREADS)
     k_apply_noalloc(ApplyGeom a, int64_t n, int k, void* scratch, const cplx* __restrict__ v,
                     cplx* __restrict__ z) {
-  for (int r = 0; r < k; ++r)  // columns one after the other: the scratch slices are reused
-    apply_cluster<R, cplx, 1>(a, blockIdx.x / 2, v, 1, z, 1, (int64_t)r * n, 1, (CT<R>*)scratch);
+  // columns one after the other: the scratch slices are reused.  After a bounded wait gave up
+  // (in either CTA: apply_cluster returns the same value in both), the cluster stops, so no
+  // barrier of the ring is initialised again while a copy might still complete on it.
+  for (int r = 0; r < k; ++r)
+    if (apply_cluster<R, cplx, 1>(a, blockIdx.x / 2, v, 1, z, 1, (int64_t)r * n, 1, (CT<R>*)scratch)) break;
 }
 
 ApplyGeom apply_geom(const oras_handle* h);
@@ -36,11 +39,11 @@ using namespace oras;
 
 extern "C" int oras_precond_noalloc(oras_handle* h, const oras_complex* v, oras_complex* z, int32_t k) {
   if (!h) return ORAS_ERR_INVALID_ARG;
-  if (!h->factored) { h->err = "oras_precond_noalloc: call oras_factor first"; return ORAS_ERR_STATE; }
   if (!v || !z || k < 1 || k > MAX_RHS) { h->err = "oras_precond_noalloc: bad k or NULL vector"; return ORAS_ERR_INVALID_ARG; }
   const auto& m = h->mesh;
   const auto& d = h->dev;
-  const size_t el = d.factor_bits == 64 ? sizeof(CT<double>) : sizeof(CT<float>);
+  // the size check needs only the host set-up (subdomain orders, factor precision)
+  const size_t el = h->opt.factor_bits == 64 ? sizeof(CT<double>) : sizeof(CT<float>);
   int64_t total_np = 0;
   for (int s = 0; s < m.nsub; ++s) total_np += m.sub_np[s];
   const size_t need = (size_t)total_np * el;
@@ -49,6 +52,7 @@ extern "C" int oras_precond_noalloc(oras_handle* h, const oras_complex* v, oras_
              " bytes of scratch, more than the fixed " + std::to_string(NOALLOC_SCRATCH_BYTES) + " bytes";
     return ORAS_ERR_INVALID_ARG;
   }
+  if (!h->factored) { h->err = "oras_precond_noalloc: call oras_factor first"; return ORAS_ERR_STATE; }
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {

@@ -33,7 +33,7 @@ namespace {
 
 struct Request {
   int64_t ticket = 0;
-  std::vector<double> xyz, dipoles;
+  std::vector<double> xyz, dipoles, beta;
   std::vector<int32_t> tets, part;
   std::vector<oras_complex> eps, mu, rhs;
   oras_problem prob{};
@@ -293,6 +293,7 @@ int64_t oras_submit(oras_server* S, const oras_problem* p, const oras_options* o
     q->eps.assign(p->eps_r, p->eps_r + p->nt);
     if (p->mu_r) q->mu.assign(p->mu_r, p->mu_r + p->nt);
     if (p->part) q->part.assign(p->part, p->part + p->nt);
+    if (p->beta_face) q->beta.assign(p->beta_face, p->beta_face + 4 * p->nt);
     if (rhs) q->rhs.assign(rhs, rhs + n * k);
     if (dipoles) q->dipoles.assign(dipoles, dipoles + 6 * k);
   } catch (const std::bad_alloc&) {
@@ -305,6 +306,7 @@ int64_t oras_submit(oras_server* S, const oras_problem* p, const oras_options* o
   q->prob.eps_r = q->eps.data();
   q->prob.mu_r = p->mu_r ? q->mu.data() : nullptr;
   q->prob.part = p->part ? q->part.data() : nullptr;
+  q->prob.beta_face = p->beta_face ? q->beta.data() : nullptr;
   if (o) {
     q->opt = *o;
     q->has_opt = true;

@@ -46,14 +46,14 @@ class oras_complex(C.Structure):
 class oras_problem(C.Structure):
     _fields_ = [("nv", C.c_int64), ("xyz", C.c_void_p), ("nt", C.c_int64), ("tets", C.c_void_p),
                 ("eps_r", C.c_void_p), ("mu_r", C.c_void_p), ("k0", C.c_double), ("r", C.c_int32),
-                ("nsub", C.c_int32), ("overlap", C.c_int32), ("part", C.c_void_p)]
+                ("nsub", C.c_int32), ("overlap", C.c_int32), ("part", C.c_void_p), ("beta_face", C.c_void_p)]
 
 
 class oras_options(C.Structure):
     _fields_ = [("restart", C.c_int32), ("max_iter", C.c_int32), ("factor_bits", C.c_int32),
                 ("weights", C.c_int32), ("overlap_kind", C.c_int32), ("lu_engine", C.c_int32),
                 ("lu_panel", C.c_int32), ("lu_group", C.c_int32), ("transmission", C.c_int32),
-                ("graphs", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("graphs", C.c_int32), ("wait_ms", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class oras_info(C.Structure):
@@ -110,6 +110,7 @@ EXPORTS = {
     "oras_reset_timings": (C.c_int, [C.c_void_p]),
     "oras_launch_count": (C.c_int64, []),
     "oras_precond_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "oras_wait_selftest": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "oras_footprint": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
     "oras_release_memory": (C.c_int, [C.c_int32]),
     "oras_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_int32]),
@@ -166,7 +167,7 @@ def _c128(a):
     return np.ascontiguousarray(a, dtype=np.complex128)
 
 
-def _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part):
+def _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part, beta_face=None):
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     tets = np.ascontiguousarray(tets, dtype=np.int32)
     keep = [xyz, tets]
@@ -185,11 +186,15 @@ def _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part):
         pa = np.ascontiguousarray(part, dtype=np.int32)
         keep.append(pa)
         p.part = pa.ctypes.data
+    if beta_face is not None:
+        bf = np.ascontiguousarray(beta_face, dtype=np.float64).reshape(-1, 4)
+        keep.append(bf)
+        p.beta_face = bf.ctypes.data
     return p, keep
 
 
 def _options(restart=0, max_iter=0, factor_bits=0, weights=0, overlap_kind=0, lu_engine=0, lu_panel=0, lu_group=0,
-             transmission=0, graphs=0):
+             transmission=0, graphs=0, wait_ms=0):
     o = oras_options()
     o.restart, o.max_iter, o.factor_bits, o.weights, o.overlap_kind = restart, max_iter, factor_bits, weights, overlap_kind
     o.lu_engine = lu_engine
@@ -197,12 +202,14 @@ def _options(restart=0, max_iter=0, factor_bits=0, weights=0, overlap_kind=0, lu
     o.lu_group = lu_group
     o.transmission = transmission
     o.graphs = graphs
+    o.wait_ms = wait_ms
     return o
 
 
-def oras_create(xyz, tets, r, nsub, overlap, part=None, **opts):
-    """Host integer set-up; returns the handle (c_void_p)."""
-    p, keep = _problem(xyz, tets, None, None, 1.0, r, nsub, overlap, part)
+def oras_create(xyz, tets, r, nsub, overlap, part=None, beta_face=None, **opts):
+    """Host integer set-up; returns the handle (c_void_p).  beta_face: (nt, 4) impedance
+    coefficients of the outer faces (face q of tet t is opposite tets[t, q]) or None."""
+    p, keep = _problem(xyz, tets, None, None, 1.0, r, nsub, overlap, part, beta_face)
     o = _options(**opts)
     h = C.c_void_p()
     _check(None, lib.oras_create(C.byref(p), C.byref(o), C.byref(h)))
@@ -210,11 +217,11 @@ def oras_create(xyz, tets, r, nsub, overlap, part=None, **opts):
     return h
 
 
-def oras_setup(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part=None, **opts):
+def oras_setup(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part=None, beta_face=None, **opts):
     """oras_create + oras_factor: host mesh xyz (nv, 3), tets (nt, 4), per-tet complex eps_r and
     mu_r (None: 1), wave number k0, degree r, nsub subdomains (RCB unless part is given),
-    overlap layers; opts are oras_options fields.  Returns the handle."""
-    p, keep = _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part)
+    overlap layers, beta_face (nt, 4) or None; opts are oras_options fields.  Returns the handle."""
+    p, keep = _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part, beta_face)
     o = _options(**opts)
     h = C.c_void_p()
     _check(None, lib.oras_setup(C.byref(p), C.byref(o), C.byref(h)))
@@ -410,6 +417,15 @@ def oras_precond_noalloc(h, v, z, k=1):
     """z = M^{-1} v without any device allocation; v, z: torch CUDA complex128 tensors holding
     N x k column-major data (shape (k, N) contiguous, or (N,) for k = 1)."""
     return _check(h, lib.oras_precond_noalloc(h, _ptr(v), _ptr(z), int(k)))
+
+
+def oras_wait_selftest(h):
+    """Runs every bounded-wait primitive on a condition nothing satisfies, with the handle's
+    wait_ms; returns (rc, detail): ORAS_ERR_DEVICE_TIMEOUT and the mask 7 when each gave up."""
+    detail = C.c_int32()
+    rc = lib.oras_wait_selftest(h, C.byref(detail))
+    _check(h, rc, allow=(ORAS_OK, ORAS_ERR_DEVICE_TIMEOUT))
+    return rc, detail.value
 
 
 def oras_autotune(h):

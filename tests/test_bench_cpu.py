@@ -18,27 +18,48 @@ def test_peak_ratio_is_the_nominal_tf32_over_bf16():
 
 
 def test_roofline_of_a_tensor_bound_factorisation():
+    """The update runs inside a seconds-long step: its peak is the sustained bf16 rate times the
+    nominal tf32/bf16 ratio.  Every class with a work model gets its own object."""
     timings = {"lu_update": (800.0, 400), "apply": (300.0, 17), "spmv": (2.0, 17), "orth": (0.0, 0)}
     flops = 4.0e14
-    dom, r = bench.roofline(timings, flops, 8.0e10, 2, 6779.4, 1890.3)
+    dom, rs = bench.roofline(timings, flops, 8.0e10, 2, 6779.4, 1714.6, spmv=1.0e10)
+    r = rs[dom]
     assert dom == "lu_update" and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
     assert r["achieved"] == pytest.approx(flops * 2 / 0.8 / 1e12)
-    assert r["peak"] == pytest.approx(1890.3 * 1.1 / 2.25)
+    assert r["peak"] == pytest.approx(1714.6 * 1.1 / 2.25)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert rs["apply"]["achieved"] == pytest.approx(8.0e10 * 17 / 0.3 / 1e9)
+    assert rs["spmv"]["achieved"] == pytest.approx(1.0e10 / 0.002 / 1e9)
+    assert rs["spmv"]["frac"] == pytest.approx(rs["spmv"]["achieved"] / 6779.4)
 
 
 def test_roofline_of_an_hbm_bound_apply():
     timings = {"lu_update": (100.0, 50), "apply": (300.0, 20)}
-    dom, r = bench.roofline(timings, 1e13, 5.0e10, 1, 6779.4, 1890.3)
+    dom, rs = bench.roofline(timings, 1e13, 5.0e10, 1, 6779.4, 1714.6)
+    r = rs[dom]
     assert dom == "apply" and r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(5.0e10 * 20 / 0.3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6779.4)
+    assert "spmv" not in rs                   # no work model given
 
 
 def test_roofline_of_fp64_factors_is_alu_bound():
-    dom, r = bench.roofline({"lu_update": (1000.0, 10)}, 1e12, 1.0, 1, 6779.4, 1890.3, factor_bits=64)
+    dom, rs = bench.roofline({"lu_update": (1000.0, 10)}, 1e12, 1.0, 1, 6779.4, 1714.6, factor_bits=64)
+    r = rs[dom]
     assert dom == "lu_update" and r["bound"] == "alu"
     assert r["achieved"] == pytest.approx(1.0) and r["peak"] == bench.FP64_NOMINAL_TFLOPS
+
+
+def test_spmv_and_apply_byte_models():
+    """SpMV: 20 B per stored entry (16 B values + 4 B column), 8 B row pointer per row, input
+    8 B (FP32) or 16 B (FP64) and output 16 B per row and right-hand side.  Apply passes: groups
+    of up to 4 right-hand sides with FP32 factors (2 with FP64); the sizes are the live columns."""
+    assert bench.spmv_bytes(10, 100, 1, True) == 20 * 100 + 8 * 11 + 24 * 10
+    assert bench.spmv_bytes(10, 100, 3, False) == 20 * 100 + 8 * 11 + 32 * 30
+    assert bench.apply_group_sizes(32, 32) == [4] * 8
+    assert bench.apply_group_sizes(7, 32) == [4, 3]         # the last pass: 3 live columns of 4
+    assert bench.apply_group_sizes(3, 64) == [2, 1]
+    assert bench.rhs_groups(20, 8) == [8, 8, 4]
 
 
 def test_stored_traffic_needs_the_current_kernel_version(tmp_path, monkeypatch):

@@ -365,7 +365,9 @@ def test_tensor_core_lu_matches_cuda_core_lu(O, n, r, nsub, delta):
         v = rng.normal(size=p.topo.ndof) + 1j * rng.normal(size=p.topo.ndof)
         zt, zc = O.oras_precond(ht, v), O.oras_precond(hc, v)
         assert np.all(np.isfinite(zt))
-        assert rel(zt, zc) <= 2e-2, rel(zt, zc)
+        # the two differ by the TF32 rounding of the tensor-core update's operands (unit
+        # roundoff 2^-11), the same reading as the FP32 apply's bar against the FP64 oracle
+        assert rel(zt, zc) <= (TOL_APPLY_F32_R3 if r == 3 else TOL_APPLY_F32), rel(zt, zc)
         b = p.B[:, 0]
         x, info, rc = O.oras_solve(ht, b, 1e-8)
         assert rc == O.ORAS_OK

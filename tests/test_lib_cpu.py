@@ -130,3 +130,57 @@ def test_release_memory_of_a_missing_device_is_an_error(O):
     with pytest.raises(O.OrasError) as e:
         O.oras_release_memory(9999)
     assert e.value.code in (O.ORAS_ERR_INVALID_ARG, O.ORAS_ERR_CUDA)
+
+
+def test_noalloc_rejects_oversized_scratch_on_host(O):
+    """The allocation-free apply keeps its local vectors in a fixed 16 MiB device array; a problem
+    whose padded subdomain orders times the FP64 entry size exceed it is rejected from the host
+    set-up alone (INVALID_ARG with the needed size), before any device work.  The vector pointers
+    are never dereferenced on this path."""
+    import ctypes as C
+    xyz, tets = synth.kuhn_cube(24)
+    h = O.oras_create(xyz, tets, 2, 256, 1, factor_bits=64)
+    try:
+        total = sum(O.oras_subdomain_size(h, s)[2] for s in range(256))
+        assert total * 16 > 16 << 20
+        dummy = (C.c_double * 4)()
+        rc = O.lib.oras_precond_noalloc(h, C.cast(dummy, C.c_void_p), C.cast(dummy, C.c_void_p), 1)
+        assert rc == O.ORAS_ERR_INVALID_ARG
+        msg = O.lib.oras_last_error(h).decode()
+        assert str(total * 16) in msg and "16777216" in msg
+    finally:
+        O.oras_destroy(h)
+    xyz4, tets4 = synth.kuhn_cube(4)
+    h = O.oras_create(xyz4, tets4, 2, 8, 1)
+    try:  # a problem that fits: the next check is the call order (no oras_factor yet)
+        dummy = (C.c_double * 4)()
+        rc = O.lib.oras_precond_noalloc(h, C.cast(dummy, C.c_void_p), C.cast(dummy, C.c_void_p), 1)
+        assert rc == O.ORAS_ERR_STATE
+    finally:
+        O.oras_destroy(h)
+
+
+def test_beta_face_validation(O):
+    """beta_face entries of outer faces must be finite and positive (Sec. 2: beta > 0); entries of
+    interior faces are ignored."""
+    xyz, tets = synth.kuhn_cube(3)
+    topo = topology.build(tets, len(xyz), 1)
+    beta = np.full((len(tets), 4), 7.5)
+    # interior-face entries may hold anything
+    inner = np.ones((len(tets), 4), dtype=bool)
+    st = np.sort(tets, axis=1)
+    for t in range(len(tets)):
+        for lf in range(4):
+            if topo.face_tets[topo.tet_faces[t, lf], 1] < 0:
+                opp = st[t, (3, 2, 1, 0)[lf]]
+                inner[t, list(tets[t]).index(opp)] = False
+    assert (~inner).sum() == 12 * 9          # 2 triangles on each of the 6 n^2 boundary squares
+    beta[inner] = -1.0
+    h = O.oras_create(xyz, tets, 1, 4, 1, beta_face=beta)
+    O.oras_destroy(h)
+    t, q = np.argwhere(~inner)[5]
+    bad = beta.copy()
+    bad[t, q] = 0.0
+    with pytest.raises(O.OrasError) as e:
+        O.oras_create(xyz, tets, 1, 4, 1, beta_face=bad)
+    assert e.value.code == O.ORAS_ERR_INVALID_ARG

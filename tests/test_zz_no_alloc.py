@@ -24,8 +24,10 @@ def test_noalloc_apply_matches_regular_apply_twice():
     w = synth.small(n=4, r=2, nsub=8, overlap=1)
     xyz, tets = w.mesh()
     eps, mu = w.materials(xyz, tets)
-    for bits in (32, 64):
-        h = O.oras_setup(xyz, tets, eps, mu, w.k0, w.r, w.nsub, w.overlap, factor_bits=bits)
+    # ORAS with FP32 and FP64 factors, and OAS (no partition of unity: the overlapping
+    # contributions are summed into z, which the call clears first)
+    for bits, weights in ((32, O.ORAS_WEIGHTS_POU), (64, O.ORAS_WEIGHTS_POU), (32, O.ORAS_WEIGHTS_NONE)):
+        h = O.oras_setup(xyz, tets, eps, mu, w.k0, w.r, w.nsub, w.overlap, factor_bits=bits, weights=weights)
         try:
             n = O.oras_ndof(h)
             rng = np.random.default_rng(bits)
@@ -40,6 +42,6 @@ def test_noalloc_apply_matches_regular_apply_twice():
                 torch.cuda.synchronize()
                 got = zd.cpu().numpy().T
                 err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-                assert err <= 1e-12, (bits, call, err)
+                assert err <= 1e-12, (bits, weights, call, err)
         finally:
             O.oras_destroy(h)
