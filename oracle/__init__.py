@@ -11,10 +11,12 @@ What it computes (paper: Bonazzoli, Dolean, Rapetti, Tournier, arXiv:1605.04521)
   degree-r Nedelec degrees of freedom (Sec. 3).
 * `basis`     -- the generators w^{k,e} = lambda^k w^e of Sec. 3 and the selected
   linearly independent subset; point evaluation of values and curls.
-* `elements`  -- exact element matrices of the weak form of Sec. 2 (curl-curl,
-  mass, impedance boundary term) by the barycentric monomial integration rule.
+* `elements`  -- element matrices of the weak form of Sec. 2 (curl-curl, mass,
+  impedance boundary term) from their definition: conical-product quadrature,
+  exact for the degree-2r integrands, of the directly evaluated generators and
+  curls.
 * `quadrature`-- Gauss-Jacobi rules (Golub-Welsch) and conical-product rules on
-  triangles and tetrahedra; used for loads and for independent checks.
+  triangles and tetrahedra; used for the element matrices and the loads.
 * `assemble`  -- global sparse matrix of Sec. 4 (A u_j = b_j) and right-hand sides.
 * `dd`        -- recursive coordinate bisection, overlapping subdomains, restriction
   R_s, partition of unity D_s, local impedance matrices A_s, and the ORAS

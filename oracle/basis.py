@@ -154,3 +154,35 @@ def eval_local_basis(r, verts, x):
     val = np.stack([eval_generator(d[3], d[4], d[5], lam, glam) for d in dofs], axis=1)
     cur = np.stack([eval_generator_curl(d[3], d[4], d[5], lam, glam) for d in dofs], axis=1)
     return val, cur
+
+
+def eval_basis_batch(r, lam, glam):
+    """Values and curls of the local basis of many tetrahedra at the same barycentric points.
+
+    lam[P,4] barycentric coordinates of the points (the same in every tetrahedron), glam[T,4,3]
+    barycentric gradients of each tetrahedron.  Returns values [T,P,n_local,3] and curls
+    [T,P,n_local,3], evaluated from the definitions of Sec. 3 exactly as eval_generator and
+    eval_generator_curl do for one tetrahedron:
+        w = lambda^k (lambda_i grad lambda_j - lambda_j grad lambda_i),
+        curl w = grad(lambda^k) x w^{ij} + 2 lambda^k grad lambda_i x grad lambda_j.
+    """
+    lam = np.asarray(lam, dtype=np.float64)
+    glam = np.asarray(glam, dtype=np.float64)
+    T, P = glam.shape[0], lam.shape[0]
+    dofs = local_dofs(r)
+    val = np.empty((T, P, len(dofs), 3))
+    cur = np.empty((T, P, len(dofs), 3))
+    for a, (_, _, _, i, j, k) in enumerate(dofs):
+        k = np.array(k)
+        lk = np.prod(lam ** k, axis=1)                                       # [P]
+        w = lam[None, :, i, None] * glam[:, None, j, :] - lam[None, :, j, None] * glam[:, None, i, :]
+        grad_lk = np.zeros((T, P, 3))
+        for m in range(4):
+            if k[m] > 0:
+                km = k.copy()
+                km[m] -= 1
+                grad_lk += (k[m] * np.prod(lam ** km, axis=1))[None, :, None] * glam[:, None, m, :]
+        val[:, :, a, :] = lk[None, :, None] * w
+        cur[:, :, a, :] = (np.cross(grad_lk, w) +
+                           2.0 * lk[None, :, None] * np.cross(glam[:, i, :], glam[:, j, :])[:, None, :])
+    return val, cur

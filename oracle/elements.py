@@ -1,113 +1,29 @@
-"""Exact element matrices of the curl-curl weak form (oracle; test infrastructure).
+"""Element matrices of the curl-curl weak form (oracle; test infrastructure).
 
 Weak form (Sec. 2, variational formulation):
     int_Omega [ mu_r^{-1} curl E . curl v - k0^2 eps_r E . v ]
       + int_Gamma i beta (E x n) . (v x n)  =  int_Gamma g . v .
-Every generator lambda^k w^{ij} (Sec. 3) is a sum of terms  c * lambda^alpha * grad(lambda_m),
-and its curl a sum of terms  c * lambda^beta * (grad lambda_p x grad lambda_m)  because
-curl(f grad g) = grad f x grad g.  Products of two terms are then integrated exactly with
-    int_T lambda^alpha = 6 |T| alpha! / (|alpha| + 3)!          (volume)
-    int_f lambda^alpha = 2 |f| alpha! / (|alpha| + 2)!          (face, alpha_opp = 0)
-and the geometric factors are G_pq = grad lambda_p . grad lambda_q and
-(grad l_p x grad l_m).(grad l_q x grad l_n) = G_pq G_mn - G_pn G_mq.
-On a face f with opposite vertex o, (u x n).(v x n) = u.v - (u.n)(v.n) and
-n = grad lambda_o / |grad lambda_o|, so the tangential Gram matrix is
-G^T_pq = G_pq - G_po G_qo / G_oo, and |f| = 3 |T| |grad lambda_o|.
+The matrices are computed from their definition: the degree-r generators lambda^k w^{ij} of
+Sec. 3 and their curls (product formula) are evaluated at the points of a conical-product
+Gauss-Jacobi rule (oracle.quadrature) and the integrands are summed with its weights,
+
+    M_T[a,b] = int_T w_a . w_b,                K_T[a,b] = int_T curl w_a . curl w_b,
+    S_f[a,b] = int_f (w_a x n) . (w_b x n).
+
+w_a is a polynomial of degree r and curl w_a of degree r - 1, so the integrands have degree at
+most 2r; the n-point rule in each collapsed direction is exact to total degree 2n - 1, so
+n = r + 1 points give the exact integrals up to rounding.  The affine map of the reference
+simplex contributes the factor 6|T| (volume, rule weights summing to 1/6) or 2|f| (face,
+weights summing to 1/2); on a face f opposite the local vertex o the unit normal is
+grad(lambda_o) / |grad(lambda_o)| (its sign does not matter in S_f) and |f| = 3 |T| |grad lambda_o|.
 """
 from __future__ import annotations
 
-from functools import lru_cache
-from math import factorial
-
 import numpy as np
 
-from . import basis
+from . import basis, quadrature
 
-
-def _fact(alpha):
-    out = 1
-    for a in alpha:
-        out *= factorial(a)
-    return out
-
-
-def vol_coef(alpha):
-    """int_T lambda^alpha / |T|."""
-    return 6.0 * _fact(alpha) / factorial(sum(alpha) + 3)
-
-
-def face_coef(alpha):
-    """int_f lambda^alpha / |f| for alpha supported on the face."""
-    return 2.0 * _fact(alpha) / factorial(sum(alpha) + 2)
-
-
-def _terms(d):
-    """lambda^k (lambda_i grad l_j - lambda_j grad l_i) as [(c, alpha, m)]."""
-    _, _, _, i, j, k = d
-    a1 = list(k)
-    a1[i] += 1
-    a2 = list(k)
-    a2[j] += 1
-    return [(1.0, tuple(a1), j), (-1.0, tuple(a2), i)]
-
-
-def _curl_terms(d):
-    """curl of the generator as [(c, beta, p, m)] meaning c lambda^beta (grad l_p x grad l_m)."""
-    out = []
-    for c, alpha, m in _terms(d):
-        for p in range(4):
-            if alpha[p] > 0:
-                beta = list(alpha)
-                beta[p] -= 1
-                out.append((c * alpha[p], tuple(beta), p, m))
-    return out
-
-
-def _add(a, b):
-    return tuple(x + y for x, y in zip(a, b))
-
-
-@lru_cache(maxsize=None)
-def mass_coefficients(r):
-    dofs = basis.local_dofs(r)
-    n = len(dofs)
-    C = np.zeros((n, n, 4, 4))
-    for a, da in enumerate(dofs):
-        for b, db in enumerate(dofs):
-            for ca, aa, ma in _terms(da):
-                for cb, ab, mb in _terms(db):
-                    C[a, b, ma, mb] += ca * cb * vol_coef(_add(aa, ab))
-    return C
-
-
-@lru_cache(maxsize=None)
-def stiffness_coefficients(r):
-    dofs = basis.local_dofs(r)
-    n = len(dofs)
-    C = np.zeros((n, n, 4, 4, 4, 4))
-    ct = [_curl_terms(d) for d in dofs]
-    for a in range(n):
-        for b in range(n):
-            for ca, ba, pa, ma in ct[a]:
-                for cb, bb, pb, mb in ct[b]:
-                    C[a, b, pa, ma, pb, mb] += ca * cb * vol_coef(_add(ba, bb))
-    return C.reshape(n, n, 16, 16)
-
-
-@lru_cache(maxsize=None)
-def face_coefficients(r, opp):
-    dofs = basis.local_dofs(r)
-    n = len(dofs)
-    C = np.zeros((n, n, 4, 4))
-    for a, da in enumerate(dofs):
-        for b, db in enumerate(dofs):
-            for ca, aa, ma in _terms(da):
-                for cb, ab, mb in _terms(db):
-                    al = _add(aa, ab)
-                    if al[opp] != 0:
-                        continue
-                    C[a, b, ma, mb] += ca * cb * face_coef(tuple(al[v] for v in range(4) if v != opp))
-    return C
+CHUNK = 2048     # tetrahedra evaluated together (bounds the memory of the point values)
 
 
 def geometry(xyz, st):
@@ -123,17 +39,26 @@ def geometry(xyz, st):
     return grads, vol, G
 
 
-def cross_gram(G):
-    """X[t,(p,m),(q,n)] = (grad l_p x grad l_m).(grad l_q x grad l_n)."""
-    X = (np.einsum("tpq,tmn->tpmqn", G, G) - np.einsum("tpn,tmq->tpmqn", G, G))
-    return X.reshape(len(G), 16, 16)
+def _gram(F, w):
+    """sum_p w_p F[t,p,a,:] . F[t,p,b,:] for F [T,P,n,3] -> [T,n,n]."""
+    Fw = F * np.sqrt(w)[None, :, None, None]
+    Fw = Fw.transpose(0, 2, 1, 3).reshape(F.shape[0], F.shape[2], -1)   # [T, n, P*3]
+    return Fw @ Fw.transpose(0, 2, 1)
 
 
 def element_mass_stiffness(xyz, st, r):
-    """Exact M_T[t,a,b] = int w_a.w_b and K_T[t,a,b] = int curl w_a . curl w_b (real)."""
-    _, vol, G = geometry(xyz, st)
-    M = vol[:, None, None] * np.einsum("abpq,tpq->tab", mass_coefficients(r), G)
-    K = vol[:, None, None] * np.einsum("abxy,txy->tab", stiffness_coefficients(r), cross_gram(G))
+    """M_T[t,a,b] = int w_a . w_b and K_T[t,a,b] = int curl w_a . curl w_b (real), by the
+    (r+1)-point conical-product rule on every tetrahedron."""
+    st = np.asarray(st)
+    lam, w = quadrature.tet_rule(r + 1)
+    n = basis.n_local(r)
+    M = np.empty((len(st), n, n))
+    K = np.empty((len(st), n, n))
+    for c0 in range(0, len(st), CHUNK):
+        grads, vol, _ = geometry(xyz, st[c0:c0 + CHUNK])
+        val, cur = basis.eval_basis_batch(r, lam, grads)
+        M[c0:c0 + CHUNK] = 6.0 * vol[:, None, None] * _gram(val, w)
+        K[c0:c0 + CHUNK] = 6.0 * vol[:, None, None] * _gram(cur, w)
     return M, K
 
 
@@ -143,23 +68,38 @@ def element_matrices(xyz, st, r, eps_r, mu_r, k0):
     return (1.0 / mu_r)[:, None, None] * K - (k0 ** 2) * eps_r[:, None, None] * M
 
 
+def face_points(lf, r):
+    """Barycentric points [P,4] of the (r+1)-point triangle rule on local face lf (the opposite
+    coordinate is zero) and the rule's weights (sum 1/2)."""
+    lam3, w = quadrature.tri_rule(r + 1)
+    lam = np.zeros((lam3.shape[0], 4))
+    lam[:, list(basis.LOCAL_FACES[lf])] = lam3
+    return lam, w
+
+
 def face_matrices(xyz, st, tets_idx, local_face, r):
     """S_f[a,b] = int_f (w_a x n).(w_b x n) for faces given as (tet, local face) pairs.
 
-    Returned in the tet-local numbering (n_local x n_local, zero outside the face DOFs).
+    Returned in the tet-local numbering (n_local x n_local; zero rows and columns for the DOFs
+    whose tangential trace vanishes on the face).
     """
     tets_idx = np.asarray(tets_idx)
     local_face = np.asarray(local_face)
-    _, vol, G = geometry(xyz, st[tets_idx])
-    out = np.zeros((len(tets_idx), basis.n_local(r), basis.n_local(r)))
+    n = basis.n_local(r)
+    out = np.zeros((len(tets_idx), n, n))
     for lf in range(4):
         sel = np.nonzero(local_face == lf)[0]
         if len(sel) == 0:
             continue
         o = basis.FACE_OPPOSITE[lf]
-        Gs = G[sel]
-        goo = Gs[:, o, o]
-        GT = Gs - Gs[:, :, o][:, :, None] * Gs[:, :, o][:, None, :] / goo[:, None, None]
-        area = 3.0 * vol[sel] * np.sqrt(goo)
-        out[sel] = area[:, None, None] * np.einsum("abpq,tpq->tab", face_coefficients(r, o), GT)
+        lam, w = face_points(lf, r)
+        for c0 in range(0, len(sel), CHUNK):
+            part = sel[c0:c0 + CHUNK]
+            grads, vol, _ = geometry(xyz, st[tets_idx[part]])
+            gn = np.linalg.norm(grads[:, o], axis=1)
+            nrm = grads[:, o] / gn[:, None]
+            area = 3.0 * vol * gn
+            val, _ = basis.eval_basis_batch(r, lam, grads)
+            tan = np.cross(val, nrm[:, None, None, :])
+            out[part] = 2.0 * area[:, None, None] * _gram(tan, w)
     return out

@@ -155,31 +155,48 @@ def test_r1_element_matrices_closed_form():
 
 
 @pytest.mark.parametrize("r", [1, 2, 3])
-def test_exact_matrices_match_quadrature(r):
-    """Exact monomial integration vs conical-product quadrature of the basis evaluated with
-    the product formula curl(l^k w) = grad l^k x w + 2 l^k grad l_i x grad l_j."""
+def test_element_matrices_match_exact_monomial_rule(r):
+    """The oracle integrates by quadrature of the evaluated basis; the same matrices computed
+    without quadrature, by the exact monomial rule int_T lambda^alpha = 6|T| alpha!/(|alpha|+3)!
+    over the term expansion of each generator (tests/elem_tables.py), agree to 1e-12."""
+    import elem_tables
     rng = np.random.default_rng(10 + r)
-    lam_q, w_q = quadrature.tet_rule(r + 2)
-    lam_f, w_f = quadrature.tri_rule(r + 2)
     for _ in range(3):
         verts = random_tet(rng)
         st = np.array([[0, 1, 2, 3]])
         M, K = elements.element_mass_stiffness(verts, st, r)
-        vol = abs(np.linalg.det(verts[1:] - verts[0])) / 6
-        x = lam_q @ verts
-        val, cur = basis.eval_local_basis(r, verts, x)
-        Mq = 6 * vol * np.einsum("p,pai,pbi->ab", w_q, val, val)
-        Kq = 6 * vol * np.einsum("p,pai,pbi->ab", w_q, cur, cur)
-        assert np.abs(M[0] - Mq).max() < 1e-12 * np.abs(Mq).max()
-        assert np.abs(K[0] - Kq).max() < 1e-12 * np.abs(Kq).max()
-        for lf, fv in enumerate(basis.LOCAL_FACES):
+        Me, Ke = elem_tables.element_mass_stiffness(verts, st, r)
+        assert np.abs(M - Me).max() < 1e-12 * np.abs(Me).max()
+        assert np.abs(K - Ke).max() < 1e-12 * np.abs(Ke).max()
+        for lf in range(4):
             S = elements.face_matrices(verts, st, [0], [lf], r)[0]
+            Se = elem_tables.face_matrices(verts, st, [0], [lf], r)[0]
+            assert np.abs(S - Se).max() < 1e-12 * np.abs(Se).max()
+
+
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_batched_basis_matches_pointwise_basis(r):
+    """The batched evaluation the oracle integrates with (shared barycentric points, per-tet
+    gradients) equals the one-tetrahedron evaluation at physical points (barycentrics solved from
+    the coordinates), values and curls, and its face quadrature reproduces the tangential mass of
+    a face integrated in physical coordinates."""
+    rng = np.random.default_rng(20 + r)
+    lam_q, _ = quadrature.tet_rule(r + 1)
+    for _ in range(3):
+        verts = random_tet(rng)
+        g = basis.barycentric_gradients(verts)
+        vb, cb = basis.eval_basis_batch(r, lam_q, g[None])
+        vp, cp = basis.eval_local_basis(r, verts, lam_q @ verts)
+        assert np.abs(vb[0] - vp).max() < 1e-12 * max(1.0, np.abs(vp).max())
+        assert np.abs(cb[0] - cp).max() < 1e-12 * max(1.0, np.abs(cp).max())
+        lam_f, w_f = quadrature.tri_rule(r + 2)
+        for lf, fv in enumerate(basis.LOCAL_FACES):
+            S = elements.face_matrices(verts, np.array([[0, 1, 2, 3]]), [0], [lf], r)[0]
             pf = verts[list(fv)]
             nrm = np.cross(pf[1] - pf[0], pf[2] - pf[0])
             area = np.linalg.norm(nrm) / 2
             nrm /= np.linalg.norm(nrm)
-            xf = lam_f @ pf
-            vf, _ = basis.eval_local_basis(r, verts, xf)
+            vf, _ = basis.eval_local_basis(r, verts, lam_f @ pf)
             tf = np.cross(vf, nrm[None, None, :])
             Sq = 2 * area * np.einsum("p,pai,pbi->ab", w_f, tf, tf)
             assert np.abs(S - Sq).max() < 1e-12 * np.abs(Sq).max()
@@ -553,3 +570,122 @@ def test_oras_converges_faster_than_oas(n, r, nsub):
     it_oras = fgmres.fgmres(lambda v: P.A @ v, P.oras.apply, b, 1e-8, 50, 5000).iterations
     it_oas = fgmres.fgmres(lambda v: P.A @ v, oas.apply, b, 1e-8, 50, 5000).iterations
     assert it_oras < it_oas
+
+
+# ---------------------------------------------------------------- impedance terms, closed form
+
+def _constant_field_coefficients(topo, xyz, r, c):
+    """Coefficient vector of the constant field c (= grad(c . x), in V_h for every r), fitted
+    tetrahedron by tetrahedron from point values; the fit must be exact and consistent."""
+    u, fit, agree = _fit_gradient(topo, xyz, r, lambda t, lam, g, x: np.broadcast_to(c, x.shape).copy())
+    assert fit < 1e-11 and agree < 1e-10
+    return u
+
+
+def _jittered_kuhn(n, seed):
+    """Kuhn cube with interior vertices moved (boundary vertices stay on the cube faces, so the
+    outer normals stay the axis directions) -- general interior face normals."""
+    xyz, tets = synth.kuhn_cube(n)
+    rng = np.random.default_rng(seed)
+    inner = np.all((xyz > 1e-12) & (xyz < 1 - 1e-12), axis=1)
+    xyz = xyz.copy()
+    xyz[inner] += rng.uniform(-0.2, 0.2, size=(inner.sum(), 3)) / n
+    return xyz, tets
+
+
+def _face_geometry(xyz, st, t, lf):
+    """Area and unit normal of local face lf of tetrahedron t, from the vertex coordinates."""
+    pf = xyz[st[t, list(basis.LOCAL_FACES[lf])]]
+    nrm = np.cross(pf[1] - pf[0], pf[2] - pf[0])
+    area = np.linalg.norm(nrm) / 2
+    return area, nrm / np.linalg.norm(nrm)
+
+
+@pytest.mark.parametrize("r", [1, 2, 3])
+@pytest.mark.parametrize("caller_beta", [False, True])
+def test_global_matrix_on_a_constant_field(r, caller_beta):
+    """For a constant field E = c (curl E = 0) the weak form of Sec. 2 gives, independently of the
+    basis,  u^T A u = -k0^2 sum_T eps_T |T| |c|^2 + i sum_{outer f} beta_f |f| |c x n_f|^2,
+    with beta_f the caller's per-face table (looked up through the caller's vertex order) or
+    k0 sqrt(Re eps) of the adjacent tetrahedron.  A wrong beta, face, area or normal fails it."""
+    xyz, tets = _jittered_kuhn(2, seed=r)
+    rng = np.random.default_rng(100 + r)
+    tets = np.array([rng.permutation(t) for t in tets])     # caller's vertex order is arbitrary
+    topo = topology.build(tets, len(xyz), r)
+    eps = rng.uniform(30, 60, len(tets)) - 1j * rng.uniform(5, 25, len(tets))
+    mu = np.ones(len(tets), dtype=np.complex128)
+    k0 = synth.K0
+    beta_face = rng.uniform(4.0, 20.0, size=(len(tets), 4)) if caller_beta else None
+    beta_lf = None if beta_face is None else assemble.face_beta_table(tets, beta_face)
+    A = assemble.global_matrix(topo, xyz, eps, mu, k0, beta_lf)
+    for c in (np.array([1.0, 0.0, 0.0]), np.array([0.3, -1.2, 0.7])):
+        u = _constant_field_coefficients(topo, xyz, r, c)
+        _, vol, _ = elements.geometry(xyz, topo.st)
+        expect = -k0 ** 2 * np.sum(eps * vol) * (c @ c)
+        for f in topo.boundary_faces():
+            t = topo.face_tets[f, 0]
+            lf = int(np.nonzero(topo.tet_faces[t] == f)[0][0])
+            area, nrm = _face_geometry(xyz, topo.st, t, lf)
+            if caller_beta:   # face lf of the sorted tet is opposite the caller's vertex with that id
+                opp = topo.st[t, basis.FACE_OPPOSITE[lf]]
+                beta = beta_face[t, list(tets[t]).index(opp)]
+            else:
+                beta = k0 * np.sqrt(eps[t].real)
+            expect += 1j * beta * area * np.sum(np.cross(c, nrm) ** 2)
+        got = u @ (A @ u)
+        assert abs(got - expect) <= 1e-11 * abs(expect), (got, expect)
+
+
+@pytest.mark.parametrize("r", [1, 2])
+@pytest.mark.parametrize("delta", [0, 1])
+def test_local_matrix_interface_term_on_a_constant_field(r, delta):
+    """Impedance transmission of Sec. 4 in closed form: for the constant field c restricted to
+    N_s,  u_s^T A_s u_s = -k0^2 sum_{T in Omega_s} eps_T |T| |c|^2
+    + i sum_{f outer face of Omega_s} beta_f |f| |c x n_f|^2
+    + i sum_{f interface face of Omega_s} w~_f |f| |c x n_f|^2,
+    w~_f = k0 sqrt(Re eps) of the tetrahedron of f inside Omega_s^delta (the materials differ
+    from tetrahedron to tetrahedron, so the outside one would fail), every face found from the
+    geometry alone."""
+    xyz, tets = _jittered_kuhn(3, seed=7 + r)
+    topo = topology.build(tets, len(xyz), r)
+    rng = np.random.default_rng(200 + r)
+    eps = rng.uniform(30, 60, len(tets)) - 1j * rng.uniform(5, 25, len(tets))
+    mu = np.ones(len(tets), dtype=np.complex128)
+    k0 = synth.K0
+    dec = dd.decompose(topo, xyz, 4, delta)
+    c = np.array([0.4, 1.0, -0.6])
+    u = _constant_field_coefficients(topo, xyz, r, c)
+    _, vol, _ = elements.geometry(xyz, topo.st)
+    for s in range(4):
+        As = dd.local_matrix(topo, xyz, eps, mu, k0, dec, s)
+        us = u[dec.dofs[s]]
+        inside = np.zeros(topo.nt, dtype=bool)
+        inside[dec.tets[s]] = True
+        expect = -k0 ** 2 * np.sum(eps[inside] * vol[inside]) * (c @ c)
+        n_iface = 0
+        for t in dec.tets[s]:
+            for lf in range(4):
+                a, b = topo.face_tets[topo.tet_faces[t, lf]]
+                other = b if a == t else a
+                if other >= 0 and inside[other]:
+                    continue
+                area, nrm = _face_geometry(xyz, topo.st, t, lf)
+                coef = k0 * np.sqrt(eps[t].real)       # outer face: beta; interface: w~ of t
+                expect += 1j * coef * area * np.sum(np.cross(c, nrm) ** 2)
+                n_iface += other >= 0
+        assert n_iface > 0
+        got = us @ (As @ us)
+        assert abs(got - expect) <= 1e-11 * abs(expect), (s, got, expect)
+
+
+def test_face_beta_table_brute_force():
+    """beta of the sorted local face lf = the caller's entry of the face opposite the same vertex."""
+    rng = np.random.default_rng(5)
+    tets = np.array([rng.permutation(10)[:4] for _ in range(20)])
+    beta = rng.uniform(1, 2, size=(20, 4))
+    tab = assemble.face_beta_table(tets, beta)
+    for t in range(20):
+        st = sorted(tets[t])
+        for lf, fv in enumerate(basis.LOCAL_FACES):
+            opp = (set(range(4)) - set(fv)).pop()
+            assert tab[t, lf] == beta[t, list(tets[t]).index(st[opp])]
