@@ -67,6 +67,11 @@ enum { ORAS_MEM_HOST = 0, ORAS_MEM_DEVICE = 1 };
 enum { ORAS_WEIGHTS_POU = 0 /* ORAS: R_s^T D_s */, ORAS_WEIGHTS_NONE = 1 /* OAS, Sec. 4 */ };
 enum { ORAS_OVERLAP_VERTEX = 0, ORAS_OVERLAP_FACE = 1 };
 enum { ORAS_LU_AUTO = 0 /* tensor cores for FP32 factors */, ORAS_LU_CUDA_CORES = 1 };
+/* Preconditioner apply with FP32 factors: AUTO streams the factor arena once per group of up to
+ * 32 right-hand sides through tcgen05 tensor-core products (TF32 operands, FP32 accumulation)
+ * when a call has 8 or more columns, and once per group of up to 4 on the CUDA cores (FP32)
+ * otherwise; CUDA_CORES always takes the CUDA-core groups. */
+enum { ORAS_APPLY_AUTO = 0, ORAS_APPLY_CUDA_CORES = 1 };
 /* Transmission condition of the local problems (Sec. 4): impedance (ORAS: A_s = sum of the
  * element matrices of Omega_s^delta + i w~ S on its boundary faces) or Dirichlet (RAS:
  * A_s = R_s A R_s^T, the rows and columns N_s of the global matrix). */
@@ -120,7 +125,8 @@ typedef struct {
                               /*   kernel returns and the call reports ORAS_ERR_DEVICE_TIMEOUT */
                               /*   [2000]; waits of a CTA for its own copies in flight before  */
                               /*   it exits never use less than 2000                           */
-  int32_t reserved[5];
+  int32_t apply_engine;       /* ORAS_APPLY_AUTO [default] or ORAS_APPLY_CUDA_CORES            */
+  int32_t reserved[4];
 } oras_options;
 
 /* Per right-hand-side outcome of oras_solve. */

@@ -10,6 +10,19 @@
 namespace oras {
 
 size_t apply_yglob_bytes(const oras_handle* h, int kr);
+// tensor-core passes (apply_tc.cu)
+bool apply_tc_available(const oras_handle* h);
+size_t apply_tc_ybytes(const oras_handle* h, int kt);
+int apply_tc_f64out(const oras_handle* h, const cplx* v, cplx* z, int k, int r0, int nr);
+int apply_tc_f32out(const oras_handle* h, const cplx* v, void* z, int k, int r0, int nr);
+int apply_tc_passes(int nr);
+
+// Columns from which a call takes the tensor-core passes (FP32 factors, ORAS_APPLY_AUTO).
+constexpr int APPLY_TC_MIN_K = 8;
+
+static bool use_tc(const oras_handle* h, int k) {
+  return k >= APPLY_TC_MIN_K && h->opt.factor_bits == 32 && h->opt.apply_engine != ORAS_APPLY_CUDA_CORES;
+}
 
 template <typename R, typename ZT, int KR>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(APPLY_THREADS, 1)
@@ -80,6 +93,16 @@ static int apply_t(const oras_handle* h, const cplx* v, ZT* z, int k) {
   const auto& m = h->mesh;
   const auto& d = h->dev;
   if (h->opt.weights != ORAS_WEIGHTS_POU) cudaMemsetAsync(z, 0, sizeof(ZT) * m.ndof * k, d.stream);
+  if constexpr (sizeof(R) == 4) {
+    if (use_tc(h, k) && apply_tc_available(h)) {
+      int n;
+      if constexpr (sizeof(ZT) == sizeof(cplx)) n = apply_tc_f64out(h, v, (cplx*)z, k, 0, k);
+      else n = apply_tc_f32out(h, v, (void*)z, k, 0, k);
+      if (n < 0) return -1;
+      count_launches(0);
+      return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
+  }
   const int maxkr = sizeof(R) == 4 ? APPLY_MAX_KR_F32 : APPLY_MAX_KR_F64;
   int launches = 0, rc = 0;
   for (int r0 = 0; r0 < k && rc == 0;) {
@@ -106,6 +129,7 @@ int launch_apply_f32out(const oras_handle* h, const cplx* v, void* z, int k) {
 
 // Number of apply launches (arena passes) for k right-hand sides.
 int apply_passes(const oras_handle* h, int k) {
+  if (use_tc(h, k) && apply_tc_available(h)) return apply_tc_passes(k);
   const int maxkr = h->dev.factor_bits == 64 ? APPLY_MAX_KR_F64 : APPLY_MAX_KR_F32;
   int n = 0;
   for (int r0 = 0; r0 < k; ++n) r0 += std::min(group_kr(k - r0, maxkr), k - r0);
@@ -126,16 +150,18 @@ static size_t yglob_bytes_kr(const oras_handle* h) {
 
 // Global scratch for the local vectors when a group of kr right-hand sides runs (0: shared memory).
 size_t apply_yglob_bytes(const oras_handle* h, int kr) {
-  if (h->dev.factor_bits == 64) return kr <= 1 ? yglob_bytes_kr<double, 1>(h) : yglob_bytes_kr<double, 2>(h);
+  if (h->opt.factor_bits == 64) return kr <= 1 ? yglob_bytes_kr<double, 1>(h) : yglob_bytes_kr<double, 2>(h);
   if (kr <= 1) return yglob_bytes_kr<float, 1>(h);
   if (kr == 2) return yglob_bytes_kr<float, 2>(h);
   return yglob_bytes_kr<float, 4>(h);
 }
 
-// Largest scratch any group of a k-vector apply needs.
+// Largest scratch any group of a k-vector apply needs (the tensor-core passes keep their y strips
+// in global memory: at most 32 columns per pass, complex FP32).
 size_t apply_yglob_bytes_for(const oras_handle* h, int k) {
-  const int maxkr = h->dev.factor_bits == 64 ? APPLY_MAX_KR_F64 : APPLY_MAX_KR_F32;
+  const int maxkr = h->opt.factor_bits == 64 ? APPLY_MAX_KR_F64 : APPLY_MAX_KR_F32;
   size_t b = 0;
+  if (use_tc(h, k)) b = apply_tc_ybytes(h, k > 16 ? 32 : (k > 8 ? 16 : 8));
   for (int r0 = 0; r0 < k;) {
     const int kr = group_kr(k - r0, maxkr);
     b = std::max(b, apply_yglob_bytes(h, kr));

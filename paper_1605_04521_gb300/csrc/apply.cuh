@@ -1,8 +1,8 @@
 // Device body of the ORAS preconditioner apply for one subdomain (Sec. 4):
 //   y = P_s R_s v ;  y = L_s^{-1} y ;  y = U_s^{-1} y ;  z += R_s^T D_s y
-// Block substitution over the tiled factor arena (split re/im planes; tiles on/below the block
-// diagonal row-major, above it column-major) with inverted diagonal blocks, so every step is a
-// TB x TB tile times a TB x KR block of KR right-hand sides.  One pass over the arena serves all
+// Block substitution over the tiled factor arena (split re/im planes, every tile row-major once the
+// factorisation has finished) with inverted diagonal blocks, so every step is a TB x TB tile times a
+// TB x KR block of KR right-hand sides: warp w takes rows 8w..8w+7, lane l the column pair 2l, 2l+1.  One pass over the arena serves all
 // KR right-hand sides: the factor bytes are read once per group, not once per vector.
 //
 // A cluster of two CTAs works on one subdomain.  CTA c owns the block rows (strips) I with
@@ -95,8 +95,7 @@ struct ApplySmem {
   static __host__ __device__ size_t bar_off(int S, int64_t ys) { return (size_t)S * slot(ys); }
   static __host__ __device__ size_t recv_off(int S, int64_t ys) { return bar_off(S, ys) + (size_t)(2 * S + 2) * 8; }
   static __host__ __device__ size_t part_off(int S, int64_t ys) { return recv_off(S, ys) + 2 * TB * KR * C; }
-  static __host__ __device__ size_t red_off(int S, int64_t ys) { return part_off(S, ys) + TB * KR * C; }
-  static __host__ __device__ size_t rvec_off(int S, int64_t ys) { return red_off(S, ys) + 8 * TB * KR * C; }
+  static __host__ __device__ size_t rvec_off(int S, int64_t ys) { return part_off(S, ys) + TB * KR * C; }
   static __host__ __device__ size_t y_off(int S, int64_t ys) { return rvec_off(S, ys) + TB * KR * C; }
   static __host__ __device__ size_t total(int S, int64_t ys) { return y_off(S, ys) + (size_t)ys * TB * KR * C; }
 };
@@ -118,7 +117,6 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
   uint64_t* msg = empty + S;                                // [2]
   CT<R>* recv = (CT<R>*)(smem_raw + Sm::recv_off(S, ys));   // [2][TB*KR]
   CT<R>* part = (CT<R>*)(smem_raw + Sm::part_off(S, ys));   // [TB*KR] this CTA's partial sums
-  CT<R>* red = (CT<R>*)(smem_raw + Sm::red_off(S, ys));     // [8][TB*KR] per-warp partial sums
   CT<R>* rvec = (CT<R>*)(smem_raw + Sm::rvec_off(S, ys));   // [TB*KR]
   __shared__ int abort_flag;
   __shared__ int peer_abort;                                // set by the partner CTA at the end
@@ -246,80 +244,40 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
           if (ok) ok = stage(T, Y);
           if (!ok) continue;  // keep the barrier sequence uniform; no more work after a timeout
           const CT<R>* yJ = ysm ? y + (J / 2) * NV : Y;
-          if (fwd) {  // row-major tile: warp rows 8w..8w+7, lane columns 2l, 2l+1
-            CT<R> y0[KR], y1[KR];
+          // row-major tile: warp rows 8w..8w+7, lane columns 2l, 2l+1
+          CT<R> y0[KR], y1[KR];
 #pragma unroll
-            for (int r = 0; r < KR; ++r) ld_cpair(yJ + r * TB + 2 * lane, y0[r], y1[r]);
+          for (int r = 0; r < KR; ++r) ld_cpair(yJ + r * TB + 2 * lane, y0[r], y1[r]);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int e = (warp * 8 + q) * TB + 2 * lane;
-              R r0, r1, i0, i1;
-              ld_pair(T + e, r0, r1);
-              ld_pair(T + TILE_PLANE + e, i0, i1);
+          for (int q = 0; q < 8; ++q) {
+            const int e = (warp * 8 + q) * TB + 2 * lane;
+            R r0, r1, i0, i1;
+            ld_pair(T + e, r0, r1);
+            ld_pair(T + TILE_PLANE + e, i0, i1);
 #pragma unroll
-              for (int r = 0; r < KR; ++r) {
-                CT<R>& t = acc[q][r];
-                t.re = fma(r0, y0[r].re, t.re); t.re = fma(-i0, y0[r].im, t.re);
-                t.re = fma(r1, y1[r].re, t.re); t.re = fma(-i1, y1[r].im, t.re);
-                t.im = fma(r0, y0[r].im, t.im); t.im = fma(i0, y0[r].re, t.im);
-                t.im = fma(r1, y1[r].im, t.im); t.im = fma(i1, y1[r].re, t.im);
-              }
-            }
-          } else {  // column-major tile: warp columns 8w..8w+7, lane rows 2l, 2l+1
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int col = warp * 8 + q;
-              const int e = col * TB + 2 * lane;
-              R r0, r1, i0, i1;
-              ld_pair(T + e, r0, r1);
-              ld_pair(T + TILE_PLANE + e, i0, i1);
-#pragma unroll
-              for (int r = 0; r < KR; ++r) {
-                const CT<R> yc = yJ[r * TB + col];
-                CT<R>& a0 = acc[2 * (q & 3)][r];      // row 2l
-                CT<R>& a1 = acc[2 * (q & 3) + 1][r];  // row 2l+1
-                a0.re = fma(r0, yc.re, a0.re); a0.re = fma(-i0, yc.im, a0.re);
-                a0.im = fma(r0, yc.im, a0.im); a0.im = fma(i0, yc.re, a0.im);
-                a1.re = fma(r1, yc.re, a1.re); a1.re = fma(-i1, yc.im, a1.re);
-                a1.im = fma(r1, yc.im, a1.im); a1.im = fma(i1, yc.re, a1.im);
-              }
+            for (int r = 0; r < KR; ++r) {
+              CT<R>& t = acc[q][r];
+              t.re = fma(r0, y0[r].re, t.re); t.re = fma(-i0, y0[r].im, t.re);
+              t.re = fma(r1, y1[r].re, t.re); t.re = fma(-i1, y1[r].im, t.re);
+              t.im = fma(r0, y0[r].im, t.im); t.im = fma(i0, y0[r].re, t.im);
+              t.im = fma(r1, y1[r].im, t.im); t.im = fma(i1, y1[r].re, t.im);
             }
           }
           release();
         }
         // reduce to the TB x KR partial sums of this CTA in part[]
-        if (fwd) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-#pragma unroll
-            for (int r = 0; r < KR; ++r) {
-              CT<R> t = acc[q][r];
-              for (int o = 16; o > 0; o >>= 1) {
-                t.re += __shfl_down_sync(0xffffffffu, t.re, o);
-                t.im += __shfl_down_sync(0xffffffffu, t.im, o);
-              }
-              if (lane == 0) part[r * TB + warp * 8 + q] = t;
-            }
-          named_sync(1, APPLY_CONSUMERS);
-        } else {
+        for (int q = 0; q < 8; ++q)
 #pragma unroll
           for (int r = 0; r < KR; ++r) {
-            CT<R> p0 = {R(0), R(0)}, p1 = {R(0), R(0)};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              p0.re += acc[2 * q][r].re; p0.im += acc[2 * q][r].im;
-              p1.re += acc[2 * q + 1][r].re; p1.im += acc[2 * q + 1][r].im;
+            CT<R> t = acc[q][r];
+            for (int o = 16; o > 0; o >>= 1) {
+              t.re += __shfl_down_sync(0xffffffffu, t.re, o);
+              t.im += __shfl_down_sync(0xffffffffu, t.im, o);
             }
-            st_cpair(red + warp * NV + r * TB + 2 * lane, p0, p1);
+            if (lane == 0) part[r * TB + warp * 8 + q] = t;
           }
-          named_sync(1, APPLY_CONSUMERS);
-          for (int q = tid; q < NV; q += APPLY_CONSUMERS) {
-            CT<R> t = red[q];
-            for (int w = 1; w < 8; ++w) { t.re += red[w * NV + q].re; t.im += red[w * NV + q].im; }
-            part[q] = t;
-          }
-          named_sync(1, APPLY_CONSUMERS);
-        }
+        named_sync(1, APPLY_CONSUMERS);
         if (!owner) {
           // send the partial sums to the owner's receive buffer, then signal it
           for (int q = tid; q < NV; q += APPLY_CONSUMERS) {
@@ -351,11 +309,10 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
         if (ok) ok = stage(T, Y);
         if (!ok) {
           named_sync(1, APPLY_CONSUMERS);
-          if (!fwd) named_sync(1, APPLY_CONSUMERS);
           publish();
           continue;
         }
-        if (fwd) {  // Linv, row-major
+        {  // y_I = Linv_I r (forward) or Uinv_I r (backward): row-major inverse of the diagonal block
           CT<R> r0v[KR], r1v[KR];
 #pragma unroll
           for (int r = 0; r < KR; ++r) ld_cpair(rvec + r * TB + 2 * lane, r0v[r], r1v[r]);
@@ -377,37 +334,6 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
             }
           }
           release();
-        } else {  // Uinv, column-major
-          CT<R> p0[KR], p1[KR];
-#pragma unroll
-          for (int r = 0; r < KR; ++r) p0[r] = p1[r] = {R(0), R(0)};
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int col = warp * 8 + q;
-            const int e = col * TB + 2 * lane;
-            R r0, r1, i0, i1;
-            ld_pair(T + e, r0, r1);
-            ld_pair(T + TILE_PLANE + e, i0, i1);
-#pragma unroll
-            for (int r = 0; r < KR; ++r) {
-              const CT<R> rc = rvec[r * TB + col];
-              p0[r].re += r0 * rc.re - i0 * rc.im;
-              p0[r].im += r0 * rc.im + i0 * rc.re;
-              p1[r].re += r1 * rc.re - i1 * rc.im;
-              p1[r].im += r1 * rc.im + i1 * rc.re;
-            }
-          }
-          release();
-#pragma unroll
-          for (int r = 0; r < KR; ++r) {
-            st_cpair(red + warp * NV + r * TB + 2 * lane, p0[r], p1[r]);
-          }
-          named_sync(1, APPLY_CONSUMERS);
-          for (int q = tid; q < NV; q += APPLY_CONSUMERS) {
-            CT<R> t = red[q];
-            for (int w = 1; w < 8; ++w) { t.re += red[w * NV + q].re; t.im += red[w * NV + q].im; }
-            yI[q] = t;
-          }
         }
         if (!ysm) fence_proxy_async_global();  // y_I is read next by bulk copies
         named_sync(1, APPLY_CONSUMERS);

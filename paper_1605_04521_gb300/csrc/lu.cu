@@ -717,13 +717,16 @@ __device__ void invert_block(const CT<R>* D, CT<R>* X) {
   }
 }
 
-// Stores L^{-1} with row-major planes at Li and U^{-1} with column-major planes at Ui.
+// Stores L^{-1} with row-major planes at Li and U^{-1} at Ui, with row-major planes when
+// u_rowmajor (the preconditioner apply) or column-major planes (the B operand of the tensor-core
+// tile solves, K-major along the row index).
 template <typename R>
-__device__ void store_inverses(const CT<R>* X, R* Li, R* Ui) {
+__device__ void store_inverses(const CT<R>* X, R* Li, R* Ui, bool u_rowmajor) {
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
     const int hi = e / TB, lo = e % TB;
     const CT<R> l = X[lo * PS + hi];                // Linv(i = hi, j = lo): row-major storage
-    const CT<R> u = X[TB * PS + hi * PS + lo];      // Uinv(i = lo, j = hi): column-major storage
+    const CT<R> u = u_rowmajor ? X[TB * PS + lo * PS + hi]   // Uinv(i = hi, j = lo)
+                               : X[TB * PS + hi * PS + lo];  // Uinv(i = lo, j = hi)
     Li[e] = l.re;
     Li[TILE_PLANE + e] = l.im;
     Ui[e] = u.re;
@@ -731,10 +734,10 @@ __device__ void store_inverses(const CT<R>* X, R* Li, R* Ui) {
   }
 }
 
-// Inverses of the diagonal blocks of the factors: Linv_I = L_II^{-1} (unit lower) stored with
-// row-major planes and Uinv_I = U_II^{-1} stored with column-major planes, so that the in-block
-// substitution steps of the preconditioner apply become tile matrix-vector products like the
-// off-diagonal ones (block substitution with inverted diagonal blocks).
+// Inverses of the diagonal blocks of the factors: Linv_I = L_II^{-1} (unit lower) and
+// Uinv_I = U_II^{-1}, both stored with row-major planes, so that the in-block substitution steps of
+// the preconditioner apply become tile matrix-vector products like the off-diagonal ones (block
+// substitution with inverted diagonal blocks).
 template <typename R>
 __global__ void __launch_bounds__(INV_THREADS) k_lu_diag_inv(LuArgs a, void* arena, void* inv, const int64_t* inv_off) {
   extern __shared__ unsigned char smem_raw[];
@@ -753,7 +756,36 @@ __global__ void __launch_bounds__(INV_THREADS) k_lu_diag_inv(LuArgs a, void* are
   invert_block<R>(D, X);
   __syncthreads();
   R* Li = (R*)inv + (inv_off[s] + I) * 4 * TILE_PLANE;
-  store_inverses<R>(X, Li, Li + 2 * TILE_PLANE);
+  store_inverses<R>(X, Li, Li + 2 * TILE_PLANE, true);
+}
+
+// After the factorisation: the tiles above the block diagonal (U), stored with column-major planes
+// while the trailing updates read them as K-major operands, are transposed in place to row-major
+// planes, so that every factor tile is row-major for the preconditioner apply (the tensor-core
+// apply reads every tile as a K-major operand along its column index).  One block per upper tile
+// x = J (J - 1) / 2 + I (I < J) of subdomain blockIdx.y.
+template <typename R>
+__global__ void __launch_bounds__(256) k_lu_upper_rowmajor(LuArgs a, void* arena) {
+  extern __shared__ unsigned char smem_raw[];
+  R* buf = (R*)smem_raw;  // [2][TB][TB + 1]
+  const int s = blockIdx.y;
+  const int64_t nts = a.np[s] / TB;
+  const int64_t x = blockIdx.x;
+  int64_t J = (int64_t)((1.0 + sqrt(1.0 + 8.0 * (double)x)) * 0.5);
+  while (J * (J - 1) / 2 > x) --J;
+  while ((J + 1) * J / 2 <= x) ++J;
+  const int64_t I = x - J * (J - 1) / 2;
+  if (J >= nts || I >= J) return;
+  R* T = tile_base<R>(arena, a, s, I, J);
+  for (int e = threadIdx.x; e < 2 * TB * TB; e += blockDim.x) {
+    const int p = e / (TB * TB), q = e % (TB * TB);   // plane, column-major index j * TB + i
+    buf[p * TB * (TB + 1) + (q / TB) * (TB + 1) + (q % TB)] = T[e];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * TB * TB; e += blockDim.x) {
+    const int p = e / (TB * TB), q = e % (TB * TB);   // row-major index i * TB + j
+    T[e] = buf[p * TB * (TB + 1) + (q % TB) * (TB + 1) + (q / TB)];
+  }
 }
 
 // The step's factored diagonal block (from the tournament root): written to tile (k, k) and
@@ -778,7 +810,7 @@ __global__ void __launch_bounds__(INV_THREADS) k_lu_step_inv(LuArgs a, void* are
   invert_block<R>(D, X);
   __syncthreads();
   R* Li = (R*)arena + (scratch_base + 2 * s) * 2 * TILE_PLANE;
-  store_inverses<R>(X, Li, Li + 2 * TILE_PLANE);
+  store_inverses<R>(X, Li, Li + 2 * TILE_PLANE, false);
 }
 
 // number of output tiles of the update regions for the largest subdomain
@@ -898,6 +930,15 @@ static int lu_run(oras_handle* h) {
   }
   k_gidx<<<(unsigned)((total + 255) / 256), 256, 0, d.stream>>>(total, d.perm, d.sub_np_off, d.sub_ns,
                                                               d.sub_ns_off, d.sub_dofs, m.nsub, d.gidx);
+  if (max_nts > 1) {
+    const size_t smem_t2 = (size_t)2 * TB * (TB + 1) * sizeof(R);
+    allow_max_smem((const void*)k_lu_upper_rowmajor<R>);
+    const int64_t upper = (int64_t)max_nts * (max_nts - 1) / 2;
+    int pb = prof_begin(h);
+    k_lu_upper_rowmajor<R><<<dim3((unsigned)upper, m.nsub), 256, smem_t2, d.stream>>>(a, d.arena);
+    prof_end(h, KC_LU_SWAP, pb, 1);
+    count_launches(1);
+  }
   {
     allow_max_smem((const void*)k_lu_diag_inv<R>);
     int pb = prof_begin(h);

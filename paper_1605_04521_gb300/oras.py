@@ -35,6 +35,8 @@ ORAS_OVERLAP_VERTEX = 0
 ORAS_OVERLAP_FACE = 1
 ORAS_LU_AUTO = 0
 ORAS_LU_CUDA_CORES = 1
+ORAS_APPLY_AUTO = 0
+ORAS_APPLY_CUDA_CORES = 1
 ORAS_TRANSMISSION_IMPEDANCE = 0
 ORAS_TRANSMISSION_DIRICHLET = 1
 
@@ -53,7 +55,8 @@ class oras_options(C.Structure):
     _fields_ = [("restart", C.c_int32), ("max_iter", C.c_int32), ("factor_bits", C.c_int32),
                 ("weights", C.c_int32), ("overlap_kind", C.c_int32), ("lu_engine", C.c_int32),
                 ("lu_panel", C.c_int32), ("lu_group", C.c_int32), ("transmission", C.c_int32),
-                ("graphs", C.c_int32), ("wait_ms", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("graphs", C.c_int32), ("wait_ms", C.c_int32), ("apply_engine", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class oras_info(C.Structure):
@@ -194,7 +197,7 @@ def _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part, beta_face=None)
 
 
 def _options(restart=0, max_iter=0, factor_bits=0, weights=0, overlap_kind=0, lu_engine=0, lu_panel=0, lu_group=0,
-             transmission=0, graphs=0, wait_ms=0):
+             transmission=0, graphs=0, wait_ms=0, apply_engine=0):
     o = oras_options()
     o.restart, o.max_iter, o.factor_bits, o.weights, o.overlap_kind = restart, max_iter, factor_bits, weights, overlap_kind
     o.lu_engine = lu_engine
@@ -203,6 +206,7 @@ def _options(restart=0, max_iter=0, factor_bits=0, weights=0, overlap_kind=0, lu
     o.transmission = transmission
     o.graphs = graphs
     o.wait_ms = wait_ms
+    o.apply_engine = apply_engine
     return o
 
 
