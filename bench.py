@@ -52,12 +52,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="head16",
-                    choices=["head16", "cube8", "head8", "krylov24", "batch32", "head32r3"],
+                    choices=["head16", "cube8", "head8", "krylov24", "batch32", "batch12", "head32r3"],
                     help="head16: the benchmark workload; cube8: 8^3 r=1 plane wave (FP64 factors); "
                          "head8: 8^3 r=2 8 subdomains (1.9 GB arena, for kernel profiles); krylov24: "
                          "24^3 r=2 512 subdomains without overlap (464 MB matrix, small arena, for Krylov "
                          "kernel profiles); batch32: 24^3 r=2 256 subdomains, 32 dipoles solved together; "
-                         "head32r3: 32^3 r=3 4096 subdomains without overlap (3.7 M DOFs)")
+                         "batch12: 12^3 r=2 32 subdomains, 32 dipoles (3 GB arena, for profiles of the "
+                         "multi-right-hand-side apply); head32r3: 32^3 r=3 4096 subdomains without overlap (3.7 M DOFs)")
+    ap.add_argument("--apply-engine", default="auto", choices=["auto", "cuda"],
+                    help="auto: tensor-core apply for 8 or more right-hand sides; cuda: CUDA-core apply only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--serve-count", type=int, default=50,
@@ -90,6 +93,10 @@ def workload(name):
         return w
     if name == "batch32":
         return synth.config(2)
+    if name == "batch12":
+        w = synth.small(n=12, r=2, nsub=32, overlap=1, nrhs=32, restart=100)
+        w.name = "head12_r2_s32_d1_32dipoles_profile"
+        return w
     if name == "head32r3":
         return synth.config(4)
     return synth.config(0)
@@ -218,9 +225,19 @@ def rhs_groups(k, per_pass):
     return [min(per_pass, k - r0) for r0 in range(0, k, per_pass)]
 
 
-def apply_group_sizes(k, factor_bits):
-    """Right-hand sides of each apply pass: groups of up to 4 (FP32 factors) or 2 (FP64), the
-    last one rounded up to a power of two (its unused lanes carry zeros)."""
+def apply_group_sizes(k, factor_bits, tensor_cores=False):
+    """Live right-hand sides of each apply pass: with the tensor-core apply (FP32 factors, 8 or
+    more columns) passes of up to 32 (a pass of 8, 16 or 32 lanes, the unused ones zero);
+    otherwise CUDA-core groups of up to 4 (FP32 factors) or 2 (FP64), the last one rounded up to a
+    power of two (its unused lanes carry zeros)."""
+    if tensor_cores and factor_bits == 32 and k >= 8:
+        out, r0 = [], 0
+        while r0 < k:
+            rem = k - r0
+            kt = 32 if rem > 16 else (16 if rem > 8 else 8)
+            out.append(min(kt, rem))
+            r0 += min(kt, rem)
+        return out
     maxkr = 4 if factor_bits == 32 else 2
     out, r0 = [], 0
     while r0 < k:
@@ -502,7 +519,11 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     t_mesh0 = time.perf_counter()
-    h = O.oras_create(xyz, tets, w.r, w.nsub, w.overlap, factor_bits=w.factor_bits, restart=w.restart)
+    eng = O.ORAS_APPLY_CUDA_CORES if args.apply_engine == "cuda" else O.ORAS_APPLY_AUTO
+    if args.apply_engine == "cuda":
+        w.name += "_cuda_core_apply"
+    h = O.oras_create(xyz, tets, w.r, w.nsub, w.overlap, factor_bits=w.factor_bits, restart=w.restart,
+                      apply_engine=eng)
     t_mesh = time.perf_counter() - t_mesh0
     O.oras_set_stream(h, stream.cuda_stream)
     eps_d = torch.from_numpy(eps).to(dev)
@@ -512,7 +533,7 @@ def run_ours(args, world, rank, local):
         panel, tune_ms = args.lu_panel, {}
         O.oras_destroy(h)
         h = O.oras_create(xyz, tets, w.r, w.nsub, w.overlap, factor_bits=w.factor_bits, restart=w.restart,
-                          lu_panel=panel)
+                          lu_panel=panel, apply_engine=eng)
         O.oras_set_stream(h, stream.cuda_stream)
         O.oras_factor(h, eps_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
     else:
@@ -569,7 +590,8 @@ def run_ours(args, world, rank, local):
     x_last = x_d.cpu().numpy()
     iters = max(i["iterations"] for i in infos[-1])
     fb = 16 if w.factor_bits == 64 else 8
-    groups = apply_group_sizes(krhs, w.factor_bits)
+    tc_apply = args.apply_engine == "auto" and w.factor_bits == 32 and krhs >= 8
+    groups = apply_group_sizes(krhs, w.factor_bits, tc_apply)
     upd_flops, _ = work_model(O, h, w.nsub, 1, fb)
     # bytes of one apply launch, averaged over the launches of a step (groups of right-hand sides)
     apply_bytes = sum(work_model(O, h, w.nsub, g, fb)[1] for g in groups) / len(groups)
@@ -590,6 +612,9 @@ def run_ours(args, world, rank, local):
         else:
             ru["traffic_note"] = ("null: profiles/roofline_traffic.json holds no ncu capture of this workload and "
                                   "panel width on the current update kernel (" + UPDATE_VERSION + ")")
+    if "apply" in roofs and tc_apply:
+        roofs["apply"]["kernel"] = ("k_apply_tc (ORAS preconditioner, tcgen05 kind::tf32 products, up to 32 "
+                                    "right-hand sides per arena pass)")
     roof = roofs[dom]
     arena = O.oras_arena_bytes(h)
     O.oras_destroy(h)
@@ -604,7 +629,7 @@ def run_ours(args, world, rank, local):
     e0 = time.perf_counter()
     for _ in range(e2e_steps):
         he = O.oras_setup(xyz, tets, eps, mu, w.k0, w.r, w.nsub, w.overlap, factor_bits=w.factor_bits,
-                          restart=w.restart, lu_panel=panel, lu_group=group)
+                          restart=w.restart, lu_panel=panel, lu_group=group, apply_engine=eng)
         xe, info_e, rc = O.oras_solve(he, b_host, w.tol, k=krhs)
         x_host[:] = np.asarray(xe).reshape(n, krhs)
         O.oras_destroy(he)

@@ -120,6 +120,49 @@ struct AtcArgs {
   int64_t dinv_tiles;       // tiles of the inverted-diagonal array (tensor map extent)
 };
 
+// Item kinds of a CTA's stream of work (atc_stream).
+enum { ATC_ITEM_TILE = 0, ATC_ITEM_DIAG = 1, ATC_ITEM_COMMIT = 2 };
+
+// The order in which CTA c loads and multiplies: f(kind, I, J, slot) for
+//   ATC_ITEM_TILE   (I, J): off-diagonal tile of strip I times y_J, into the accumulator of strip `slot`;
+//   ATC_ITEM_DIAG   (I)   : the inverted diagonal block of owned strip I times r_I;
+//   ATC_ITEM_COMMIT (slot): strip `slot` has all its products (its accumulator may be read out).
+// Strip slots number the strips in processing order (forward strips 0..nts-1, then backward from
+// the last).  CTA c takes the tiles of its own block columns J % 2 == c.  Look-ahead: the strip
+// that follows an owned strip I is owned by the partner, and all its tiles here but the one in
+// block column I need only y values finalised earlier -- they are issued before the diagonal
+// product of strip I, so the tensor cores work through them while the epilogue waits for the
+// partner's partial sums of strip I; the one tile that needs y_I comes right after it.
+template <typename F>
+__device__ __forceinline__ void atc_stream(int c, int64_t nts, F&& f) {
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = pass == 0;
+    for (int64_t it = 0; it < nts; ++it) {
+      const int64_t I = fwd ? it : nts - 1 - it;
+      const int64_t slot = (int64_t)pass * nts + it;
+      if ((I & 1) != c) {
+        if (it == 0) f(ATC_ITEM_COMMIT, I, I, slot);  // no owned strip before it: nothing to multiply
+        continue;
+      }
+      // the owned strip: block columns J % 2 == c below (forward) or above (backward) I
+      if (fwd) for (int64_t J = c; J < I; J += 2) f(ATC_ITEM_TILE, I, J, slot);
+      else for (int64_t J = I + 2; J < nts; J += 2) f(ATC_ITEM_TILE, I, J, slot);
+      f(ATC_ITEM_COMMIT, I, I, slot);
+      const bool next = it + 1 < nts;
+      const int64_t I1 = fwd ? I + 1 : I - 1;
+      if (next) {  // the partner's next strip: every tile but the one in block column I
+        if (fwd) for (int64_t J = c; J < I; J += 2) f(ATC_ITEM_TILE, I1, J, slot + 1);
+        else for (int64_t J = I + 2; J < nts; J += 2) f(ATC_ITEM_TILE, I1, J, slot + 1);
+      }
+      f(ATC_ITEM_DIAG, I, I, slot);
+      if (next) {
+        f(ATC_ITEM_TILE, I1, I, slot + 1);
+        f(ATC_ITEM_COMMIT, I1, I1, slot + 1);
+      }
+    }
+  }
+}
+
 // One pass of KT right-hand sides (columns off .. off+nr-1 of v and z) for subdomain s.
 template <int KT, typename ZT>
 __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, const CUtensorMap* dmap, int s,
@@ -216,15 +259,12 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
         if (++slot == S) { slot = 0; phase ^= 1u; }
         return true;
       };
-      for (int64_t I = 0; I < nts && ok; ++I) {
-        for (int64_t J = c; J < I && ok; J += 2) ok = issue(false, I, J, 0, J / 2 + 1);
-        if (ok && (I & 1) == c) ok = issue(true, I, I, 0, 0);
-      }
-      for (int64_t I = nts - 1; I >= 0 && ok; --I) {
-        for (int64_t J = I + 1 + ((I + 1 + c) & 1); J < nts && ok; J += 2)
-          ok = issue(false, I, J, 0, 2 * nown_s - J / 2);
-        if (ok && (I & 1) == c) ok = issue(true, I, I, 1, 0);
-      }
+      atc_stream(c, nts, [&](int kind, int64_t I, int64_t J, int64_t slot_s) {
+        if (!ok || kind == ATC_ITEM_COMMIT) return;
+        const bool fwd = slot_s < nts;
+        if (kind == ATC_ITEM_DIAG) ok = issue(true, I, I, fwd ? 0 : 1, 0);
+        else ok = issue(false, I, J, 0, fwd ? J / 2 + 1 : 2 * nown_s - J / 2);
+      });
       if (!ok) {
         atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
         abort_flag = 1;
@@ -239,7 +279,7 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
       constexpr uint32_t idesc = atc_idesc<N>();
       int slot = 0;
       uint32_t phase = 0;
-      int64_t strips = 0, owned = 0;
+      int64_t owned = 0;
       bool ok = true;
       auto tile_mma = [&](uint32_t dcol, uint32_t bsaddr, bool first) {
         const uint32_t asaddr = smem_u32(ring + (size_t)slot * Sh::STAGE);
@@ -252,28 +292,16 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
             atc_mma(tbase + dcol, ad, bd, idesc, (first && ch == 0 && k8 == 0) ? 0u : 1u);
           }
       };
-      for (int pass = 0; pass < 2; ++pass) {
-        const bool fwd = pass == 0;
-        for (int64_t it = 0; it < nts; ++it) {
-          const int64_t I = fwd ? it : nts - 1 - it;
-          const int b = (int)(strips & 1);
-          const int64_t use = strips >> 1;
-          if (ok && use >= 1 && !mbar_wait(&acce[b], (uint32_t)((use - 1) & 1), false, a.wait_ns)) ok = false;
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int64_t J0 = fwd ? c : I + 1 + ((I + 1 + c) & 1), J1 = fwd ? I : nts;
-          bool first = true;
-          for (int64_t J = J0; J < J1 && ok; J += 2) {
-            if (!mbar_wait(&full[slot], phase, false, a.wait_ns)) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            tile_mma((uint32_t)(b * N), smem_u32(ring + (size_t)slot * Sh::STAGE + ATC_TILE), first);
-            first = false;
-            atc_commit(&empty[slot]);
-            if (++slot == S) { slot = 0; phase ^= 1u; }
-          }
+      int started = 0;  // bit b: the open strip of accumulator b has had its first product
+      atc_stream(c, nts, [&](int kind, int64_t I, int64_t J, int64_t slot_s) {
+        const int b = (int)(slot_s & 1);
+        if (kind == ATC_ITEM_COMMIT) {
           atc_commit(&accf[b]);  // arrives when this strip's products are in tensor memory
-          ++strips;
-          if ((I & 1) != c) continue;
-          // owner: the inverted diagonal block times r (written into rB by the epilogue)
+          started &= ~(1 << b);
+          return;
+        }
+        if (kind == ATC_ITEM_DIAG) {
+          // the inverted diagonal block times r (written into rB by the epilogue)
           if (ok && !mbar_wait(rbf, (uint32_t)(owned & 1), false, a.wait_ns)) ok = false;
           if (ok && !mbar_wait(&full[slot], phase, false, a.wait_ns)) ok = false;
           if (ok) {
@@ -284,8 +312,22 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
           }
           atc_commit(dgd);
           ++owned;
+          return;
         }
-      }
+        if (!ok) return;
+        const bool first = !(started & (1 << b));
+        const int64_t use = slot_s >> 1;
+        if (first && use >= 1 && !mbar_wait(&acce[b], (uint32_t)((use - 1) & 1), false, a.wait_ns)) {
+          ok = false;
+          return;
+        }
+        if (!mbar_wait(&full[slot], phase, false, a.wait_ns)) { ok = false; return; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tile_mma((uint32_t)(b * N), smem_u32(ring + (size_t)slot * Sh::STAGE + ATC_TILE), first);
+        started |= 1 << b;
+        atc_commit(&empty[slot]);
+        if (++slot == S) { slot = 0; phase ^= 1u; }
+      });
       if (!ok) {
         atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
         abort_flag = 1;

@@ -142,23 +142,42 @@ __global__ void __launch_bounds__(256) k_spmv_df(int64_t n, const int64_t* __res
   }
 }
 
-// partials[b][r] = sum over this block's slice of conj(a) * b  (complex), or |a|^2 if b == nullptr
-__device__ void block_reduce_store(cplx* vals, int k, cplx* partials) {
-  // vals: per-thread accumulators for r in 0..k-1 are reduced across the block
-  __shared__ cplx sh[RED_THREADS / 32][MAX_RHS];
+// Reductions over [N][k] multi-vectors (element e belongs to right-hand side e % k).  The grid's
+// threads are cut to a multiple of k, teff = floor(T / k) k, and thread t < teff visits the
+// elements t, t + teff, t + 2 teff, ...: all of one right-hand side r = t % k, so each thread
+// keeps a single accumulator.  Block partial sums per right-hand side are formed in a fixed order
+// (warp shuffles over the lanes of the same r when k divides 32, else a sequential sum of the
+// block's per-thread values), then the fixed-order sum over blocks (sum_partials): the results do
+// not depend on scheduling.
+__device__ __forceinline__ int64_t red_teff(int k) {
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  return T / k * k;
+}
+
+// partials[blockIdx.x][r] = sum of the per-thread values v of the block's threads with RHS r
+__device__ void block_reduce_store(cplx v, int k, cplx* partials) {
+  __shared__ cplx sh[RED_THREADS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = 0; r < k; ++r) {
-    cplx v = vals[r];
-    for (int o = 16; o > 0; o >>= 1) {
-      v.re += __shfl_down_sync(0xffffffffu, v.re, o);
-      v.im += __shfl_down_sync(0xffffffffu, v.im, o);
+  const int64_t base = (int64_t)blockIdx.x * blockDim.x;
+  if (32 % k == 0) {  // lane l holds RHS l % k (blockDim and 32 are multiples of k)
+    for (int o = 16; o >= k; o >>= 1) {
+      v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+      v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
     }
-    if (lane == 0) sh[warp][r] = v;
+    if (lane < k) sh[warp * k + lane] = v;
+    __syncthreads();
+    if (threadIdx.x < k) {
+      cplx t = {0.0, 0.0};
+      for (int w = 0; w < RED_THREADS / 32; ++w) t = cadd(t, sh[w * k + threadIdx.x]);
+      partials[(int64_t)blockIdx.x * k + threadIdx.x] = t;
+    }
+    return;
   }
+  sh[threadIdx.x] = v;
   __syncthreads();
   for (int r = threadIdx.x; r < k; r += blockDim.x) {
     cplx t = {0.0, 0.0};
-    for (int w = 0; w < RED_THREADS / 32; ++w) t = cadd(t, sh[w][r]);
+    for (int q = (int)(((int64_t)r - base % k + k) % k); q < RED_THREADS; q += k) t = cadd(t, sh[q]);
     partials[(int64_t)blockIdx.x * k + r] = t;
   }
 }
@@ -173,16 +192,14 @@ __device__ __forceinline__ cplx sum_partials(const cplx* partials, int k, int r)
 // first dot of step j: partial <V_0, w>
 __global__ void __launch_bounds__(RED_THREADS) k_dot(int64_t nk, int k, const cplx* __restrict__ a,
                                                      const cplx* __restrict__ b, cplx* __restrict__ partials) {
-  cplx acc[MAX_RHS];
-  for (int r = 0; r < k; ++r) acc[r] = {0.0, 0.0};
-  // nk = N * k; element e belongs to RHS e % k.  Stride keeps e % k fixed per thread when
-  // the total thread count is a multiple of k (k divides 64 * ... is not assumed: loop over r).
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
-    int r = (int)(e % k);
-    cplx x = a[e], y = b[e];
-    acc[r].re += x.re * y.re + x.im * y.im;
-    acc[r].im += x.re * y.im - x.im * y.re;
-  }
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, teff = red_teff(k);
+  cplx acc = {0.0, 0.0};
+  if (t < teff)
+    for (int64_t e = t; e < nk; e += teff) {
+      const cplx x = a[e], y = b[e];
+      acc.re += x.re * y.re + x.im * y.im;
+      acc.im += x.re * y.im - x.im * y.re;
+    }
   block_reduce_store(acc, k, partials);
 }
 
@@ -197,20 +214,23 @@ __global__ void __launch_bounds__(RED_THREADS) k_mgs_step(int64_t nk, int k, int
     if (blockIdx.x == 0) H[((int64_t)r * (m + 1) + i) * m + j] = hs[r];
   }
   __syncthreads();
-  cplx acc[MAX_RHS];
-  for (int r = 0; r < k; ++r) acc[r] = {0.0, 0.0};
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
-    int r = (int)(e % k);
-    cplx h = hs[r], v = Vi[e], x = w[e];
-    x.re -= h.re * v.re - h.im * v.im;
-    x.im -= h.re * v.im + h.im * v.re;
-    w[e] = x;
-    if (Vn) {
-      cplx u = Vn[e];
-      acc[r].re += u.re * x.re + u.im * x.im;
-      acc[r].im += u.re * x.im - u.im * x.re;
-    } else {
-      acc[r].re += x.re * x.re + x.im * x.im;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, teff = red_teff(k);
+  cplx acc = {0.0, 0.0};
+  if (t < teff) {
+    const cplx h = hs[t % k];
+    for (int64_t e = t; e < nk; e += teff) {
+      const cplx v = Vi[e];
+      cplx x = w[e];
+      x.re -= h.re * v.re - h.im * v.im;
+      x.im -= h.re * v.im + h.im * v.re;
+      w[e] = x;
+      if (Vn) {
+        const cplx u = Vn[e];
+        acc.re += u.re * x.re + u.im * x.im;
+        acc.im += u.re * x.im - u.im * x.re;
+      } else {
+        acc.re += x.re * x.re + x.im * x.im;
+      }
     }
   }
   block_reduce_store(acc, k, pout);
@@ -304,14 +324,14 @@ __global__ void k_xupdate(int64_t nk, int k, int m, int kk, const ZT* __restrict
 // r = b - A x (SpMV output in r already holds A x): r = b - r; partial |r|^2
 __global__ void __launch_bounds__(RED_THREADS) k_residual(int64_t nk, int k, const cplx* __restrict__ b,
                                                           cplx* __restrict__ r, cplx* __restrict__ partials) {
-  cplx acc[MAX_RHS];
-  for (int q = 0; q < k; ++q) acc[q] = {0.0, 0.0};
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
-    int q = (int)(e % k);
-    cplx v = csub(b[e], r[e]);
-    r[e] = v;
-    acc[q].re += v.re * v.re + v.im * v.im;
-  }
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, teff = red_teff(k);
+  cplx acc = {0.0, 0.0};
+  if (t < teff)
+    for (int64_t e = t; e < nk; e += teff) {
+      const cplx v = csub(b[e], r[e]);
+      r[e] = v;
+      acc.re += v.re * v.re + v.im * v.im;
+    }
   block_reduce_store(acc, k, partials);
 }
 

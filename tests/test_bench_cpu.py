@@ -60,6 +60,10 @@ def test_spmv_and_apply_byte_models():
     assert bench.apply_group_sizes(7, 32) == [4, 3]         # the last pass: 3 live columns of 4
     assert bench.apply_group_sizes(3, 64) == [2, 1]
     assert bench.rhs_groups(20, 8) == [8, 8, 4]
+    assert bench.apply_group_sizes(32, 32, True) == [32]
+    assert bench.apply_group_sizes(40, 32, True) == [32, 8]
+    assert bench.apply_group_sizes(12, 32, True) == [12]
+    assert bench.apply_group_sizes(4, 32, True) == [4]          # below 8 columns: CUDA-core groups
 
 
 def test_stored_traffic_needs_the_current_kernel_version(tmp_path, monkeypatch):
