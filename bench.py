@@ -52,13 +52,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="head16",
-                    choices=["head16", "cube8", "head8", "krylov24", "batch32", "batch12", "head32r3"],
+                    choices=["head16", "cube8", "head8", "krylov24", "batch32", "batch12", "batch8", "head32r3"],
                     help="head16: the benchmark workload; cube8: 8^3 r=1 plane wave (FP64 factors); "
                          "head8: 8^3 r=2 8 subdomains (1.9 GB arena, for kernel profiles); krylov24: "
                          "24^3 r=2 512 subdomains without overlap (464 MB matrix, small arena, for Krylov "
                          "kernel profiles); batch32: 24^3 r=2 256 subdomains, 32 dipoles solved together; "
-                         "batch12: 12^3 r=2 32 subdomains, 32 dipoles (3 GB arena, for profiles of the "
-                         "multi-right-hand-side apply); head32r3: 32^3 r=3 4096 subdomains without overlap (3.7 M DOFs)")
+                         "batch12: 12^3 r=2 32 subdomains, 32 dipoles; batch8: 8^3 r=2 8 subdomains, 32 "
+                         "dipoles (2 GB arena, for profiles of the multi-right-hand-side apply); head32r3: 32^3 r=3 4096 subdomains without overlap (3.7 M DOFs)")
     ap.add_argument("--apply-engine", default="auto", choices=["auto", "cuda"],
                     help="auto: tensor-core apply for 8 or more right-hand sides; cuda: CUDA-core apply only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -93,6 +93,10 @@ def workload(name):
         return w
     if name == "batch32":
         return synth.config(2)
+    if name == "batch8":
+        w = synth.small(n=8, r=2, nsub=8, overlap=1, nrhs=32, restart=30)
+        w.name = "head8_r2_s8_d1_32dipoles_profile"
+        return w
     if name == "batch12":
         w = synth.small(n=12, r=2, nsub=32, overlap=1, nrhs=32, restart=100)
         w.name = "head12_r2_s32_d1_32dipoles_profile"
@@ -282,7 +286,8 @@ def roofline(timings, upd_flops_per_factor, apply_bytes, factors, hbm, bf16_sus,
     """Roofline objects of the kernel classes timed with CUDA events inside the step: the
     dominant class (largest device time) first, then the others that have a work model.  The
     TF32 peak is the measured sustained bf16 rate (the update runs inside a seconds-long step)
-    times the nominal tf32/bf16 ratio.  spmv = (bytes of all SpMV launches of the timed steps)."""
+    times the nominal tf32/bf16 ratio.  spmv = bytes of the Arnoldi SpMV launches (class "spmv":
+    FP32-valued vectors) of the timed steps; the FP64 true-residual SpMV is its own class."""
     cls = {c: v for c, v in timings.items() if v[1] > 0}
     dom = max(cls, key=lambda c: cls[c][0])
     out = {}
@@ -310,7 +315,8 @@ def roofline(timings, upd_flops_per_factor, apply_bytes, factors, hbm, bf16_sus,
         ms, _ = cls["spmv"]
         achieved = spmv / (ms / 1e3) / 1e9
         out["spmv"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                       "traffic": None, "kernel": "k_spmv_df (Arnoldi) + k_spmv (true residual)"}
+                       "traffic": None, "kernel": "k_spmv_df (Arnoldi SpMV of the FP32-valued preconditioned "
+                                                 "vectors on the FP32 pipes)"}
     if dom not in out:
         out[dom] = {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
                     "traffic": None, "kernel": dom}
@@ -600,8 +606,8 @@ def run_ours(args, world, rank, local):
     for info in infos:
         it = max(i["iterations"] for i in info)
         cyc = max(i["restarts"] for i in info)
-        spmv_total += it * sum(spmv_bytes(n, nnz, g, w.factor_bits == 32) for g in rhs_groups(krhs, 8))
-        spmv_total += cyc * sum(spmv_bytes(n, nnz, g, False) for g in rhs_groups(krhs, 8))
+        if w.factor_bits == 32:   # the Arnoldi SpMV (class "spmv"); true residuals are class "spmv64"
+            spmv_total += it * sum(spmv_bytes(n, nnz, g, True) for g in rhs_groups(krhs, 8))
     dom, roofs = roofline(timings, upd_flops, apply_bytes, args.steps, hbm, bf16_sus, w.factor_bits, spmv_total)
     if "lu_update" in roofs and w.factor_bits == 32:
         ru = roofs["lu_update"]
@@ -610,8 +616,10 @@ def run_ours(args, world, rank, local):
             ru["traffic_note"] = ("DRAM read+write bytes per launch, averaged over every trailing-update launch of "
                                   "a factorisation, from the ncu capture recorded in profiles/roofline_traffic.json")
         else:
-            ru["traffic_note"] = ("null: profiles/roofline_traffic.json holds no ncu capture of this workload and "
-                                  "panel width on the current update kernel (" + UPDATE_VERSION + ")")
+            ru["traffic_note"] = ("null: the update's DRAM traffic is captured on the 8^3 profile workload at panel width "
+                                  "24 (profiles/k_lu_update_tc_head8_r2.md: 165 MB per launch, 8.1e-3 B/flop); it does "
+                                  "not grow in proportion to the flops between workloads (the left-looking column "
+                                  "updates re-read the panel), so it is not scaled to this one")
     if "apply" in roofs and tc_apply:
         roofs["apply"]["kernel"] = ("k_apply_tc (ORAS preconditioner, tcgen05 kind::tf32 products, up to 32 "
                                     "right-hand sides per arena pass)")

@@ -417,8 +417,10 @@ void oras_server_destroy(oras_server* srv);
  * CUDA event pairs on the handle's stream while timing is on: t[2c] = milliseconds and
  * t[2c+1] = kernel launches of class c, for c = 0 element and face matrices, 1 global CSR
  * values, 2 local matrices (incl. arena clear), 3 LU tournament pivoting, 4 LU row
- * interchanges, 5 LU triangular tile solves, 6 LU trailing updates, 7 preconditioner apply,
- * 8 SpMV, 9 orthogonalisation and Givens, 10 other.  n: entries of t (22 covers all). */
+ * interchanges and the final transposition of the U tiles, 5 LU triangular tile solves, 6 LU
+ * trailing updates, 7 preconditioner apply, 8 SpMV of FP32-valued vectors (Arnoldi with FP32
+ * factors), 9 orthogonalisation and Givens, 10 other, 11 SpMV of FP64 vectors (true residual;
+ * Arnoldi with FP64 factors).  n: entries of t (24 covers all). */
 int oras_timings(const oras_handle* h, double* t, int32_t n);
 /* Zeroes the accumulators of oras_timings. */
 int oras_reset_timings(oras_handle* h);

@@ -834,7 +834,7 @@ static int fgmres(oras_handle* h, int k, double tol, oras_info* info) {
       // true residual r = b - A x
       int pb = prof_begin(h);
       launch_spmv_f64(h, d.xk, d.tmp, k);
-      prof_end(h, KC_SPMV, pb, (k + 7) / 8);
+      prof_end(h, KC_SPMV64, pb, (k + 7) / 8);
       launch_residual(h, k, d.bk, d.tmp, pA);
       launch_norms(h, k, pA, beta_d);
       CK(cudaMemcpyAsync(hp, beta_d, k * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
@@ -865,7 +865,7 @@ static int fgmres(oras_handle* h, int k, double tol, oras_info* info) {
         prof_end(h, KC_APPLY, pb, apply_passes(h, k));
         pb = prof_begin(h);
         spmv_z(h, k, j, d.w);
-        prof_end(h, KC_SPMV, pb, (k + 7) / 8);
+        prof_end(h, d.factor_bits == 64 ? KC_SPMV64 : KC_SPMV, pb, (k + 7) / 8);
         pb = prof_begin(h);
         launch_dot(h, d.V, d.w, pA, k);
         cplx* pin = pA;

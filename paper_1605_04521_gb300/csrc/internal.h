@@ -169,7 +169,7 @@ struct Device {
 // ------------------------------------------------------------------ instrumentation
 // Kernel classes timed with CUDA event pairs on the handle's stream when timing is on.
 enum KClass { KC_ELEMENT = 0, KC_GLOBAL_ROWS, KC_LOCAL_ROWS, KC_LU_TOURNAMENT, KC_LU_SWAP, KC_LU_TRSM,
-              KC_LU_UPDATE, KC_APPLY, KC_SPMV, KC_ORTH, KC_OTHER, KC_COUNT };
+              KC_LU_UPDATE, KC_APPLY, KC_SPMV, KC_ORTH, KC_OTHER, KC_SPMV64, KC_COUNT };
 int prof_begin(const oras_handle* h);                 // -1 when timing is off
 void prof_end(const oras_handle* h, int cls, int begin, int launches);
 void count_launches(int n);                           // process-wide launch counter

@@ -96,45 +96,62 @@ __global__ void k_split_vals(int64_t nnz, const cplx* __restrict__ vals, float4*
   out[p] = make_float4(rh, ih, (float)(v.re - (double)rh), (float)(v.im - (double)ih));
 }
 
-// y = A x with x complex FP32 ([N][k]), y FP64 ([N][k]).  Sixteen lanes per row (two rows per
-// warp); KC right-hand sides per pass (kc <= KC of them live), so the single-vector product keeps
-// few registers and many rows in flight.
+// y = A x with x complex FP32 ([N][k]), y FP64 ([N][k]).  SPMV_LPR lanes per row (32 / SPMV_LPR
+// rows per warp); KC right-hand sides per pass (kc <= KC of them live).  The kernel is bound by the
+// latency of its dependent loads (column index, then the gathered x), so each lane issues the
+// (value, column) loads of SPMV_UNR of its entries at once, then their x gathers, then the
+// arithmetic: SPMV_UNR entries in flight per lane.
+constexpr int SPMV_LPR = 8;
+constexpr int SPMV_UNR = 4;
+
 template <int KC>
 __global__ void __launch_bounds__(256) k_spmv_df(int64_t n, const int64_t* __restrict__ rowptr,
                                                  const int32_t* __restrict__ cols, const float4* __restrict__ vals,
                                                  const CT<float>* __restrict__ x, cplx* __restrict__ y, int k,
                                                  int r0, int kc) {
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
-  const int sl = threadIdx.x & 15;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SPMV_LPR;
+  const int sl = threadIdx.x % SPMV_LPR;
   const bool live = row < n;
   float rh[KC], rl[KC], ih[KC], il[KC];
 #pragma unroll
   for (int q = 0; q < KC; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.0f;
   if (live) {
     const int64_t p1 = rowptr[row + 1];
-#pragma unroll 2
-    for (int64_t p = rowptr[row] + sl; p < p1; p += 16) {
-      const float4 a = vals[p];
-      const int64_t c = cols[p];
-      const CT<float>* xc = x + c * k + r0;
+    for (int64_t p = rowptr[row] + sl; p < p1; p += SPMV_LPR * SPMV_UNR) {
+      float4 a[SPMV_UNR];
+      int64_t c[SPMV_UNR];
 #pragma unroll
-      for (int q = 0; q < KC; ++q)
-        if (q < kc) {
-          const CT<float> xv = xc[q];
-          df_mac(rh[q], rl[q], a.x, a.z, xv.re);    // + a_re x_re
-          df_mac(rh[q], rl[q], -a.y, -a.w, xv.im);  // - a_im x_im
-          df_mac(ih[q], il[q], a.x, a.z, xv.im);    // + a_re x_im
-          df_mac(ih[q], il[q], a.y, a.w, xv.re);    // + a_im x_re
-        }
+      for (int u = 0; u < SPMV_UNR; ++u) {
+        const int64_t pu = p + (int64_t)u * SPMV_LPR;
+        const bool in = pu < p1;
+        a[u] = in ? vals[pu] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        c[u] = in ? (int64_t)cols[pu] : -1;
+      }
+      CT<float> xv[SPMV_UNR][KC];
+#pragma unroll
+      for (int u = 0; u < SPMV_UNR; ++u)
+#pragma unroll
+        for (int q = 0; q < KC; ++q)
+          xv[u][q] = (c[u] >= 0 && q < kc) ? x[c[u] * k + r0 + q] : CT<float>{0.0f, 0.0f};
+#pragma unroll
+      for (int u = 0; u < SPMV_UNR; ++u)
+#pragma unroll
+        for (int q = 0; q < KC; ++q)
+          if (q < kc) {
+            df_mac(rh[q], rl[q], a[u].x, a[u].z, xv[u][q].re);    // + a_re x_re
+            df_mac(rh[q], rl[q], -a[u].y, -a[u].w, xv[u][q].im);  // - a_im x_im
+            df_mac(ih[q], il[q], a[u].x, a[u].z, xv[u][q].im);    // + a_re x_im
+            df_mac(ih[q], il[q], a[u].y, a[u].w, xv[u][q].re);    // + a_im x_re
+          }
     }
   }
 #pragma unroll
   for (int q = 0; q < KC; ++q) {
     if (q >= kc) break;
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-      const float h2 = __shfl_down_sync(0xffffffffu, rh[q], o, 16), l2 = __shfl_down_sync(0xffffffffu, rl[q], o, 16);
-      const float h3 = __shfl_down_sync(0xffffffffu, ih[q], o, 16), l3 = __shfl_down_sync(0xffffffffu, il[q], o, 16);
+    for (int o = SPMV_LPR / 2; o > 0; o >>= 1) {
+      const float h2 = __shfl_down_sync(0xffffffffu, rh[q], o, SPMV_LPR), l2 = __shfl_down_sync(0xffffffffu, rl[q], o, SPMV_LPR);
+      const float h3 = __shfl_down_sync(0xffffffffu, ih[q], o, SPMV_LPR), l3 = __shfl_down_sync(0xffffffffu, il[q], o, SPMV_LPR);
       df_add(rh[q], rl[q], h2, l2);
       df_add(ih[q], il[q], h3, l3);
     }
@@ -394,7 +411,7 @@ void launch_spmv_f64(const oras_handle* h, const cplx* x, cplx* y, int k) { spmv
 void launch_spmv_f32(const oras_handle* h, const void* x, cplx* y, int k) {
   const auto& m = h->mesh;
   const auto& d = h->dev;
-  const int64_t blocks = (m.ndof * 16 + 255) / 256;
+  const int64_t blocks = (m.ndof * SPMV_LPR + 255) / 256;
   for (int r0 = 0; r0 < k; r0 += 8) {
     const int kc = k - r0 < 8 ? k - r0 : 8;
     const CT<float>* xx = (const CT<float>*)x;

@@ -258,19 +258,25 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_tournament(LuArgs a, void* ar
 // ------------------------------------------------------------------ FP32 tournament, rows in registers
 // Same tournament as above, with the elimination done on register-resident rows: thread t owns
 // candidate row t (64 complex values in registers).  No row is moved: the chosen pivot row is
-// marked and broadcast through shared memory for the rank-1 update of the rows not yet chosen.
+// marked and its values are broadcast through shared memory.
 // Pivot choice: max |Re| + |Im| over unchosen rows, ties to the lowest candidate position.
 //
-// The 64 columns are eliminated in 8 blocks of 8 by a runtime loop: within a block the column
-// indices are compile-time (registers stay registers), and after each block every row is
-// rotated left by 8 so the next block's columns come to positions 0..7 (after the 8th rotation
-// the rows are back in their original order).  The loop body stays small enough for the
-// instruction cache; positions >= 64 - 8*block hold already eliminated columns and are skipped
-// block by block.
+// Blocked elimination, 8 columns at a time (within a block the column indices are compile-time,
+// so the rows stay in registers; after each block every row is rotated left by 8 so the next
+// block's columns come to positions 0..7, and after the 8th rotation the rows are back in their
+// original order).  Inside a block the pivots are found column by column and only the block's 8
+// columns are updated; each warp's best candidate publishes its in-block values before the
+// block-wide choice, so one barrier per column suffices.  At the end of the block, the columns
+// right of it receive one rank-8 update from the block's 8 pivot rows, whose own values there are
+// first brought up to date by a triangular correction with the block's multipliers (blocked
+// right-looking LU: U12 = L11^{-1} A12, A22 -= L21 U12).  Positions >= 64 - 8*block hold columns
+// eliminated in earlier blocks (multipliers) and are skipped block by block.
+constexpr int LU_WARPS = LU_THREADS / 32;
 struct RegGepp {
-  float2 prow[8][TB];           // pivot rows of the current block (rotated like the rows)
-  float wv[2][8];
-  int wi[2][8];
+  float2 cand[2][LU_WARPS][8];  // each warp's best candidate's in-block values (by column parity)
+  float wv[2][LU_WARPS];
+  int wi[2][LU_WARPS];
+  float2 P[8][TB];              // the block's pivot rows (rotated positions), corrected at block end
   int order[TB];                // pivot rank -> candidate position
 };
 
@@ -285,6 +291,7 @@ __device__ __forceinline__ void gepp_regs(float (&xr)[TB], float (&xi)[TB], bool
 #pragma unroll 1
   for (int cb = 0; cb < TB / 8; ++cb) {
     const int lim = TB - 8 * cb;  // rotated positions >= lim: columns eliminated in earlier blocks
+    int my_c8 = -1;               // in-block column at which this row became a pivot in this block
 #pragma unroll
     for (int c8 = 0; c8 < 8; ++c8) {
       const int c = 8 * cb + c8;
@@ -293,51 +300,104 @@ __device__ __forceinline__ void gepp_regs(float (&xr)[TB], float (&xi)[TB], bool
       if (v != v) v = 0.0f;  // a non-finite entry still lets a row be chosen
       int key = t;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_down_sync(0xffffffffu, v, o);
-        const int ok = __shfl_down_sync(0xffffffffu, key, o);
+      for (int o = 16; o > 0; o >>= 1) {  // butterfly: every lane ends with the warp's best
+        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int ok = __shfl_xor_sync(0xffffffffu, key, o);
         if (ov > v || (ov == v && ok < key)) { v = ov; key = ok; }
+      }
+      if (t == key && v >= 0.0f) {  // the warp's candidate publishes its in-block values
+#pragma unroll
+        for (int j = c8; j < 8; ++j) g.cand[b][warp][j] = make_float2(xr[j], xi[j]);
       }
       if (lane == 0) { g.wv[b][warp] = v; g.wi[b][warp] = key; }
       __syncthreads();
       float bv = g.wv[b][0];
-      int bk = g.wi[b][0];
+      int bk = g.wi[b][0], bw = 0;
 #pragma unroll
-      for (int w = 1; w < LU_THREADS / 32; ++w)
-        if (g.wv[b][w] > bv || (g.wv[b][w] == bv && g.wi[b][w] < bk)) { bv = g.wv[b][w]; bk = g.wi[b][w]; }
+      for (int w = 1; w < LU_WARPS; ++w) {
+        const float ov = g.wv[b][w];
+        const int ok = g.wi[b][w];
+        if (ov > bv || (ov == bv && ok < bk)) { bv = ov; bk = ok; bw = w; }
+      }
       if (t == bk && bv >= 0.0f) {
         chosen = true;
         myrank = c;
         mypiv = bv;
+        my_c8 = c8;
         g.order[c] = t;
-#pragma unroll
-        for (int j = 0; j < TB; ++j) g.prow[c8][j] = make_float2(xr[j], xi[j]);
       }
-      __syncthreads();
-      if (bv > 0.0f && valid && !chosen) {
-        const float2 p = g.prow[c8][c8];
+      if (bv > 0.0f && valid && !chosen) {  // multiplier and update of the block's later columns
+        const float2 p = g.cand[b][bw][c8];
         const float den = p.x * p.x + p.y * p.y;
         const float lr = (xr[c8] * p.x + xi[c8] * p.y) / den, li = (xi[c8] * p.x - xr[c8] * p.y) / den;
         xr[c8] = lr;
         xi[c8] = li;
 #pragma unroll
         for (int j = c8 + 1; j < 8; ++j) {
-          const float2 u = g.prow[c8][j];
+          const float2 u = g.cand[b][bw][j];
           xr[j] -= lr * u.x - li * u.y;
           xi[j] -= lr * u.y + li * u.x;
         }
+      } else if (!(bv > 0.0f) && valid && !chosen) {  // exactly zero column: no elimination
+        xr[c8] = 0.0f;
+        xi[c8] = 0.0f;
+      }
+    }
+    // the block's pivot rows: in-block multipliers and U values, then the stale part right of it
+    if (my_c8 >= 0) {
 #pragma unroll
-        for (int jb = 1; jb < TB / 8; ++jb) {
-          if (8 * jb < lim) {  // the same for the whole block: no divergence
+      for (int jb = 0; jb < TB / 8; ++jb)
+        if (8 * jb < lim) {
 #pragma unroll
-            for (int j = 8 * jb; j < 8 * jb + 8; ++j) {
-              const float2 u = g.prow[c8][j];
-              xr[j] -= lr * u.x - li * u.y;
-              xi[j] -= lr * u.y + li * u.x;
-            }
+          for (int j = 8 * jb; j < 8 * jb + 8; ++j) g.P[my_c8][j] = make_float2(xr[j], xi[j]);
+        }
+    }
+    __syncthreads();
+    // U12 = L11^{-1} A12: pivot row c8 right of the block minus its multipliers times the earlier ones
+    if (warp == 0) {
+      for (int j = 8 + lane; j < lim; j += 32) {
+#pragma unroll
+        for (int c8 = 1; c8 < 8; ++c8) {
+          float2 acc = g.P[c8][j];
+#pragma unroll
+          for (int q = 0; q < c8; ++q) {
+            const float2 l = g.P[c8][q], u = g.P[q][j];
+            acc.x -= l.x * u.x - l.y * u.y;
+            acc.y -= l.x * u.y + l.y * u.x;
           }
+          g.P[c8][j] = acc;
         }
       }
+    }
+    __syncthreads();
+    if (my_c8 >= 0) {  // the block's pivot rows take their corrected values
+#pragma unroll
+      for (int jb = 1; jb < TB / 8; ++jb)
+        if (8 * jb < lim) {
+#pragma unroll
+          for (int j = 8 * jb; j < 8 * jb + 8; ++j) {
+            const float2 u = g.P[my_c8][j];
+            xr[j] = u.x;
+            xi[j] = u.y;
+          }
+        }
+    } else if (valid && !chosen) {  // A22 -= L21 U12: rank-8 update right of the block
+#pragma unroll
+      for (int jb = 1; jb < TB / 8; ++jb)
+        if (8 * jb < lim) {
+#pragma unroll
+          for (int j = 8 * jb; j < 8 * jb + 8; ++j) {
+            float ar = xr[j], ai = xi[j];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float2 u = g.P[q][j];
+              ar -= xr[q] * u.x - xi[q] * u.y;
+              ai -= xr[q] * u.y + xi[q] * u.x;
+            }
+            xr[j] = ar;
+            xi[j] = ai;
+          }
+        }
     }
     // rotate left by 8: the next block's columns move to positions 0..7
     float tr[8], ti[8];

@@ -257,7 +257,7 @@ def oras_set_timing(h, on):
 
 
 KERNEL_CLASSES = ["element", "global_rows", "local_rows", "lu_tournament", "lu_swap", "lu_trsm",
-                  "lu_update", "apply", "spmv", "orth", "other"]
+                  "lu_update", "apply", "spmv", "orth", "other", "spmv64"]
 
 
 def oras_timings(h):
