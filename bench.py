@@ -59,6 +59,8 @@ def parse():
                          "kernel profiles); batch32: 24^3 r=2 256 subdomains, 32 dipoles solved together; "
                          "batch12: 12^3 r=2 32 subdomains, 32 dipoles; batch8: 8^3 r=2 8 subdomains, 32 "
                          "dipoles (2 GB arena, for profiles of the multi-right-hand-side apply); head32r3: 32^3 r=3 4096 subdomains without overlap (3.7 M DOFs)")
+    ap.add_argument("--block", type=int, default=0,
+                    help="1: solve the workload's right-hand sides as one block (block FGMRES)")
     ap.add_argument("--apply-engine", default="auto", choices=["auto", "cuda"],
                     help="auto: tensor-core apply for 8 or more right-hand sides; cuda: CUDA-core apply only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -528,8 +530,10 @@ def run_ours(args, world, rank, local):
     eng = O.ORAS_APPLY_CUDA_CORES if args.apply_engine == "cuda" else O.ORAS_APPLY_AUTO
     if args.apply_engine == "cuda":
         w.name += "_cuda_core_apply"
+    if args.block:
+        w.name += "_block_fgmres"
     h = O.oras_create(xyz, tets, w.r, w.nsub, w.overlap, factor_bits=w.factor_bits, restart=w.restart,
-                      apply_engine=eng)
+                      apply_engine=eng, block=args.block)
     t_mesh = time.perf_counter() - t_mesh0
     O.oras_set_stream(h, stream.cuda_stream)
     eps_d = torch.from_numpy(eps).to(dev)
@@ -539,7 +543,7 @@ def run_ours(args, world, rank, local):
         panel, tune_ms = args.lu_panel, {}
         O.oras_destroy(h)
         h = O.oras_create(xyz, tets, w.r, w.nsub, w.overlap, factor_bits=w.factor_bits, restart=w.restart,
-                          lu_panel=panel, apply_engine=eng)
+                          lu_panel=panel, apply_engine=eng, block=args.block)
         O.oras_set_stream(h, stream.cuda_stream)
         O.oras_factor(h, eps_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
     else:
@@ -637,7 +641,7 @@ def run_ours(args, world, rank, local):
     e0 = time.perf_counter()
     for _ in range(e2e_steps):
         he = O.oras_setup(xyz, tets, eps, mu, w.k0, w.r, w.nsub, w.overlap, factor_bits=w.factor_bits,
-                          restart=w.restart, lu_panel=panel, lu_group=group, apply_engine=eng)
+                          restart=w.restart, lu_panel=panel, lu_group=group, apply_engine=eng, block=args.block)
         xe, info_e, rc = O.oras_solve(he, b_host, w.tol, k=krhs)
         x_host[:] = np.asarray(xe).reshape(n, krhs)
         O.oras_destroy(he)

@@ -126,7 +126,10 @@ typedef struct {
                               /*   [2000]; waits of a CTA for its own copies in flight before  */
                               /*   it exits never use less than 2000                           */
   int32_t apply_engine;       /* ORAS_APPLY_AUTO [default] or ORAS_APPLY_CUDA_CORES            */
-  int32_t reserved[4];
+  int32_t block;              /* 1: oras_solve treats its k > 1 columns as one block (block      */
+                              /*   flexible GMRES, Sec. 6); 0: k independent recurrences that   */
+                              /*   share every kernel launch (pseudo-block, Sec. 5) [0]         */
+  int32_t reserved[3];
 } oras_options;
 
 /* Per right-hand-side outcome of oras_solve. */
@@ -194,7 +197,12 @@ int oras_set_stream(oras_handle* h, void* stream);
 /* Solves A x_j = b_j for the k columns of rhs by FGMRES(m), x0 = 0, right-preconditioned
  * by ORAS, with FP64 Arnoldi (modified Gram-Schmidt), FP64 Givens rotations and an FP64
  * true-residual check at the end of every cycle; the k recurrences run together (pseudo-
- * block, Sec. 5).  rhs, x: N x k column-major in `mem`; info: k host structs or NULL.
+ * block, Sec. 5).  With oras_options.block and k > 1: block FGMRES (Sec. 6 Block GMRES): one
+ * block Krylov space for all k columns, FP64 block modified Gram-Schmidt between blocks, each new
+ * block orthonormalised by CholQR2, the block least-squares problem kept triangular by
+ * Householder reflections; info[j].iterations then counts block steps.  A block that becomes
+ * numerically rank deficient (CholQR2 breakdown) ends the solve with ORAS_NOT_CONVERGED and the
+ * last iterate.  rhs, x: N x k column-major in `mem`; info: k host structs or NULL.
  * Returns ORAS_OK when every column reached ||b - A x|| / ||b|| <= tol,
  * ORAS_NOT_CONVERGED when max_iter ran out for some column.  Errors: STATE (no
  * oras_factor yet), INVALID_ARG (k < 1 or > 64, tol <= 0), CUDA, OUT_OF_MEMORY,

@@ -49,6 +49,12 @@ void launch_to_internal(const oras_handle* h, int k, const cplx* src, cplx* dst)
 void launch_to_external(const oras_handle* h, int k, const cplx* src, cplx* dst);
 int red_blocks();
 int launch_wait_selftest(const oras_handle* h);
+// shared with the block FGMRES driver (block_fgmres.cpp)
+int ensure_ws(oras_handle* h, int k, int m);
+int precond_to_z(oras_handle* h, const cplx* v, int k, int j);
+void spmv_z(oras_handle* h, int k, int j, cplx* y);
+int status_code(oras_handle* h, const int32_t* st);
+int fgmres_block(oras_handle* h, int p, double tol, oras_info* info);
 }  // namespace oras
 
 using namespace oras;
@@ -348,7 +354,7 @@ static int factor_device(oras_handle* h) {
 
 
 // Return code for the device status flags st[8] (read back from Device::status).
-static int status_code(oras_handle* h, const int32_t* st) {
+int oras::status_code(oras_handle* h, const int32_t* st) {
   if (st[ST_ERR] == DEV_SINGULAR) {
     h->err = "local matrix of subdomain " + std::to_string(st[ST_SUB]) + " has a zero pivot column";
     return ORAS_ERR_SINGULAR_LOCAL;
@@ -662,7 +668,7 @@ int oras_global_csr(oras_handle* h, int64_t* rowptr, int32_t* cols, oras_complex
 }  // extern "C"
 
 // ------------------------------------------------------------------ Krylov workspace
-static int ensure_ws(oras_handle* h, int k, int m) {
+int oras::ensure_ws(oras_handle* h, int k, int m) {
   auto& d = h->dev;
   const int64_t N = h->mesh.ndof;
   if (int rc = ensure_ybuf(h, k)) return rc;
@@ -723,7 +729,7 @@ static int store_output(oras_handle* h, const cplx* src, int k, int mem, oras_co
   return ORAS_OK;
 }
 
-static int precond_to_z(oras_handle* h, const cplx* v, int k, int j) {
+int oras::precond_to_z(oras_handle* h, const cplx* v, int k, int j) {
   auto& d = h->dev;
   size_t nk = (size_t)h->mesh.ndof * k;
   int rc = d.factor_bits == 64 ? launch_apply_f64out(h, v, d.Zd + nk * j, k)
@@ -732,7 +738,7 @@ static int precond_to_z(oras_handle* h, const cplx* v, int k, int j) {
   return rc ? ORAS_ERR_CUDA : ORAS_OK;
 }
 
-static void spmv_z(oras_handle* h, int k, int j, cplx* y) {
+void oras::spmv_z(oras_handle* h, int k, int j, cplx* y) {
   auto& d = h->dev;
   size_t nk = (size_t)h->mesh.ndof * k;
   if (d.factor_bits == 64) launch_spmv_f64(h, d.Zd + nk * j, y, k);
@@ -925,7 +931,12 @@ int oras_solve(oras_handle* h, const oras_complex* rhs, int32_t k, double tol, o
   if (rc) return rc;
   rc = load_input(h, rhs, k, mem, h->dev.bk);
   if (rc) return rc;
-  rc = fgmres(h, k, tol, info);
+  if (h->opt.block && k > 1) {
+    rc = fgmres_block(h, k, tol, info);
+    prof_resolve(h);
+  } else {
+    rc = fgmres(h, k, tol, info);
+  }
   if (rc < 0) return rc;
   int rc2 = store_output(h, h->dev.xk, k, mem, x);
   if (rc2) return rc2;

@@ -56,7 +56,7 @@ class oras_options(C.Structure):
                 ("weights", C.c_int32), ("overlap_kind", C.c_int32), ("lu_engine", C.c_int32),
                 ("lu_panel", C.c_int32), ("lu_group", C.c_int32), ("transmission", C.c_int32),
                 ("graphs", C.c_int32), ("wait_ms", C.c_int32), ("apply_engine", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("block", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class oras_info(C.Structure):
@@ -197,7 +197,7 @@ def _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part, beta_face=None)
 
 
 def _options(restart=0, max_iter=0, factor_bits=0, weights=0, overlap_kind=0, lu_engine=0, lu_panel=0, lu_group=0,
-             transmission=0, graphs=0, wait_ms=0, apply_engine=0):
+             transmission=0, graphs=0, wait_ms=0, apply_engine=0, block=0):
     o = oras_options()
     o.restart, o.max_iter, o.factor_bits, o.weights, o.overlap_kind = restart, max_iter, factor_bits, weights, overlap_kind
     o.lu_engine = lu_engine
@@ -207,6 +207,7 @@ def _options(restart=0, max_iter=0, factor_bits=0, weights=0, overlap_kind=0, lu
     o.graphs = graphs
     o.wait_ms = wait_ms
     o.apply_engine = apply_engine
+    o.block = block
     return o
 
 
