@@ -15,7 +15,8 @@
 // swizzled K-major image of the B operand, so one 1-D bulk copy stages them next to their tile.
 //
 // Work split and protocol as in the CUDA-core apply (apply.cuh): a cluster of two CTAs per
-// subdomain; CTA c owns the strips I with I % 2 == c and streams the tiles of its own block
+// subdomain (or, when the subdomains alone fill every SM, one CTA per subdomain that owns every
+// strip: no partial sums to exchange, and a deeper ring); CTA c owns the strips I with I % 2 == c and streams the tiles of its own block
 // columns J % 2 == c; for every strip each CTA accumulates its partial product in tensor memory;
 // the non-owner sends its 64 x KT partial sums to the owner through distributed shared memory;
 // the owner forms r = b_I - both partials, writes r into shared memory in the B layout, and one
@@ -41,7 +42,7 @@ constexpr uint32_t ATC_HALF = 64 * 128;           // 64 rows x 128 B: one plane 
 constexpr uint32_t ATC_CHUNK_A = 2 * ATC_HALF;    // one K-chunk (32 columns) of a tile, both planes
 constexpr uint32_t ATC_TILE = 2 * ATC_CHUNK_A;    // 32 KB
 
-template <int KT>
+template <int KT, bool SOLO = false>
 struct AtcShape {
   static_assert(KT == 8 || KT == 16 || KT == 32, "right-hand sides per pass");
   static constexpr int N = 2 * KT;                          // MMA N (multiple of 16 for M = 128)
@@ -54,7 +55,7 @@ struct AtcShape {
   static __host__ __device__ size_t rb_off(int S) { return (size_t)S * STAGE; }
   static __host__ __device__ size_t xch_off(int S) { return rb_off(S) + YB; }
   static __host__ __device__ size_t recv_off(int S) { return xch_off(S) + XCH; }
-  static __host__ __device__ size_t bar_off(int S) { return (recv_off(S) + 2 * RECV + 15) & ~(size_t)15; }
+  static __host__ __device__ size_t bar_off(int S) { return (recv_off(S) + (SOLO ? 0 : 2 * RECV) + 15) & ~(size_t)15; }
   // full[S], empty[S], accf[2], acce[2], rbf, dgd, msg[2], fin
   static __host__ __device__ size_t total(int S) { return bar_off(S) + (size_t)(2 * S + 9) * 8 + 1024; }
   static_assert(STAGE % 1024 == 0 && YB % 1024 == 0, "swizzle-atom alignment of the stages");
@@ -133,26 +134,34 @@ enum { ATC_ITEM_TILE = 0, ATC_ITEM_DIAG = 1, ATC_ITEM_COMMIT = 2 };
 // block column I need only y values finalised earlier -- they are issued before the diagonal
 // product of strip I, so the tensor cores work through them while the epilogue waits for the
 // partner's partial sums of strip I; the one tile that needs y_I comes right after it.
-template <typename F>
+//
+// SOLO (one CTA per subdomain, every strip owned): the strip after I is again this CTA's; its tiles
+// but the one in block column I are issued before the diagonal product of strip I, so they overlap
+// the epilogue of strip I in the same way.
+template <bool SOLO, typename F>
 __device__ __forceinline__ void atc_stream(int c, int64_t nts, F&& f) {
+  constexpr int ST = SOLO ? 1 : 2;  // block-column stride of this CTA
   for (int pass = 0; pass < 2; ++pass) {
     const bool fwd = pass == 0;
     for (int64_t it = 0; it < nts; ++it) {
       const int64_t I = fwd ? it : nts - 1 - it;
       const int64_t slot = (int64_t)pass * nts + it;
-      if ((I & 1) != c) {
+      if (!SOLO && (I & 1) != c) {
         if (it == 0) f(ATC_ITEM_COMMIT, I, I, slot);  // no owned strip before it: nothing to multiply
         continue;
       }
-      // the owned strip: block columns J % 2 == c below (forward) or above (backward) I
-      if (fwd) for (int64_t J = c; J < I; J += 2) f(ATC_ITEM_TILE, I, J, slot);
-      else for (int64_t J = I + 2; J < nts; J += 2) f(ATC_ITEM_TILE, I, J, slot);
-      f(ATC_ITEM_COMMIT, I, I, slot);
+      // the owned strip: block columns J % ST == c below (forward) or above (backward) I.  Solo,
+      // they were issued with the previous strip's (all but the first strip of a pass).
+      if (!SOLO || it == 0) {
+        if (fwd) for (int64_t J = c; J < I; J += ST) f(ATC_ITEM_TILE, I, J, slot);
+        else for (int64_t J = I + ST; J < nts; J += ST) f(ATC_ITEM_TILE, I, J, slot);
+        f(ATC_ITEM_COMMIT, I, I, slot);
+      }
       const bool next = it + 1 < nts;
       const int64_t I1 = fwd ? I + 1 : I - 1;
-      if (next) {  // the partner's next strip: every tile but the one in block column I
-        if (fwd) for (int64_t J = c; J < I; J += 2) f(ATC_ITEM_TILE, I1, J, slot + 1);
-        else for (int64_t J = I + 2; J < nts; J += 2) f(ATC_ITEM_TILE, I1, J, slot + 1);
+      if (next) {  // the next strip: every tile but the one in block column I
+        if (fwd) for (int64_t J = c; J < I; J += ST) f(ATC_ITEM_TILE, I1, J, slot + 1);
+        else for (int64_t J = I + ST; J < nts; J += ST) f(ATC_ITEM_TILE, I1, J, slot + 1);
       }
       f(ATC_ITEM_DIAG, I, I, slot);
       if (next) {
@@ -163,13 +172,15 @@ __device__ __forceinline__ void atc_stream(int c, int64_t nts, F&& f) {
   }
 }
 
-// One pass of KT right-hand sides (columns off .. off+nr-1 of v and z) for subdomain s.
-template <int KT, typename ZT>
+// One pass of KT right-hand sides (columns off .. off+nr-1 of v and z) for subdomain s: a cluster
+// of two CTAs, or with SOLO one CTA that owns every strip (no partial sums to exchange).
+template <int KT, typename ZT, bool SOLO>
 __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, const CUtensorMap* dmap, int s,
                                  const cplx* __restrict__ v, int64_t vs, ZT* __restrict__ z, int64_t zs,
                                  int64_t off, int nr, unsigned char* yglob) {
-  using Sh = AtcShape<KT>;
+  using Sh = AtcShape<KT, SOLO>;
   constexpr int N = Sh::N;
+  constexpr int ST = SOLO ? 1 : 2;  // block-column stride of this CTA
   const ApplyGeom& a = aa.g;
   extern __shared__ __align__(1024) unsigned char atc_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)atc_raw + 1023) & ~(uintptr_t)1023);
@@ -177,7 +188,7 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
   unsigned char* ring = sm;
   unsigned char* rB = sm + Sh::rb_off(S);
   float* xch = (float*)(sm + Sh::xch_off(S));
-  float2* recv = (float2*)(sm + Sh::recv_off(S));          // [2][64][KT]
+  float2* recv = (float2*)(sm + Sh::recv_off(S));          // [2][64][KT] (clusters only)
   uint64_t* full = (uint64_t*)(sm + Sh::bar_off(S));
   uint64_t* empty = full + S;
   uint64_t* accf = empty + S;                               // [2] strip accumulator ready
@@ -188,11 +199,12 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
   uint64_t* fin = msg + 2;                                  // every MMA of this CTA done
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, peer_abort, ydone, ep_ok;
-  const int c = (int)cluster_rank();
+  const int c = SOLO ? 0 : (int)cluster_rank();
   const int64_t ns = a.ns[s], np = a.np[s], nts = np / TB;
-  const int64_t own0 = (nts + 1) / 2;
+  const int64_t own0 = SOLO ? nts : (nts + 1) / 2;
   const int64_t nown_s = c ? nts - own0 : own0;
-  unsigned char* ysub = yglob + ((a.np_off[s] / TB) + (c ? own0 : 0)) * (int64_t)Sh::YB;  // this CTA's strips
+  // this CTA's strips (own strip I is number I / ST among them)
+  unsigned char* ysub = yglob + ((a.np_off[s] / TB) + (c ? own0 : 0)) * (int64_t)Sh::YB;
   const int64_t toff = a.tile_off[s];
   const int64_t ioff = a.inv_off[s];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -223,7 +235,7 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  cluster_sync_all();  // the partner may signal our barriers from here on
+  if (!SOLO) cluster_sync_all();  // the partner may signal our barriers from here on
   const uint32_t tbase = tmem_base;
 
   if (warp == 4) {
@@ -241,7 +253,7 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
           if (!wait_counter(&ydone, (int)need, a.wait_ns)) return false;
           fence_proxy_async_global();
           mbar_expect_tx(&full[slot], ATC_TILE + Sh::YB);
-          bulk_g2s(dst + ATC_TILE, ysub + (J / 2) * (int64_t)Sh::YB, Sh::YB, &full[slot]);
+          bulk_g2s(dst + ATC_TILE, ysub + (J / ST) * (int64_t)Sh::YB, Sh::YB, &full[slot]);
           const int zt = (int)(toff + I * nts + J);
           for (int ch = 0; ch < 2; ++ch) {
             atc_tma(dst + ch * ATC_CHUNK_A, amap, 32 * ch, 0, zt, &full[slot]);
@@ -259,11 +271,11 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
         if (++slot == S) { slot = 0; phase ^= 1u; }
         return true;
       };
-      atc_stream(c, nts, [&](int kind, int64_t I, int64_t J, int64_t slot_s) {
+      atc_stream<SOLO>(c, nts, [&](int kind, int64_t I, int64_t J, int64_t slot_s) {
         if (!ok || kind == ATC_ITEM_COMMIT) return;
         const bool fwd = slot_s < nts;
         if (kind == ATC_ITEM_DIAG) ok = issue(true, I, I, fwd ? 0 : 1, 0);
-        else ok = issue(false, I, J, 0, fwd ? J / 2 + 1 : 2 * nown_s - J / 2);
+        else ok = issue(false, I, J, 0, fwd ? J / ST + 1 : 2 * nown_s - J / ST);
       });
       if (!ok) {
         atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
@@ -293,7 +305,7 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
           }
       };
       int started = 0;  // bit b: the open strip of accumulator b has had its first product
-      atc_stream(c, nts, [&](int kind, int64_t I, int64_t J, int64_t slot_s) {
+      atc_stream<SOLO>(c, nts, [&](int kind, int64_t I, int64_t J, int64_t slot_s) {
         const int b = (int)(slot_s & 1);
         if (kind == ATC_ITEM_COMMIT) {
           atc_commit(&accf[b]);  // arrives when this strip's products are in tensor memory
@@ -379,10 +391,10 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
       const bool fwd = pass == 0;
       for (int64_t it = 0; it < nts; ++it) {
         const int64_t I = fwd ? it : nts - 1 - it;
-        const bool owner = (I & 1) == c;
+        const bool owner = SOLO || (I & 1) == c;
         const int b = (int)(strips & 1);
         const int64_t use = strips >> 1;
-        const int64_t J0 = fwd ? c : I + 1 + ((I + 1 + c) & 1), J1 = fwd ? I : nts;
+        const int64_t J0 = fwd ? c : (SOLO ? I + 1 : I + 1 + ((I + 1 + c) & 1)), J1 = fwd ? I : nts;
         const bool have = J0 < J1;
         ok = uniform_wait(&accf[b], (uint32_t)(use & 1), false);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -405,10 +417,10 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
           continue;
         }
         // owner: r = b_I - own partial - partner partial, written into rB (B layout)
-        ok = uniform_wait(&msg[kr & 1], (uint32_t)((kr >> 1) & 1), true);
-        unsigned char* yI = ysub + (I / 2) * (int64_t)Sh::YB;
+        if (!SOLO) ok = uniform_wait(&msg[kr & 1], (uint32_t)((kr >> 1) & 1), true);
+        unsigned char* yI = ysub + (I / ST) * (int64_t)Sh::YB;
         if (tid < 64) {
-          const float2* pr = recv + (kr & 1) * 64 * KT + i * KT;
+          const float2* pr = SOLO ? nullptr : recv + (kr & 1) * 64 * KT + i * KT;
           const int64_t pos = I * TB + i;
 #pragma unroll
           for (int r = 0; r < KT; ++r) {
@@ -424,7 +436,7 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
               br = *(const float*)(yI + sw128_off(r, i, Sh::CHUNK_B));
               bi = *(const float*)(yI + sw128_off(KT + r, i, Sh::CHUNK_B));
             }
-            const float2 p2 = pr[r];
+            const float2 p2 = SOLO ? make_float2(0.0f, 0.0f) : pr[r];
             *(float*)(rB + sw128_off(r, i, Sh::CHUNK_B)) = br - d[r].x - p2.x;
             *(float*)(rB + sw128_off(KT + r, i, Sh::CHUNK_B)) = bi - d[r].y - p2.y;
           }
@@ -462,7 +474,7 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
       for (int64_t q = tid; q < nown_s * TB * KT; q += ATC_EPI) {
         const int64_t st = q / (TB * KT);
         const int r = (int)((q / TB) % KT), ii = (int)(q % TB);
-        const int64_t pos = (2 * st + c) * TB + ii;
+        const int64_t pos = (ST * st + c) * TB + ii;
         if (pos >= ns || r >= nr) continue;
         const unsigned char* yst = ysub + st * (int64_t)Sh::YB;
         const float re = *(const float*)(yst + sw128_off(r, ii, Sh::CHUNK_B));
@@ -479,6 +491,7 @@ __device__ bool apply_cluster_tc(const AtcArgs& aa, const CUtensorMap* amap, con
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(Sh::TMEM_COLS));
+  if (SOLO) return abort_flag != 0;
   if (threadIdx.x == 0 && abort_flag) st_remote_u32(map_to_rank(&peer_abort, (uint32_t)(c ^ 1)), 1u);
   cluster_sync_all();  // the partner must not touch our shared memory after we exit
   return abort_flag != 0 || peer_abort != 0;
@@ -488,7 +501,15 @@ template <int KT, typename ZT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(ATC_THREADS, 1)
     k_apply_tc(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap dmap, AtcArgs aa,
                int k, int r0, int nr, unsigned char* yglob, const cplx* __restrict__ v, ZT* __restrict__ z) {
-  apply_cluster_tc<KT, ZT>(aa, &amap, &dmap, blockIdx.x / 2, v, k, z, k, r0, nr, yglob);
+  apply_cluster_tc<KT, ZT, false>(aa, &amap, &dmap, blockIdx.x / 2, v, k, z, k, r0, nr, yglob);
+}
+
+// One CTA per subdomain (launched when the subdomains alone fill every SM).
+template <int KT, typename ZT>
+__global__ void __launch_bounds__(ATC_THREADS, 1)
+    k_apply_tc_solo(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap dmap, AtcArgs aa,
+                    int k, int r0, int nr, unsigned char* yglob, const cplx* __restrict__ v, ZT* __restrict__ z) {
+  apply_cluster_tc<KT, ZT, true>(aa, &amap, &dmap, blockIdx.x, v, k, z, k, r0, nr, yglob);
 }
 
 // ------------------------------------------------------------------ host side
@@ -526,11 +547,24 @@ static bool atc_map(void* base, int64_t tiles, CUtensorMap* map) {
 ApplyGeom apply_geom(const oras_handle* h);
 constexpr size_t ATC_SMEM_LIMIT = 227 * 1024 - 1024;  // opt-in shared memory less the static part
 
-template <int KT>
+template <int KT, bool SOLO>
 static int atc_stages() {
   for (int q = 4; q >= 2; --q)
-    if (AtcShape<KT>::total(q) <= ATC_SMEM_LIMIT) return q;
+    if (AtcShape<KT, SOLO>::total(q) <= ATC_SMEM_LIMIT) return q;
   return 0;
+}
+
+// One CTA per subdomain when the subdomains alone give every SM a CTA (no partial sums to
+// exchange, so the ring has room for one more stage); else a two-CTA cluster per subdomain.
+static bool atc_solo(const oras_handle* h) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0) sms = n;
+    else return false;
+  }
+  return h->mesh.nsub >= sms;
 }
 
 // Right-hand sides per tensor-core pass for a group of `rem` columns.
@@ -548,7 +582,7 @@ size_t apply_tc_ybytes(const oras_handle* h, int kt) {
 bool apply_tc_available(const oras_handle* h) {
   if (h->dev.factor_bits != 32 || !h->dev.arena || !h->dev.dinv) return false;
   if (h->opt.apply_engine == ORAS_APPLY_CUDA_CORES) return false;
-  if (!atc_stages<8>() || !atc_stages<16>() || !atc_stages<32>()) return false;
+  if (!atc_stages<8, false>() || !atc_stages<16, false>() || !atc_stages<32, false>()) return false;
   CUtensorMap m;
   return atc_map(h->dev.arena, h->mesh.arena_tiles + 2 * h->mesh.nsub, &m);
 }
@@ -563,12 +597,20 @@ static int atc_launch(const oras_handle* h, const cplx* v, ZT* z, int k, int r0,
   if (!d.ybuf || d.ybuf_bytes < apply_tc_ybytes(h, KT)) return -1;
   AtcArgs aa;
   aa.g = apply_geom(h);
-  aa.g.stages = atc_stages<KT>();
   aa.dinv_tiles = dtiles;
-  const size_t smem = AtcShape<KT>::total(aa.g.stages);
-  allow_max_smem((const void*)k_apply_tc<KT, ZT>);
-  k_apply_tc<KT, ZT><<<2 * m.nsub, ATC_THREADS, smem, d.stream>>>(amap, dmap, aa, k, r0, nr,
-                                                                   (unsigned char*)d.ybuf, v, z);
+  if (atc_solo(h)) {
+    aa.g.stages = atc_stages<KT, true>();
+    const size_t smem = AtcShape<KT, true>::total(aa.g.stages);
+    allow_max_smem((const void*)k_apply_tc_solo<KT, ZT>);
+    k_apply_tc_solo<KT, ZT><<<m.nsub, ATC_THREADS, smem, d.stream>>>(amap, dmap, aa, k, r0, nr,
+                                                                      (unsigned char*)d.ybuf, v, z);
+  } else {
+    aa.g.stages = atc_stages<KT, false>();
+    const size_t smem = AtcShape<KT, false>::total(aa.g.stages);
+    allow_max_smem((const void*)k_apply_tc<KT, ZT>);
+    k_apply_tc<KT, ZT><<<2 * m.nsub, ATC_THREADS, smem, d.stream>>>(amap, dmap, aa, k, r0, nr,
+                                                                     (unsigned char*)d.ybuf, v, z);
+  }
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -433,14 +433,18 @@ def oras_wait_selftest(h):
     return rc, detail.value
 
 
+AUTOTUNE_WIDTHS = (4, 8, 12, 16, 24, 32, 48)
+
+
 def oras_autotune(h):
     """Returns (panel width chosen, {(width, group): factorisation ms} (empty when cached)).
     The chosen raster group is oras_lu_group(h)."""
     panel = C.c_int32()
-    ms = np.full(8, -1.0)
-    _check(h, lib.oras_autotune(h, C.byref(panel), _ptr(ms), 8))
-    cands = [(w, 8) for w in (4, 8, 12, 16, 24)]
-    best_w = max(((w, t) for (w, _), t in zip(cands, ms[:5]) if t >= 0), key=lambda x: -x[1], default=(panel.value, 0))[0]
+    ms = np.full(10, -1.0)
+    _check(h, lib.oras_autotune(h, C.byref(panel), _ptr(ms), 10))
+    cands = [(w, 8) for w in AUTOTUNE_WIDTHS]
+    best_w = max(((w, t) for (w, _), t in zip(cands, ms[:len(AUTOTUNE_WIDTHS)]) if t >= 0), key=lambda x: -x[1],
+                 default=(panel.value, 0))[0]
     cands += [(best_w, g) for g in (16, 32, 64)]
     times = {c: t for c, t in zip(cands, ms) if t >= 0}
     return panel.value, times
