@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="head16",
-                    choices=["head16", "cube8", "head8", "krylov24", "batch32", "batch12", "batch8", "head32r3"],
+                    choices=["head16", "cube8", "head8", "krylov24", "batch32", "batch12", "batch8",
+                             "head32r3"],
                     help="head16: the benchmark workload; cube8: 8^3 r=1 plane wave (FP64 factors); "
                          "head8: 8^3 r=2 8 subdomains (1.9 GB arena, for kernel profiles); krylov24: "
                          "24^3 r=2 512 subdomains without overlap (464 MB matrix, small arena, for Krylov "

@@ -69,7 +69,8 @@ __global__ void k_block_sum(int p, const cplx* __restrict__ partials, cplx* __re
   const int pp = p * p;
   for (int pr = blockIdx.x * blockDim.x + threadIdx.x; pr < pp; pr += gridDim.x * blockDim.x) {
     cplx t = {0.0, 0.0};
-    for (int b = 0; b < BLK_BLOCKS; ++b) t = cadd(t, partials[(int64_t)b * pp + pr]);
+#pragma unroll 16
+    for (int b = 0; b < BLK_BLOCKS; ++b) t = cadd(t, partials[(int64_t)b * pp + pr]);  // loads hoisted
     out[pr] = t;
   }
 }

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) k_spmv_df(int64_t n, const int64_t* __res
 // elements t, t + teff, t + 2 teff, ...: all of one right-hand side r = t % k, so each thread
 // keeps a single accumulator.  Block partial sums per right-hand side are formed in a fixed order
 // (warp shuffles over the lanes of the same r when k divides 32, else a sequential sum of the
-// block's per-thread values), then the fixed-order sum over blocks (sum_partials): the results do
+// block's per-thread values), then the fixed-order sum over blocks (sum_partials_warp): the results do
 // not depend on scheduling.
 __device__ __forceinline__ int64_t red_teff(int k) {
   const int64_t T = (int64_t)gridDim.x * blockDim.x;
@@ -199,10 +199,26 @@ __device__ void block_reduce_store(cplx v, int k, cplx* partials) {
   }
 }
 
-// Fixed-order sum of the block partials of the previous pass.
-__device__ __forceinline__ cplx sum_partials(const cplx* partials, int k, int r) {
-  cplx t = {0.0, 0.0};
-  for (int b = 0; b < RED_BLOCKS; ++b) t = cadd(t, partials[(int64_t)b * k + r]);
+// Fixed-order sum of the block partials of the previous pass, by one warp: lane l loads the
+// partials of blocks l, l + 32, ... at once (their loads overlap instead of each waiting for the
+// previous add), adds them in that order, and a fixed xor-shuffle tree combines the lanes.  Every
+// lane returns the total.
+__device__ __forceinline__ cplx sum_partials_warp(const cplx* partials, int k, int r, int lane) {
+  constexpr int PER = (RED_BLOCKS + 31) / 32;
+  cplx v[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int b = lane + 32 * q;
+    v[q] = b < RED_BLOCKS ? partials[(int64_t)b * k + r] : cplx{0.0, 0.0};
+  }
+  cplx t = v[0];
+#pragma unroll
+  for (int q = 1; q < PER; ++q) t = cadd(t, v[q]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    t.re += __shfl_xor_sync(0xffffffffu, t.re, o);
+    t.im += __shfl_xor_sync(0xffffffffu, t.im, o);
+  }
   return t;
 }
 
@@ -226,9 +242,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_mgs_step(int64_t nk, int k, int
                                                           cplx* __restrict__ w, const cplx* __restrict__ pin,
                                                           cplx* __restrict__ pout, cplx* __restrict__ H) {
   __shared__ cplx hs[MAX_RHS];
-  for (int r = threadIdx.x; r < k; r += blockDim.x) {
-    hs[r] = sum_partials(pin, k, r);
-    if (blockIdx.x == 0) H[((int64_t)r * (m + 1) + i) * m + j] = hs[r];
+  for (int r = threadIdx.x >> 5; r < k; r += blockDim.x >> 5) {  // one warp per right-hand side
+    const cplx t = sum_partials_warp(pin, k, r, threadIdx.x & 31);
+    if ((threadIdx.x & 31) == 0) {
+      hs[r] = t;
+      if (blockIdx.x == 0) H[((int64_t)r * (m + 1) + i) * m + j] = t;
+    }
   }
   __syncthreads();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, teff = red_teff(k);
@@ -261,7 +280,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_mgs_finish(int64_t nk, int k, i
                                                             double* __restrict__ cs, cplx* __restrict__ sn,
                                                             cplx* __restrict__ g, double* __restrict__ res) {
   __shared__ double hn[MAX_RHS];
-  for (int r = threadIdx.x; r < k; r += blockDim.x) hn[r] = sqrt(sum_partials(pin, k, r).re);
+  for (int r = threadIdx.x >> 5; r < k; r += blockDim.x >> 5) {  // one warp per right-hand side
+    const cplx t = sum_partials_warp(pin, k, r, threadIdx.x & 31);
+    if ((threadIdx.x & 31) == 0) hn[r] = sqrt(t.re);
+  }
   __syncthreads();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
     int r = (int)(e % k);
@@ -354,8 +376,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_residual(int64_t nk, int k, con
 
 // norms[r] = sqrt(sum partials) (single block)
 __global__ void k_norms(int k, const cplx* __restrict__ partials, double* __restrict__ out) {
-  int r = threadIdx.x;
-  if (r < k) out[r] = sqrt(sum_partials(partials, k, r).re);
+  for (int r = threadIdx.x >> 5; r < k; r += blockDim.x >> 5) {  // one warp per right-hand side
+    const cplx t = sum_partials_warp(partials, k, r, threadIdx.x & 31);
+    if ((threadIdx.x & 31) == 0) out[r] = sqrt(t.re);
+  }
 }
 
 // V0 = r / beta for active RHS (0 otherwise); g = (beta, 0, ...)
@@ -462,7 +486,7 @@ void launch_residual(const oras_handle* h, int k, const cplx* b, cplx* r, cplx* 
   count_launches(1);
 }
 void launch_norms(const oras_handle* h, int k, const cplx* partials, double* out) {
-  k_norms<<<1, 64, 0, h->dev.stream>>>(k, partials, out);
+  k_norms<<<1, 256, 0, h->dev.stream>>>(k, partials, out);
   count_launches(1);
 }
 void launch_restart(const oras_handle* h, int k, int m, const cplx* rv, const double* beta, const int32_t* active,
