@@ -256,10 +256,13 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_tournament(LuArgs a, void* ar
 }
 
 // ------------------------------------------------------------------ FP32 tournament, rows in registers
-// Same tournament as above, with the elimination done on register-resident rows: thread t owns
-// candidate row t (64 complex values in registers).  No row is moved: the chosen pivot row is
-// marked and its values are broadcast through shared memory.
-// Pivot choice: max |Re| + |Im| over unchosen rows, ties to the lowest candidate position.
+// Same tournament as above, with the elimination done on register-resident rows: candidate row r
+// is held by threads 2r (the real parts of its 64 entries) and 2r+1 (the imaginary parts), so a
+// block of 512 threads carries 256 rows at about 100 registers per thread and 16 warps per SM
+// hide the latency of each column's block-wide pivot choice.  No row is moved: the chosen pivot
+// row is marked and its values are broadcast through shared memory.
+// Pivot choice: max |Re| + |Im| over unchosen rows (to a relative 2^-14: the key keeps the top
+// 14 mantissa bits of the magnitude), ties to the lowest candidate position.
 //
 // Blocked elimination, 8 columns at a time (within a block the column indices are compile-time,
 // so the rows stay in registers; after each block every row is rotated left by 8 so the next
@@ -271,18 +274,32 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_tournament(LuArgs a, void* ar
 // first brought up to date by a triangular correction with the block's multipliers (blocked
 // right-looking LU: U12 = L11^{-1} A12, A22 -= L21 U12).  Positions >= 64 - 8*block hold columns
 // eliminated in earlier blocks (multipliers) and are skipped block by block.
-constexpr int LU_WARPS = LU_THREADS / 32;
-struct RegGepp {
-  float2 cand[2][LU_WARPS][8];  // each warp's best candidate's in-block values (by column parity)
-  float wv[2][LU_WARPS];
-  int wi[2][LU_WARPS];
-  float2 P[8][TB];              // the block's pivot rows (rotated positions), corrected at block end
-  int order[TB];                // pivot rank -> candidate position
+//
+// With the two parts of a complex entry in two threads, a complex multiply-subtract
+// x -= l * u becomes, in each thread, x_part -= al * Re(u) + be * Im(u) with (al, be) = (Re l,
+// -Im l) for the real part and (Im l, Re l) for the imaginary part.
+constexpr int RI_THREADS = 512;
+constexpr int RI_ROWS = RI_THREADS / 2;
+constexpr int RI_WARPS = RI_THREADS / 32;
+struct RiGepp {
+  alignas(16) float candr[2][RI_WARPS][8];             // each warp's best candidate's in-block values
+  alignas(16) float candi[2][RI_WARPS][8];
+  uint32_t wk[2][RI_WARPS];                            // each warp's best pivot key (by column parity)
+  alignas(16) float Pr[8][TB];                         // the block's pivot rows (rotated positions)
+  alignas(16) float Pi[8][TB];
+  int order[TB];                                       // pivot rank -> candidate position
 };
 
-__device__ __forceinline__ void gepp_regs(float (&xr)[TB], float (&xi)[TB], bool valid, RegGepp& g, int& myrank,
-                                          float& mypiv) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+// Pivot key of candidate position `row` (< 256) with magnitude v >= 0: the magnitude's bits with
+// the 9 lowest replaced by a validity bit and 255 - row, so the largest key has the largest
+// magnitude and, among equal magnitudes, the lowest position.  0 means no candidate.
+__device__ __forceinline__ uint32_t pivot_key(float v, int row) {
+  return (__float_as_uint(v) & 0xFFFFFE00u) | 0x100u | (uint32_t)(255 - row);
+}
+
+__device__ __forceinline__ void gepp_ri(float (&x)[TB], bool valid, RiGepp& g, int& myrank, float& mypiv) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, row = t >> 1, part = t & 1;
   bool chosen = false;
   myrank = -1;
   mypiv = 0.0f;
@@ -296,117 +313,127 @@ __device__ __forceinline__ void gepp_regs(float (&xr)[TB], float (&xi)[TB], bool
     for (int c8 = 0; c8 < 8; ++c8) {
       const int c = 8 * cb + c8;
       const int b = c8 & 1;
-      float v = (valid && !chosen) ? fabsf(xr[c8]) + fabsf(xi[c8]) : -1.0f;
+      const float xo = __shfl_xor_sync(FULL, x[c8], 1);  // the other part of this entry
+      const float xre = part ? xo : x[c8], xim = part ? x[c8] : xo;
+      float v = fabsf(xre) + fabsf(xim);
       if (v != v) v = 0.0f;  // a non-finite entry still lets a row be chosen
-      int key = t;
+      uint32_t k = (valid && !chosen) ? pivot_key(v, row) : 0u;
+      k = __reduce_max_sync(FULL, k);  // the warp's best (both parts of a row hold the same key)
+      if (k != 0u && 255 - (int)(k & 0xFFu) == row) {  // the warp's candidate publishes its in-block values
+        float* dst = part ? g.candi[b][warp] : g.candr[b][warp];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {  // butterfly: every lane ends with the warp's best
-        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int ok = __shfl_xor_sync(0xffffffffu, key, o);
-        if (ov > v || (ov == v && ok < key)) { v = ov; key = ok; }
+        for (int j = c8; j < 8; ++j) dst[j] = x[j];
       }
-      if (t == key && v >= 0.0f) {  // the warp's candidate publishes its in-block values
-#pragma unroll
-        for (int j = c8; j < 8; ++j) g.cand[b][warp][j] = make_float2(xr[j], xi[j]);
-      }
-      if (lane == 0) { g.wv[b][warp] = v; g.wi[b][warp] = key; }
+      if (lane == 0) g.wk[b][warp] = k;
       __syncthreads();
-      float bv = g.wv[b][0];
-      int bk = g.wi[b][0], bw = 0;
-#pragma unroll
-      for (int w = 1; w < LU_WARPS; ++w) {
-        const float ov = g.wv[b][w];
-        const int ok = g.wi[b][w];
-        if (ov > bv || (ov == bv && ok < bk)) { bv = ov; bk = ok; bw = w; }
-      }
-      if (t == bk && bv >= 0.0f) {
+      const uint32_t bk = __reduce_max_sync(FULL, g.wk[b][lane & (RI_WARPS - 1)]);
+      const int brow = 255 - (int)(bk & 0xFFu), bw = brow >> 4;  // rows 16w..16w+15 are warp w's
+      const bool nonzero = (bk >> 9) != 0u;
+      if (bk != 0u && row == brow) {
         chosen = true;
         myrank = c;
-        mypiv = bv;
+        mypiv = nonzero ? v : 0.0f;
         my_c8 = c8;
-        g.order[c] = t;
+        if (part == 0) g.order[c] = row;
       }
-      if (bv > 0.0f && valid && !chosen) {  // multiplier and update of the block's later columns
-        const float2 p = g.cand[b][bw][c8];
-        const float den = p.x * p.x + p.y * p.y;
-        const float lr = (xr[c8] * p.x + xi[c8] * p.y) / den, li = (xi[c8] * p.x - xr[c8] * p.y) / den;
-        xr[c8] = lr;
-        xi[c8] = li;
+      if (nonzero && valid && !chosen) {  // multiplier and update of the block's later columns
+        const float4* cr = reinterpret_cast<const float4*>(g.candr[b][bw]);
+        const float4* ci = reinterpret_cast<const float4*>(g.candi[b][bw]);
+        float ur[8], ui[8];
+        *reinterpret_cast<float4*>(ur) = cr[0];
+        *reinterpret_cast<float4*>(ur + 4) = cr[1];
+        *reinterpret_cast<float4*>(ui) = ci[0];
+        *reinterpret_cast<float4*>(ui + 4) = ci[1];
+        const float pr = ur[c8], pi = ui[c8];
+        const float rden = __frcp_rn(pr * pr + pi * pi);
+        const float lr = (xre * pr + xim * pi) * rden, li = (xim * pr - xre * pi) * rden;
+        const float al = part ? li : lr, be = part ? lr : -li;
+        x[c8] = al;
 #pragma unroll
-        for (int j = c8 + 1; j < 8; ++j) {
-          const float2 u = g.cand[b][bw][j];
-          xr[j] -= lr * u.x - li * u.y;
-          xi[j] -= lr * u.y + li * u.x;
-        }
-      } else if (!(bv > 0.0f) && valid && !chosen) {  // exactly zero column: no elimination
-        xr[c8] = 0.0f;
-        xi[c8] = 0.0f;
+        for (int j = c8 + 1; j < 8; ++j) x[j] -= al * ur[j] + be * ui[j];
+      } else if (!nonzero && valid && !chosen) {  // exactly zero column: no elimination
+        x[c8] = 0.0f;
       }
     }
     // the block's pivot rows: in-block multipliers and U values, then the stale part right of it
     if (my_c8 >= 0) {
+      float* dst = part ? g.Pi[my_c8] : g.Pr[my_c8];
 #pragma unroll
       for (int jb = 0; jb < TB / 8; ++jb)
         if (8 * jb < lim) {
 #pragma unroll
-          for (int j = 8 * jb; j < 8 * jb + 8; ++j) g.P[my_c8][j] = make_float2(xr[j], xi[j]);
+          for (int j = 8 * jb; j < 8 * jb + 8; ++j) dst[j] = x[j];
         }
+    }
+    // the row's 8 multipliers as (al, be) pairs (exchanged before any divergence)
+    float nal[8], nbe[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float xo = __shfl_xor_sync(FULL, x[q], 1);
+      const float lr = part ? xo : x[q], li = part ? x[q] : xo;
+      nal[q] = -(part ? li : lr);
+      nbe[q] = -(part ? lr : -li);
     }
     __syncthreads();
     // U12 = L11^{-1} A12: pivot row c8 right of the block minus its multipliers times the earlier ones
-    if (warp == 0) {
-      for (int j = 8 + lane; j < lim; j += 32) {
+    if (t < lim - 8) {
+      const int j = 8 + t;
+      float ur[8], ui[8];
 #pragma unroll
-        for (int c8 = 1; c8 < 8; ++c8) {
-          float2 acc = g.P[c8][j];
+      for (int q = 0; q < 8; ++q) { ur[q] = g.Pr[q][j]; ui[q] = g.Pi[q][j]; }
 #pragma unroll
-          for (int q = 0; q < c8; ++q) {
-            const float2 l = g.P[c8][q], u = g.P[q][j];
-            acc.x -= l.x * u.x - l.y * u.y;
-            acc.y -= l.x * u.y + l.y * u.x;
-          }
-          g.P[c8][j] = acc;
+      for (int c8 = 1; c8 < 8; ++c8) {
+#pragma unroll
+        for (int q = 0; q < c8; ++q) {
+          const float lr = g.Pr[c8][q], li = g.Pi[c8][q];
+          ur[c8] -= lr * ur[q] - li * ui[q];
+          ui[c8] -= lr * ui[q] + li * ur[q];
         }
+        g.Pr[c8][j] = ur[c8];
+        g.Pi[c8][j] = ui[c8];
       }
     }
     __syncthreads();
     if (my_c8 >= 0) {  // the block's pivot rows take their corrected values
+      const float* src = part ? g.Pi[my_c8] : g.Pr[my_c8];
 #pragma unroll
       for (int jb = 1; jb < TB / 8; ++jb)
         if (8 * jb < lim) {
 #pragma unroll
-          for (int j = 8 * jb; j < 8 * jb + 8; ++j) {
-            const float2 u = g.P[my_c8][j];
-            xr[j] = u.x;
-            xi[j] = u.y;
-          }
+          for (int j = 8 * jb; j < 8 * jb + 8; ++j) x[j] = src[j];
         }
     } else if (valid && !chosen) {  // A22 -= L21 U12: rank-8 update right of the block
 #pragma unroll
       for (int jb = 1; jb < TB / 8; ++jb)
         if (8 * jb < lim) {
 #pragma unroll
-          for (int j = 8 * jb; j < 8 * jb + 8; ++j) {
-            float ar = xr[j], ai = xi[j];
+          for (int h4 = 0; h4 < 2; ++h4) {
+            const int j0 = 8 * jb + 4 * h4;
+            float a0 = x[j0], a1 = x[j0 + 1], a2 = x[j0 + 2], a3 = x[j0 + 3];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-              const float2 u = g.P[q][j];
-              ar -= xr[q] * u.x - xi[q] * u.y;
-              ai -= xr[q] * u.y + xi[q] * u.x;
+              const float4 ur = *reinterpret_cast<const float4*>(&g.Pr[q][j0]);
+              const float4 ui = *reinterpret_cast<const float4*>(&g.Pi[q][j0]);
+              a0 = fmaf(nbe[q], ui.x, fmaf(nal[q], ur.x, a0));
+              a1 = fmaf(nbe[q], ui.y, fmaf(nal[q], ur.y, a1));
+              a2 = fmaf(nbe[q], ui.z, fmaf(nal[q], ur.z, a2));
+              a3 = fmaf(nbe[q], ui.w, fmaf(nal[q], ur.w, a3));
             }
-            xr[j] = ar;
-            xi[j] = ai;
+            x[j0] = a0;
+            x[j0 + 1] = a1;
+            x[j0 + 2] = a2;
+            x[j0 + 3] = a3;
           }
         }
     }
     // rotate left by 8: the next block's columns move to positions 0..7
-    float tr[8], ti[8];
+    float tr[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) { tr[j] = xr[j]; ti[j] = xi[j]; }
+    for (int j = 0; j < 8; ++j) tr[j] = x[j];
 #pragma unroll
-    for (int j = 0; j < TB - 8; ++j) { xr[j] = xr[j + 8]; xi[j] = xi[j + 8]; }
+    for (int j = 0; j < TB - 8; ++j) x[j] = x[j + 8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) { xr[TB - 8 + j] = tr[j]; xi[TB - 8 + j] = ti[j]; }
+    for (int j = 0; j < 8; ++j) x[TB - 8 + j] = tr[j];
   }
 }
 
@@ -421,7 +448,7 @@ __device__ __forceinline__ void flag_bad(const LuArgs& a, int s, int code) {
 // fallback (the first panel row) so that no later access leaves the matrix.
 __device__ __forceinline__ int32_t pick_checked(const LuArgs& a, int s, const int32_t* ids, int order, int64_t R0,
                                                 int64_t np, int code) {
-  if (order >= 0 && order < LU_THREADS) {
+  if (order >= 0 && order < RI_ROWS) {
     const int32_t r = ids[order];
     if (r >= R0 && r < np) return r;
   }
@@ -429,24 +456,25 @@ __device__ __forceinline__ int32_t pick_checked(const LuArgs& a, int s, const in
   return (int32_t)R0;
 }
 
-__device__ __forceinline__ void load_row_regs(void* arena, const LuArgs& a, int s, int32_t row, float (&xr)[TB],
-                                              float (&xi)[TB]) {
-  const float* T = tile_base<float>(arena, a, s, row / TB, a.k) + (row % TB) * TB;
+// one part (0: real, 1: imaginary) of matrix row `row` in tile column k
+__device__ __forceinline__ void load_part_regs(void* arena, const LuArgs& a, int s, int32_t row, int part,
+                                               float (&x)[TB]) {
+  const float* T = tile_base<float>(arena, a, s, row / TB, a.k) + part * TILE_PLANE + (row % TB) * TB;
 #pragma unroll
   for (int j = 0; j < TB; j += 4) {
-    const float4 r = *(const float4*)(T + j), i = *(const float4*)(T + TILE_PLANE + j);
-    xr[j] = r.x; xr[j + 1] = r.y; xr[j + 2] = r.z; xr[j + 3] = r.w;
-    xi[j] = i.x; xi[j + 1] = i.y; xi[j + 2] = i.z; xi[j + 3] = i.w;
+    const float4 v = *(const float4*)(T + j);
+    x[j] = v.x; x[j + 1] = v.y; x[j + 2] = v.z; x[j + 3] = v.w;
   }
 }
 
-__global__ void __launch_bounds__(LU_THREADS, 1) k_lu_tournament_rg(LuArgs a, void* arena) {
-  constexpr int CH = LU_THREADS;  // one candidate row per thread
-  __shared__ RegGepp g;
+__global__ void __launch_bounds__(RI_THREADS, 1) k_lu_tournament_ri(LuArgs a, void* arena) {
+  constexpr int CH = RI_ROWS;  // one candidate row per thread pair
+  static_assert(CH == LuCfg<float>::CH, "chunk rows");
+  __shared__ RiGepp g;
   __shared__ int32_t ids[CH];
   __shared__ int32_t nids[TB];
   __shared__ int s_old;
-  const int s = blockIdx.y, t = threadIdx.x;
+  const int s = blockIdx.y, t = threadIdx.x, row = t >> 1, part = t & 1;
   const int64_t np = a.np[s], nts = np / TB;
   if (a.k >= nts) return;
   const int64_t R0 = (int64_t)a.k * TB;
@@ -456,19 +484,19 @@ __global__ void __launch_bounds__(LU_THREADS, 1) k_lu_tournament_rg(LuArgs a, vo
   if (c >= nch) return;
   int64_t mrem = rows_total - (int64_t)c * CH;
   const int m = (int)(mrem < CH ? mrem : CH);
-  float xr[TB], xi[TB];
+  float x[TB];
   int myrank;
   float mypiv;
-  ids[t] = t < m ? (int32_t)(R0 + (int64_t)c * CH + t) : -1;
-  bool okrow = t < m;
-  if (okrow) load_row_regs(arena, a, s, ids[t], xr, xi);
+  if (t < CH) ids[t] = t < m ? (int32_t)(R0 + (int64_t)c * CH + t) : -1;
+  bool okrow = row < m;
+  if (okrow) load_part_regs(arena, a, s, (int32_t)(R0 + (int64_t)c * CH + row), part, x);
   __syncthreads();
   int32_t* cand = a.cand + (int64_t)s * a.slots * TB;
   int32_t* cnt = a.cnt + (int64_t)s * a.slots;
   int level_off = 0, n_l = nch, j = c, code = 1;
   // leaf elimination, then one merge per level while this block arrives last at its parent
   for (;;) {
-    gepp_regs(xr, xi, okrow, g, myrank, mypiv);
+    gepp_ri(x, okrow, g, myrank, mypiv);
     if (t < TB) nids[t] = pick_checked(a, s, ids, g.order[t], R0, np, code);
     __syncthreads();
     if (n_l > 1 && t < TB) cand[(level_off + j) * TB + t] = nids[t];
@@ -490,11 +518,11 @@ __global__ void __launch_bounds__(LU_THREADS, 1) k_lu_tournament_rg(LuArgs a, vo
       if (s_old != nsib - 1) return;  // a sibling still to arrive will merge
       if (t == 0) cnt[next_off + parent] = 0;
       __threadfence();
-      ids[t] = t < nsib * TB ? ((volatile int32_t*)cand)[(level_off + first + t / TB) * TB + (t % TB)] : -1;
+      if (t < CH) ids[t] = t < nsib * TB ? ((volatile int32_t*)cand)[(level_off + first + t / TB) * TB + (t % TB)] : -1;
       __syncthreads();
-      okrow = t < nsib * TB && ids[t] >= R0 && ids[t] < np;
-      if (t < nsib * TB && !okrow) flag_bad(a, s, 2);
-      if (okrow) load_row_regs(arena, a, s, ids[t], xr, xi);
+      okrow = row < nsib * TB && ids[row] >= R0 && ids[row] < np;
+      if (part == 0 && row < nsib * TB && !okrow) flag_bad(a, s, 2);
+      if (okrow) load_part_regs(arena, a, s, ids[row], part, x);
       level_off = next_off; n_l = n_next; j = parent;
       code = 3;
       merge = true;
@@ -503,11 +531,11 @@ __global__ void __launch_bounds__(LU_THREADS, 1) k_lu_tournament_rg(LuArgs a, vo
     if (!merge) break;  // this block holds the root's result
   }
   // root: the chosen rows, in pivot order, are L11\U11 of the step
-  CT<float>* dg = (CT<float>*)a.diag + (int64_t)s * TB * TB;
+  float* dg = reinterpret_cast<float*>((CT<float>*)a.diag + (int64_t)s * TB * TB);
   if (myrank >= 0) {
 #pragma unroll
-    for (int q = 0; q < TB; ++q) dg[q * TB + myrank] = {xr[q], xi[q]};
-    if (!(mypiv > 0.0f)) {
+    for (int q = 0; q < TB; ++q) dg[2 * (q * TB + myrank) + part] = x[q];
+    if (part == 0 && !(mypiv > 0.0f)) {
       atomicCAS(&a.status[ST_ERR], DEV_OK, DEV_SINGULAR);
       a.status[ST_SUB] = s;
     }
@@ -521,15 +549,15 @@ __global__ void __launch_bounds__(LU_THREADS, 1) k_lu_tournament_rg(LuArgs a, vo
         if (posv[q] == pos) return rowv[q];
       return pos;
     };
-    auto pos_of = [&](int32_t row) {
+    auto pos_of = [&](int32_t r) {
       for (int q = 0; q < nm; ++q)
-        if (rowv[q] == row) return posv[q];
-      return row;
+        if (rowv[q] == r) return posv[q];
+      return r;
     };
-    auto set = [&](int32_t pos, int32_t row) {
+    auto set = [&](int32_t pos, int32_t r) {
       for (int q = 0; q < nm; ++q)
-        if (posv[q] == pos) { rowv[q] = row; return; }
-      posv[nm] = pos; rowv[nm] = row; ++nm;
+        if (posv[q] == pos) { rowv[q] = r; return; }
+      posv[nm] = pos; rowv[nm] = r; ++nm;
     };
     for (int i = 0; i < TB; ++i) {
       int32_t tgt = (int32_t)(R0 + i);
@@ -952,7 +980,7 @@ static int lu_run(oras_handle* h) {
       }
       int pb = prof_begin(h);
       if (sizeof(R) == 4)
-        k_lu_tournament_rg<<<dim3(nch, m.nsub), LU_THREADS, 0, d.stream>>>(a, d.arena);
+        k_lu_tournament_ri<<<dim3(nch, m.nsub), RI_THREADS, 0, d.stream>>>(a, d.arena);
       else
         k_lu_tournament<R><<<dim3(nch, m.nsub), LU_THREADS, smem_t, d.stream>>>(a, d.arena);
       prof_end(h, KC_LU_TOURNAMENT, pb, 1);
