@@ -317,12 +317,12 @@ int oras_wait_selftest(oras_handle* h, int32_t* detail);
  * trailing update; trades the inner panel updates against the passes over the trailing matrix)
  * and the raster group of the tensor-core update (output blocks that share operands in L2).
  * Factorises the handle's current problem (materials of the last oras_factor, on the handle's
- * stream) once per candidate width 4, 8, 12, 16, 24, 32, 48 (group 8), then once per group 16, 32,
+ * stream) once per candidate width 4, 8, 12, 16, 24, 32, 48, 64 (group 8), then once per group 16, 32,
  * 64 at the best width, keeps the fastest pair in the handle's options (lu_panel, lu_group) and
  * leaves the factors of that pair.  The choice is cached for the process under the problem's shape
  * (factor precision, LU engine, padded subdomain orders): a later handle of the same shape takes
  * it without timing.  panel: chosen width (or NULL); ms[0..nms): the candidates' factorisation
- * times in milliseconds, widths then groups (10 entries; -1 when taken from the cache; NULL
+ * times in milliseconds, widths then groups (11 entries; -1 when taken from the cache; NULL
  * allowed).
  * Errors: INVALID_ARG, STATE (no oras_factor yet), and those of oras_factor. */
 int oras_autotune(oras_handle* h, int32_t* panel, double* ms, int32_t nms);
@@ -428,7 +428,9 @@ void oras_server_destroy(oras_server* srv);
  * interchanges and the final transposition of the U tiles, 5 LU triangular tile solves, 6 LU
  * trailing updates, 7 preconditioner apply, 8 SpMV of FP32-valued vectors (Arnoldi with FP32
  * factors), 9 orthogonalisation and Givens, 10 other, 11 SpMV of FP64 vectors (true residual;
- * Arnoldi with FP64 factors).  n: entries of t (24 covers all). */
+ * Arnoldi with FP64 factors), 12 LU panel updates (the column a left-looking panel step brings
+ * up to date and the step's pivot tile row; class 6 is then the trailing update after each
+ * panel).  n: entries of t (26 covers all). */
 int oras_timings(const oras_handle* h, double* t, int32_t n);
 /* Zeroes the accumulators of oras_timings. */
 int oras_reset_timings(oras_handle* h);

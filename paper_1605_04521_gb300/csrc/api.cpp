@@ -229,8 +229,8 @@ static int alloc_factor_space(oras_handle* h, int bits) {
   auto& m = h->mesh;
   auto& d = h->dev;
   size_t el = bits == 64 ? 16 : 8;
-  // the factor tiles, then 2 scratch tiles per subdomain (inverted diagonal blocks of a step)
-  size_t bytes = (size_t)(m.arena_tiles + 2 * m.nsub) * TB * TB * el;
+  // the factor tiles, then LU_SCRATCH scratch tiles per subdomain (inverted diagonal blocks)
+  size_t bytes = (size_t)(m.arena_tiles + (int64_t)LU_SCRATCH * m.nsub) * TB * TB * el;
   if (d.arena && d.factor_bits == bits && d.arena_bytes == bytes) return ORAS_OK;
   dfree_s(d.arena, d.stream);
   cudaError_t e = pool_malloc(&d.arena, bytes, d.stream);
@@ -300,7 +300,7 @@ int64_t footprint_bytes(const oras_handle* h, int k) {
   add(8 * 4);                                                       // status
   // factor space
   const int slots = 2 * lu_max_chunks(m.max_np, bits) + 16;
-  add((m.arena_tiles + 2 * m.nsub) * TB * TB * (int64_t)el);
+  add((m.arena_tiles + (int64_t)LU_SCRATCH * m.nsub) * TB * TB * (int64_t)el);
   add((int64_t)m.nsub * slots * TB * 4);
   add((int64_t)m.nsub * slots * 4);
   add((int64_t)m.nsub * (2 * TB * 2 + 1) * 4);
@@ -489,7 +489,7 @@ static std::map<std::vector<int64_t>, std::pair<int, int>> g_tune_cache;  // sha
 int oras_autotune(oras_handle* h, int32_t* panel, double* ms, int32_t nms) {
   if (!h) return ORAS_ERR_INVALID_ARG;
   if (!h->factored) { h->err = "oras_autotune: call oras_factor first"; return ORAS_ERR_STATE; }
-  static const int widths[] = {4, 8, 12, 16, 24, 32, 48};
+  static const int widths[] = {4, 8, 12, 16, 24, 32, 48, 64};
   static const int groups[] = {16, 32, 64};  // after the widths, which run with the default group 8
   constexpr int NW = sizeof(widths) / sizeof(widths[0]), NG = sizeof(groups) / sizeof(groups[0]);
   std::vector<int64_t> key = {h->opt.factor_bits, h->opt.lu_engine, h->mesh.nsub};

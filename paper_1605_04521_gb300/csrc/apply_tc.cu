@@ -584,7 +584,7 @@ bool apply_tc_available(const oras_handle* h) {
   if (h->opt.apply_engine == ORAS_APPLY_CUDA_CORES) return false;
   if (!atc_stages<8, false>() || !atc_stages<16, false>() || !atc_stages<32, false>()) return false;
   CUtensorMap m;
-  return atc_map(h->dev.arena, h->mesh.arena_tiles + 2 * h->mesh.nsub, &m);
+  return atc_map(h->dev.arena, h->mesh.arena_tiles + (int64_t)LU_SCRATCH * h->mesh.nsub, &m);
 }
 
 template <int KT, typename ZT>
@@ -593,7 +593,7 @@ static int atc_launch(const oras_handle* h, const cplx* v, ZT* z, int k, int r0,
   const auto& d = h->dev;
   CUtensorMap amap, dmap;
   const int64_t dtiles = (int64_t)(d.dinv_bytes / (2 * TB * TB * sizeof(float)));
-  if (!atc_map(d.arena, m.arena_tiles + 2 * m.nsub, &amap) || !atc_map(d.dinv, dtiles, &dmap)) return -1;
+  if (!atc_map(d.arena, m.arena_tiles + (int64_t)LU_SCRATCH * m.nsub, &amap) || !atc_map(d.dinv, dtiles, &dmap)) return -1;
   if (!d.ybuf || d.ybuf_bytes < apply_tc_ybytes(h, KT)) return -1;
   AtcArgs aa;
   aa.g = apply_geom(h);

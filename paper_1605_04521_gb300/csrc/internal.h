@@ -15,6 +15,10 @@
 namespace oras {
 
 constexpr int TB = 64;            // tile order of the local-factor arena (TB x TB complex)
+constexpr int LU_SUB = 8;         // sub-panel width (tile columns) of the LU's left-looking steps
+// scratch tiles per subdomain after the factor tiles: the inverted unit-lower diagonal blocks
+// L_kk^{-1} of a sub-panel's steps (slots 0 .. LU_SUB-1) and U_kk^{-1} of the current step
+constexpr int LU_SCRATCH = LU_SUB + 1;
 constexpr int MAX_NFL = 15;       // face-local DOFs r(r+2) for r <= 3
 constexpr int MAX_NL = 45;        // tet-local DOFs for r <= 3
 constexpr int MAX_RHS = 64;
@@ -169,7 +173,7 @@ struct Device {
 // ------------------------------------------------------------------ instrumentation
 // Kernel classes timed with CUDA event pairs on the handle's stream when timing is on.
 enum KClass { KC_ELEMENT = 0, KC_GLOBAL_ROWS, KC_LOCAL_ROWS, KC_LU_TOURNAMENT, KC_LU_SWAP, KC_LU_TRSM,
-              KC_LU_UPDATE, KC_APPLY, KC_SPMV, KC_ORTH, KC_OTHER, KC_SPMV64, KC_COUNT };
+              KC_LU_UPDATE, KC_APPLY, KC_SPMV, KC_ORTH, KC_OTHER, KC_SPMV64, KC_LU_PANEL, KC_COUNT };
 int prof_begin(const oras_handle* h);                 // -1 when timing is off
 void prof_end(const oras_handle* h, int cls, int begin, int launches);
 void count_launches(int n);                           // process-wide launch counter

@@ -2,27 +2,38 @@
 // P_s A_s = L_s U_s, over the tiled arena (TB x TB complex tiles, split re/im planes, row-major
 // on and below the block diagonal, column-major above it).
 //
-// Two-level blocked LU: right-looking across outer panels W tile columns wide, left-looking
-// inside a panel.  Every tile column k of a panel is processed for all subdomains at once by
-//  0. bringing column k, on and below the diagonal, up to date with the panel's earlier steps
-//     (C_Ik -= sum_{k0 <= j < k} L_Ij U_jk: one tile column written per step, where updating
-//     all the panel's remaining columns after every step would rewrite each of them up to W
-//     times);
+// Blocked LU: right-looking across outer panels W tile columns wide; inside a panel, sub-panels
+// of LU_SUB columns, left-looking inside a sub-panel.  Every tile column k of a panel is
+// processed for all subdomains at once by
+//  0. bringing column k, on and below the diagonal, up to date with the sub-panel's earlier
+//     steps (C_Ik -= sum_{k1 <= j < k} L_Ij U_jk, k1 the sub-panel's first step: one tile
+//     column written per step, where updating all the sub-panel's remaining columns after
+//     every step would rewrite each of them up to LU_SUB times);
 //  1. tournament pivoting of the tall panel column: chunks of rows are reduced with partial
 //     pivoting (pivot = max |Re| + |Im|, first on ties) to TB candidate rows each; candidate
-//     sets are merged the same way up a tree (4-way for FP32, 2-way for FP64); the root's choice is the pivot
-//     sequence of the step and its factored TB x TB block is L11\U11 (communication-avoiding
-//     LU, Grigori, Demmel, Xiang 2011);
+//     sets are merged the same way up a tree (4-way for FP32, 2-way for FP64); the root's
+//     choice is the pivot sequence of the step and its factored TB x TB block is L11\U11
+//     (communication-avoiding LU, Grigori, Demmel, Xiang 2011);
 //  2. the row interchanges of the step, applied to every column (one permutation of at most
 //     2 TB rows);
-//  3. the pivot tile row, right of column k, receives the updates of the panel's earlier
-//     steps (C_kJ -= sum_{k0 <= j < k} L_kj U_jJ);
-//  4. L21 = A21 U11^{-1} below and U12 = L11^{-1} A12 along the whole tile row.
+//  3. the pivot tile row, right of column k and inside the panel, receives the updates of the
+//     sub-panel's earlier steps (C_kJ -= sum_{k1 <= j < k} L_kj U_jJ);
+//  4. L21 = A21 U11^{-1} below and U12 = L11^{-1} A12 along the tile row inside the panel.
+// Beyond the panel, the pivot rows of a sub-panel are completed after its last step (a blocked
+// triangular solve with the panel's L): one product brings in the panel's earlier sub-panels
+// (C_kJ -= sum_{k0 <= j < k1} L_kj U_jJ for the sub-panel's rows k), then row by row the
+// sub-panel's earlier rows and U_kJ = L_kk^{-1} C_kJ -- so a pivot row's U beyond the panel
+// re-reads at most LU_SUB - 1 earlier U rows one at a time instead of up to W - 1.  (The
+// CUDA-core path, FP64 factors, does step 3 along the whole row, as in the unblocked form.)
+// After the last step of a sub-panel, a mid update brings the panel's later columns, for every
+// row below, up to date with the sub-panel (C_IJ -= sum_{k1 <= j < k1 + LU_SUB} L_Ij U_jJ, I, J
+// past the sub-panel, J inside the panel): the left-looking steps then reach back LU_SUB - 1
+// columns at most instead of W - 1, which bounds the panel's re-reads of its own L columns.
 // After the W columns of a panel, the trailing matrix gets one update with a W-tile-deep
 // contraction, C_IJ -= sum_k L_Ik U_kJ, which reads and writes every trailing tile once per
-// panel instead of once per column.  Right of column k, every row not yet a pivot row stays
-// in the state of the panel's start until then, so a row interchange never mixes rows that
-// have received different updates.
+// panel instead of once per column.  Right of column k, every row not yet a pivot row is in
+// one common state (the panel's start beyond the panel, the last mid update inside it) until
+// then, so a row interchange never mixes rows that have received different updates.
 // The tree merge uses "last arriver continues" counters, so no block ever waits for another.
 #include <algorithm>
 #include <climits>
@@ -877,9 +888,11 @@ __global__ void __launch_bounds__(256) k_lu_upper_rowmajor(LuArgs a, void* arena
 }
 
 // The step's factored diagonal block (from the tournament root): written to tile (k, k) and
-// inverted into the subdomain's two scratch tiles for the tensor-core triangular solves.
+// inverted into the subdomain's scratch tiles for the tensor-core triangular solves: L_kk^{-1}
+// into slot `slot` (kept until the sub-panel's rows are solved beyond the panel), U_kk^{-1}
+// into slot LU_SUB.
 template <typename R>
-__global__ void __launch_bounds__(INV_THREADS) k_lu_step_inv(LuArgs a, void* arena, int64_t scratch_base) {
+__global__ void __launch_bounds__(INV_THREADS) k_lu_step_inv(LuArgs a, void* arena, int64_t scratch_base, int slot) {
   extern __shared__ unsigned char smem_raw[];
   CT<R>* D = (CT<R>*)smem_raw;  // [TB][PS]
   CT<R>* X = D + TB * PS;       // [2][TB][PS]
@@ -897,8 +910,9 @@ __global__ void __launch_bounds__(INV_THREADS) k_lu_step_inv(LuArgs a, void* are
   __syncthreads();
   invert_block<R>(D, X);
   __syncthreads();
-  R* Li = (R*)arena + (scratch_base + 2 * s) * 2 * TILE_PLANE;
-  store_inverses<R>(X, Li, Li + 2 * TILE_PLANE, false);
+  R* Li = (R*)arena + (scratch_base + (int64_t)LU_SCRATCH * s + slot) * 2 * TILE_PLANE;
+  R* Ui = (R*)arena + (scratch_base + (int64_t)LU_SCRATCH * s + LU_SUB) * 2 * TILE_PLANE;
+  store_inverses<R>(X, Li, Ui, false);
 }
 
 // number of output tiles of the update regions for the largest subdomain
@@ -947,19 +961,27 @@ static int lu_run(oras_handle* h) {
   const size_t smem_i = (size_t)3 * TB * PS * sizeof(CT<R>);
   allow_max_smem((const void*)k_lu_step_inv<R>);
   const bool tc = sizeof(R) == 4 && h->opt.lu_engine == ORAS_LU_AUTO && tc_update_available(h);
-  auto update = [&](const UpdArgs& u) {
+  auto update = [&](const UpdArgs& u, int cls) {
     if (tc) {
-      launch_update_tc(h, u, max_nts);
+      launch_update_tc(h, u, max_nts, cls);
       return;
     }
     int64_t blocks = region_blocks(u, max_nts);
     if (blocks <= 0) return;
     int pb = prof_begin(h);
     k_lu_update<R><<<dim3((unsigned)blocks, m.nsub), 256, smem_u, d.stream>>>(a, u, d.arena);
-    prof_end(h, KC_LU_UPDATE, pb, 1);
+    prof_end(h, cls, pb, 1);
     count_launches(1);
   };
   const int W = h->opt.lu_panel > 0 ? h->opt.lu_panel : 8;  // outer panel width in tile columns
+  auto panel_update = [&](int kk0, int kk1, Region r) {
+    UpdArgs u;
+    u.kk0 = kk0;
+    u.kk1 = kk1;
+    u.nreg = 1;
+    u.reg[0] = r;
+    update(u, KC_LU_PANEL);
+  };
   for (int k0 = 0; k0 < max_nts; k0 += W) {
     const int kend = k0 + W;
     for (int k = k0; k < kend && k < max_nts; ++k) {
@@ -967,16 +989,13 @@ static int lu_run(oras_handle* h) {
       int64_t rows_max = m.max_np - (int64_t)k * TB;
       int nch = (int)((rows_max + CH - 1) / CH);
       int64_t nrem = max_nts - k - 1;
-      if (k > k0) {
-        // left-looking panel step: column k, on and below the diagonal, receives the updates of
-        // the panel's earlier steps just before its pivot search (every row there is in the same
-        // state, so the row interchanges stay consistent)
-        UpdArgs u;
-        u.kk0 = k0;
-        u.kk1 = k;
-        u.nreg = 1;
-        u.reg[0] = {k, INT_MAX, k, k + 1};
-        update(u);
+      const int k1 = k0 + (k - k0) / LU_SUB * LU_SUB;  // first step of the sub-panel
+      if (k > k1) {
+        // left-looking sub-panel step: column k, on and below the diagonal, receives the updates
+        // of the sub-panel's earlier steps just before its pivot search (earlier sub-panels
+        // reached it through their mid updates; every row there is in the same state, so the
+        // row interchanges stay consistent)
+        panel_update(k1, k, {k, INT_MAX, k, k + 1});
       }
       int pb = prof_begin(h);
       if (sizeof(R) == 4)
@@ -987,34 +1006,59 @@ static int lu_run(oras_handle* h) {
       pb = prof_begin(h);
       k_lu_swap<R><<<dim3(max_nts + 1, m.nsub), 256, smem_s, d.stream>>>(a, d.arena);
       prof_end(h, KC_LU_SWAP, pb, 1);
-      if (k > k0) {
-        // the pivot tile row right of column k, from the panel's earlier steps: the rows below
-        // keep those updates deferred (panel columns until their own step, the rest until the
-        // outer update), so a pivot row swapped up from there receives them now
-        UpdArgs u;
-        u.kk0 = k0;
-        u.kk1 = k;
-        u.nreg = 1;
-        u.reg[0] = {k, k + 1, k + 1, INT_MAX};
-        update(u);
+      // the pivot tile row right of column k: the rows below keep updates deferred (the panel's
+      // columns until their sub-panel's mid update or their own step, the rest until the outer
+      // update), so a pivot row swapped up from there receives them now -- inside the panel
+      // from the sub-panel's earlier steps; beyond the panel from all the panel's earlier steps,
+      // here (CUDA-core path) or, on the tensor-core path, for the sub-panel's rows together
+      // after its last step
+      if (tc) {
+        if (k > k1) panel_update(k1, k, {k, k + 1, k + 1, kend});
+      } else if (k > k0) {
+        if (k1 == k0) {
+          panel_update(k0, k, {k, k + 1, k + 1, INT_MAX});
+        } else {
+          if (k > k1) panel_update(k1, k, {k, k + 1, k + 1, kend});
+          panel_update(k0, k, {k, k + 1, kend, INT_MAX});
+        }
       }
       pb = prof_begin(h);
       if (tc) {
-        k_lu_step_inv<R><<<m.nsub, INV_THREADS, smem_i, d.stream>>>(a, d.arena, m.arena_tiles);
-        launch_trsm_tc(h, k, max_nts);
+        k_lu_step_inv<R><<<m.nsub, INV_THREADS, smem_i, d.stream>>>(a, d.arena, m.arena_tiles, k - k1);
+        launch_trsm_tc(h, k, max_nts, true, k + 1, kend, k - k1);
         prof_end(h, KC_LU_TRSM, pb, 2);
       } else {
         k_lu_trsm<R><<<dim3((unsigned)(2 * nrem + 1), m.nsub), TB, smem_r, d.stream>>>(a, d.arena);
         prof_end(h, KC_LU_TRSM, pb, 1);
       }
       count_launches(3);
+      const int kb = k + 1;  // first step after this one
+      if (kb - k1 == LU_SUB || kb == kend || kb == max_nts) {
+        if (tc && kend < max_nts) {
+          // the sub-panel's rows beyond the panel (a blocked triangular solve with the panel's L):
+          // first the contributions of the panel's earlier sub-panels in one product, then row by
+          // row those of the sub-panel's earlier rows and the solve with L_rr^{-1}
+          if (k1 > k0) panel_update(k0, k1, {k1, kb, kend, INT_MAX});
+          for (int r = k1; r < kb; ++r) {
+            if (r > k1) panel_update(k1, r, {r, r + 1, kend, INT_MAX});
+            pb = prof_begin(h);
+            launch_trsm_tc(h, r, max_nts, false, kend, INT_MAX, r - k1);
+            prof_end(h, KC_LU_TRSM, pb, 1);
+          }
+        }
+        if (kb < kend && kb < max_nts) {
+          // mid update: the panel's later columns, for every row below the sub-panel, from the
+          // sub-panel's steps
+          panel_update(k1, kb, {kb, INT_MAX, kb, kend});
+        }
+      }
     }
     UpdArgs u;  // outer update of the trailing matrix
     u.kk0 = k0;
     u.kk1 = kend;
     u.nreg = 1;
     u.reg[0] = {kend, INT_MAX, kend, INT_MAX};
-    update(u);
+    update(u, KC_LU_UPDATE);
   }
   k_gidx<<<(unsigned)((total + 255) / 256), 256, 0, d.stream>>>(total, d.perm, d.sub_np_off, d.sub_ns,
                                                               d.sub_ns_off, d.sub_dofs, m.nsub, d.gidx);

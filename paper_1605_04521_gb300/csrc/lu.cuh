@@ -30,7 +30,9 @@ __host__ __device__ __forceinline__ void region_clip(const Region& r, int64_t nt
 // tensor-core trailing update (lu_tc.cu): returns false when it cannot run (then the caller
 // uses the CUDA-core kernel)
 bool tc_update_available(oras_handle* h);
-int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts);
-int launch_trsm_tc(oras_handle* h, int k, int max_nts);
+int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts, int cls);
+// tile solves of step k with the inverted diagonal blocks in the scratch slots: the tiles below
+// the diagonal (when lower) and row k's tiles in columns [ju0, ju1)
+int launch_trsm_tc(oras_handle* h, int k, int max_nts, bool lower, int ju0, int ju1, int l_slot);
 
 }  // namespace oras

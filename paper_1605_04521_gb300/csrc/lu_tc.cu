@@ -19,6 +19,7 @@
 // bounded; a timeout sets the device status flag.
 #include <cuda.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -286,13 +287,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
 //   right:  U_kJ^T = A_kJ^T L11^{-T}        (A_kJ column-major: its storage rows are the rows of
 //                                            the transpose, K-major; the result lands in the
 //                                            same storage positions)
-// Each CTA takes two tiles of one side (M = 128), N = 64, K = 64, and overwrites them.
+// Each CTA takes two tiles of one side (M = 128), N = 64, K = 64, and overwrites them.  A launch
+// covers the tiles below the diagonal (rows k+1 .. nts-1, when `lower`) and the tiles of row k
+// in columns [ju0, ju1) (clipped to the subdomain).
 struct TrsmArgs {
   const int64_t* np;
   const int64_t* tile_off;
   float* arena;
-  int64_t scratch_base;   // first scratch tile: subdomain s uses scratch_base + 2 s (+0 L^-1, +1 U^-1)
+  int64_t scratch_base;   // first scratch tile: subdomain s uses scratch_base + LU_SCRATCH s + slot
   int k;
+  int l_slot;             // scratch slot of L_kk^{-1} (U_kk^{-1} is in slot LU_SUB)
+  int lower;              // solve the tiles below the diagonal
+  int nbl;                // CTAs of the lower side (the largest subdomain's), the rest take row k
+  int ju0, ju1;           // columns of row k to solve
   int32_t* status;
 };
 
@@ -307,17 +314,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_trsm_tc(const __grid_const
   const int64_t nts = a.np[s] / TB;
   const int k = a.k;
   if (k >= nts) return;
-  const int64_t nrem = nts - k - 1, nb = (nrem + 1) / 2;
   const int64_t b = blockIdx.x;
-  if (b >= 2 * nb) return;
-  const bool lower = b < nb;
-  const int64_t t0 = k + 1 + 2 * (lower ? b : b - nb);
-  const bool two = t0 + 1 < nts;
+  const bool lower = b < a.nbl;
+  int64_t t0, tend;
+  if (lower) {
+    t0 = k + 1 + 2 * b;
+    tend = nts;
+  } else {
+    t0 = a.ju0 + 2 * (b - a.nbl);
+    tend = a.ju1 < nts ? a.ju1 : nts;
+  }
+  if (t0 >= tend) return;
+  const bool two = t0 + 1 < tend;
   const int64_t t1 = two ? t0 + 1 : t0;
   const int64_t toff = a.tile_off[s];
   const int zA0 = (int)(lower ? toff + t0 * nts + k : toff + (int64_t)k * nts + t0);
   const int zA1 = (int)(lower ? toff + t1 * nts + k : toff + (int64_t)k * nts + t1);
-  const int zB = (int)(a.scratch_base + 2 * s + (lower ? 1 : 0));
+  const int zB = (int)(a.scratch_base + (int64_t)LU_SCRATCH * s + (lower ? LU_SUB : a.l_slot));
   unsigned char* st = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -423,7 +436,7 @@ static_assert(sizeof(CUtensorMap) == sizeof(((oras_handle*)nullptr)->tc_map), "t
 static bool make_map(const oras_handle* h, CUtensorMap* map) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
-  const int64_t tiles = h->mesh.arena_tiles + 2 * h->mesh.nsub;
+  const int64_t tiles = h->mesh.arena_tiles + (int64_t)LU_SCRATCH * h->mesh.nsub;
   if (tiles >= (int64_t(1) << 31)) return false;
   cuuint64_t dims[3] = {64, 128, (cuuint64_t)tiles};
   cuuint64_t strides[2] = {64 * sizeof(float), 128 * 64 * sizeof(float)};
@@ -437,7 +450,7 @@ static bool make_map(const oras_handle* h, CUtensorMap* map) {
 
 bool tc_update_available(oras_handle* h) {
   if (h->dev.factor_bits != 32 || !h->dev.arena) return false;
-  const int64_t tiles = h->mesh.arena_tiles + 2 * h->mesh.nsub;
+  const int64_t tiles = h->mesh.arena_tiles + (int64_t)LU_SCRATCH * h->mesh.nsub;
   if (h->tc_map_base != h->dev.arena || h->tc_map_tiles != tiles) {
     CUtensorMap map;
     h->tc_map_ok = make_map(h, &map);
@@ -448,12 +461,14 @@ bool tc_update_available(oras_handle* h) {
   return h->tc_map_ok;
 }
 
-int launch_trsm_tc(oras_handle* h, int k, int max_nts) {
+int launch_trsm_tc(oras_handle* h, int k, int max_nts, bool lower, int ju0, int ju1, int l_slot) {
   const auto& m = h->mesh;
   const auto& d = h->dev;
-  const int64_t nrem = max_nts - k - 1;
-  if (nrem <= 0) return 0;
-  const int64_t blocks = 2 * ((nrem + 1) / 2);
+  const int64_t nbl = lower ? std::max<int64_t>(0, (max_nts - k - 1 + 1) / 2) : 0;
+  const int64_t ue = std::min<int64_t>(ju1, max_nts);
+  const int64_t nbu = ue > ju0 ? (ue - ju0 + 1) / 2 : 0;
+  const int64_t blocks = nbl + nbu;
+  if (blocks <= 0) return 0;
   CUtensorMap map;
   std::memcpy(&map, h->tc_map, sizeof(map));
   TrsmArgs a;
@@ -462,6 +477,11 @@ int launch_trsm_tc(oras_handle* h, int k, int max_nts) {
   a.arena = (float*)d.arena;
   a.scratch_base = m.arena_tiles;
   a.k = k;
+  a.l_slot = l_slot;
+  a.lower = lower ? 1 : 0;
+  a.nbl = (int)nbl;
+  a.ju0 = ju0;
+  a.ju1 = ju1;
   a.status = d.status;
   const size_t smem = (size_t)2 * TRSM_CHUNK_BYTES + 1024;
   allow_max_smem((const void*)k_lu_trsm_tc);
@@ -482,7 +502,7 @@ static int64_t update_blocks(const UpdArgs& u, int max_nts) {
 }
 
 template <int BN>
-static void launch_update_shape(oras_handle* h, const UpdArgs& u, int64_t blocks) {
+static void launch_update_shape(oras_handle* h, const UpdArgs& u, int64_t blocks, int cls) {
   const auto& d = h->dev;
   CUtensorMap map;
   std::memcpy(&map, h->tc_map, sizeof(map));
@@ -496,13 +516,13 @@ static void launch_update_shape(oras_handle* h, const UpdArgs& u, int64_t blocks
   allow_max_smem((const void*)k_lu_update_tc<BN>);
   int pb = prof_begin(h);
   k_lu_update_tc<BN><<<dim3((unsigned)blocks, h->mesh.nsub), TC_THREADS, TcShape<BN>::SMEM, d.stream>>>(map, a);
-  prof_end(h, KC_LU_UPDATE, pb, 1);
+  prof_end(h, cls, pb, 1);
   count_launches(1);
 }
 
 // Regions one tile column wide (the column a left-looking panel step brings up to date) take
 // the 128 x 64 output blocks; wider ones the 128 x 256 blocks.
-int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts) {
+int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts, int cls) {
   int64_t width = 0;
   for (int q = 0; q < u.nreg; ++q) {
     int64_t i0, i1, j0, j1;
@@ -511,10 +531,10 @@ int launch_update_tc(oras_handle* h, const UpdArgs& u, int max_nts) {
   }
   if (width <= 1) {
     const int64_t blocks = update_blocks<1>(u, max_nts);
-    if (blocks > 0) launch_update_shape<1>(h, u, blocks);
+    if (blocks > 0) launch_update_shape<1>(h, u, blocks, cls);
   } else {
     const int64_t blocks = update_blocks<4>(u, max_nts);
-    if (blocks > 0) launch_update_shape<4>(h, u, blocks);
+    if (blocks > 0) launch_update_shape<4>(h, u, blocks, cls);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -258,7 +258,7 @@ def oras_set_timing(h, on):
 
 
 KERNEL_CLASSES = ["element", "global_rows", "local_rows", "lu_tournament", "lu_swap", "lu_trsm",
-                  "lu_update", "apply", "spmv", "orth", "other", "spmv64"]
+                  "lu_update", "apply", "spmv", "orth", "other", "spmv64", "lu_panel"]
 
 
 def oras_timings(h):
@@ -433,15 +433,15 @@ def oras_wait_selftest(h):
     return rc, detail.value
 
 
-AUTOTUNE_WIDTHS = (4, 8, 12, 16, 24, 32, 48)
+AUTOTUNE_WIDTHS = (4, 8, 12, 16, 24, 32, 48, 64)
 
 
 def oras_autotune(h):
     """Returns (panel width chosen, {(width, group): factorisation ms} (empty when cached)).
     The chosen raster group is oras_lu_group(h)."""
     panel = C.c_int32()
-    ms = np.full(10, -1.0)
-    _check(h, lib.oras_autotune(h, C.byref(panel), _ptr(ms), 10))
+    ms = np.full(len(AUTOTUNE_WIDTHS) + 3, -1.0)
+    _check(h, lib.oras_autotune(h, C.byref(panel), _ptr(ms), len(ms)))
     cands = [(w, 8) for w in AUTOTUNE_WIDTHS]
     best_w = max(((w, t) for (w, _), t in zip(cands, ms[:len(AUTOTUNE_WIDTHS)]) if t >= 0), key=lambda x: -x[1],
                  default=(panel.value, 0))[0]

@@ -137,3 +137,13 @@ def test_work_model_closed_forms():
     big = bench.work_model(_FakeLib([12749]), None, 1, 1)[0]
     assert big == pytest.approx(8.0 / 3.0 * 12749 ** 3, rel=0.01)
     assert apply_bytes == pytest.approx(8.0 * sum(n * n for n in sizes) + 3 * 36.0 * sum(sizes))
+
+
+def test_roofline_sums_panel_and_trailing_updates():
+    """The panel updates (class lu_panel) and the trailing updates share one kernel and one flop
+    model: their times add up for the update's achieved rate and for the dominant class."""
+    timings = {"lu_update": (500.0, 20), "lu_panel": (300.0, 400), "apply": (700.0, 17)}
+    dom, rs = bench.roofline(timings, 4e14, 1e9, 1, 6761.6, 1718.2)
+    assert dom == "lu_update"
+    assert abs(rs["lu_update"]["achieved"] - 4e14 / 0.8 / 1e12) < 1e-9
+    assert "lu_panel" not in rs
