@@ -2,9 +2,9 @@
 // P_s A_s = L_s U_s, over the tiled arena (TB x TB complex tiles, split re/im planes, row-major
 // on and below the block diagonal, column-major above it).
 //
-// Blocked LU: right-looking across outer panels W tile columns wide; inside a panel, sub-panels
-// of LU_SUB columns, left-looking inside a sub-panel.  Every tile column k of a panel is
-// processed for all subdomains at once by
+// Blocked LU: right-looking across outer panels W tile columns wide (one trailing update per
+// panel), sub-panels of LU_SUB columns inside a panel, left-looking inside a sub-panel.  Every
+// tile column k is processed for all subdomains at once by
 //  0. bringing column k, on and below the diagonal, up to date with the sub-panel's earlier
 //     steps (C_Ik -= sum_{k1 <= j < k} L_Ij U_jk, k1 the sub-panel's first step: one tile
 //     column written per step, where updating all the sub-panel's remaining columns after
@@ -16,24 +16,27 @@
 //     (communication-avoiding LU, Grigori, Demmel, Xiang 2011);
 //  2. the row interchanges of the step, applied to every column (one permutation of at most
 //     2 TB rows);
-//  3. the pivot tile row, right of column k and inside the panel, receives the updates of the
-//     sub-panel's earlier steps (C_kJ -= sum_{k1 <= j < k} L_kj U_jJ);
-//  4. L21 = A21 U11^{-1} below and U12 = L11^{-1} A12 along the tile row inside the panel.
-// Beyond the panel, the pivot rows of a sub-panel are completed after its last step (a blocked
-// triangular solve with the panel's L): one product brings in the panel's earlier sub-panels
-// (C_kJ -= sum_{k0 <= j < k1} L_kj U_jJ for the sub-panel's rows k), then row by row the
-// sub-panel's earlier rows and U_kJ = L_kk^{-1} C_kJ -- so a pivot row's U beyond the panel
-// re-reads at most LU_SUB - 1 earlier U rows one at a time instead of up to W - 1.  (The
-// CUDA-core path, FP64 factors, does step 3 along the whole row, as in the unblocked form.)
-// After the last step of a sub-panel, a mid update brings the panel's later columns, for every
-// row below, up to date with the sub-panel (C_IJ -= sum_{k1 <= j < k1 + LU_SUB} L_Ij U_jJ, I, J
-// past the sub-panel, J inside the panel): the left-looking steps then reach back LU_SUB - 1
-// columns at most instead of W - 1, which bounds the panel's re-reads of its own L columns.
+//  3. the pivot tile row, right of column k, receives the updates it still lacks
+//     (C_kJ -= sum_j L_kj U_jJ over the steps listed below);
+//  4. L21 = A21 U11^{-1} below and U12 = L11^{-1} A12 along (part of) the tile row.
+// Tensor-core path (FP32 factors).  At a sub-panel's start its LU_SUB columns, for every row from
+// k1 down, receive the updates of the panel's earlier sub-panels in one contraction (the
+// sub-panel level is left-looking too); steps 3-4 cover the pivot row inside the sub-panel
+// only; after the sub-panel's last step its rows are completed right of it by a blocked
+// triangular solve with the panel's L: one product brings in the panel's earlier sub-panels,
+// then row by row the sub-panel's earlier rows and U_kJ = L_kk^{-1} C_kJ (the sub-panel's
+// L_kk^{-1} wait in scratch tiles for this).  A pivot row thus re-reads at most LU_SUB - 1
+// earlier U rows one at a time instead of up to W - 1, and the left-looking steps at most
+// LU_SUB - 1 earlier L columns.
+// CUDA-core path (FP64 factors, or the CUDA-core engine).  After a sub-panel's last step a mid
+// update brings the panel's later columns, for every row below, up to date with the sub-panel;
+// step 3 covers the pivot row inside the panel from the sub-panel's earlier steps and beyond it
+// from all the panel's earlier steps; step 4 the whole row.
 // After the W columns of a panel, the trailing matrix gets one update with a W-tile-deep
 // contraction, C_IJ -= sum_k L_Ik U_kJ, which reads and writes every trailing tile once per
 // panel instead of once per column.  Right of column k, every row not yet a pivot row is in
-// one common state (the panel's start beyond the panel, the last mid update inside it) until
-// then, so a row interchange never mixes rows that have received different updates.
+// one common state until then, so a row interchange never mixes rows that have received
+// different updates.
 // The tree merge uses "last arriver continues" counters, so no block ever waits for another.
 #include <algorithm>
 #include <climits>
@@ -989,12 +992,17 @@ static int lu_run(oras_handle* h) {
       int64_t rows_max = m.max_np - (int64_t)k * TB;
       int nch = (int)((rows_max + CH - 1) / CH);
       int64_t nrem = max_nts - k - 1;
-      const int k1 = k0 + (k - k0) / LU_SUB * LU_SUB;  // first step of the sub-panel
+      const int k1 = k0 + (k - k0) / LU_SUB * LU_SUB;                    // first step of the sub-panel
+      const int ks = std::min(std::min(k1 + LU_SUB, kend), max_nts);     // first step after it
+      if (tc && k == k1 && k1 > k0) {
+        // sub-panel start (tensor-core path): its columns, for every row from k1 down, receive
+        // the updates of the panel's earlier sub-panels in one contraction
+        panel_update(k0, k1, {k1, INT_MAX, k1, ks});
+      }
       if (k > k1) {
         // left-looking sub-panel step: column k, on and below the diagonal, receives the updates
-        // of the sub-panel's earlier steps just before its pivot search (earlier sub-panels
-        // reached it through their mid updates; every row there is in the same state, so the
-        // row interchanges stay consistent)
+        // of the sub-panel's earlier steps just before its pivot search (every row there is in
+        // the same state, so the row interchanges stay consistent)
         panel_update(k1, k, {k, INT_MAX, k, k + 1});
       }
       int pb = prof_begin(h);
@@ -1006,14 +1014,14 @@ static int lu_run(oras_handle* h) {
       pb = prof_begin(h);
       k_lu_swap<R><<<dim3(max_nts + 1, m.nsub), 256, smem_s, d.stream>>>(a, d.arena);
       prof_end(h, KC_LU_SWAP, pb, 1);
-      // the pivot tile row right of column k: the rows below keep updates deferred (the panel's
-      // columns until their sub-panel's mid update or their own step, the rest until the outer
-      // update), so a pivot row swapped up from there receives them now -- inside the panel
-      // from the sub-panel's earlier steps; beyond the panel from all the panel's earlier steps,
-      // here (CUDA-core path) or, on the tensor-core path, for the sub-panel's rows together
-      // after its last step
+      // the pivot tile row right of column k: the rows below keep updates deferred, so a pivot
+      // row swapped up from there receives them now.  Tensor-core path: inside the sub-panel from
+      // its earlier steps (the rest of the row is solved with the sub-panel's other rows after
+      // its last step).  CUDA-core path: inside the panel from the sub-panel's earlier steps
+      // (earlier sub-panels reached it through their mid updates), beyond the panel from all the
+      // panel's earlier steps.
       if (tc) {
-        if (k > k1) panel_update(k1, k, {k, k + 1, k + 1, kend});
+        if (k > k1 && k + 1 < ks) panel_update(k1, k, {k, k + 1, k + 1, ks});
       } else if (k > k0) {
         if (k1 == k0) {
           panel_update(k0, k, {k, k + 1, k + 1, INT_MAX});
@@ -1025,30 +1033,30 @@ static int lu_run(oras_handle* h) {
       pb = prof_begin(h);
       if (tc) {
         k_lu_step_inv<R><<<m.nsub, INV_THREADS, smem_i, d.stream>>>(a, d.arena, m.arena_tiles, k - k1);
-        launch_trsm_tc(h, k, max_nts, true, k + 1, kend, k - k1);
+        launch_trsm_tc(h, k, max_nts, true, k + 1, ks, k - k1);
         prof_end(h, KC_LU_TRSM, pb, 2);
       } else {
         k_lu_trsm<R><<<dim3((unsigned)(2 * nrem + 1), m.nsub), TB, smem_r, d.stream>>>(a, d.arena);
         prof_end(h, KC_LU_TRSM, pb, 1);
       }
       count_launches(3);
-      const int kb = k + 1;  // first step after this one
-      if (kb - k1 == LU_SUB || kb == kend || kb == max_nts) {
-        if (tc && kend < max_nts) {
-          // the sub-panel's rows beyond the panel (a blocked triangular solve with the panel's L):
+      const int kb = k + 1;
+      if (kb == ks) {  // the sub-panel's last step
+        if (tc && kb < max_nts) {
+          // the sub-panel's rows right of it (a blocked triangular solve with the panel's L):
           // first the contributions of the panel's earlier sub-panels in one product, then row by
           // row those of the sub-panel's earlier rows and the solve with L_rr^{-1}
-          if (k1 > k0) panel_update(k0, k1, {k1, kb, kend, INT_MAX});
+          if (k1 > k0) panel_update(k0, k1, {k1, kb, kb, INT_MAX});
           for (int r = k1; r < kb; ++r) {
-            if (r > k1) panel_update(k1, r, {r, r + 1, kend, INT_MAX});
+            if (r > k1) panel_update(k1, r, {r, r + 1, kb, INT_MAX});
             pb = prof_begin(h);
-            launch_trsm_tc(h, r, max_nts, false, kend, INT_MAX, r - k1);
+            launch_trsm_tc(h, r, max_nts, false, kb, INT_MAX, r - k1);
             prof_end(h, KC_LU_TRSM, pb, 1);
           }
         }
-        if (kb < kend && kb < max_nts) {
-          // mid update: the panel's later columns, for every row below the sub-panel, from the
-          // sub-panel's steps
+        if (!tc && kb < kend && kb < max_nts) {
+          // mid update (CUDA-core path): the panel's later columns, for every row below the
+          // sub-panel, from the sub-panel's steps
           panel_update(k1, kb, {kb, INT_MAX, kb, kend});
         }
       }
