@@ -258,7 +258,7 @@ def apply_group_sizes(k, factor_bits, tensor_cores=False):
 
 TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 # the LU schedule and update kernel the committed counters must have been taken on
-UPDATE_VERSION = "tcgen05 update with 128x256 and 128x64 blocks, left-looking panel steps"
+UPDATE_VERSION = "tcgen05 update with 128x256 and 128x64 blocks, sub-panel schedule (left-looking sub-panels of 8 steps)"
 
 
 def measured_traffic(kernel, workload, panel):
@@ -629,9 +629,9 @@ def run_ours(args, world, rank, local):
                                   "a factorisation, from the ncu capture recorded in profiles/roofline_traffic.json")
         else:
             ru["traffic_note"] = ("null: the update's DRAM traffic is captured on the 8^3 profile workload at panel width "
-                                  "24 (profiles/k_lu_update_tc_head8_r2.md: 165 MB per launch, 8.1e-3 B/flop); it does "
-                                  "not grow in proportion to the flops between workloads (the left-looking column "
-                                  "updates re-read the panel), so it is not scaled to this one")
+                                  "24 (profiles/k_lu_update_tc_head8.md, profiles/roofline_traffic.json); it does not "
+                                  "grow in proportion to the flops between workloads (the panel updates re-read the "
+                                  "panel's own rows and columns), so it is not scaled to this one")
     if "apply" in roofs and tc_apply:
         roofs["apply"]["kernel"] = ("k_apply_tc (ORAS preconditioner, tcgen05 kind::tf32 products, up to 32 "
                                     "right-hand sides per arena pass)")
