@@ -780,16 +780,17 @@ __global__ void k_gidx(int64_t total, const int32_t* perm, const int64_t* np_off
 // substitution steps of the preconditioner apply become tile matrix-vector products like the
 // off-diagonal ones (block substitution with inverted diagonal blocks).
 // Inverts a factored diagonal block held column-major (padded) in D: X[0] gets the columns of
-// L^{-1} (unit lower), X[1] those of U^{-1}.  One warp per column (warps take the 2 TB columns
-// in turn), lanes own rows lane and lane + 32; column-oriented substitution, the pivot entry
-// broadcast by shuffle at each step:
+// L^{-1} (unit lower), X[1] those of U^{-1}.  Tasks [task0, task1) of the 2 TB columns (L's
+// columns first), one warp per column in turn; lanes own rows lane and lane + 32; column-oriented
+// substitution, the pivot entry broadcast by shuffle at each step, with the reciprocals of U's
+// diagonal precomputed in rd:
 //   L x = e_t:  x = e_t; for l = t .. TB-2:  x_i -= L(i,l) x_l  (i > l)
-//   U x = e_j:  b = e_j; for l = j .. 0:     x_l = b_l / U(l,l);  b_i -= U(i,l) x_l  (i < l)
+//   U x = e_j:  b = e_j; for l = j .. 0:     x_l = b_l rd_l;  b_i -= U(i,l) x_l  (i < l)
 template <typename R>
-__device__ void invert_block(const CT<R>* D, CT<R>* X) {
+__device__ void invert_block(const CT<R>* D, const CT<R>* rd, CT<R>* X, int task0, int task1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int i0 = lane, i1 = lane + 32;
-  for (int task = warp; task < 2 * TB; task += nw) {
+  for (int task = task0 + warp; task < task1; task += nw) {
     if (task < TB) {
       const int t = task;
       CT<R> x0 = {R(i0 == t ? 1 : 0), R(0)}, x1 = {R(i1 == t ? 1 : 0), R(0)};
@@ -807,7 +808,7 @@ __device__ void invert_block(const CT<R>* D, CT<R>* X) {
       for (int l = j; l >= 0; --l) {
         const CT<R> own = l < 32 ? b0 : b1;
         const CT<R> bl = {__shfl_sync(0xffffffffu, own.re, l & 31), __shfl_sync(0xffffffffu, own.im, l & 31)};
-        const CT<R> xl = mulc(bl, invc(D[l * PS + l]));
+        const CT<R> xl = mulc(bl, rd[l]);
         if (i0 < l) b0 = subc(b0, mulc(D[l * PS + i0], xl));
         else if (i0 == l) b0 = xl;
         if (i1 < l) b1 = subc(b1, mulc(D[l * PS + i1], xl));
@@ -821,19 +822,29 @@ __device__ void invert_block(const CT<R>* D, CT<R>* X) {
 
 // Stores L^{-1} with row-major planes at Li and U^{-1} at Ui, with row-major planes when
 // u_rowmajor (the preconditioner apply) or column-major planes (the B operand of the tensor-core
-// tile solves, K-major along the row index).
+// tile solves, K-major along the row index).  A null pointer skips that factor.
 template <typename R>
 __device__ void store_inverses(const CT<R>* X, R* Li, R* Ui, bool u_rowmajor) {
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
     const int hi = e / TB, lo = e % TB;
-    const CT<R> l = X[lo * PS + hi];                // Linv(i = hi, j = lo): row-major storage
-    const CT<R> u = u_rowmajor ? X[TB * PS + lo * PS + hi]   // Uinv(i = hi, j = lo)
-                               : X[TB * PS + hi * PS + lo];  // Uinv(i = lo, j = hi)
-    Li[e] = l.re;
-    Li[TILE_PLANE + e] = l.im;
-    Ui[e] = u.re;
-    Ui[TILE_PLANE + e] = u.im;
+    if (Li) {
+      const CT<R> l = X[lo * PS + hi];                // Linv(i = hi, j = lo): row-major storage
+      Li[e] = l.re;
+      Li[TILE_PLANE + e] = l.im;
+    }
+    if (Ui) {
+      const CT<R> u = u_rowmajor ? X[TB * PS + lo * PS + hi]   // Uinv(i = hi, j = lo)
+                                 : X[TB * PS + hi * PS + lo];  // Uinv(i = lo, j = hi)
+      Ui[e] = u.re;
+      Ui[TILE_PLANE + e] = u.im;
+    }
   }
+}
+
+// reciprocals of the diagonal of the factored block in D
+template <typename R>
+__device__ __forceinline__ void diag_reciprocals(const CT<R>* D, CT<R>* rd) {
+  if (threadIdx.x < TB) rd[threadIdx.x] = invc(D[threadIdx.x * PS + threadIdx.x]);
 }
 
 // Inverses of the diagonal blocks of the factors: Linv_I = L_II^{-1} (unit lower) and
@@ -845,6 +856,7 @@ __global__ void __launch_bounds__(INV_THREADS) k_lu_diag_inv(LuArgs a, void* are
   extern __shared__ unsigned char smem_raw[];
   CT<R>* D = (CT<R>*)smem_raw;  // [TB][PS]: D[j*PS+i] = LU(i,j)
   CT<R>* X = D + TB * PS;       // [2][TB][PS]
+  CT<R>* rd = X + 2 * TB * PS;  // [TB]
   const int s = blockIdx.y;
   const int64_t nts = a.np[s] / TB;
   const int64_t I = blockIdx.x;
@@ -855,7 +867,9 @@ __global__ void __launch_bounds__(INV_THREADS) k_lu_diag_inv(LuArgs a, void* are
     D[j * PS + i] = tload<R>(T, true, i, j);
   }
   __syncthreads();
-  invert_block<R>(D, X);
+  diag_reciprocals<R>(D, rd);
+  __syncthreads();
+  invert_block<R>(D, rd, X, 0, 2 * TB);
   __syncthreads();
   R* Li = (R*)inv + (inv_off[s] + I) * 4 * TILE_PLANE;
   store_inverses<R>(X, Li, Li + 2 * TILE_PLANE, true);
@@ -893,13 +907,15 @@ __global__ void __launch_bounds__(256) k_lu_upper_rowmajor(LuArgs a, void* arena
 // The step's factored diagonal block (from the tournament root): written to tile (k, k) and
 // inverted into the subdomain's scratch tiles for the tensor-core triangular solves: L_kk^{-1}
 // into slot `slot` (kept until the sub-panel's rows are solved beyond the panel), U_kk^{-1}
-// into slot LU_SUB.
+// into slot LU_SUB.  Two blocks per subdomain (blockIdx.x): 0 inverts L and writes the tile,
+// 1 inverts U.
 template <typename R>
 __global__ void __launch_bounds__(INV_THREADS) k_lu_step_inv(LuArgs a, void* arena, int64_t scratch_base, int slot) {
   extern __shared__ unsigned char smem_raw[];
   CT<R>* D = (CT<R>*)smem_raw;  // [TB][PS]
   CT<R>* X = D + TB * PS;       // [2][TB][PS]
-  const int s = blockIdx.x;
+  CT<R>* rd = X + 2 * TB * PS;  // [TB]
+  const int s = blockIdx.y, half = blockIdx.x;
   const int64_t nts = a.np[s] / TB;
   const int k = a.k;
   if (k >= nts) return;
@@ -908,14 +924,16 @@ __global__ void __launch_bounds__(INV_THREADS) k_lu_step_inv(LuArgs a, void* are
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
     const CT<R> v = dg[e];
     D[(e / TB) * PS + (e % TB)] = v;
-    tstore<R>(dst, true, e % TB, e / TB, v);
+    if (half == 0) tstore<R>(dst, true, e % TB, e / TB, v);
   }
   __syncthreads();
-  invert_block<R>(D, X);
+  if (half == 1) diag_reciprocals<R>(D, rd);
+  __syncthreads();
+  invert_block<R>(D, rd, X, half * TB, (half + 1) * TB);
   __syncthreads();
   R* Li = (R*)arena + (scratch_base + (int64_t)LU_SCRATCH * s + slot) * 2 * TILE_PLANE;
   R* Ui = (R*)arena + (scratch_base + (int64_t)LU_SCRATCH * s + LU_SUB) * 2 * TILE_PLANE;
-  store_inverses<R>(X, Li, Ui, false);
+  store_inverses<R>(X, half == 0 ? Li : nullptr, half == 1 ? Ui : nullptr, false);
 }
 
 // number of output tiles of the update regions for the largest subdomain
@@ -961,7 +979,7 @@ static int lu_run(oras_handle* h) {
   allow_max_smem((const void*)k_lu_swap<R>);
   allow_max_smem((const void*)k_lu_trsm<R>);
   allow_max_smem((const void*)k_lu_update<R>);
-  const size_t smem_i = (size_t)3 * TB * PS * sizeof(CT<R>);
+  const size_t smem_i = ((size_t)3 * TB * PS + TB) * sizeof(CT<R>);
   allow_max_smem((const void*)k_lu_step_inv<R>);
   const bool tc = sizeof(R) == 4 && h->opt.lu_engine == ORAS_LU_AUTO && tc_update_available(h);
   auto update = [&](const UpdArgs& u, int cls) {
@@ -1032,7 +1050,7 @@ static int lu_run(oras_handle* h) {
       }
       pb = prof_begin(h);
       if (tc) {
-        k_lu_step_inv<R><<<m.nsub, INV_THREADS, smem_i, d.stream>>>(a, d.arena, m.arena_tiles, k - k1);
+        k_lu_step_inv<R><<<dim3(2, m.nsub), INV_THREADS, smem_i, d.stream>>>(a, d.arena, m.arena_tiles, k - k1);
         launch_trsm_tc(h, k, max_nts, true, k + 1, ks, k - k1);
         prof_end(h, KC_LU_TRSM, pb, 2);
       } else {
