@@ -57,8 +57,10 @@ def boundary_face_list(topo: Topology):
     return bf, t, lf
 
 
-def global_matrix(topo: Topology, xyz, eps_r, mu_r, k0, beta_lf=None):
-    """beta_lf: [T, 4] beta per sorted local face (face_beta_table) or None (derived)."""
+def global_matrix(topo: Topology, xyz, eps_r, mu_r, k0, beta_lf=None, mask=None):
+    """beta_lf: [T, 4] beta per sorted local face (face_beta_table) or None (derived).  mask:
+    Boolean [ndof] of the degrees of freedom constrained by metallic faces (oracle.ports), whose
+    rows and columns become identity rows and columns."""
     AT = elements.element_matrices(xyz, topo.st, topo.r, eps_r, mu_r, k0)
     bf, bt, blf = boundary_face_list(topo)
     if len(bf):
@@ -71,6 +73,9 @@ def global_matrix(topo: Topology, xyz, eps_r, mu_r, k0, beta_lf=None):
     A = sp.coo_matrix((AT.ravel(), (rows, cols)), shape=(topo.ndof, topo.ndof)).tocsr()
     A.sum_duplicates()
     A.sort_indices()
+    if mask is not None and mask.any():
+        from .ports import constrain
+        A = constrain(A, mask)
     return A
 
 

@@ -122,9 +122,11 @@ def decompose(topo: Topology, xyz, nsub, delta, part=None, kind="vertex") -> Dec
     return Decomposition(part=part, tets=tets, dofs=dofs, pou=pou, owner=owner, iface=iface)
 
 
-def local_matrix(topo: Topology, xyz, eps_r, mu_r, k0, dec: Decomposition, s, beta_lf=None):
+def local_matrix(topo: Topology, xyz, eps_r, mu_r, k0, dec: Decomposition, s, beta_lf=None, mask=None):
     """Dense A_s: element terms of Omega_s^delta + outer impedance (beta of the caller's table
-    beta_lf [T, 4] when given) + interface impedance (omega~ of the inside tetrahedron)."""
+    beta_lf [T, 4] when given) + interface impedance (omega~ of the inside tetrahedron).  mask:
+    Boolean [ndof] of the degrees of freedom constrained by metallic faces: their local rows and
+    columns become identity rows and columns (the local problem posed on V, Sec. 2)."""
     Ns = dec.dofs[s]
     ts = dec.tets[s]
     n = len(Ns)
@@ -151,6 +153,11 @@ def local_matrix(topo: Topology, xyz, eps_r, mu_r, k0, dec: Decomposition, s, be
         lt = np.searchsorted(Ns, topo.dofmap[np.array(ft_t)])
         for q in range(len(ft_t)):
             A[np.ix_(lt[q], lt[q])] += 1j * coef[q] * S[q]
+    if mask is not None:
+        fixed = np.nonzero(mask[Ns])[0]
+        A[fixed, :] = 0.0
+        A[:, fixed] = 0.0
+        A[fixed, fixed] = 1.0
     return A
 
 
@@ -168,7 +175,7 @@ class ORAS:
     (RAS), which needs the global matrix A_global."""
 
     def __init__(self, topo, xyz, eps_r, mu_r, k0, dec: Decomposition, weights="pou",
-                 transmission="impedance", A_global=None, beta_lf=None):
+                 transmission="impedance", A_global=None, beta_lf=None, mask=None):
         self.dec = dec
         self.n = topo.ndof
         self.lu = []
@@ -176,7 +183,7 @@ class ORAS:
             if transmission == "dirichlet":
                 A = restricted_matrix(A_global, dec, s)
             else:
-                A = local_matrix(topo, xyz, eps_r, mu_r, k0, dec, s, beta_lf)
+                A = local_matrix(topo, xyz, eps_r, mu_r, k0, dec, s, beta_lf, mask)
             self.lu.append(sla.lu_factor(A, check_finite=False))
         self.weights = weights
 

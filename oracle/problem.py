@@ -6,7 +6,7 @@ from dataclasses import dataclass
 import numpy as np
 import scipy.sparse.linalg as spla
 
-from . import assemble, dd, fgmres, topology
+from . import assemble, dd, fgmres, ports, topology
 
 
 @dataclass
@@ -22,26 +22,37 @@ class OracleProblem:
     B: np.ndarray          # [N, k]
     dec: object = None
     oras: object = None
+    mask: object = None    # degrees of freedom constrained by metallic faces (or None)
 
 
 def build(xyz, tets, eps_r, mu_r, k0, r, sources, nsub=None, delta=None, part=None,
-          with_oras=True, beta_face=None):
+          with_oras=True, beta_face=None, face_kind=None):
     """beta_face: [T, 4] impedance coefficients on the face opposite the caller's vertex
-    tets[t, q] (outer faces only), or None (derived from the materials)."""
+    tets[t, q] (outer faces only), or None (derived from the materials).  face_kind: [T, 4] on
+    the same faces, 1 = metallic (E x n = 0), 0 = impedance, or None.  sources: ("plane", d, p),
+    ("dipole", x0, dir) or ("port", oracle.ports.Port, None)."""
     topo = topology.build(tets, xyz.shape[0], r)
     beta_lf = None if beta_face is None else assemble.face_beta_table(tets, beta_face)
-    A = assemble.global_matrix(topo, xyz, eps_r, mu_r, k0, beta_lf)
+    mask = None
+    if face_kind is not None:
+        mask = ports.constrained_dofs(topo, xyz, ports.face_kind_table(tets, face_kind))
+    A = assemble.global_matrix(topo, xyz, eps_r, mu_r, k0, beta_lf, mask)
     cols = []
     for kind, a, b in sources:
         if kind == "plane":
-            cols.append(assemble.plane_wave_load(topo, xyz, eps_r, mu_r, k0, a, b, beta_lf=beta_lf))
+            col = assemble.plane_wave_load(topo, xyz, eps_r, mu_r, k0, a, b, beta_lf=beta_lf)
+        elif kind == "port":
+            col = ports.port_load(topo, xyz, mu_r, a)
         else:
-            cols.append(assemble.dipole_load(topo, xyz, a, b))
+            col = assemble.dipole_load(topo, xyz, a, b)
+        if mask is not None:
+            col[mask] = 0.0
+        cols.append(col)
     B = np.stack(cols, axis=1) if cols else np.zeros((topo.ndof, 0), dtype=np.complex128)
-    prob = OracleProblem(xyz, tets, eps_r, mu_r, k0, r, topo, A, B)
+    prob = OracleProblem(xyz, tets, eps_r, mu_r, k0, r, topo, A, B, mask=mask)
     if with_oras and nsub is not None:
         prob.dec = dd.decompose(topo, xyz, nsub, delta, part)
-        prob.oras = dd.ORAS(topo, xyz, eps_r, mu_r, k0, prob.dec, beta_lf=beta_lf)
+        prob.oras = dd.ORAS(topo, xyz, eps_r, mu_r, k0, prob.dec, beta_lf=beta_lf, mask=mask)
     return prob
 
 
