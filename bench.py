@@ -73,6 +73,9 @@ def parse():
                     help="where the nvidia-smi clock samples of the timed region are written (default: the temp dir)")
     ap.add_argument("--factor-bits", type=int, default=0, choices=[0, 32, 64],
                     help="local factor precision (0: the workload's; 64: the plain FP64 path)")
+    ap.add_argument("--ports", type=int, default=1,
+                    help="1: also time the 16-port chamber on the 16^3 mesh (metallic bottom, 16 ports "
+                         "transmitting together, 16 x 16 scattering matrix, Sec. 5.1)")
     ap.add_argument("--fp64-path", type=int, default=1,
                     help="1: also time the plain FP64 single-RHS path against the FP32-factor path on the "
                          "workloads where the FP64 factorisation finishes (head8, cube8)")
@@ -459,6 +462,86 @@ def serving_replay(O, count, slots, device=0, max_iter=60):
             "continuous_batching": mix, "sequential_one_slot": seq}
 
 
+# ------------------------------------------------------------------ ports and scattering matrix
+def chamber_ports(beta):
+    """16 ports of 0.5 x 0.5 on the four side faces of the unit cube (a 2 x 2 grid on each face),
+    the TE10 mode pointing up (z): a synthetic stand-in for the antenna rings of Sec. 5."""
+    out = []
+    for z0 in (0.0, 0.5):
+        for c0 in (0.0, 0.5):
+            out.append(((0.0, c0, z0), (0.0, 0.5, 0.0), (0.0, 0.0, 0.5)))
+            out.append(((1.0, c0, z0), (0.0, 0.5, 0.0), (0.0, 0.0, 0.5)))
+            out.append(((c0, 0.0, z0), (0.5, 0.0, 0.0), (0.0, 0.0, 0.5)))
+            out.append(((c0, 1.0, z0), (0.5, 0.0, 0.0), (0.0, 0.0, 0.5)))
+    return [(o, u, v, beta) for o, u, v in out]
+
+
+def ports_measure(O, dev, stream, steps=1, warmup=1):
+    """The 16^3 benchmark mesh and medium with a metallic bottom (Sec. 2 eq. metallicbc) and 16
+    ports on the side faces (Silver-Mueller condition, eq. wgi, with the TE10 wavenumber of a
+    ceramic-filled guide of width 0.5).  One step = oras_factor + oras_solve of the 16 port loads
+    together (each port transmitting, eq. wgj), CUDA events on the handle's stream; then the 16 x 16
+    scattering matrix (eq. sij) of the fields, timed as a host call (port selection, copy of the
+    fields, device integrals and fixed-order sums), and its reciprocity error ||S - S^T|| / ||S||
+    (A = A^T and equal ports make S symmetric)."""
+    import torch
+    w = workload("head16")
+    xyz, tets = w.mesh()
+    eps, mu = w.materials(xyz, tets)
+    nt = len(tets)
+    beta_p = float(np.sqrt(w.k0 ** 2 * 59.0 - (np.pi / 0.5) ** 2))
+    kind = np.zeros((nt, 4), dtype=np.uint8)
+    for q in range(4):  # the face opposite vertex q lies in z = 0
+        others = np.stack([xyz[tets[:, j], 2] for j in range(4) if j != q], axis=1)
+        kind[np.all(np.abs(others) < 1e-12, axis=1), q] = O.ORAS_FACE_METALLIC
+    beta = np.full((nt, 4), beta_p)
+    ps = [O.port(*a) for a in chamber_ports(beta_p)]
+    h = O.oras_create(xyz, tets, w.r, w.nsub, w.overlap, beta_face=beta, face_kind=kind, restart=w.restart)
+    try:
+        O.oras_set_stream(h, stream.cuda_stream)
+        eps_d = torch.from_numpy(eps).to(dev)
+        mu_d = torch.from_numpy(mu).to(dev)
+        O.oras_factor(h, eps_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
+        O.oras_autotune(h)
+        n = O.oras_ndof(h)
+        B = np.stack([O.oras_rhs_port(h, p) for p in ps], axis=1)
+        k = B.shape[1]
+        Bd = torch.from_numpy(np.ascontiguousarray(B.T)).to(dev)      # column-major N x k
+        Xd = torch.empty_like(Bd)
+        info = None
+
+        def one():
+            O.oras_factor(h, eps_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
+            _, inf, rc = O.oras_solve(h, Bd, w.tol, k=k, mem=O.ORAS_MEM_DEVICE, out=Xd)
+            if rc != O.ORAS_OK:
+                raise RuntimeError("port solve did not converge")
+            return inf
+        for _ in range(warmup):
+            one()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            info = one()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        X = Xd.cpu().numpy().T
+        t0 = time.perf_counter()
+        S = O.oras_s_matrix(h, ps, X)
+        s_ms = (time.perf_counter() - t0) * 1e3
+        return {"workload": "16^3 x 6 tets, r = 2, 64 subdomains, 2 layers, head-like medium; metallic bottom; "
+                            "16 ports of 0.5 x 0.5 on the side faces, beta = %.3f" % beta_p,
+                "ndof": n, "rhs": k, "solves_per_s": k * 1e3 / ms, "ms_per_step": ms,
+                "iterations_max": max(i["iterations"] for i in info),
+                "worst_true_relres": max(i["relres"] for i in info),
+                "s_matrix_ms": s_ms, "reciprocity_error": O.oras_s_error(S, S.T),
+                "s_diag_mean_abs": float(np.abs(np.diag(S)).mean()),
+                "s_offdiag_max_abs": float(np.abs(S - np.diag(np.diag(S))).max())}
+    finally:
+        O.oras_destroy(h)
+
+
 # ------------------------------------------------------------------ plain FP64 path
 def fp64_path(O, dev, stream, steps=2, warmup=1):
     """The plain FP64 single-right-hand-side GPU path (FP64 local factors, CUDA-core FP64 LU,
@@ -658,6 +741,12 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(time.perf_counter() - e0, world)
     e2e_val = world * e2e_steps * krhs / e2e_s
+    port_res = None
+    if rank == 0 and args.ports:
+        try:
+            port_res = ports_measure(O, dev, stream)
+        except Exception as e:  # noqa: BLE001
+            port_res = {"error": f"{type(e).__name__}: {e}"}
     fp64 = None
     if rank == 0 and args.fp64_path:
         try:
@@ -701,6 +790,7 @@ def run_ours(args, world, rank, local):
                     "path": "oras_setup (host mesh + materials) + oras_solve (host rhs -> host x) + oras_destroy"},
             "gpu_launches": int(launches),
             "fp64_path": fp64,
+            "ports": port_res,
             "serving": serving,
             "clocks": clk,
             "peaks": {"hbm_gbs": hbm, "bf16_tflops": bf16, "bf16_tflops_sustained": bf16_sus, "source": src},

@@ -99,7 +99,18 @@ typedef struct {
                               /*   later oras_factor of the handle.  NULL: beta = k0       */
                               /*   sqrt(Re mu_r Re eps_r) of the adjacent tetrahedron,     */
                               /*   from the materials of each oras_factor                  */
+  const uint8_t* face_kind;   /* [nt][4] boundary condition on the same faces as beta_face: */
+                              /*   ORAS_FACE_IMPEDANCE (0) or ORAS_FACE_METALLIC (1, E x n  */
+                              /*   = 0 on Gamma_w, Sec. 2 eq. metallicbc; outer faces only).*/
+                              /*   NULL: every outer face is an impedance face              */
 } oras_problem;
+
+/* Boundary condition of an outer face (oras_problem.face_kind).  On metallic faces the
+ * degrees of freedom whose basis functions have a nonzero tangential trace there (those of the
+ * face's edges and of the face) are constrained to zero: their rows and columns of A and of
+ * every A_s become identity rows and columns, right-hand sides are zero there (oras_solve zeroes
+ * them), and beta_face is not read for those faces. */
+enum { ORAS_FACE_IMPEDANCE = 0, ORAS_FACE_METALLIC = 1 };
 
 /* Solver options.  Zero-initialised fields take the defaults given in brackets. */
 typedef struct {
@@ -147,7 +158,7 @@ typedef struct {
 const char* oras_last_error(const oras_handle* h);
 
 /* Version of the ABI described here.  No counterpart in the paper.  Never fails. */
-int32_t oras_abi_version(void);  /* 2: oras_problem.beta_face, oras_options.wait_ms */
+int32_t oras_abi_version(void);  /* 3: oras_problem.face_kind, ports (2: beta_face, wait_ms) */
 
 /* ---------------------------------------------------------------- set-up */
 
@@ -157,7 +168,8 @@ int32_t oras_abi_version(void);  /* 2: oras_problem.beta_face, oras_options.wait
  * R_s), Boolean partition of unity D_s (sum_s R_s^T D_s R_s = I), interface faces and the
  * CSR pattern of A.  p->eps_r, p->mu_r, p->k0 are ignored here.
  * Errors: INVALID_ARG (r not in 1..3, nsub < 1 or > nt, overlap < 0, NULL arrays, a
- * beta_face entry of an outer face that is not finite and > 0),
+ * beta_face entry of an outer impedance face that is not finite and > 0, a face_kind entry
+ * that is not 0 or 1, or 1 on an interior face),
  * BAD_MESH (vertex id out of range, repeated vertex, zero-volume tetrahedron, part entry
  * out of range), UNSUPPORTED (more than 2^31-1 DOFs or 2^21 vertices). */
 int oras_create(const oras_problem* p, const oras_options* o, oras_handle** out);
@@ -230,6 +242,48 @@ int oras_rhs_plane_wave(oras_handle* h, const double* d, const oras_complex* p, 
 int oras_rhs_dipole(oras_handle* h, const double* x0, const double* dir, oras_complex* b,
                     int32_t mem);
 
+/* ---------------------------------------------------------------- waveguide ports (Sec. 2, 5)
+ * A rectangular port on the outer boundary: the rectangle {origin + s u + t v : s, t in
+ * [0, 1]}, u and v orthogonal, lying in the plane of the outer faces it covers.  Its faces are
+ * the outer faces whose centroid ((x0 + x1) + x2) / 3 (vertices in ascending id order) lies in
+ * the rectangle: 0 <= s, t <= 1 and distance to its plane at most 1e-9 (|u| + |v|).  Its
+ * fundamental TE10 mode is E0(x) = sin(pi s) v / |v|, s = (x - origin) . u / |u|^2; beta > 0 is
+ * the propagation wavenumber along the waveguide (give the same beta to the port's faces in
+ * oras_problem.beta_face for the Silver-Mueller condition of eq. wgi).  Face integrals use the
+ * collapsed Gauss-Legendre product rule with 12 x 12 points per face. */
+typedef struct {
+  double origin[3];
+  double u[3];                /* width edge: the mode varies as sin(pi s) along it          */
+  double v[3];                /* height edge: the mode points along it                      */
+  double beta;                /* propagation wavenumber along the waveguide (> 0)          */
+} oras_port;
+
+/* Port vector p_a = int_port w_a . E0 (N values, real parts; imaginary parts zero) and its
+ * norm N = int_port |E0|^2.  p: N values in `mem`; norm: host (NULL allowed).
+ * Errors: INVALID_ARG (NULL arguments, u or v zero or not orthogonal to 1e-12, beta <= 0, no
+ * outer face in the port), STATE (no oras_factor yet), CUDA. */
+int oras_port_vector(oras_handle* h, const oras_port* port, oras_complex* p, double* norm, int32_t mem);
+
+/* Load of a transmitting port (Sec. 2 eq. wgj): the incoming TE10 mode E_in = E0 exp(i beta
+ * zeta) (zeta along the outward normal n, so the wave travels into the domain) gives the data
+ * g = mu_r^{-1} (curl E_in) x n + i beta n x (E_in x n) = i beta (1 + 1/mu_r) E0 on the port,
+ * and b_a = int_port g . w_a (mu_r of the face's tetrahedron; constrained entries zero).
+ * b: N values in `mem`.  Errors: as oras_port_vector. */
+int oras_rhs_port(oras_handle* h, const oras_port* port, oras_complex* b, int32_t mem);
+
+/* Scattering coefficients (Sec. 5.1 eq. sij) of k fields at nports ports:
+ *   S[i * k + j] = int_{port i} conj(E_j) . E0_i / int_{port i} |E0_i|^2
+ *              = sum_a conj(x[a + j N]) p_i[a] / N_i,
+ * x: the fields (N x k column-major in `mem`, e.g. oras_solve's output); on the transmitting
+ * port the total field is used, as the formula is printed.  S: host [nports][k].  Sums in a
+ * fixed order on the device.  Errors: as oras_port_vector, INVALID_ARG (k or nports < 1). */
+int oras_s_matrix(oras_handle* h, int32_t nports, const oras_port* ports, const oras_complex* x, int32_t k,
+                  oras_complex* S, int32_t mem);
+
+/* Relative error of Sec. 5.2 (eq. errsij): sqrt(sum |S - S_ref|^2) / sqrt(sum |S_ref|^2) over
+ * n entries (host arrays).  Returns -1 for NULL arrays, n < 1 or a zero S_ref. */
+double oras_s_error(const oras_complex* S, const oras_complex* S_ref, int64_t n);
+
 /* ---------------------------------------------------------------- queries (host data)
  * The mesh, numbering and subdomain data of oras_create (Sec. 3-4), copied to the caller's
  * host arrays.  Counts return -1 for a NULL handle; the int-returning calls return
@@ -240,6 +294,8 @@ int32_t oras_nlocal(const oras_handle* h);          /* n_loc = r(r+2)(r+3)/2, or
 int32_t oras_nsub(const oras_handle* h);            /* N_sub, or -1                      */
 /* out: [nt][n_loc] global DOF ids (local numbering in the header comment). */
 int oras_dofmap(const oras_handle* h, int32_t* out);
+/* out: [N] 1 for the degrees of freedom constrained by metallic faces, else 0. */
+int oras_constrained_dofs(const oras_handle* h, uint8_t* out);
 /* out: [nt] non-overlapping subdomain of each tetrahedron. */
 int oras_partition(const oras_handle* h, int32_t* out);
 /* Sizes of subdomain s: #N_s, #Omega_s^delta tetrahedra, padded factor order. */

@@ -20,6 +20,12 @@ int launch_faces(const oras_handle* h);
 int launch_global_rows(const oras_handle* h, double k0);
 int launch_local_rows(const oras_handle* h, double k0);
 int launch_dipole(const oras_handle* h, const double* x0, const double* dir, cplx* b, int* found);
+void launch_mask_fixed(const oras_handle* h, cplx* v, int k);
+int launch_port(const oras_handle* h, const double* o, const double* u, const double* v, double beta, int load,
+                const double* qs, const double* qw, int nq, const uint8_t* inport, cplx* pface, double* nface,
+                cplx* out, double* norm_d);
+int launch_port_dots(const oras_handle* h, int64_t nd, const int32_t* dofs, const cplx* p, const cplx* x, int k,
+                     const double* norm_d, cplx* S);
 int launch_plane(const oras_handle* h, const double* dvec, const oras_complex* pvec, double k0,
                  const double* qs, const double* qw, int nq, cplx* bface, cplx* b);
 int launch_lu(oras_handle* h);
@@ -141,7 +147,7 @@ static cudaError_t dput(T*& p, const std::vector<T>& v, cudaStream_t s) {
 }
 
 static void dfree_all(Device& d) {
-  void* ptrs[] = {d.xyz, d.st, d.dofmap, d.tinc_ptr, d.tinc, d.if_tet0, d.if_lf0, d.if_tet1, d.if_dofs, d.if_beta,
+  void* ptrs[] = {d.xyz, d.st, d.dofmap, d.tinc_ptr, d.tinc, d.if_tet0, d.if_lf0, d.if_tet1, d.if_dofs, d.if_beta, d.fixed,
                   d.finc_ptr, d.finc, d.rowptr, d.cols, d.sub_ns, d.sub_np, d.sub_ns_off, d.sub_tile_off,
                   d.sub_dofs, d.sub_pou, d.member, d.cm, d.ck, d.cs, d.fl, d.tc, d.ta, d.tm, d.eps, d.mu,
                   d.elem, d.fmat, d.vals, d.vals_df, d.arena, d.perm, d.gidx, d.sub_np_off, d.lu_cand, d.lu_cnt,
@@ -177,6 +183,7 @@ static int upload(oras_handle* h) {
   CK(dput(d.if_tet1, m.if_tet1, s));
   CK(dput(d.if_dofs, m.if_dofs, s));
   if (!m.if_beta.empty()) CK(dput(d.if_beta, m.if_beta, s));
+  if (!m.fixed.empty()) CK(dput(d.fixed, m.fixed, s));
   CK(dput(d.finc_ptr, m.finc_ptr, s));
   CK(dput(d.finc, m.finc, s));
   CK(dput(d.rowptr, m.rowptr, s));
@@ -284,7 +291,7 @@ int64_t footprint_bytes(const oras_handle* h, int k) {
   auto add = [&](int64_t x) { b += std::max<int64_t>(x, 1); ++nalloc; };
   // upload
   for (int64_t x : {vb(m.xyz), vb(m.st), vb(m.dofmap), vb(m.tinc_ptr), vb(m.tinc), vb(m.if_tet0), vb(m.if_lf0),
-                    vb(m.if_tet1), vb(m.if_dofs), vb(m.if_beta), vb(m.finc_ptr), vb(m.finc), vb(m.rowptr), vb(m.cols),
+                    vb(m.if_tet1), vb(m.if_dofs), vb(m.if_beta), vb(m.fixed), vb(m.finc_ptr), vb(m.finc), vb(m.rowptr), vb(m.cols),
                     vb(m.sub_ns), vb(m.sub_np), vb(m.sub_ns_off), vb(m.sub_tile_off), vb(m.sub_dofs),
                     vb(m.sub_pou), vb(m.member), (int64_t)(m.nsub + 1) * 8, vb(T.cm), vb(T.ck), vb(T.cs),
                     (int64_t)T.fl.size() * 4, vb(T.tc), (int64_t)T.ta.size() * 4, (int64_t)T.tm.size() * 4})
@@ -381,7 +388,7 @@ static int sync_status(oras_handle* h) {
 
 extern "C" {
 
-int32_t oras_abi_version(void) { return 2; }
+int32_t oras_abi_version(void) { return 3; }
 
 const char* oras_last_error(const oras_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
 
@@ -604,6 +611,13 @@ int32_t oras_nlocal(const oras_handle* h) { return h ? h->mesh.nl : -1; }
 int32_t oras_nsub(const oras_handle* h) { return h ? h->mesh.nsub : -1; }
 int64_t oras_nnz(const oras_handle* h) { return h ? (int64_t)h->mesh.cols.size() : -1; }
 int64_t oras_arena_bytes(const oras_handle* h) { return h ? (int64_t)h->dev.arena_bytes : -1; }
+
+int oras_constrained_dofs(const oras_handle* h, uint8_t* out) {
+  if (!h || !out) return ORAS_ERR_INVALID_ARG;
+  if (h->mesh.fixed.empty()) std::memset(out, 0, (size_t)h->mesh.ndof);
+  else std::memcpy(out, h->mesh.fixed.data(), (size_t)h->mesh.ndof);
+  return ORAS_OK;
+}
 
 int oras_dofmap(const oras_handle* h, int32_t* out) {
   if (!h || !out) return ORAS_ERR_INVALID_ARG;
@@ -931,6 +945,7 @@ int oras_solve(oras_handle* h, const oras_complex* rhs, int32_t k, double tol, o
   if (rc) return rc;
   rc = load_input(h, rhs, k, mem, h->dev.bk);
   if (rc) return rc;
+  launch_mask_fixed(h, h->dev.bk, k);  // metallic faces: zero right-hand side on constrained unknowns
   if (h->opt.block && k > 1) {
     rc = fgmres_block(h, k, tol, info);
     prof_resolve(h);
@@ -999,6 +1014,7 @@ int oras_rhs_dipole(oras_handle* h, const double* x0, const double* dir, oras_co
   if (rc) return rc;
   int* found = (int*)(d.scal + 4);
   if (launch_dipole(h, x0, dir, d.tmp, found)) CK(cudaGetLastError());
+  launch_mask_fixed(h, d.tmp, 1);
   int hf = 0;
   CK(cudaMemcpyAsync(&hf, found, sizeof(int), cudaMemcpyDeviceToHost, d.stream));
   CK(cudaStreamSynchronize(d.stream));
@@ -1044,12 +1060,192 @@ int oras_rhs_plane_wave(oras_handle* h, const double* dvec, const oras_complex* 
   cplx* bface = nullptr;
   CK(dalloc(bface, (size_t)std::max<int64_t>(1, h->mesh.nif) * h->mesh.nfl));
   rc = launch_plane(h, dvec, pvec, h->k0, qs, qw, nq, bface, d.tmp);
+  launch_mask_fixed(h, d.tmp, 1);
   cudaError_t e = cudaMemcpyAsync(b, d.tmp, sizeof(cplx) * h->mesh.ndof,
                                   mem == ORAS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, d.stream);
   cudaFreeAsync(bface, d.stream);
   cudaStreamSynchronize(d.stream);
   if (rc || e != cudaSuccess) { h->err = "oras_rhs_plane_wave: launch failed"; return ORAS_ERR_CUDA; }
   return ORAS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ waveguide ports
+namespace {
+struct PortSel {
+  std::vector<uint8_t> inport;   // [nif]
+  std::vector<int32_t> dofs;     // sorted unique degrees of freedom of the port's faces
+};
+
+// the outer faces whose centroid lies in the port rectangle (the decision in FP64 on the host,
+// vertices in ascending id order)
+int select_port(oras_handle* h, const oras_port* P, PortSel& out) {
+  const auto& m = h->mesh;
+  const double* o = P->origin;
+  const double* u = P->u;
+  const double* v = P->v;
+  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2], vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const double uv = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+  if (!(uu > 0.0) || !(vv > 0.0) || !(std::fabs(uv) <= 1e-12 * std::sqrt(uu * vv)) || !(P->beta > 0.0)) {
+    h->err = "port: u and v must be nonzero and orthogonal, beta > 0";
+    return ORAS_ERR_INVALID_ARG;
+  }
+  double n[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+  const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  for (double& c : n) c /= nn;
+  const double tol = 1e-9 * (std::sqrt(uu) + std::sqrt(vv));
+  static const int FACES[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+  out.inport.assign(m.nif, 0);
+  out.dofs.clear();
+  for (int64_t i = 0; i < m.nif; ++i) {
+    if (m.if_tet1[i] >= 0) continue;
+    const int64_t t = m.if_tet0[i];
+    const int lf = m.if_lf0[i];
+    double c[3];
+    for (int dd = 0; dd < 3; ++dd) {
+      const double x0 = m.xyz[(int64_t)m.st[t * 4 + FACES[lf][0]] * 3 + dd];
+      const double x1 = m.xyz[(int64_t)m.st[t * 4 + FACES[lf][1]] * 3 + dd];
+      const double x2 = m.xyz[(int64_t)m.st[t * 4 + FACES[lf][2]] * 3 + dd];
+      c[dd] = ((x0 + x1) + x2) / 3.0;
+    }
+    const double d[3] = {c[0] - o[0], c[1] - o[1], c[2] - o[2]};
+    const double s = (d[0] * u[0] + d[1] * u[1] + d[2] * u[2]) / uu;
+    const double tt = (d[0] * v[0] + d[1] * v[1] + d[2] * v[2]) / vv;
+    const double dn = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
+    if (std::fabs(dn) <= tol && s >= 0.0 && s <= 1.0 && tt >= 0.0 && tt <= 1.0) {
+      out.inport[i] = 1;
+      for (int af = 0; af < m.nfl; ++af) out.dofs.push_back(m.if_dofs[i * m.nfl + af]);
+    }
+  }
+  if (out.dofs.empty()) {
+    h->err = "port: no outer face lies in the port rectangle";
+    return ORAS_ERR_INVALID_ARG;
+  }
+  std::sort(out.dofs.begin(), out.dofs.end());
+  out.dofs.erase(std::unique(out.dofs.begin(), out.dofs.end()), out.dofs.end());
+  return ORAS_OK;
+}
+
+// device scratch of the port integrals
+struct PortBufs {
+  uint8_t* inport = nullptr;
+  cplx* pface = nullptr;
+  double* nface = nullptr;
+  double* norm = nullptr;
+  int32_t* dofs = nullptr;
+  cplx* S = nullptr;
+  cudaStream_t s = nullptr;
+  ~PortBufs() {
+    for (void* p : {(void*)inport, (void*)pface, (void*)nface, (void*)norm, (void*)dofs, (void*)S})
+      if (p) cudaFreeAsync(p, s);
+  }
+};
+
+// p (load = 0) or the port load b (load = 1) into out (device [N]), norm into bufs.norm
+int port_integrals(oras_handle* h, const oras_port* P, int load, PortSel& sel, PortBufs& B, cplx* out) {
+  auto& m = h->mesh;
+  auto& d = h->dev;
+  int rc = select_port(h, P, sel);
+  if (rc) return rc;
+  B.s = d.stream;
+  if (!B.inport) {
+    CK(dalloc(B.inport, (size_t)m.nif));
+    CK(dalloc(B.pface, (size_t)m.nif * m.nfl));
+    CK(dalloc(B.nface, (size_t)m.nif));
+    CK(dalloc(B.norm, (size_t)1));
+  }
+  CK(cudaMemcpyAsync(B.inport, sel.inport.data(), (size_t)m.nif, cudaMemcpyHostToDevice, d.stream));
+  const int nq = 12;
+  double qs[16], qw[16];
+  gauss_legendre01(nq, qs, qw);
+  if (launch_port(h, P->origin, P->u, P->v, P->beta, load, qs, qw, nq, B.inport, B.pface, B.nface, out, B.norm)) {
+    h->err = "port: launch failed";
+    return ORAS_ERR_CUDA;
+  }
+  if (load) launch_mask_fixed(h, out, 1);
+  return ORAS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int oras_port_vector(oras_handle* h, const oras_port* port, oras_complex* p, double* norm, int32_t mem) {
+  if (!h || !port || !p) return ORAS_ERR_INVALID_ARG;
+  if (!h->factored) { h->err = "oras_port_vector: call oras_factor first"; return ORAS_ERR_STATE; }
+  auto& d = h->dev;
+  int rc = ensure_ws(h, 1, h->opt.restart);
+  if (rc) return rc;
+  PortSel sel;
+  PortBufs B;
+  rc = port_integrals(h, port, 0, sel, B, d.tmp);
+  if (rc) return rc;
+  double hn = 0.0;
+  CK(cudaMemcpyAsync(&hn, B.norm, sizeof(double), cudaMemcpyDeviceToHost, d.stream));
+  CK(cudaMemcpyAsync(p, d.tmp, sizeof(cplx) * h->mesh.ndof,
+                     mem == ORAS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, d.stream));
+  CK(cudaStreamSynchronize(d.stream));
+  if (norm) *norm = hn;
+  return ORAS_OK;
+}
+
+int oras_rhs_port(oras_handle* h, const oras_port* port, oras_complex* b, int32_t mem) {
+  if (!h || !port || !b) return ORAS_ERR_INVALID_ARG;
+  if (!h->factored) { h->err = "oras_rhs_port: call oras_factor first"; return ORAS_ERR_STATE; }
+  auto& d = h->dev;
+  int rc = ensure_ws(h, 1, h->opt.restart);
+  if (rc) return rc;
+  PortSel sel;
+  PortBufs B;
+  rc = port_integrals(h, port, 1, sel, B, d.tmp);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(b, d.tmp, sizeof(cplx) * h->mesh.ndof,
+                     mem == ORAS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, d.stream));
+  CK(cudaStreamSynchronize(d.stream));
+  return ORAS_OK;
+}
+
+int oras_s_matrix(oras_handle* h, int32_t nports, const oras_port* ports, const oras_complex* x, int32_t k,
+                  oras_complex* S, int32_t mem) {
+  if (!h || !ports || !x || !S || nports < 1 || k < 1 || k > MAX_RHS) return ORAS_ERR_INVALID_ARG;
+  if (!h->factored) { h->err = "oras_s_matrix: call oras_factor first"; return ORAS_ERR_STATE; }
+  auto& d = h->dev;
+  int rc = ensure_ws(h, k, h->opt.restart);
+  if (rc) return rc;
+  rc = load_input(h, x, k, mem, d.bk);  // [N][k] internal layout
+  if (rc) return rc;
+  PortBufs B;
+  B.s = d.stream;
+  CK(dalloc(B.S, (size_t)nports * k));
+  for (int i = 0; i < nports; ++i) {
+    PortSel sel;
+    rc = port_integrals(h, &ports[i], 0, sel, B, d.tmp);
+    if (rc) return rc;
+    if (B.dofs) cudaFreeAsync(B.dofs, d.stream);
+    B.dofs = nullptr;
+    CK(dalloc(B.dofs, sel.dofs.size()));
+    CK(cudaMemcpyAsync(B.dofs, sel.dofs.data(), sel.dofs.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                       d.stream));
+    if (launch_port_dots(h, (int64_t)sel.dofs.size(), B.dofs, d.tmp, d.bk, k, B.norm, B.S + (int64_t)i * k)) {
+      h->err = "oras_s_matrix: launch failed";
+      return ORAS_ERR_CUDA;
+    }
+    CK(cudaStreamSynchronize(d.stream));  // the host port selection of the next port reuses the buffers
+  }
+  CK(cudaMemcpyAsync(S, B.S, sizeof(cplx) * nports * k, cudaMemcpyDeviceToHost, d.stream));
+  CK(cudaStreamSynchronize(d.stream));
+  return ORAS_OK;
+}
+
+double oras_s_error(const oras_complex* S, const oras_complex* S_ref, int64_t n) {
+  if (!S || !S_ref || n < 1) return -1.0;
+  double num = 0.0, den = 0.0;
+  for (int64_t q = 0; q < n; ++q) {
+    const double dr = S[q].re - S_ref[q].re, di = S[q].im - S_ref[q].im;
+    num += dr * dr + di * di;
+    den += S_ref[q].re * S_ref[q].re + S_ref[q].im * S_ref[q].im;
+  }
+  return den > 0.0 ? std::sqrt(num / den) : -1.0;
 }
 
 }  // extern "C"

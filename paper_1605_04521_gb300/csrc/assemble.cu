@@ -120,6 +120,7 @@ struct RowArgs {
   const cplx* elem; const double* fmat;
   const cplx* eps; const cplx* mu;
   const double* if_beta;     // [nif] caller's beta of outer faces, or nullptr (derived)
+  const uint8_t* fixed;      // [ndof] constrained by a metallic face (identity row and column), or nullptr
   const uint32_t* member; int64_t member_words;
   int dirichlet;             // local rows: 1 = rows of the global matrix (RAS), 0 = ORAS local problem
 };
@@ -199,6 +200,14 @@ __global__ void k_global_rows(RowArgs A, int64_t ndof, int maxnnz, cplx* __restr
   int64_t r0 = A.rowptr[g];
   int rn = (int)(A.rowptr[g + 1] - r0);
   accumulate_row<false>(A, g, 0, acc, rn, A.cols + r0);
+  if (A.fixed) {  // metallic faces: identity rows and columns of the constrained unknowns
+    const bool gf = A.fixed[g] != 0;
+    for (int p = threadIdx.x & 31; p < rn; p += 32) {
+      const int32_t c = A.cols[r0 + p];
+      vals[r0 + p] = (gf || A.fixed[c]) ? cplx{c == g ? 1.0 : 0.0, 0.0} : acc[p];
+    }
+    return;
+  }
   for (int p = threadIdx.x & 31; p < rn; p += 32) vals[r0 + p] = acc[p];
 }
 
@@ -233,6 +242,10 @@ __global__ void k_local_rows(RowArgs A, int nsub, int64_t total_rows, const int6
   }
   const int32_t* Ns = sub_dofs + ns_off[s];
   const int64_t g = Ns[li];
+  if (A.fixed && A.fixed[g]) {  // constrained by a metallic face: identity row (the arena is cleared)
+    if (lane == 0) put(li, li, R(1), R(0));
+    return;
+  }
   cplx* acc = sacc + w * maxnnz;
   int64_t r0 = A.rowptr[g];
   int rn = (int)(A.rowptr[g + 1] - r0);
@@ -240,6 +253,7 @@ __global__ void k_local_rows(RowArgs A, int nsub, int64_t total_rows, const int6
   if (A.dirichlet) accumulate_row<false>(A, g, s, acc, rn, rc);  // R_s A R_s^T: the global row
   else accumulate_row<true>(A, g, s, acc, rn, rc);
   for (int p = lane; p < rn; p += 32) {
+    if (A.fixed && A.fixed[rc[p]]) continue;  // constrained column: zero
     int lj = bsearch32(Ns, (int)ns, rc[p]);
     if (lj >= 0) put(li, lj, R(acc[p].re), R(acc[p].im));
   }
@@ -400,6 +414,122 @@ __global__ void k_gather_faces(int64_t ndof, int nfl, const int64_t* __restrict_
   b[g] = s;
 }
 
+// v[g][r] = 0 for the constrained degrees of freedom ([N][k] layout)
+__global__ void k_mask_fixed(int64_t ndof, int k, const uint8_t* __restrict__ fixed, cplx* __restrict__ v) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ndof * k) return;
+  if (fixed[e / k]) v[e] = {0.0, 0.0};
+}
+
+// ------------------------------------------------------------------ waveguide ports (Sec. 2, Sec. 5.1)
+struct PortArgs {
+  double o[3], u[3], vhat[3];
+  double inv_uu;          // 1 / |u|^2
+  double beta;
+  int load;               // 0: p_a = int w_a . E0;  1: b_a = int i beta (1 + 1/mu) E0 . w_a
+  int nq;
+  double qs[16], qw[16];  // Gauss-Legendre on [0, 1]
+};
+
+// per impedance face f in the port (inport[f]): pface[f][af] = int_f c_f E0 . w_af and
+// nface[f] = int_f |E0|^2, collapsed Gauss-Legendre product rule; zero for the other faces
+__global__ void k_port_faces(int64_t nif, int nfl, const double* __restrict__ xyz, const int32_t* __restrict__ st,
+                             const int32_t* __restrict__ tet0, const int32_t* __restrict__ lf0,
+                             const uint8_t* __restrict__ inport, const int32_t* __restrict__ fl,
+                             const cplx* __restrict__ mu, const double* tc, const int32_t* ta, const int32_t* tm,
+                             PortArgs P, cplx* __restrict__ pface, double* __restrict__ nface) {
+  const int64_t f = blockIdx.x;
+  const int af = threadIdx.x;
+  if (f >= nif || af >= nfl) return;
+  if (!inport[f]) {
+    pface[f * nfl + af] = {0.0, 0.0};
+    if (af == 0) nface[f] = 0.0;
+    return;
+  }
+  const int FACES[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+  const int OPP[4] = {3, 2, 1, 0};
+  const int64_t t = tet0[f];
+  const int lf = lf0[f], o = OPP[lf];
+  int32_t v[4];
+  for (int q = 0; q < 4; ++q) v[q] = st[t * 4 + q];
+  double gl[4][3], vol;
+  tet_geometry(xyz, v, gl, vol);
+  const double go = sqrt(gl[o][0] * gl[o][0] + gl[o][1] * gl[o][1] + gl[o][2] * gl[o][2]);
+  const double area = 3.0 * vol * go;
+  const double pi = 3.14159265358979323846;
+  const int a = fl[lf * nfl + af];
+  double acc = 0.0, accn = 0.0;
+  for (int i = 0; i < P.nq; ++i)
+    for (int j = 0; j < P.nq; ++j) {
+      const double uu = P.qs[i], vv = P.qs[j] * (1.0 - P.qs[i]);
+      const double wq = P.qw[i] * P.qw[j] * (1.0 - P.qs[i]);
+      double lam[4] = {0, 0, 0, 0};
+      lam[FACES[lf][0]] = 1.0 - uu - vv;
+      lam[FACES[lf][1]] = uu;
+      lam[FACES[lf][2]] = vv;
+      double x[3];
+      for (int dd = 0; dd < 3; ++dd)
+        x[dd] = lam[0] * xyz[(int64_t)v[0] * 3 + dd] + lam[1] * xyz[(int64_t)v[1] * 3 + dd] +
+                lam[2] * xyz[(int64_t)v[2] * 3 + dd] + lam[3] * xyz[(int64_t)v[3] * 3 + dd];
+      const double s = ((x[0] - P.o[0]) * P.u[0] + (x[1] - P.o[1]) * P.u[1] + (x[2] - P.o[2]) * P.u[2]) * P.inv_uu;
+      const double amp = sin(pi * s);
+      double wv[3];
+      basis_value(a, lam, gl, tc, ta, tm, wv);
+      acc += wq * amp * (P.vhat[0] * wv[0] + P.vhat[1] * wv[1] + P.vhat[2] * wv[2]);
+      accn += wq * amp * amp;
+    }
+  cplx c = {1.0, 0.0};
+  if (P.load) {  // i beta (1 + 1/mu)
+    const cplx m = mu ? mu[t] : cplx{1.0, 0.0};
+    const double den = m.re * m.re + m.im * m.im;
+    const cplx f1 = {1.0 + m.re / den, -m.im / den};
+    c = {-P.beta * f1.im, P.beta * f1.re};
+  }
+  pface[f * nfl + af] = {2.0 * area * acc * c.re, 2.0 * area * acc * c.im};
+  if (af == 0) nface[f] = 2.0 * area * accn;
+}
+
+// out = sum of x[0..n) in a fixed order (one block of 256 threads: strided partial sums, then a tree)
+__global__ void k_sum_fixed(int64_t n, const double* __restrict__ x, double* __restrict__ out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += 256) s += x[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// S[j] = sum over the port's degrees of freedom d of conj(x[d][j]) p[d] / norm, one block per
+// column j, fixed-order partial sums and tree
+__global__ void k_port_dots(int64_t nd, const int32_t* __restrict__ dofs, const cplx* __restrict__ p,
+                            const cplx* __restrict__ x, int k, const double* __restrict__ norm,
+                            cplx* __restrict__ S) {
+  __shared__ double sr[256], si[256];
+  const int j = blockIdx.x;
+  double ar = 0.0, ai = 0.0;
+  for (int64_t q = threadIdx.x; q < nd; q += 256) {
+    const int32_t d = dofs[q];
+    const cplx xv = x[(int64_t)d * k + j], pv = p[d];
+    ar += xv.re * pv.re + xv.im * pv.im;  // conj(x) p
+    ai += xv.re * pv.im - xv.im * pv.re;
+  }
+  sr[threadIdx.x] = ar;
+  si[threadIdx.x] = ai;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sr[threadIdx.x] += sr[threadIdx.x + w];
+      si[threadIdx.x] += si[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) S[j] = {sr[0] / *norm, si[0] / *norm};
+}
+
 // ------------------------------------------------------------------ launchers
 int launch_element(const oras_handle* h, double k0) {
   const auto& m = h->mesh;
@@ -432,6 +562,7 @@ static RowArgs row_args(const oras_handle* h, double k0) {
   A.rowptr = d.rowptr; A.cols = d.cols;
   A.elem = d.elem; A.fmat = d.fmat; A.eps = d.eps; A.mu = d.mu;
   A.if_beta = d.if_beta;
+  A.fixed = d.fixed;
   A.member = d.member; A.member_words = m.member_words;
   A.dirichlet = h->opt.transmission == ORAS_TRANSMISSION_DIRICHLET ? 1 : 0;
   return A;
@@ -505,6 +636,51 @@ int launch_plane(const oras_handle* h, const double* dvec, const oras_complex* p
   count_launches(1);
   k_gather_faces<<<(unsigned)((m.ndof + 255) / 256), 256, 0, d.stream>>>(m.ndof, m.nfl, d.finc_ptr, d.finc,
                                                                         bface, b);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+void launch_mask_fixed(const oras_handle* h, cplx* v, int k) {
+  const auto& m = h->mesh;
+  if (!h->dev.fixed) return;
+  const int64_t n = m.ndof * k;
+  k_mask_fixed<<<(unsigned)((n + 255) / 256), 256, 0, h->dev.stream>>>(m.ndof, k, h->dev.fixed, v);
+  count_launches(1);
+}
+
+// p (or the load b) of one port into out [N], its norm into *norm_d (device); inport: [nif]
+// device flags of the port's faces; pface/nface: device scratch [nif * nfl] / [nif]
+int launch_port(const oras_handle* h, const double* o, const double* u, const double* v, double beta, int load,
+                const double* qs, const double* qw, int nq, const uint8_t* inport, cplx* pface, double* nface,
+                cplx* out, double* norm_d) {
+  const auto& m = h->mesh;
+  const auto& d = h->dev;
+  PortArgs P;
+  double uu = 0.0, vv = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    P.o[i] = o[i];
+    P.u[i] = u[i];
+    uu += u[i] * u[i];
+    vv += v[i] * v[i];
+  }
+  for (int i = 0; i < 3; ++i) P.vhat[i] = v[i] / std::sqrt(vv);
+  P.inv_uu = 1.0 / uu;
+  P.beta = beta;
+  P.load = load;
+  P.nq = nq;
+  for (int i = 0; i < nq; ++i) { P.qs[i] = qs[i]; P.qw[i] = qw[i]; }
+  k_port_faces<<<(unsigned)m.nif, 32, 0, d.stream>>>(m.nif, m.nfl, d.xyz, d.st, d.if_tet0, d.if_lf0, inport, d.fl,
+                                                     d.mu, d.tc, d.ta, d.tm, P, pface, nface);
+  k_gather_faces<<<(unsigned)((m.ndof + 255) / 256), 256, 0, d.stream>>>(m.ndof, m.nfl, d.finc_ptr, d.finc,
+                                                                        pface, out);
+  k_sum_fixed<<<1, 256, 0, d.stream>>>(m.nif, nface, norm_d);
+  count_launches(3);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_port_dots(const oras_handle* h, int64_t nd, const int32_t* dofs, const cplx* p, const cplx* x, int k,
+                     const double* norm_d, cplx* S) {
+  k_port_dots<<<(unsigned)k, 256, 0, h->dev.stream>>>(nd, dofs, p, x, k, norm_d, S);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

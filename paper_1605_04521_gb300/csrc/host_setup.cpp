@@ -399,15 +399,50 @@ int host_setup(const oras_problem* p, int overlap_kind, HostMesh& m, std::string
   m.nif = (int64_t)m.if_face.size();
   // caller's impedance coefficients: face (t, q) of the caller is the one opposite the caller's
   // vertex tets[4t+q]; the sorted local face lf is opposite the sorted vertex 3 - lf
+  // the caller's face index q of the face (t, sorted local face lf)
+  auto caller_face = [&](int64_t t, int lf) {
+    const int32_t vo = m.st[t * 4 + (3 - lf)];
+    int q = 0;
+    while (q < 4 && p->tets[t * 4 + q] != vo) ++q;
+    return q;
+  };
+  // metallic faces (Sec. 2 eq. metallicbc): every entry 0 or 1, 1 only on outer faces
+  std::vector<uint8_t> metal_if(m.nif, 0);
+  m.fixed.clear();
+  m.nfixed = 0;
+  if (p->face_kind) {
+    for (int64_t t = 0; t < m.nt; ++t)
+      for (int lf = 0; lf < 4; ++lf) {
+        const int q = caller_face(t, lf);
+        const uint8_t kd = q < 4 ? p->face_kind[t * 4 + q] : 0;
+        if (kd > 1) {
+          err = "oras_create: face_kind of face " + std::to_string(q) + " of tetrahedron " + std::to_string(t) +
+                " is neither 0 (impedance) nor 1 (metallic)";
+          return ORAS_ERR_INVALID_ARG;
+        }
+        if (kd == 1 && m.face_tets[(int64_t)m.tet_faces[t * 4 + lf] * 2 + 1] >= 0) {
+          err = "oras_create: face " + std::to_string(q) + " of tetrahedron " + std::to_string(t) +
+                " is metallic but interior";
+          return ORAS_ERR_INVALID_ARG;
+        }
+      }
+    for (int64_t i = 0; i < m.nif; ++i)
+      if (m.if_tet1[i] < 0) {
+        const int q = caller_face(m.if_tet0[i], m.if_lf0[i]);
+        metal_if[i] = q < 4 && p->face_kind[(int64_t)m.if_tet0[i] * 4 + q] == 1;
+      }
+  }
   m.if_beta.clear();
   if (p->beta_face) {
     m.if_beta.assign(m.nif, 0.0);
     for (int64_t i = 0; i < m.nif; ++i) {
       if (m.if_tet1[i] >= 0) continue;
+      if (metal_if[i]) {  // not read: the face's degrees of freedom are constrained
+        m.if_beta[i] = 1.0;
+        continue;
+      }
       const int64_t t = m.if_tet0[i];
-      const int32_t vo = m.st[t * 4 + (3 - m.if_lf0[i])];
-      int q = 0;
-      while (q < 4 && p->tets[t * 4 + q] != vo) ++q;
+      const int q = caller_face(t, m.if_lf0[i]);
       const double b = q < 4 ? p->beta_face[t * 4 + q] : NAN;
       if (!(std::isfinite(b) && b > 0.0)) {
         err = "oras_create: beta_face of the outer face " + std::to_string(q) + " of tetrahedron " +
@@ -423,6 +458,16 @@ int host_setup(const oras_problem* p, int overlap_kind, HostMesh& m, std::string
   for (int64_t i = 0; i < m.nif; ++i)
     for (int af = 0; af < nfl; ++af)
       m.if_dofs[i * nfl + af] = m.dofmap[(int64_t)m.if_tet0[i] * nl + fld[m.if_lf0[i]][af]];
+  // constrained degrees of freedom: those of the edges and of the face of every metallic face
+  // (the face-local degrees of freedom: the only ones with a tangential trace on the face)
+  if (p->face_kind) {
+    m.fixed.assign(ndof, 0);
+    for (int64_t i = 0; i < m.nif; ++i)
+      if (metal_if[i])
+        for (int af = 0; af < nfl; ++af) m.fixed[m.if_dofs[i * nfl + af]] = 1;
+    for (int64_t g = 0; g < ndof; ++g) m.nfixed += m.fixed[g];
+    if (m.nfixed == 0) m.fixed.clear();
+  }
   m.finc_ptr.assign(ndof + 1, 0);
   for (int64_t i = 0; i < m.nif * nfl; ++i) m.finc_ptr[m.if_dofs[i] + 1]++;
   for (int64_t g = 0; g < ndof; ++g) m.finc_ptr[g + 1] += m.finc_ptr[g];

@@ -79,6 +79,8 @@ struct HostMesh {
   std::vector<int32_t> if_face, if_tet0, if_lf0, if_tet1;  // tet1 = -1 on the outer boundary
   std::vector<int32_t> if_dofs;   // [nif][nfl] global DOFs, intrinsic face order
   std::vector<double> if_beta;    // [nif] caller's beta of outer faces (empty: derived per factor)
+  std::vector<uint8_t> fixed;     // [ndof] 1: constrained by a metallic face (empty: none)
+  int64_t nfixed = 0;
   std::vector<int64_t> finc_ptr;  // [ndof+1]
   std::vector<int32_t> finc;      // slot*nfl + a_f
   // CSR pattern of A
@@ -118,6 +120,7 @@ struct Device {
   int32_t* if_tet0 = nullptr; int32_t* if_lf0 = nullptr; int32_t* if_tet1 = nullptr;
   int32_t* if_dofs = nullptr;
   double* if_beta = nullptr;                    // [nif] or nullptr (beta derived from the materials)
+  uint8_t* fixed = nullptr;                     // [ndof] constrained degrees of freedom, or nullptr
   int64_t* finc_ptr = nullptr;
   int32_t* finc = nullptr;
   int64_t* rowptr = nullptr;

@@ -34,6 +34,7 @@ namespace {
 struct Request {
   int64_t ticket = 0;
   std::vector<double> xyz, dipoles, beta;
+  std::vector<uint8_t> face_kind;
   std::vector<int32_t> tets, part;
   std::vector<oras_complex> eps, mu, rhs;
   oras_problem prob{};
@@ -294,6 +295,7 @@ int64_t oras_submit(oras_server* S, const oras_problem* p, const oras_options* o
     if (p->mu_r) q->mu.assign(p->mu_r, p->mu_r + p->nt);
     if (p->part) q->part.assign(p->part, p->part + p->nt);
     if (p->beta_face) q->beta.assign(p->beta_face, p->beta_face + 4 * p->nt);
+    if (p->face_kind) q->face_kind.assign(p->face_kind, p->face_kind + 4 * p->nt);
     if (rhs) q->rhs.assign(rhs, rhs + n * k);
     if (dipoles) q->dipoles.assign(dipoles, dipoles + 6 * k);
   } catch (const std::bad_alloc&) {
@@ -307,6 +309,7 @@ int64_t oras_submit(oras_server* S, const oras_problem* p, const oras_options* o
   q->prob.mu_r = p->mu_r ? q->mu.data() : nullptr;
   q->prob.part = p->part ? q->part.data() : nullptr;
   q->prob.beta_face = p->beta_face ? q->beta.data() : nullptr;
+  q->prob.face_kind = p->face_kind ? q->face_kind.data() : nullptr;
   if (o) {
     q->opt = *o;
     q->has_opt = true;

@@ -39,6 +39,8 @@ ORAS_APPLY_AUTO = 0
 ORAS_APPLY_CUDA_CORES = 1
 ORAS_TRANSMISSION_IMPEDANCE = 0
 ORAS_TRANSMISSION_DIRICHLET = 1
+ORAS_FACE_IMPEDANCE = 0
+ORAS_FACE_METALLIC = 1
 
 
 class oras_complex(C.Structure):
@@ -48,7 +50,12 @@ class oras_complex(C.Structure):
 class oras_problem(C.Structure):
     _fields_ = [("nv", C.c_int64), ("xyz", C.c_void_p), ("nt", C.c_int64), ("tets", C.c_void_p),
                 ("eps_r", C.c_void_p), ("mu_r", C.c_void_p), ("k0", C.c_double), ("r", C.c_int32),
-                ("nsub", C.c_int32), ("overlap", C.c_int32), ("part", C.c_void_p), ("beta_face", C.c_void_p)]
+                ("nsub", C.c_int32), ("overlap", C.c_int32), ("part", C.c_void_p), ("beta_face", C.c_void_p),
+                ("face_kind", C.c_void_p)]
+
+
+class oras_port(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("u", C.c_double * 3), ("v", C.c_double * 3), ("beta", C.c_double)]
 
 
 class oras_options(C.Structure):
@@ -93,6 +100,11 @@ EXPORTS = {
                              C.POINTER(oras_info), C.c_int32]),
     "oras_rhs_plane_wave": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "oras_rhs_dipole": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "oras_port_vector": (C.c_int, [C.c_void_p, C.POINTER(oras_port), C.c_void_p, C.POINTER(C.c_double), C.c_int32]),
+    "oras_rhs_port": (C.c_int, [C.c_void_p, C.POINTER(oras_port), C.c_void_p, C.c_int32]),
+    "oras_s_matrix": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
+    "oras_s_error": (C.c_double, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "oras_constrained_dofs": (C.c_int, [C.c_void_p, C.c_void_p]),
     "oras_ndof": (C.c_int64, [C.c_void_p]),
     "oras_nlocal": (C.c_int32, [C.c_void_p]),
     "oras_nsub": (C.c_int32, [C.c_void_p]),
@@ -170,7 +182,7 @@ def _c128(a):
     return np.ascontiguousarray(a, dtype=np.complex128)
 
 
-def _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part, beta_face=None):
+def _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part, beta_face=None, face_kind=None):
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     tets = np.ascontiguousarray(tets, dtype=np.int32)
     keep = [xyz, tets]
@@ -193,6 +205,10 @@ def _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part, beta_face=None)
         bf = np.ascontiguousarray(beta_face, dtype=np.float64).reshape(-1, 4)
         keep.append(bf)
         p.beta_face = bf.ctypes.data
+    if face_kind is not None:
+        fk = np.ascontiguousarray(face_kind, dtype=np.uint8).reshape(-1, 4)
+        keep.append(fk)
+        p.face_kind = fk.ctypes.data
     return p, keep
 
 
@@ -211,10 +227,11 @@ def _options(restart=0, max_iter=0, factor_bits=0, weights=0, overlap_kind=0, lu
     return o
 
 
-def oras_create(xyz, tets, r, nsub, overlap, part=None, beta_face=None, **opts):
+def oras_create(xyz, tets, r, nsub, overlap, part=None, beta_face=None, face_kind=None, **opts):
     """Host integer set-up; returns the handle (c_void_p).  beta_face: (nt, 4) impedance
-    coefficients of the outer faces (face q of tet t is opposite tets[t, q]) or None."""
-    p, keep = _problem(xyz, tets, None, None, 1.0, r, nsub, overlap, part, beta_face)
+    coefficients of the outer faces (face q of tet t is opposite tets[t, q]) or None; face_kind:
+    (nt, 4) ORAS_FACE_IMPEDANCE / ORAS_FACE_METALLIC on the same faces, or None."""
+    p, keep = _problem(xyz, tets, None, None, 1.0, r, nsub, overlap, part, beta_face, face_kind)
     o = _options(**opts)
     h = C.c_void_p()
     _check(None, lib.oras_create(C.byref(p), C.byref(o), C.byref(h)))
@@ -222,11 +239,13 @@ def oras_create(xyz, tets, r, nsub, overlap, part=None, beta_face=None, **opts):
     return h
 
 
-def oras_setup(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part=None, beta_face=None, **opts):
+def oras_setup(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part=None, beta_face=None, face_kind=None,
+               **opts):
     """oras_create + oras_factor: host mesh xyz (nv, 3), tets (nt, 4), per-tet complex eps_r and
     mu_r (None: 1), wave number k0, degree r, nsub subdomains (RCB unless part is given),
-    overlap layers, beta_face (nt, 4) or None; opts are oras_options fields.  Returns the handle."""
-    p, keep = _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part, beta_face)
+    overlap layers, beta_face (nt, 4) or None, face_kind (nt, 4) or None; opts are oras_options
+    fields.  Returns the handle."""
+    p, keep = _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part, beta_face, face_kind)
     o = _options(**opts)
     h = C.c_void_p()
     _check(None, lib.oras_setup(C.byref(p), C.byref(o), C.byref(h)))
@@ -405,6 +424,54 @@ def oras_rhs_dipole(h, x0, direction, mem=ORAS_MEM_HOST, out=None):
     if mem == ORAS_MEM_HOST:
         out = np.empty(oras_ndof(h), dtype=np.complex128)
     _check(h, lib.oras_rhs_dipole(h, _ptr(x0), _ptr(d), _ptr(out), mem))
+    return out
+
+
+def port(origin, u, v, beta):
+    """oras_port of the rectangle {origin + s u + t v}, TE10 mode sin(pi s) v/|v|."""
+    P = oras_port()
+    for i in range(3):
+        P.origin[i], P.u[i], P.v[i] = float(origin[i]), float(u[i]), float(v[i])
+    P.beta = float(beta)
+    return P
+
+
+def oras_port_vector(h, P):
+    """(p, norm): p_a = int_port w_a . E0 (complex128 [N], real values) and int_port |E0|^2."""
+    out = np.empty(oras_ndof(h), dtype=np.complex128)
+    nrm = C.c_double()
+    _check(h, lib.oras_port_vector(h, C.byref(P), _ptr(out), C.byref(nrm), ORAS_MEM_HOST))
+    return out, nrm.value
+
+
+def oras_rhs_port(h, P):
+    """Load of the port transmitting its incoming TE10 mode (complex128 [N])."""
+    out = np.empty(oras_ndof(h), dtype=np.complex128)
+    _check(h, lib.oras_rhs_port(h, C.byref(P), _ptr(out), ORAS_MEM_HOST))
+    return out
+
+
+def oras_s_matrix(h, ports, X):
+    """S [nports, k] of the fields X ((N,) or (N, k) complex, host)."""
+    n = oras_ndof(h)
+    X = np.asfortranarray(np.asarray(X, dtype=np.complex128).reshape(n, -1))
+    k = X.shape[1]
+    arr = (oras_port * len(ports))(*ports)
+    S = np.empty((len(ports), k), dtype=np.complex128)
+    _check(h, lib.oras_s_matrix(h, len(ports), C.cast(arr, C.c_void_p), _ptr(X), k, _ptr(S), ORAS_MEM_HOST))
+    return S
+
+
+def oras_s_error(S, S_ref):
+    """Relative error of Sec. 5.2 between two scattering matrices (the library's host formula)."""
+    S = _c128(S).ravel()
+    R = _c128(S_ref).ravel()
+    return float(lib.oras_s_error(_ptr(S), _ptr(R), S.size))
+
+
+def oras_constrained_dofs(h):
+    out = np.empty(oras_ndof(h), dtype=np.uint8)
+    _check(h, lib.oras_constrained_dofs(h, _ptr(out)))
     return out
 
 

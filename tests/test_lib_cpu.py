@@ -184,3 +184,67 @@ def test_beta_face_validation(O):
     with pytest.raises(O.OrasError) as e:
         O.oras_create(xyz, tets, 1, 4, 1, beta_face=bad)
     assert e.value.code == O.ORAS_ERR_INVALID_ARG
+
+
+def _wall_kinds(xyz, tets, walls):
+    kind = np.zeros((len(tets), 4), dtype=np.uint8)
+    for t in range(len(tets)):
+        for q in range(4):
+            P = xyz[[tets[t][j] for j in range(4) if j != q]]
+            for ax, val in walls:
+                if np.all(np.abs(P[:, ax] - val) < 1e-12):
+                    kind[t, q] = 1
+    return kind
+
+
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_constrained_dofs_bit_exact(O, r):
+    """The degrees of freedom the host set-up constrains for metallic faces (the face-local ones
+    of each metallic face) equal the oracle's, found by evaluating the tangential traces of the
+    basis functions (Sec. 2 eq. metallicbc), for the four side walls of a 3^3 cube and a caller's
+    vertex order that is not sorted."""
+    from oracle import ports
+    xyz, tets = synth.kuhn_cube(3)
+    rng = np.random.default_rng(9)
+    tets = np.array([rng.permutation(t) for t in tets])
+    kind = _wall_kinds(xyz, tets, [(0, 0.0), (0, 1.0), (1, 0.0), (1, 1.0)])
+    topo = topology.build(tets, len(xyz), r)
+    ref = ports.constrained_dofs(topo, xyz, ports.face_kind_table(tets, kind))
+    h = O.oras_create(xyz, tets, r, 4, 1, face_kind=kind)
+    try:
+        got = O.oras_constrained_dofs(h)
+        assert np.array_equal(got.astype(bool), ref)
+    finally:
+        O.oras_destroy(h)
+    h = O.oras_create(xyz, tets, r, 4, 1)
+    try:
+        assert not O.oras_constrained_dofs(h).any()
+    finally:
+        O.oras_destroy(h)
+
+
+def test_face_kind_validation(O):
+    """face_kind entries must be 0 or 1, and 1 only on outer faces; beta_face is not read on
+    metallic faces."""
+    xyz, tets = synth.kuhn_cube(2)
+    kind = _wall_kinds(xyz, tets, [(0, 0.0)])
+    beta = np.full((len(tets), 4), 3.0)
+    beta[kind == 1] = 0.0                      # not read on metallic faces
+    h = O.oras_create(xyz, tets, 2, 2, 1, beta_face=beta, face_kind=kind)
+    O.oras_destroy(h)
+    bad = kind.copy()
+    bad[0, 0] = 2
+    with pytest.raises(O.OrasError) as e:
+        O.oras_create(xyz, tets, 2, 2, 1, face_kind=bad)
+    assert e.value.code == O.ORAS_ERR_INVALID_ARG
+    topo = topology.build(tets, len(xyz), 1)
+    st = np.sort(tets, axis=1)
+    t, lf = next((t, lf) for t in range(len(tets)) for lf in range(4)
+                 if topo.face_tets[topo.tet_faces[t, lf], 1] >= 0)
+    inner = np.zeros_like(kind)
+    inner[t, list(tets[t]).index(st[t, (3, 2, 1, 0)[lf]])] = 1
+    with pytest.raises(O.OrasError) as e:
+        O.oras_create(xyz, tets, 2, 2, 1, face_kind=inner)
+    assert e.value.code == O.ORAS_ERR_INVALID_ARG
+    assert abs(O.oras_s_error(np.array([1 + 1j, 2.0]), np.array([1 + 1j, 2.0]))) == 0.0
+    assert abs(O.oras_s_error(np.array([2.0, 4.0]), np.array([1.0, 2.0])) - 1.0) < 1e-15
