@@ -140,7 +140,10 @@ typedef struct {
   int32_t block;              /* 1: oras_solve treats its k > 1 columns as one block (block      */
                               /*   flexible GMRES, Sec. 6); 0: k independent recurrences that   */
                               /*   share every kernel launch (pseudo-block, Sec. 5) [0]         */
-  int32_t reserved[3];
+  int32_t recycle;            /* k > 0: one-column oras_solve runs GCRO-DR(restart, k) and keeps */
+                              /*   its deflation subspace in the handle for the next solve (Sec. */
+                              /*   6, recycling across the imaging loop's systems) [0]          */
+  int32_t reserved[2];
 } oras_options;
 
 /* Per right-hand-side outcome of oras_solve. */
@@ -156,6 +159,16 @@ typedef struct {
  * counterpart in the paper (error reporting).  Never fails; the string stays valid until the
  * next failing call on h or its destruction. */
 const char* oras_last_error(const oras_handle* h);
+
+/* Eigenvalues w[n] and unit eigenvectors V (row-major n x n, column j for w[j]; NULL allowed) of
+ * the dense complex matrix A (row-major n x n, host): the QR algorithm the recycling solver uses
+ * for its harmonic Ritz problems, exported for tests.  No counterpart in the paper.  Returns OK,
+ * INVALID_ARG (n < 1, NULL A or w) or NOT_CONVERGED. */
+int oras_dense_eig(int32_t n, const oras_complex* A, oras_complex* w, oras_complex* V);
+
+/* Drops the deflation subspace that GCRO-DR solves (oras_options.recycle) keep in the handle, so
+ * that the next solve starts without recycling.  INVALID_ARG for a NULL handle. */
+int oras_recycle_reset(oras_handle* h);
 
 /* Version of the ABI described here.  No counterpart in the paper.  Never fails. */
 int32_t oras_abi_version(void);  /* 3: oras_problem.face_kind, ports (2: beta_face, wait_ms) */
@@ -214,7 +227,14 @@ int oras_set_stream(oras_handle* h, void* stream);
  * block orthonormalised by CholQR2, the block least-squares problem kept triangular by
  * Householder reflections; info[j].iterations then counts block steps.  A block that becomes
  * numerically rank deficient (CholQR2 breakdown) ends the solve with ORAS_NOT_CONVERGED and the
- * last iterate.  rhs, x: N x k column-major in `mem`; info: k host structs or NULL.
+ * last iterate.  With oras_options.recycle = r > 0 and k = 1: GCRO-DR(restart, r) (Sec. 6
+ * subspace recycling; Parks, de Sturler et al. 2006) on A M^{-1}: deflated restarting with the
+ * r harmonic Ritz vectors of smallest harmonic Ritz value, FP64 Gram-Schmidt against the
+ * recycled C and the Arnoldi basis, and the deflation subspace kept in the handle for the next
+ * solve (after an oras_factor with new materials it is recycled: C rebuilt from A M^{-1} U with r
+ * products); info[0].iterations then counts the products with A M^{-1} (Arnoldi steps and the r
+ * products that rebuild C).  Entries of the right-hand sides at unknowns constrained by metallic
+ * faces are taken as zero.  rhs, x: N x k column-major in `mem`; info: k host structs or NULL.
  * Returns ORAS_OK when every column reached ||b - A x|| / ||b|| <= tol,
  * ORAS_NOT_CONVERGED when max_iter ran out for some column.  Errors: STATE (no
  * oras_factor yet), INVALID_ARG (k < 1 or > 64, tol <= 0), CUDA, OUT_OF_MEMORY,

@@ -61,6 +61,7 @@ int precond_to_z(oras_handle* h, const cplx* v, int k, int j);
 void spmv_z(oras_handle* h, int k, int j, cplx* y);
 int status_code(oras_handle* h, const int32_t* st);
 int fgmres_block(oras_handle* h, int p, double tol, oras_info* info);
+int gcrodr_solve(oras_handle* h, double tol, oras_info* info);
 }  // namespace oras
 
 using namespace oras;
@@ -416,6 +417,11 @@ int oras_create(const oras_problem* p, const oras_options* o, oras_handle** out)
     delete h;
     return ORAS_ERR_INVALID_ARG;
   }
+  if (h->opt.recycle < 0 || h->opt.recycle >= h->opt.restart) {
+    g_err = "oras_create: recycle must be in [0, restart)";
+    delete h;
+    return ORAS_ERR_INVALID_ARG;
+  }
   int rc;
   try {
     rc = host_setup(p, h->opt.overlap_kind, h->mesh, g_err);
@@ -569,7 +575,10 @@ void oras_destroy(oras_handle* h) {
     if (g) cudaGraphExecDestroy(g);
   if (h->dev.uploaded) {
     cudaStreamSynchronize(h->dev.stream);
+    if (h->rc_U) cudaFreeAsync(h->rc_U, h->dev.stream);
     dfree_all(h->dev);
+  } else if (h->rc_U) {
+    cudaFree(h->rc_U);
   }
   delete h;
 }
@@ -948,6 +957,9 @@ int oras_solve(oras_handle* h, const oras_complex* rhs, int32_t k, double tol, o
   launch_mask_fixed(h, h->dev.bk, k);  // metallic faces: zero right-hand side on constrained unknowns
   if (h->opt.block && k > 1) {
     rc = fgmres_block(h, k, tol, info);
+    prof_resolve(h);
+  } else if (h->opt.recycle > 0 && k == 1) {
+    rc = gcrodr_solve(h, tol, info);
     prof_resolve(h);
   } else {
     rc = fgmres(h, k, tol, info);

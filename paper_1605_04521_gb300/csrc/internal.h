@@ -268,4 +268,8 @@ struct oras_handle {
   const void* graph_Z = nullptr;
   const void* graph_arena = nullptr;
   const void* graph_ybuf = nullptr;
+  // GCRO-DR (oras_options.recycle): the deflation subspace U kept for the next solve
+  oras::cplx* rc_U = nullptr;
+  int rc_k = 0;
+  int64_t rc_n = 0;
 };

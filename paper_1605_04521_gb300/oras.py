@@ -63,7 +63,7 @@ class oras_options(C.Structure):
                 ("weights", C.c_int32), ("overlap_kind", C.c_int32), ("lu_engine", C.c_int32),
                 ("lu_panel", C.c_int32), ("lu_group", C.c_int32), ("transmission", C.c_int32),
                 ("graphs", C.c_int32), ("wait_ms", C.c_int32), ("apply_engine", C.c_int32),
-                ("block", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("block", C.c_int32), ("recycle", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class oras_info(C.Structure):
@@ -105,6 +105,8 @@ EXPORTS = {
     "oras_s_matrix": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
     "oras_s_error": (C.c_double, [C.c_void_p, C.c_void_p, C.c_int64]),
     "oras_constrained_dofs": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "oras_dense_eig": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "oras_recycle_reset": (C.c_int, [C.c_void_p]),
     "oras_ndof": (C.c_int64, [C.c_void_p]),
     "oras_nlocal": (C.c_int32, [C.c_void_p]),
     "oras_nsub": (C.c_int32, [C.c_void_p]),
@@ -213,7 +215,7 @@ def _problem(xyz, tets, eps_r, mu_r, k0, r, nsub, overlap, part, beta_face=None,
 
 
 def _options(restart=0, max_iter=0, factor_bits=0, weights=0, overlap_kind=0, lu_engine=0, lu_panel=0, lu_group=0,
-             transmission=0, graphs=0, wait_ms=0, apply_engine=0, block=0):
+             transmission=0, graphs=0, wait_ms=0, apply_engine=0, block=0, recycle=0):
     o = oras_options()
     o.restart, o.max_iter, o.factor_bits, o.weights, o.overlap_kind = restart, max_iter, factor_bits, weights, overlap_kind
     o.lu_engine = lu_engine
@@ -224,6 +226,7 @@ def _options(restart=0, max_iter=0, factor_bits=0, weights=0, overlap_kind=0, lu
     o.wait_ms = wait_ms
     o.apply_engine = apply_engine
     o.block = block
+    o.recycle = recycle
     return o
 
 
@@ -467,6 +470,23 @@ def oras_s_error(S, S_ref):
     S = _c128(S).ravel()
     R = _c128(S_ref).ravel()
     return float(lib.oras_s_error(_ptr(S), _ptr(R), S.size))
+
+
+def oras_dense_eig(A):
+    """(eigenvalues, unit eigenvectors as columns) of a small dense complex matrix, by the
+    library's host QR algorithm."""
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    w = np.empty(n, dtype=np.complex128)
+    V = np.empty((n, n), dtype=np.complex128)
+    rc = lib.oras_dense_eig(n, _ptr(A), _ptr(w), _ptr(V))
+    if rc != ORAS_OK:
+        raise OrasError(rc, "oras_dense_eig failed")
+    return w, V
+
+
+def oras_recycle_reset(h):
+    _check(h, lib.oras_recycle_reset(h))
 
 
 def oras_constrained_dofs(h):
