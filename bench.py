@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--ports", type=int, default=1,
                     help="1: also time the 16-port chamber on the 16^3 mesh (metallic bottom, 16 ports "
                          "transmitting together, 16 x 16 scattering matrix, Sec. 5.1)")
+    ap.add_argument("--recycling", type=int, default=1,
+                    help="1: also time a sequence of three slowly varying systems on the 24^3 Krylov workload "
+                         "with FGMRES(50) and with GCRO-DR(50, 10) recycling its subspace (Sec. 6)")
     ap.add_argument("--fp64-path", type=int, default=1,
                     help="1: also time the plain FP64 single-RHS path against the FP32-factor path on the "
                          "workloads where the FP64 factorisation finishes (head8, cube8)")
@@ -542,6 +545,54 @@ def ports_measure(O, dev, stream, steps=1, warmup=1):
         O.oras_destroy(h)
 
 
+# ------------------------------------------------------------------ subspace recycling
+def recycling_measure(O, dev, stream, n_sys=3, m=50, k=10):
+    """A sequence of n_sys systems on the 24^3 Krylov workload (512 subdomains without overlap,
+    where FGMRES(50) restarts several times) whose permittivity changes slightly from one system to
+    the next (eps_t = eps (1 + 2e-3 t xi), xi ~ U(-1, 1) per tet, as in the imaging loop of Sec. 6).
+    Each system: oras_factor with its materials + oras_solve of one dipole, CUDA events on the
+    handle's stream.  FGMRES(m) against GCRO-DR(m, k), whose handle carries its deflation subspace
+    from one system to the next; products = applications of A M^{-1}."""
+    import torch
+    w = workload("krylov24")
+    xyz, tets = w.mesh()
+    eps, mu = w.materials(xyz, tets)
+    xi = np.random.default_rng(160504521).uniform(-1.0, 1.0, len(tets))
+    mats = [torch.from_numpy(eps * (1.0 + 2e-3 * t * xi)).to(dev) for t in range(n_sys)]
+    mu_d = torch.from_numpy(mu).to(dev)
+    kind, pt, direction = w.sources()[0]
+    out = {"workload": f"{w.n}^3 x 6 tets, r = {w.r}, {w.nsub} subdomains, overlap {w.overlap}; "
+                       f"{n_sys} systems, eps_t = eps (1 + 2e-3 t xi)", "restart": m, "recycle_k": k}
+    for name, opts in (("fgmres", dict(restart=m)), ("gcrodr", dict(restart=m, recycle=k))):
+        h = O.oras_create(xyz, tets, w.r, w.nsub, w.overlap, **opts)
+        try:
+            O.oras_set_stream(h, stream.cuda_stream)
+            per = []
+            b = x = None
+            for t, e_d in enumerate(mats):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                e0.record(stream)
+                O.oras_factor(h, e_d, mu_d, w.k0, mem=O.ORAS_MEM_DEVICE)
+                if b is None:
+                    n = O.oras_ndof(h)
+                    b = torch.empty(n, dtype=torch.complex128, device=dev)
+                    O.oras_rhs_dipole(h, pt, direction, mem=O.ORAS_MEM_DEVICE, out=b)
+                    x = torch.empty_like(b)
+                    e0.record(stream)  # the load is not part of the step
+                _, info, rc = O.oras_solve(h, b, w.tol, mem=O.ORAS_MEM_DEVICE, out=x)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                per.append({"products": info[0]["iterations"], "ms": e0.elapsed_time(e1),
+                            "true_relres": info[0]["relres"], "converged": rc == O.ORAS_OK})
+            out[name] = per
+        finally:
+            O.oras_destroy(h)
+    out["products_total"] = {nm: sum(r["products"] for r in out[nm]) for nm in ("fgmres", "gcrodr")}
+    out["ms_total"] = {nm: sum(r["ms"] for r in out[nm]) for nm in ("fgmres", "gcrodr")}
+    return out
+
+
 # ------------------------------------------------------------------ plain FP64 path
 def fp64_path(O, dev, stream, steps=2, warmup=1):
     """The plain FP64 single-right-hand-side GPU path (FP64 local factors, CUDA-core FP64 LU,
@@ -747,6 +798,12 @@ def run_ours(args, world, rank, local):
             port_res = ports_measure(O, dev, stream)
         except Exception as e:  # noqa: BLE001
             port_res = {"error": f"{type(e).__name__}: {e}"}
+    recyc = None
+    if rank == 0 and args.recycling:
+        try:
+            recyc = recycling_measure(O, dev, stream)
+        except Exception as e:  # noqa: BLE001
+            recyc = {"error": f"{type(e).__name__}: {e}"}
     fp64 = None
     if rank == 0 and args.fp64_path:
         try:
@@ -791,6 +848,7 @@ def run_ours(args, world, rank, local):
             "gpu_launches": int(launches),
             "fp64_path": fp64,
             "ports": port_res,
+            "recycling": recyc,
             "serving": serving,
             "clocks": clk,
             "peaks": {"hbm_gbs": hbm, "bf16_tflops": bf16, "bf16_tflops_sustained": bf16_sus, "source": src},

@@ -48,10 +48,13 @@ size_t rc_partials_elems();
 void launch_rc_dots(cudaStream_t st, int64_t n, int nq, const cplx* X, int64_t ldx, const cplx* w, cplx* partials,
                     cplx* out);
 void launch_rc_lincomb(cudaStream_t st, int64_t n, int nq, int nc, const cplx* X, int64_t ldx, const cplx* M,
-                       double beta, cplx* Y, int64_t ldy);
+                       double beta, cplx* Y, int64_t ldy, double alpha = 1.0);
 void launch_rc_scale(cudaStream_t st, int64_t n, const cplx* x, double s, cplx* out);
+void launch_rc_widen(cudaStream_t st, int64_t n, const void* x, cplx* out);
 int launch_apply_f64out(const oras_handle* h, const cplx* v, cplx* z, int k);
+int launch_apply_f32out(const oras_handle* h, const cplx* v, void* z, int k);
 void launch_spmv_f64(const oras_handle* h, const cplx* x, cplx* y, int k);
+void launch_spmv_f32(const oras_handle* h, const void* x, cplx* y, int k);
 int apply_passes(const oras_handle* h, int k);
 int status_code(oras_handle* h, const int32_t* st);
 
@@ -102,7 +105,7 @@ int gcrodr_solve(oras_handle* h, double tol, oras_info* info) {
   buf.s = part.s = small.s = st;
   RK(cudaMallocAsync((void**)&buf.p, sizeof(cplx) * (size_t)N * ncol, st));
   RK(cudaMallocAsync((void**)&part.p, sizeof(cplx) * rc_partials_elems(), st));
-  const size_t nsmall = (size_t)(kdef + m + 2) * std::max(kdef, 1) + 2 * (size_t)(kdef + m + 2);
+  const size_t nsmall = (size_t)(kdef + m + 2) * std::max(kdef, 1) + 2 * (size_t)(kdef + m + 2) + 1;
   RK(cudaMallocAsync((void**)&small.p, sizeof(cplx) * nsmall, st));
   cplx* W = buf.p;
   cplx* V = W + (size_t)kdef * N;
@@ -118,7 +121,7 @@ int gcrodr_solve(oras_handle* h, double tol, oras_info* info) {
   cplx* z = w + N;
   cplx* dM = small.p;                                  // small coefficient matrices
   cplx* dots = small.p + (size_t)(kdef + m + 2) * std::max(kdef, 1);
-  std::vector<cplx> hbuf(kdef + m + 2);
+  std::vector<cplx> hbuf(2 * (kdef + m + 2) + 1);
   int32_t st_h[8];
   auto put_small = [&](const std::vector<zc>& M) -> int {
     RK(cudaMemcpyAsync(dM, M.data(), sizeof(cplx) * M.size(), cudaMemcpyHostToDevice, st));
@@ -138,14 +141,23 @@ int gcrodr_solve(oras_handle* h, double tol, oras_info* info) {
     out = std::sqrt(std::max(t[0].real(), 0.0));
     return ORAS_OK;
   };
-  // zv = M^{-1} v, out = A zv
+  // zv = M^{-1} v, out = A zv.  With FP32 factors M^{-1} v is FP32-valued: the apply writes it
+  // in FP32, the SpMV takes the FP32-pipe error-free kernel (FP64-class result), and zv is its
+  // exact FP64 copy
+  const bool f32 = d.factor_bits == 32;
   auto op = [&](const cplx* v, cplx* zv, cplx* out) -> int {
     int pb = prof_begin(h);
-    if (launch_apply_f64out(h, v, zv, 1)) { h->err = "gcrodr: apply launch failed"; return ORAS_ERR_CUDA; }
+    const int arc = f32 ? launch_apply_f32out(h, v, (void*)z, 1) : launch_apply_f64out(h, v, zv, 1);
+    if (arc) { h->err = "gcrodr: apply launch failed"; return ORAS_ERR_CUDA; }
     prof_end(h, KC_APPLY, pb, apply_passes(h, 1));
     pb = prof_begin(h);
-    launch_spmv_f64(h, zv, out, 1);
-    prof_end(h, KC_SPMV64, pb, 1);
+    if (f32) {
+      launch_spmv_f32(h, (const void*)z, out, 1);
+      launch_rc_widen(st, N, (const void*)z, zv);
+    } else {
+      launch_spmv_f64(h, zv, out, 1);
+    }
+    prof_end(h, f32 ? KC_SPMV : KC_SPMV64, pb, f32 ? 2 : 1);
     return ORAS_OK;
   };
   // Y = beta Y + X coef (coef host, nq)
@@ -234,6 +246,13 @@ int gcrodr_solve(oras_handle* h, double tol, oras_info* info) {
     launch_rc_scale(st, N, r, 1.0 / rn, V);
     std::vector<zc> cvec(kk + steps + 1, zc(0.0)), zs;
     cvec[kk] = rn;
+    // least squares min || c - G z || kept by Givens rotations as the columns arrive: G is upper
+    // Hessenberg (its leading k x k block is diagonal), so column kk + j needs the rotations of the
+    // earlier columns and one new rotation; |rotated c[kk + j + 1]| is the residual estimate
+    std::vector<zc> Rg((size_t)(kk + steps) * (kk + steps), zc(0.0)), gr(cvec), rs(kk + steps);
+    std::vector<double> rc_(kk + steps);
+    const int rq = kk + steps;  // row stride of Rg
+    for (int i = 0; i < kk; ++i) Rg[(size_t)i * rq + i] = g(i, i);
     int nst = 0;
     for (int j = 0; j < steps; ++j) {
       cplx* vj = V + (size_t)j * N;
@@ -241,34 +260,62 @@ int gcrodr_solve(oras_handle* h, double tol, oras_info* info) {
       ++mv;
       int pb = prof_begin(h);
       const int nq = kk + j + 1;
-      std::vector<zc> hcol(nq, zc(0.0));
-      for (int pass = 0; pass < 2; ++pass) {  // w -= [C, V_0..V_j] ([C, V]^H w), twice
-        launch_rc_dots(st, N, nq, Wc, N, w, part.p, dots);
-        std::vector<zc> t;
-        if (int rc = get_dots(nq, t)) return rc;
-        std::vector<zc> neg(nq);
-        for (int q = 0; q < nq; ++q) {
-          hcol[q] += t[q];
-          neg[q] = -t[q];
-        }
-        if (int rc = add_comb(Wc, nq, neg, 1.0, w)) return rc;
-      }
-      double hn = 0.0;
-      if (int rc = norm_of(w, hn)) return rc;
-      for (int q = 0; q < nq; ++q) g(q, kk + j) = hcol[q];
-      g(kk + j + 1, kk + j) = hn;
-      if (hn > 0.0) launch_rc_scale(st, N, w, 1.0 / hn, V + (size_t)(j + 1) * N);
-      prof_end(h, KC_ORTH, pb, 4 * ((nq + rc_max_q() - 1) / rc_max_q()) + 4);
+      // w -= [C, V_0..V_j] ([C, V]^H w), twice (coefficients stay on the device), then ||w||
+      cplx* d1 = dots;
+      cplx* d2 = dots + nq;
+      cplx* dn = dots + 2 * nq;
+      launch_rc_dots(st, N, nq, Wc, N, w, part.p, d1);
+      launch_rc_lincomb(st, N, nq, 1, Wc, N, d1, 1.0, w, N, -1.0);
+      launch_rc_dots(st, N, nq, Wc, N, w, part.p, d2);
+      launch_rc_lincomb(st, N, nq, 1, Wc, N, d2, 1.0, w, N, -1.0);
+      launch_rc_dots(st, N, 1, w, N, w, part.p, dn);
+      RK(cudaMemcpyAsync(hbuf.data(), dots, sizeof(cplx) * (2 * nq + 1), cudaMemcpyDeviceToHost, st));
       RK(cudaMemcpyAsync(st_h, d.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
       RK(cudaStreamSynchronize(st));
       if (int sc = status_code(h, st_h)) return sc;
+      const double hn = std::sqrt(std::max(hbuf[2 * nq].re, 0.0));
+      for (int q = 0; q < nq; ++q)
+        g(q, kk + j) = zc(hbuf[q].re + hbuf[nq + q].re, hbuf[q].im + hbuf[nq + q].im);
+      g(kk + j + 1, kk + j) = hn;
+      if (hn > 0.0) launch_rc_scale(st, N, w, 1.0 / hn, V + (size_t)(j + 1) * N);
+      prof_end(h, KC_ORTH, pb, 4 * ((nq + rc_max_q() - 1) / rc_max_q()) + 5);
       nst = j + 1;
-      const int p = kk + nst + 1, q = kk + nst;
-      std::vector<zc> Gj((size_t)p * q), cj(cvec.begin(), cvec.begin() + p);
-      for (int i = 0; i < p; ++i)
-        for (int c = 0; c < q; ++c) Gj[(size_t)i * q + c] = g(i, c);
-      const double est = dense_lstsq(p, q, Gj, cj, zs) / bnorm;
+      // the new column through the earlier rotations, then its own rotation
+      const int cj = kk + j;
+      std::vector<zc> col(cj + 2);
+      for (int i = 0; i <= cj + 1; ++i) col[i] = g(i, cj);
+      for (int i = kk; i < cj; ++i) {
+        const zc x = col[i], y_ = col[i + 1];
+        col[i] = rc_[i] * x + rs[i] * y_;
+        col[i + 1] = -std::conj(rs[i]) * x + rc_[i] * y_;
+      }
+      {
+        const zc a = col[cj], b = col[cj + 1];
+        const double r = std::hypot(std::abs(a), std::abs(b));
+        double c;
+        zc s;
+        if (r == 0.0) { c = 1.0; s = 0.0; }
+        else if (std::abs(a) == 0.0) { c = 0.0; s = std::conj(b) / std::abs(b); }
+        else { c = std::abs(a) / r; s = (a / std::abs(a)) * std::conj(b) / r; }
+        rc_[cj] = c;
+        rs[cj] = s;
+        col[cj] = c * a + s * b;
+        const zc x = gr[cj], y_ = gr[cj + 1];
+        gr[cj] = c * x + s * y_;
+        gr[cj + 1] = -std::conj(s) * x + c * y_;
+      }
+      for (int i = 0; i <= cj; ++i) Rg[(size_t)i * rq + cj] = col[i];
+      const double est = std::abs(gr[cj + 1]) / bnorm;
       if (est <= tol || hn == 0.0) break;
+    }
+    {  // z from the triangular factor
+      const int q = kk + nst;
+      zs.assign(q, zc(0.0));
+      for (int i = q - 1; i >= 0; --i) {
+        zc s = gr[i];
+        for (int c = i + 1; c < q; ++c) s -= Rg[(size_t)i * rq + c] * zs[c];
+        zs[i] = s / Rg[(size_t)i * rq + i];
+      }
     }
     ++cycles;
     const int p = kk + nst + 1, q = kk + nst;

@@ -10,12 +10,13 @@ namespace oras {
 
 constexpr int RC_BLOCKS = 304;   // 2 x 152 SMs
 constexpr int RC_THREADS = 256;
-constexpr int RC_MAXQ = 8;       // columns per pass of the dot kernel (more go in further passes)
+constexpr int RC_MAXQ = 16;      // columns per pass of the dot kernel (more go in further passes)
 
-// partials[b][q] = sum over the rows of block b of conj(X_q[n]) w[n], q < nq <= RC_MAXQ
+// partials[b][q] = sum over the rows of block b of conj(X_q[n]) w[n], q < nq <= RC_MAXQ: per
+// thread, then a shuffle tree per warp, then the warps in order
 __global__ void __launch_bounds__(RC_THREADS) k_rc_dots(int64_t n, int nq, const cplx* __restrict__ X, int64_t ldx,
                                                         const cplx* __restrict__ w, cplx* __restrict__ partials) {
-  __shared__ cplx sh[RC_MAXQ][RC_THREADS];
+  __shared__ cplx sh[RC_THREADS / 32][RC_MAXQ];
   cplx acc[RC_MAXQ];
 #pragma unroll
   for (int q = 0; q < RC_MAXQ; ++q) acc[q] = {0.0, 0.0};
@@ -31,16 +32,23 @@ __global__ void __launch_bounds__(RC_THREADS) k_rc_dots(int64_t n, int nq, const
         acc[q].im += x.re * wv.im - x.im * wv.re;
       }
   }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < RC_MAXQ; ++q) sh[q][threadIdx.x] = acc[q];
-  __syncthreads();
-  for (int s = RC_THREADS / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
+  for (int q = 0; q < RC_MAXQ; ++q) {
+    cplx t = acc[q];
 #pragma unroll
-      for (int q = 0; q < RC_MAXQ; ++q) sh[q][threadIdx.x] = cadd(sh[q][threadIdx.x], sh[q][threadIdx.x + s]);
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+      t.re += __shfl_xor_sync(0xffffffffu, t.re, o);
+      t.im += __shfl_xor_sync(0xffffffffu, t.im, o);
+    }
+    if (lane == 0) sh[warp][q] = t;
   }
-  if (threadIdx.x < nq) partials[(int64_t)blockIdx.x * RC_MAXQ + threadIdx.x] = sh[threadIdx.x][0];
+  __syncthreads();
+  if (threadIdx.x < nq) {
+    cplx t = sh[0][threadIdx.x];
+    for (int v = 1; v < RC_THREADS / 32; ++v) t = cadd(t, sh[v][threadIdx.x]);
+    partials[(int64_t)blockIdx.x * RC_MAXQ + threadIdx.x] = t;
+  }
 }
 
 // out[q] = fixed-order sum over the blocks of partials[b][q]
@@ -52,10 +60,10 @@ __global__ void k_rc_sum(int nq, const cplx* __restrict__ partials, cplx* __rest
   out[q] = t;
 }
 
-// Y_c[n] = beta * Y_c[n] + sum_q X_q[n] M[q][c]  (M: nq x nc row-major on the device)
+// Y_c[n] = beta * Y_c[n] + alpha * sum_q X_q[n] M[q][c]  (M: nq x nc row-major on the device)
 __global__ void __launch_bounds__(RC_THREADS) k_rc_lincomb(int64_t n, int nq, int nc, const cplx* __restrict__ X,
-                                                           int64_t ldx, const cplx* __restrict__ M, double beta,
-                                                           cplx* __restrict__ Y, int64_t ldy) {
+                                                           int64_t ldx, const cplx* __restrict__ M, double alpha,
+                                                           double beta, cplx* __restrict__ Y, int64_t ldy) {
   const int64_t total = n * nc;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(e / n);
@@ -69,7 +77,7 @@ __global__ void __launch_bounds__(RC_THREADS) k_rc_lincomb(int64_t n, int nq, in
     }
     cplx& y = Y[c * ldy + i];
     const cplx y0 = beta == 0.0 ? cplx{0.0, 0.0} : y;
-    y = {beta * y0.re + t.re, beta * y0.im + t.im};
+    y = {beta * y0.re + alpha * t.re, beta * y0.im + alpha * t.im};
   }
 }
 
@@ -77,6 +85,12 @@ __global__ void __launch_bounds__(RC_THREADS) k_rc_lincomb(int64_t n, int nq, in
 __global__ void k_rc_scale(int64_t n, const cplx* __restrict__ x, double s, cplx* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = {s * x[i].re, s * x[i].im};
+}
+
+// out[n] = x[n] (complex FP32 to FP64, exact)
+__global__ void k_rc_widen(int64_t n, const CT<float>* __restrict__ x, cplx* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = {(double)x[i].re, (double)x[i].im};
 }
 
 static unsigned rc_grid(int64_t work) {
@@ -98,10 +112,15 @@ void launch_rc_dots(cudaStream_t st, int64_t n, int nq, const cplx* X, int64_t l
   }
 }
 
-// Y = beta Y + X M (nc columns of Y, ldy apart; M nq x nc row-major on the device)
+// Y = beta Y + alpha X M (nc columns of Y, ldy apart; M nq x nc row-major on the device)
 void launch_rc_lincomb(cudaStream_t st, int64_t n, int nq, int nc, const cplx* X, int64_t ldx, const cplx* M,
-                       double beta, cplx* Y, int64_t ldy) {
-  k_rc_lincomb<<<rc_grid(n * nc), RC_THREADS, 0, st>>>(n, nq, nc, X, ldx, M, beta, Y, ldy);
+                       double beta, cplx* Y, int64_t ldy, double alpha) {
+  k_rc_lincomb<<<rc_grid(n * nc), RC_THREADS, 0, st>>>(n, nq, nc, X, ldx, M, alpha, beta, Y, ldy);
+  count_launches(1);
+}
+
+void launch_rc_widen(cudaStream_t st, int64_t n, const void* x, cplx* out) {
+  k_rc_widen<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, (const CT<float>*)x, out);
   count_launches(1);
 }
 
