@@ -203,3 +203,29 @@ def test_face_kind_table_brute_force():
         for lf, fv in enumerate(basis.LOCAL_FACES):
             opp = (set(range(4)) - set(fv)).pop()
             assert tab[t, lf] == kind[t, list(tets[t]).index(st[opp])]
+
+
+def test_scattering_matrix_is_reciprocal():
+    """A = A^T and ports of equal size and beta make S symmetric (S_ij = S_ji): eight ports on
+    the side faces of a lossy cube with a metallic bottom, direct solves, 1e-10.  The ports' faces
+    meet the metallic bottom, so constrained unknowns lie in some ports."""
+    xyz, tets = synth.kuhn_cube(2)
+    nt = len(tets)
+    rng = np.random.default_rng(4)
+    eps = rng.uniform(30, 60, nt) - 1j * rng.uniform(5, 25, nt)
+    mu = np.ones(nt, dtype=np.complex128)
+    beta_p = float(np.sqrt(1.85 ** 2 * 59.0 - (np.pi / 0.5) ** 2))
+    P = []
+    for z0 in (0.0, 0.5):
+        P.append(ports.Port(np.array([0.0, 0.0, z0]), np.array([0.0, 0.5, 0.0]), np.array([0.0, 0.0, 0.5]), beta_p))
+        P.append(ports.Port(np.array([1.0, 0.5, z0]), np.array([0.0, 0.5, 0.0]), np.array([0.0, 0.0, 0.5]), beta_p))
+        P.append(ports.Port(np.array([0.5, 0.0, z0]), np.array([0.5, 0.0, 0.0]), np.array([0.0, 0.0, 0.5]), beta_p))
+        P.append(ports.Port(np.array([0.0, 1.0, z0]), np.array([0.5, 0.0, 0.0]), np.array([0.0, 0.0, 0.5]), beta_p))
+    kind = wall_kinds(xyz, tets, [(2, 0.0)])
+    prob = problem.build(xyz, tets, eps, mu, 1.85, 2, [("port", q, None) for q in P], with_oras=False,
+                         beta_face=np.full((nt, 4), beta_p), face_kind=kind)
+    X = spla.spsolve(prob.A.tocsc(), prob.B)
+    S = ports.s_matrix(prob.topo, xyz, P, X)
+    assert ports.s_error(S, S.T) <= 1e-10
+    assert np.linalg.norm(S - np.diag(np.diag(S))) > 1e-3 * np.linalg.norm(S)
+    assert any(np.any(prob.mask[np.nonzero(ports.port_vector(prob.topo, xyz, q)[0])[0]]) for q in P)
