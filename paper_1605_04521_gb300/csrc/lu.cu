@@ -291,7 +291,10 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_tournament(LuArgs a, void* ar
 //
 // With the two parts of a complex entry in two threads, a complex multiply-subtract
 // x -= l * u becomes, in each thread, x_part -= al * Re(u) + be * Im(u) with (al, be) = (Re l,
-// -Im l) for the real part and (Im l, Re l) for the imaginary part.
+// -Im l) for the real part and (Im l, Re l) for the imaginary part.  The block's pivot rows are
+// kept column by column ([column][pivot], the 8 values of a column contiguous), so the rank-8
+// update of one entry is 8 packed FP32 multiply-adds (fma.rn.f32x2) over pairs of pivots: the
+// pair of partial sums is added at the end.
 constexpr int RI_THREADS = 512;
 constexpr int RI_ROWS = RI_THREADS / 2;
 constexpr int RI_WARPS = RI_THREADS / 32;
@@ -299,8 +302,8 @@ struct RiGepp {
   alignas(16) float candr[2][RI_WARPS][8];             // each warp's best candidate's in-block values
   alignas(16) float candi[2][RI_WARPS][8];
   uint32_t wk[2][RI_WARPS];                            // each warp's best pivot key (by column parity)
-  alignas(16) float Pr[8][TB];                         // the block's pivot rows (rotated positions)
-  alignas(16) float Pi[8][TB];
+  alignas(16) float Pr[TB][8];                         // the block's pivot rows: [rotated position][pivot]
+  alignas(16) float Pi[TB][8];
   int order[TB];                                       // pivot rank -> candidate position
 };
 
@@ -371,22 +374,24 @@ __device__ __forceinline__ void gepp_ri(float (&x)[TB], bool valid, RiGepp& g, i
     }
     // the block's pivot rows: in-block multipliers and U values, then the stale part right of it
     if (my_c8 >= 0) {
-      float* dst = part ? g.Pi[my_c8] : g.Pr[my_c8];
+      float(*dst)[8] = part ? g.Pi : g.Pr;
 #pragma unroll
       for (int jb = 0; jb < TB / 8; ++jb)
         if (8 * jb < lim) {
 #pragma unroll
-          for (int j = 8 * jb; j < 8 * jb + 8; ++j) dst[j] = x[j];
+          for (int j = 8 * jb; j < 8 * jb + 8; ++j) dst[j][my_c8] = x[j];
         }
     }
-    // the row's 8 multipliers as (al, be) pairs (exchanged before any divergence)
-    float nal[8], nbe[8];
+    // the row's 8 negated multipliers as (al, be) parts, in pivot pairs (exchanged before any
+    // divergence)
+    float2 nal[4], nbe[4];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const float xo = __shfl_xor_sync(FULL, x[q], 1);
       const float lr = part ? xo : x[q], li = part ? x[q] : xo;
-      nal[q] = -(part ? li : lr);
-      nbe[q] = -(part ? lr : -li);
+      const float al = -(part ? li : lr), be = -(part ? lr : -li);
+      if (q & 1) { nal[q >> 1].y = al; nbe[q >> 1].y = be; }
+      else { nal[q >> 1].x = al; nbe[q >> 1].x = be; }
     }
     __syncthreads();
     // U12 = L11^{-1} A12: pivot row c8 right of the block minus its multipliers times the earlier ones
@@ -394,49 +399,47 @@ __device__ __forceinline__ void gepp_ri(float (&x)[TB], bool valid, RiGepp& g, i
       const int j = 8 + t;
       float ur[8], ui[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) { ur[q] = g.Pr[q][j]; ui[q] = g.Pi[q][j]; }
+      for (int q = 0; q < 8; ++q) { ur[q] = g.Pr[j][q]; ui[q] = g.Pi[j][q]; }
 #pragma unroll
       for (int c8 = 1; c8 < 8; ++c8) {
 #pragma unroll
         for (int q = 0; q < c8; ++q) {
-          const float lr = g.Pr[c8][q], li = g.Pi[c8][q];
+          const float lr = g.Pr[q][c8], li = g.Pi[q][c8];  // multiplier of pivot c8 in column q
           ur[c8] -= lr * ur[q] - li * ui[q];
           ui[c8] -= lr * ui[q] + li * ur[q];
         }
-        g.Pr[c8][j] = ur[c8];
-        g.Pi[c8][j] = ui[c8];
       }
+#pragma unroll
+      for (int q = 1; q < 8; ++q) { g.Pr[j][q] = ur[q]; g.Pi[j][q] = ui[q]; }
     }
     __syncthreads();
     if (my_c8 >= 0) {  // the block's pivot rows take their corrected values
-      const float* src = part ? g.Pi[my_c8] : g.Pr[my_c8];
+      const float(*src)[8] = part ? g.Pi : g.Pr;
 #pragma unroll
       for (int jb = 1; jb < TB / 8; ++jb)
         if (8 * jb < lim) {
 #pragma unroll
-          for (int j = 8 * jb; j < 8 * jb + 8; ++j) x[j] = src[j];
+          for (int j = 8 * jb; j < 8 * jb + 8; ++j) x[j] = src[j][my_c8];
         }
     } else if (valid && !chosen) {  // A22 -= L21 U12: rank-8 update right of the block
 #pragma unroll
       for (int jb = 1; jb < TB / 8; ++jb)
         if (8 * jb < lim) {
 #pragma unroll
-          for (int h4 = 0; h4 < 2; ++h4) {
-            const int j0 = 8 * jb + 4 * h4;
-            float a0 = x[j0], a1 = x[j0 + 1], a2 = x[j0 + 2], a3 = x[j0 + 3];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const float4 ur = *reinterpret_cast<const float4*>(&g.Pr[q][j0]);
-              const float4 ui = *reinterpret_cast<const float4*>(&g.Pi[q][j0]);
-              a0 = fmaf(nbe[q], ui.x, fmaf(nal[q], ur.x, a0));
-              a1 = fmaf(nbe[q], ui.y, fmaf(nal[q], ur.y, a1));
-              a2 = fmaf(nbe[q], ui.z, fmaf(nal[q], ur.z, a2));
-              a3 = fmaf(nbe[q], ui.w, fmaf(nal[q], ur.w, a3));
-            }
-            x[j0] = a0;
-            x[j0 + 1] = a1;
-            x[j0 + 2] = a2;
-            x[j0 + 3] = a3;
+          for (int j = 8 * jb; j < 8 * jb + 8; ++j) {
+            const float4* ur = reinterpret_cast<const float4*>(g.Pr[j]);
+            const float4* ui = reinterpret_cast<const float4*>(g.Pi[j]);
+            const float4 u0 = ur[0], u1 = ur[1], w0 = ui[0], w1 = ui[1];
+            float2 acc = make_float2(x[j], 0.0f);
+            acc = __ffma2_rn(nal[0], make_float2(u0.x, u0.y), acc);
+            acc = __ffma2_rn(nal[1], make_float2(u0.z, u0.w), acc);
+            acc = __ffma2_rn(nal[2], make_float2(u1.x, u1.y), acc);
+            acc = __ffma2_rn(nal[3], make_float2(u1.z, u1.w), acc);
+            acc = __ffma2_rn(nbe[0], make_float2(w0.x, w0.y), acc);
+            acc = __ffma2_rn(nbe[1], make_float2(w0.z, w0.w), acc);
+            acc = __ffma2_rn(nbe[2], make_float2(w1.x, w1.y), acc);
+            acc = __ffma2_rn(nbe[3], make_float2(w1.z, w1.w), acc);
+            x[j] = acc.x + acc.y;
           }
         }
     }
