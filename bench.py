@@ -326,7 +326,9 @@ def roofline(timings, upd_flops_per_factor, apply_bytes, factors, hbm, bf16_sus,
         ms, launches = cls["apply"]
         achieved = apply_bytes * launches / (ms / 1e3) / 1e9
         out["apply"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                        "traffic": None, "kernel": "k_apply (ORAS preconditioner, one arena pass per launch)"}
+                        "traffic": None, "kernel": "k_apply / k_apply4 (ORAS preconditioner, one arena pass per launch, or "
+                                                   "per pair of concurrent launches when the largest subdomains "
+                                                   "take four CTAs)"}
     if "spmv" in cls and spmv:
         ms, _ = cls["spmv"]
         achieved = spmv / (ms / 1e3) / 1e9

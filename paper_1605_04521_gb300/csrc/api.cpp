@@ -34,6 +34,7 @@ int launch_apply_f64out(const oras_handle* h, const cplx* v, cplx* z, int k);
 int launch_apply_f32out(const oras_handle* h, const cplx* v, void* z, int k);
 size_t apply_yglob_bytes_for(const oras_handle* h, int k);
 int apply_passes(const oras_handle* h, int k);
+int plan_apply_groups(const oras_handle* h, int num_sms, std::vector<int32_t>& order);
 void launch_spmv_f64(const oras_handle* h, const cplx* x, cplx* y, int k);
 void launch_spmv_f32(const oras_handle* h, const void* x, cplx* y, int k);
 void launch_split_vals(const oras_handle* h);
@@ -153,7 +154,7 @@ static void dfree_all(Device& d) {
                   d.sub_dofs, d.sub_pou, d.member, d.cm, d.ck, d.cs, d.fl, d.tc, d.ta, d.tm, d.eps, d.mu,
                   d.elem, d.fmat, d.vals, d.vals_df, d.arena, d.perm, d.gidx, d.sub_np_off, d.lu_cand, d.lu_cnt,
                   d.lu_ipiv, d.lu_diag, d.dinv, d.sub_inv_off, d.status, d.V, d.Zf, d.Zd, d.w, d.xk, d.bk, d.tmp, d.H, d.gcs, d.gsn,
-                  d.g, d.red, d.scal, d.ybuf, d.io};
+                  d.g, d.red, d.scal, d.ybuf, d.io, d.apply_subs};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, d.stream);
   cudaStreamSynchronize(d.stream);  // the frees have run: the memory is back in the pool
@@ -199,6 +200,22 @@ static int upload(oras_handle* h) {
   std::vector<int64_t> npoff(m.nsub + 1, 0);
   for (int q = 0; q < m.nsub; ++q) npoff[q + 1] = npoff[q] + m.sub_np[q];
   CK(dput(d.sub_np_off, npoff, s));
+  {  // the apply's work split (which subdomains take four CTAs)
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, d.device));
+    std::vector<int32_t> order;
+    d.apply_n4 = plan_apply_groups(h, nsm, order);
+    if (d.apply_n4 > 0) {
+      CK(dput(d.apply_subs, order, s));
+      d.apply_np4 = m.sub_np[order[0]];
+      d.apply_np2 = d.apply_n4 < m.nsub ? m.sub_np[order[d.apply_n4]] : 0;
+      if (!h->apply_side) {
+        CK(cudaStreamCreateWithFlags(&h->apply_side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->apply_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->apply_join, cudaEventDisableTiming));
+      }
+    }
+  }
   CK(dput(d.cm, T.cm, s));
   CK(dput(d.ck, T.ck, s));
   CK(dput(d.cs, T.cs, s));
@@ -316,6 +333,7 @@ int64_t footprint_bytes(const oras_handle* h, int k) {
   add((int64_t)(m.nsub + 1) * 8);
   add(blocks * 2 * TB * TB * (int64_t)el);                          // inverted diagonal blocks
   add((int64_t)apply_yglob_bytes_for(h, std::max(k, 1)));
+  add((int64_t)m.nsub * 4);                                         // apply work split
   // Krylov workspace and I/O staging
   const int64_t nk = N * std::max(k, 1), kk = std::max(k, 1);
   add(nk * (mm + 1) * 16);                                          // V
@@ -573,6 +591,12 @@ void oras_destroy(oras_handle* h) {
   for (auto e : h->evpool) cudaEventDestroy(e);
   for (auto g : h->step_graph)
     if (g) cudaGraphExecDestroy(g);
+  if (h->apply_side) {
+    cudaStreamSynchronize(h->apply_side);
+    cudaStreamDestroy(h->apply_side);
+  }
+  if (h->apply_fork) cudaEventDestroy(h->apply_fork);
+  if (h->apply_join) cudaEventDestroy(h->apply_join);
   if (h->dev.uploaded) {
     cudaStreamSynchronize(h->dev.stream);
     if (h->rc_U) cudaFreeAsync(h->rc_U, h->dev.stream);

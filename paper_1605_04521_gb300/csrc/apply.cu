@@ -1,10 +1,15 @@
 // ORAS preconditioner apply (Sec. 4):  z = sum_s R_s^T D_s A_s^{-1} R_s v
 // with A_s^{-1} = U_s^{-1} L_s^{-1} P_s from the batched LU.  One cluster of two CTAs per
 // subdomain (body in apply.cuh); one launch serves a group of up to KR right-hand sides, so the
-// factor arena is streamed once per group.  The local vectors live in shared memory when they fit
+// factor arena is streamed once per group.  When two CTAs per subdomain leave SMs idle and the
+// largest subdomains would set the apply's time (one CTA streams at a rate set by the bytes its
+// ring keeps in flight), those subdomains get clusters of four CTAs in a second launch on a side
+// stream, concurrent with the two-CTA launch of the others (fork and join with events).  The local vectors live in shared memory when they fit
 // next to the tile ring, else in a global scratch slice.  With the Boolean partition of unity
 // every global DOF is written by exactly one subdomain (no atomics); OAS (no D_s) accumulates with
 // atomics.
+#include <algorithm>
+
 #include "apply.cuh"
 
 namespace oras {
@@ -24,20 +29,31 @@ static bool use_tc(const oras_handle* h, int k) {
   return k >= APPLY_TC_MIN_K && h->opt.factor_bits == 32 && h->opt.apply_engine != ORAS_APPLY_CUDA_CORES;
 }
 
+// subs: the subdomain of each cluster (nullptr: cluster q takes subdomain q)
 template <typename R, typename ZT, int KR>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(APPLY_THREADS, 1)
-    k_apply(ApplyGeom a, int k, int r0, int nr, void* yglob, const cplx* __restrict__ v, ZT* __restrict__ z) {
-  apply_cluster<R, ZT, KR>(a, blockIdx.x / 2, v, k, z, k, r0, nr, (CT<R>*)yglob);
+    k_apply(ApplyGeom a, const int32_t* subs, int k, int r0, int nr, void* yglob, const cplx* __restrict__ v,
+            ZT* __restrict__ z) {
+  const int q = blockIdx.x / 2;
+  apply_cluster<R, ZT, KR, 2>(a, subs ? subs[q] : q, v, k, z, k, r0, nr, (CT<R>*)yglob);
+}
+
+template <typename R, typename ZT, int KR>
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(APPLY_THREADS, 1)
+    k_apply4(ApplyGeom a, const int32_t* subs, int k, int r0, int nr, void* yglob, const cplx* __restrict__ v,
+             ZT* __restrict__ z) {
+  apply_cluster<R, ZT, KR, 4>(a, subs[blockIdx.x / 4], v, k, z, k, r0, nr, (CT<R>*)yglob);
 }
 
 constexpr size_t SMEM_LIMIT = 227 * 1024 - 2048;  // opt-in shared memory per block less the static part
 
-// Ring depth and dynamic shared memory for KR right-hand sides per pass; y in shared memory when
-// `allow_smem_y` and it fits next to a ring of at least 3 stages (2 when nothing else fits).
-template <typename R, int KR>
-static void apply_config(const oras_handle* h, bool allow_smem_y, int* S, size_t* smem, bool* y_smem) {
-  using Sm = ApplySmem<R, KR>;
-  const int64_t ystrips = (h->mesh.max_np / TB + 1) / 2;
+// Ring depth and dynamic shared memory for KR right-hand sides per pass and G CTAs per subdomain,
+// for subdomains of padded order up to max_np; y in shared memory when `allow_smem_y` and it fits
+// next to a ring of at least 2 stages.
+template <typename R, int KR, int G>
+static void apply_config(int64_t max_np, bool allow_smem_y, int* S, size_t* smem, bool* y_smem) {
+  using Sm = ApplySmem<R, KR, G>;
+  const int64_t ystrips = (max_np / TB + G - 1) / G;
   if (allow_smem_y)
     for (int q = 8; q >= 2; --q)
       if (Sm::total(q, ystrips) <= SMEM_LIMIT) {
@@ -74,17 +90,46 @@ static int group_kr(int rem, int maxkr) {
   return kr;
 }
 
+// Largest padded order among the subdomains that take G CTAs (0: none).
+static int64_t group_max_np(const oras_handle* h, int G) {
+  const auto& d = h->dev;
+  if (d.apply_n4 == 0) return G == 2 ? h->mesh.max_np : 0;
+  return G == 4 ? d.apply_np4 : d.apply_np2;
+}
+
 template <typename R, typename ZT, int KR>
 static int apply_group(const oras_handle* h, const cplx* v, ZT* z, int k, int r0, int nr) {
   const auto& m = h->mesh;
   const auto& d = h->dev;
-  ApplyGeom a = apply_geom(h);
-  size_t smem;
-  bool y_smem;
-  apply_config<R, KR>(h, true, &a.stages, &smem, &y_smem);
-  if (!y_smem && (!d.ybuf || d.ybuf_bytes < apply_yglob_bytes(h, KR))) return -1;
+  const int n4 = d.apply_n4;
+  void* yb = nullptr;
+  ApplyGeom a2 = apply_geom(h), a4 = apply_geom(h);
+  size_t smem2 = 0, smem4 = 0;
+  bool ys2 = true, ys4 = true;
+  if (m.nsub > n4) apply_config<R, KR, 2>(group_max_np(h, 2), true, &a2.stages, &smem2, &ys2);
+  if (n4 > 0) apply_config<R, KR, 4>(group_max_np(h, 4), true, &a4.stages, &smem4, &ys4);
+  if (!ys2 || !ys4) {
+    if (!d.ybuf || d.ybuf_bytes < apply_yglob_bytes(h, KR)) return -1;
+    yb = d.ybuf;
+  }
   allow_max_smem((const void*)k_apply<R, ZT, KR>);
-  k_apply<R, ZT, KR><<<2 * m.nsub, APPLY_THREADS, smem, d.stream>>>(a, k, r0, nr, y_smem ? nullptr : d.ybuf, v, z);
+  if (n4 == 0) {  // one launch, two CTAs per subdomain
+    k_apply<R, ZT, KR><<<2 * m.nsub, APPLY_THREADS, smem2, d.stream>>>(a2, nullptr, k, r0, nr, ys2 ? nullptr : yb, v, z);
+    return 0;
+  }
+  // the largest subdomains (the first n4 of apply_subs) on the side stream, four CTAs each
+  allow_max_smem((const void*)k_apply4<R, ZT, KR>);
+  if (cudaEventRecord(h->apply_fork, d.stream) != cudaSuccess ||
+      cudaStreamWaitEvent(h->apply_side, h->apply_fork, 0) != cudaSuccess)
+    return -1;
+  k_apply4<R, ZT, KR><<<4 * n4, APPLY_THREADS, smem4, h->apply_side>>>(a4, d.apply_subs, k, r0, nr,
+                                                                       ys4 ? nullptr : yb, v, z);
+  if (m.nsub > n4)
+    k_apply<R, ZT, KR><<<2 * (m.nsub - n4), APPLY_THREADS, smem2, d.stream>>>(a2, d.apply_subs + n4, k, r0, nr,
+                                                                             ys2 ? nullptr : yb, v, z);
+  if (cudaEventRecord(h->apply_join, h->apply_side) != cudaSuccess ||
+      cudaStreamWaitEvent(d.stream, h->apply_join, 0) != cudaSuccess)
+    return -1;
   return 0;
 }
 
@@ -111,7 +156,7 @@ static int apply_t(const oras_handle* h, const cplx* v, ZT* z, int k) {
     else if (kr == 2) rc = apply_group<R, ZT, 2>(h, v, z, k, r0, nr);
     else if constexpr (sizeof(R) == 4) rc = apply_group<R, ZT, 4>(h, v, z, k, r0, nr);
     r0 += nr;
-    ++launches;
+    launches += h->dev.apply_n4 > 0 ? 2 : 1;
   }
   count_launches(launches);
   if (rc) return rc;
@@ -127,7 +172,8 @@ int launch_apply_f32out(const oras_handle* h, const cplx* v, void* z, int k) {
   return apply_t<float, CT<float>>(h, v, (CT<float>*)z, k);
 }
 
-// Number of apply launches (arena passes) for k right-hand sides.
+// Number of arena passes for k right-hand sides (each pass is one launch, or two when the largest
+// subdomains take four CTAs).
 int apply_passes(const oras_handle* h, int k) {
   if (use_tc(h, k) && apply_tc_available(h)) return apply_tc_passes(k);
   const int maxkr = h->dev.factor_bits == 64 ? APPLY_MAX_KR_F64 : APPLY_MAX_KR_F32;
@@ -140,9 +186,10 @@ template <typename R, int KR>
 static size_t yglob_bytes_kr(const oras_handle* h) {
   int S;
   size_t smem;
-  bool y_smem;
-  apply_config<R, KR>(h, true, &S, &smem, &y_smem);
-  if (y_smem) return 0;
+  bool y_smem = true, y4 = true;
+  if (h->mesh.nsub > h->dev.apply_n4) apply_config<R, KR, 2>(group_max_np(h, 2), true, &S, &smem, &y_smem);
+  if (h->dev.apply_n4 > 0) apply_config<R, KR, 4>(group_max_np(h, 4), true, &S, &smem, &y4);
+  if (y_smem && y4) return 0;
   int64_t total = 0;
   for (int s = 0; s < h->mesh.nsub; ++s) total += h->mesh.sub_np[s];
   return (size_t)total * KR * sizeof(CT<R>);
@@ -173,8 +220,31 @@ size_t apply_yglob_bytes_for(const oras_handle* h, int k) {
 // Shared-memory configuration for the allocation-free variant (local vectors in global memory).
 void apply_noalloc_config(const oras_handle* h, int* S, size_t* smem) {
   bool y_smem;
-  if (h->dev.factor_bits == 64) apply_config<double, 1>(h, false, S, smem, &y_smem);
-  else apply_config<float, 1>(h, false, S, smem, &y_smem);
+  if (h->dev.factor_bits == 64) apply_config<double, 1, 2>(h->mesh.max_np, false, S, smem, &y_smem);
+  else apply_config<float, 1, 2>(h->mesh.max_np, false, S, smem, &y_smem);
+}
+
+// Which subdomains take four CTAs: with one CTA per SM, a subdomain's apply time is about its
+// factor bytes over the CTAs streaming it.  When two CTAs per subdomain fit on the SMs in one
+// wave, the largest subdomains get four CTAs while the SMs last, as many as lower the largest
+// remaining time (bytes / CTAs), and no more.  Fills `order` (the subdomains, four-CTA ones
+// first, each part by decreasing size) and returns how many take four CTAs.
+int plan_apply_groups(const oras_handle* h, int num_sms, std::vector<int32_t>& order) {
+  const auto& m = h->mesh;
+  order.resize(m.nsub);
+  for (int s = 0; s < m.nsub; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return m.sub_np[x] > m.sub_np[y]; });
+  if (m.nsub < 1 || 2 * (int64_t)m.nsub > num_sms) return 0;
+  auto cost = [&](int n4) {  // the largest (np^2 / CTAs) over the subdomains
+    double c = 0.0;
+    if (n4 > 0) c = (double)m.sub_np[order[0]] * m.sub_np[order[0]] / 4.0;
+    if (n4 < m.nsub) c = std::max(c, (double)m.sub_np[order[n4]] * m.sub_np[order[n4]] / 2.0);
+    return c;
+  };
+  int best = 0;
+  for (int n4 = 1; n4 <= m.nsub && 2 * (int64_t)(m.nsub + n4) <= num_sms; ++n4)
+    if (cost(n4) < 0.9 * cost(best)) best = n4;
+  return best;
 }
 
 }  // namespace oras

@@ -5,20 +5,21 @@
 // TB x KR block of KR right-hand sides: warp w takes rows 8w..8w+7, lane l the column pair 2l, 2l+1.  One pass over the arena serves all
 // KR right-hand sides: the factor bytes are read once per group, not once per vector.
 //
-// A cluster of two CTAs works on one subdomain.  CTA c owns the block rows (strips) I with
-// I % 2 == c: it keeps their entries of y (shared memory, or a global slice when they do not
-// fit) and streams the tiles of the block columns J with J % 2 == c, which are exactly its own
-// strips.  For every strip both CTAs form partial sums over their own block columns; the
-// non-owner sends its TB x KR partial sums into the owner's shared memory (distributed shared
-// memory, mbarrier with cluster-scope release/acquire) and the owner applies the inverted
-// diagonal block.  Tiles stream through a ring of shared-memory stages filled by 1-D bulk TMA
+// A cluster of G CTAs (2, or 4 for the largest subdomains of a launch that leaves SMs idle) works
+// on one subdomain.  CTA c owns the block rows (strips) I with I % G == c: it keeps their entries
+// of y (shared memory, or a global slice when they do not fit) and streams the tiles of the block
+// columns J with J % G == c, which are exactly its own strips.  For every strip all G CTAs form
+// partial sums over their own block columns; the G - 1 non-owners send their TB x KR partial sums
+// into their slots of the owner's shared memory (distributed shared memory, an mbarrier that
+// counts G - 1 cluster-scope release arrivals) and the owner applies the inverted diagonal
+// block.  Tiles stream through a ring of shared-memory stages filled by 1-D bulk TMA
 // copies from one producer warp; eight consumer warps compute.  When y lives in global memory,
 // every stage also carries the TB x KR slice y_J its tile multiplies: the producer copies it once
 // the consumers have finalised strip J (a shared counter, with a proxy fence on the writer side),
 // so the consumers never wait on a global load.  Every wait is bounded (ApplyGeom::wait_ns, 2 s
 // by default); a timeout sets the device status flag and the block finishes without further
 // work, after waiting (at least 2 s) for its own bulk copies still in flight.  apply_cluster
-// returns whether either CTA of the cluster gave up, the same value in both.
+// returns whether any CTA of the cluster gave up, the same value in all.
 #pragma once
 
 #include "dev.cuh"
@@ -86,7 +87,7 @@ __device__ __forceinline__ void st_cpair(CT<double>* p, CT<double> a, CT<double>
 // right-hand sides per pass and the number of owned strips kept in shared memory (0 when y
 // lives in global memory).  All TB x KR blocks are stored [KR][TB] (one 64-entry column per
 // right-hand side), so a lane's pair of rows is contiguous for every right-hand side.
-template <typename R, int KR>
+template <typename R, int KR, int G>
 struct ApplySmem {
   static constexpr size_t C = sizeof(CT<R>);
   static constexpr uint32_t YB = TB * KR * sizeof(CT<R>);  // y slice staged beside a tile
@@ -94,7 +95,8 @@ struct ApplySmem {
   static __host__ __device__ uint32_t slot(int64_t ystrips) { return tile_bytes<R>() + (ystrips ? 0u : YB); }
   static __host__ __device__ size_t bar_off(int S, int64_t ys) { return (size_t)S * slot(ys); }
   static __host__ __device__ size_t recv_off(int S, int64_t ys) { return bar_off(S, ys) + (size_t)(2 * S + 2) * 8; }
-  static __host__ __device__ size_t part_off(int S, int64_t ys) { return recv_off(S, ys) + 2 * TB * KR * C; }
+  // receive buffers: [2 (strip parity at the owner)][G - 1 (sender slot)][TB x KR]
+  static __host__ __device__ size_t part_off(int S, int64_t ys) { return recv_off(S, ys) + 2 * (G - 1) * TB * KR * C; }
   static __host__ __device__ size_t rvec_off(int S, int64_t ys) { return part_off(S, ys) + TB * KR * C; }
   static __host__ __device__ size_t y_off(int S, int64_t ys) { return rvec_off(S, ys) + TB * KR * C; }
   static __host__ __device__ size_t total(int S, int64_t ys) { return y_off(S, ys) + (size_t)ys * TB * KR * C; }
@@ -102,11 +104,50 @@ struct ApplySmem {
 
 // v and z are [N][vs] / [N][zs] complex arrays; this pass handles right-hand sides off .. off+nr-1
 // (nr <= KR; the unused lanes of the last group carry zeros and are not stored).
-template <typename R, typename ZT, int KR>
+// The order in which CTA c of a G-CTA group streams its tiles: the forward pass strip by strip
+// (the tiles of its own block columns left of the diagonal, then the diagonal block's L^{-1} when
+// it owns the strip), then the backward pass from the last strip up (its own block columns right
+// of the diagonal, then U^{-1}).  J >= 0: tile (I, J); J == -1: the diagonal inverse of strip I.
+template <int G>
+struct TileCursor {
+  int64_t nts, I, J;
+  int c, pass;  // pass 0 forward, 1 backward, 2 finished
+  __device__ void init(int64_t n, int cc) {
+    nts = n; c = cc; I = 0; J = cc;
+    pass = n > 0 ? 0 : 2;
+    settle();
+  }
+  __device__ void settle() {  // to the first item at or after (pass, I, J)
+    for (;;) {
+      if (pass == 2) return;
+      if (J >= 0) {
+        if (J < (pass == 0 ? I : nts)) return;
+        J = (I % G == c) ? -1 : -2;
+      }
+      if (J == -1) return;
+      if (pass == 0) {
+        if (++I == nts) { pass = 1; I = nts - 1; }
+      } else if (--I < 0) {
+        pass = 2;
+        return;
+      }
+      J = pass == 0 ? c : first_right(I, c);
+    }
+  }
+  __device__ void next() {
+    J = J >= 0 ? J + G : -2;
+    settle();
+  }
+  // the first block column right of strip I in the columns of CTA c
+  static __device__ int64_t first_right(int64_t I, int c) { return I + 1 + (((int64_t)c - (I + 1)) % G + G) % G; }
+};
+
+template <typename R, typename ZT, int KR, int G>
 __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict__ v, int64_t vs,
                               ZT* __restrict__ z, int64_t zs, int64_t off, int nr, CT<R>* yglob) {
+  static_assert(G == 2 || G == 4, "CTAs per subdomain");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  using Sm = ApplySmem<R, KR>;
+  using Sm = ApplySmem<R, KR, G>;
   const int S = a.stages;
   const bool ysm = yglob == nullptr;
   const int64_t ys = ysm ? 1 : 0;                           // layout selector (see ApplySmem)
@@ -115,19 +156,20 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
   uint64_t* full = (uint64_t*)(smem_raw + Sm::bar_off(S, ys));
   uint64_t* empty = full + S;
   uint64_t* msg = empty + S;                                // [2]
-  CT<R>* recv = (CT<R>*)(smem_raw + Sm::recv_off(S, ys));   // [2][TB*KR]
+  CT<R>* recv = (CT<R>*)(smem_raw + Sm::recv_off(S, ys));   // [2][G-1][TB*KR]
   CT<R>* part = (CT<R>*)(smem_raw + Sm::part_off(S, ys));   // [TB*KR] this CTA's partial sums
   CT<R>* rvec = (CT<R>*)(smem_raw + Sm::rvec_off(S, ys));   // [TB*KR]
   __shared__ int abort_flag;
-  __shared__ int peer_abort;                                // set by the partner CTA at the end
+  __shared__ int peer_abort;                                // set by another CTA of the group at the end
   __shared__ int ydone;                                     // strips of y finalised (both passes)
   const int c = (int)cluster_rank();
   const int64_t ns = a.ns[s], np = a.np[s], nts = np / TB;
-  const int64_t own0 = (nts + 1) / 2;                   // strips owned by CTA 0
-  const int64_t nown_s = c ? nts - own0 : own0;         // strips owned by this CTA
+  auto nown_of = [&](int r) -> int64_t { return (nts - r + G - 1) / G; };  // strips I with I % G == r
+  const int64_t nown_s = nown_of(c);                    // strips owned by this CTA
   const int64_t nown = nown_s * TB;                     // owned rows
-  CT<R>* y = ysm ? (CT<R>*)(smem_raw + Sm::y_off(S, ys))
-                 : yglob + (a.np_off[s] + (c ? own0 * TB : 0)) * KR;
+  int64_t before = 0;                                   // strips owned by the lower ranks
+  for (int r = 0; r < c; ++r) before += nown_of(r);
+  CT<R>* y = ysm ? (CT<R>*)(smem_raw + Sm::y_off(S, ys)) : yglob + (a.np_off[s] + before * TB) * KR;
   const R* F = (const R*)a.arena + a.tile_off[s] * 2 * TILE_PLANE;
   const R* Dinv = (const R*)a.dinv + a.inv_off[s] * 4 * TILE_PLANE;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -138,15 +180,15 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
       mbar_init(&full[q], 1);
       mbar_init(&empty[q], APPLY_CONSUMERS / 32);
     }
-    mbar_init(&msg[0], 1);
-    mbar_init(&msg[1], 1);
+    mbar_init(&msg[0], G - 1);
+    mbar_init(&msg[1], G - 1);
     abort_flag = 0;
     peer_abort = 0;
     ydone = 0;
     fence_mbar_init();
   }
   __syncthreads();
-  cluster_sync_all();  // the partner may signal our barriers from here on
+  cluster_sync_all();  // the other CTAs may signal our barriers from here on
 
   if (warp == APPLY_CONSUMERS / 32) {
     // ---------------- producer: one lane issues the bulk copies in consumption order
@@ -172,17 +214,17 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
         return true;
       };
       bool ok = true;
-      // forward: own strip J = c + 2 jj is the (jj+1)-th finalised
-      for (int64_t I = 0; I < nts && ok; ++I) {
-        for (int64_t J = c; J < I && ok; J += 2)
-          ok = issue(F + (I * nts + J) * 2 * TILE_PLANE, ysm ? nullptr : y + (J / 2) * NV, J / 2 + 1);
-        if (ok && (I & 1) == c) ok = issue(Dinv + I * 4 * TILE_PLANE, nullptr, 0);
-      }
-      // backward: own strip jj is finalised after the forward ones, from the last strip down
-      for (int64_t I = nts - 1; I >= 0 && ok; --I) {
-        for (int64_t J = I + 1 + ((I + 1 + c) & 1); J < nts && ok; J += 2)
-          ok = issue(F + (I * nts + J) * 2 * TILE_PLANE, ysm ? nullptr : y + (J / 2) * NV, 2 * nown_s - J / 2);
-        if (ok && (I & 1) == c) ok = issue(Dinv + I * 4 * TILE_PLANE + 2 * TILE_PLANE, nullptr, 0);
+      TileCursor<G> cur;
+      for (cur.init(nts, c); ok && cur.pass != 2; cur.next()) {
+        if (cur.J < 0) {  // the owned diagonal block's L^{-1} (forward) or U^{-1} (backward)
+          ok = issue(Dinv + cur.I * 4 * TILE_PLANE + (cur.pass ? 2 * TILE_PLANE : 0), nullptr, 0);
+          continue;
+        }
+        // global y: own strip J is the (J/G + 1)-th finalised in the forward pass; in the
+        // backward pass the own strips are finalised again, from the last one down
+        const int64_t jj = cur.J / G;
+        ok = issue(F + (cur.I * nts + cur.J) * 2 * TILE_PLANE, ysm ? nullptr : y + jj * NV,
+                   cur.pass == 0 ? jj + 1 : 2 * nown_s - jj);
       }
       if (!ok) {
         atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
@@ -194,10 +236,8 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
     }
   } else {
     // ---------------- consumers
-    const uint32_t partner = (uint32_t)(c ^ 1);
     int slot = 0;
     uint32_t phase = 0;  // parity of the ring round of `slot`
-    int kr = 0, ks = 0;  // messages received / sent
     int nfin = 0;        // strips finalised by this CTA (thread 0 publishes it in ydone)
     bool ok = true;
     // waits for the next stage; T: its tile, Y: its y slice (global y) or nullptr
@@ -220,7 +260,7 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
     for (int64_t q = tid; q < nown * KR; q += APPLY_CONSUMERS) {  // q = (strip, r, row)
       const int64_t st = q / NV;
       const int r = (int)((q % NV) / TB), i = (int)(q % TB);
-      const int64_t pos = (2 * st + c) * TB + i;
+      const int64_t pos = (G * st + c) * TB + i;
       const int32_t g = a.gidx[a.np_off[s] + pos];
       const cplx val = (g >= 0 && r < nr) ? v[(int64_t)g * vs + off + r] : cplx{0.0, 0.0};
       y[q] = {R(val.re), R(val.im)};
@@ -230,20 +270,24 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
       const bool fwd = pass == 0;
       for (int64_t it = 0; it < nts; ++it) {
         const int64_t I = fwd ? it : nts - 1 - it;
-        const bool owner = (I & 1) == c;
+        const int o = (int)(I % G);                 // owner of strip I
+        const bool owner = o == c;
+        // the owner's count of owned strips before this one (both passes): receive parity
+        const int64_t seq = fwd ? I / G : 2 * nown_of(o) - 1 - I / G;
+        const int rb = (int)(seq & 1);
         // partial sums over the owned block columns of strip I
         CT<R> acc[8][KR];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
 #pragma unroll
           for (int r = 0; r < KR; ++r) acc[q][r] = {R(0), R(0)};
-        const int64_t J0 = fwd ? c : I + 1 + ((I + 1 + c) & 1), J1 = fwd ? I : nts;
-        for (int64_t J = J0; J < J1; J += 2) {
+        const int64_t J0 = fwd ? c : TileCursor<G>::first_right(I, c), J1 = fwd ? I : nts;
+        for (int64_t J = J0; J < J1; J += G) {
           const R* T = nullptr;
           const CT<R>* Y = nullptr;
           if (ok) ok = stage(T, Y);
           if (!ok) continue;  // keep the barrier sequence uniform; no more work after a timeout
-          const CT<R>* yJ = ysm ? y + (J / 2) * NV : Y;
+          const CT<R>* yJ = ysm ? y + (J / G) * NV : Y;
           // row-major tile: warp rows 8w..8w+7, lane columns 2l, 2l+1
           CT<R> y0[KR], y1[KR];
 #pragma unroll
@@ -279,29 +323,32 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
           }
         named_sync(1, APPLY_CONSUMERS);
         if (!owner) {
-          // send the partial sums to the owner's receive buffer, then signal it
-          for (int q = tid; q < NV; q += APPLY_CONSUMERS) {
-            const uint32_t dst = map_to_rank(&recv[(ks & 1) * NV + q], partner);
-            st_remote(dst, part[q].re, part[q].im);
-          }
+          // send the partial sums to this CTA's slot of the owner's receive buffer, then signal it
+          const int d = (c - o + G) % G - 1;
+          CT<R>* rs = recv + (rb * (G - 1) + d) * NV;
+          for (int q = tid; q < NV; q += APPLY_CONSUMERS) st_remote(map_to_rank(&rs[q], (uint32_t)o), part[q].re, part[q].im);
           named_sync(1, APPLY_CONSUMERS);
-          if (tid == 0) mbar_arrive_remote(map_to_rank(&msg[ks & 1], partner));
-          ++ks;
+          if (tid == 0) mbar_arrive_remote(map_to_rank(&msg[rb], (uint32_t)o));
           continue;
         }
-        // owner: r = b_I - own partial - partner partial
-        if (tid == 0 && !mbar_wait(&msg[kr & 1], (uint32_t)((kr >> 1) & 1), true, a.wait_ns)) {
+        // owner: r = b_I - own partial - the other CTAs' partials
+        if (tid == 0 && !mbar_wait(&msg[rb], (uint32_t)((seq >> 1) & 1), true, a.wait_ns)) {
           atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
           abort_flag = 1;
         }
         named_sync(1, APPLY_CONSUMERS);
         if (abort_flag) ok = false;
-        CT<R>* yI = y + (I / 2) * NV;
+        CT<R>* yI = y + (I / G) * NV;
         for (int q = tid; q < NV; q += APPLY_CONSUMERS) {
-          const CT<R> pr = recv[(kr & 1) * NV + q];
-          rvec[q] = {yI[q].re - part[q].re - pr.re, yI[q].im - part[q].im - pr.im};
+          CT<R> t = {yI[q].re - part[q].re, yI[q].im - part[q].im};
+#pragma unroll
+          for (int d = 0; d < G - 1; ++d) {
+            const CT<R> pr = recv[(rb * (G - 1) + d) * NV + q];
+            t.re -= pr.re;
+            t.im -= pr.im;
+          }
+          rvec[q] = t;
         }
-        ++kr;
         named_sync(1, APPLY_CONSUMERS);
         // y_I = inv(diag block) r
         const R* T = nullptr;
@@ -352,7 +399,7 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
       for (int64_t q = tid; q < nown * KR; q += APPLY_CONSUMERS) {
         const int64_t st = q / NV;
         const int r = (int)((q % NV) / TB), i = (int)(q % TB);
-        const int64_t pos = (2 * st + c) * TB + i;
+        const int64_t pos = (G * st + c) * TB + i;
         if (pos >= ns || r >= nr) continue;
         const CT<R> val = y[q];
         ZT* dst = z + (int64_t)Ns[pos] * zs + off + r;
@@ -365,10 +412,12 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
     }
   }
   __syncthreads();
-  // tell the partner whether this CTA gave up; the closing cluster barrier (release/acquire)
-  // makes the flag visible, so both CTAs return the same result
-  if (threadIdx.x == 0 && abort_flag) st_remote_u32(map_to_rank(&peer_abort, (uint32_t)(c ^ 1)), 1u);
-  cluster_sync_all();  // the partner must not touch our shared memory after we exit
+  // tell the others whether this CTA gave up; the closing cluster barrier (release/acquire)
+  // makes the flag visible, so all CTAs return the same result
+  if (threadIdx.x == 0 && abort_flag)
+    for (int r = 0; r < G; ++r)
+      if (r != c) st_remote_u32(map_to_rank(&peer_abort, (uint32_t)r), 1u);
+  cluster_sync_all();  // no other CTA may touch our shared memory after we exit
   return abort_flag != 0 || peer_abort != 0;
 }
 

@@ -168,6 +168,11 @@ struct Device {
   double* scal = nullptr;                       // small scalars [k][8]
   void* ybuf = nullptr;                         // apply: per-subdomain local vectors
   size_t ybuf_bytes = 0;
+  // apply work split: the first apply_n4 subdomains of apply_subs take clusters of four CTAs
+  // (largest padded order apply_np4), the rest two (apply_np2); apply_n4 == 0: two CTAs each
+  int32_t* apply_subs = nullptr;
+  int apply_n4 = 0;
+  int64_t apply_np4 = 0, apply_np2 = 0;
   cplx* io = nullptr;                           // staging for host I/O [N][k] col-major
   size_t io_elems = 0;
   double* host_pinned = nullptr;                // small pinned host scalars (per host thread)
@@ -268,6 +273,10 @@ struct oras_handle {
   const void* graph_Z = nullptr;
   const void* graph_arena = nullptr;
   const void* graph_ybuf = nullptr;
+  // the apply's side stream (four-CTA launch, concurrent with the two-CTA launch) and its
+  // fork and join events; created with the upload when some subdomains take four CTAs
+  cudaStream_t apply_side = nullptr;
+  cudaEvent_t apply_fork = nullptr, apply_join = nullptr;
   // GCRO-DR (oras_options.recycle): the deflation subspace U kept for the next solve
   oras::cplx* rc_U = nullptr;
   int rc_k = 0;

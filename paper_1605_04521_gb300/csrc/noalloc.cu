@@ -27,7 +27,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(APPLY_THREADS)
   // (in either CTA: apply_cluster returns the same value in both), the cluster stops, so no
   // barrier of the ring is initialised again while a copy might still complete on it.
   for (int r = 0; r < k; ++r)
-    if (apply_cluster<R, cplx, 1>(a, blockIdx.x / 2, v, 1, z, 1, (int64_t)r * n, 1, (CT<R>*)scratch)) break;
+    if (apply_cluster<R, cplx, 1, 2>(a, blockIdx.x / 2, v, 1, z, 1, (int64_t)r * n, 1, (CT<R>*)scratch)) break;
 }
 
 ApplyGeom apply_geom(const oras_handle* h);

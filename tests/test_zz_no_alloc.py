@@ -42,6 +42,9 @@ def test_noalloc_apply_matches_regular_apply_twice():
                 torch.cuda.synchronize()
                 got = zd.cpu().numpy().T
                 err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-                assert err <= 1e-12, (bits, weights, call, err)
+                # the regular apply may give the largest subdomains four CTAs (this one always
+                # takes two), which sums each strip's products in another order: with FP32
+                # factors the two agree to FP32 rounding, with FP64 factors to FP64 rounding
+                assert err <= (1e-5 if bits == 32 else 1e-12), (bits, weights, call, err)
         finally:
             O.oras_destroy(h)
