@@ -425,10 +425,13 @@ def serving_replay(O, count, slots, device=0, max_iter=60):
                                              tol=w.tol, restart=w.restart, factor_bits=w.factor_bits,
                                              max_iter=max_iter))
             outs = []
-            for t, (w, *_rest) in zip(tickets, prepared):
+            errors = {}
+            for q, (t, (w, *_rest)) in enumerate(zip(tickets, prepared)):
                 x, info, rc = O.oras_wait(srv, t)
                 rec = O.oras_ticket_info(srv, t)
                 outs.append((w, rc, info, rec))
+                if rc not in (O.ORAS_OK, O.ORAS_NOT_CONVERGED):
+                    errors[q] = O.oras_server_error(srv, t)
             wall = time.perf_counter() - t0
             st = O.oras_server_stats(srv)
         finally:
@@ -446,8 +449,11 @@ def serving_replay(O, count, slots, device=0, max_iter=60):
                            budget_gb=st["hbm_budget"] / 1e9, reason="footprint (arena + A + Krylov basis) above the "
                                                                       "whole HBM budget")
                       for q, (w, rc, _, rec) in enumerate(outs) if rc == O.ORAS_ERR_REJECTED]
+        failures = [dict(index=q, n=w.n, r=w.r, k=w.nrhs, nsub=w.nsub, rc=int(rc), error=errors.get(q, ""))
+                    for q, (w, rc, _, rec) in enumerate(outs)
+                    if rc not in (O.ORAS_OK, O.ORAS_NOT_CONVERGED, O.ORAS_ERR_REJECTED)]
         return {"slots": nslots, "solves_per_s": solves / (last - first) if last > first else None,
-                "rejections": rejections,
+                "rejections": rejections, "failures": failures,
                 "requests_per_s": len(done) / (last - first) if last > first else None,
                 "solves": solves, "requests_completed": len(done),
                 "rejected": sum(1 for _, rc, _, _ in outs if rc == O.ORAS_ERR_REJECTED),

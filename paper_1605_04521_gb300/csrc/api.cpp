@@ -169,6 +169,34 @@ static double* pinned_scratch() {
   return p;
 }
 
+// The apply's side stream and its fork/join events (once per handle).  Creating a stream takes
+// device memory outside the stream-ordered pool, which may hold nearly all of it under a serving
+// load: on failure the pool's unused memory is returned to the driver and the creation retried
+// once.  Returns false (nothing left behind, no error pending) when that fails too.
+static bool make_apply_side(oras_handle* h) {
+  if (h->apply_side) return true;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) == cudaSuccess) {
+      h->apply_side = st;
+      h->apply_fork = e0;
+      h->apply_join = e1;
+      return true;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (st) cudaStreamDestroy(st);
+    cudaGetLastError();
+    if (attempt == 0) {
+      cudaStreamSynchronize(h->dev.stream);
+      pool_trim(h->dev.device);
+    }
+  }
+  return false;
+}
+
 static int upload(oras_handle* h) {
   auto& m = h->mesh;
   auto& d = h->dev;
@@ -205,15 +233,12 @@ static int upload(oras_handle* h) {
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, d.device));
     std::vector<int32_t> order;
     d.apply_n4 = plan_apply_groups(h, nsm, order);
+    // the split is an optimisation: without its side stream the apply keeps two CTAs each
+    if (d.apply_n4 > 0 && !make_apply_side(h)) d.apply_n4 = 0;
     if (d.apply_n4 > 0) {
       CK(dput(d.apply_subs, order, s));
       d.apply_np4 = m.sub_np[order[0]];
       d.apply_np2 = d.apply_n4 < m.nsub ? m.sub_np[order[d.apply_n4]] : 0;
-      if (!h->apply_side) {
-        CK(cudaStreamCreateWithFlags(&h->apply_side, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&h->apply_fork, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->apply_join, cudaEventDisableTiming));
-      }
     }
   }
   CK(dput(d.cm, T.cm, s));

@@ -287,9 +287,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_lu_update_tc(const __grid_con
 //   right:  U_kJ^T = A_kJ^T L11^{-T}        (A_kJ column-major: its storage rows are the rows of
 //                                            the transpose, K-major; the result lands in the
 //                                            same storage positions)
-// Each CTA takes two tiles of one side (M = 128), N = 64, K = 64, and overwrites them.  A launch
+// One item is two tiles of one side (M = 128), N = 64, K = 64, overwritten in place.  A launch
 // covers the tiles below the diagonal (rows k+1 .. nts-1, when `lower`) and the tiles of row k
-// in columns [ju0, ju1) (clipped to the subdomain).
+// in columns [ju0, ju1) (clipped to the subdomain).  The first `gl` CTAs of a subdomain take the
+// lower side's items in turn (item x, x + gl, ...), the others the row's; each CTA keeps its
+// side's inverse tile in shared memory and runs its items through a pipeline: warp 0 loads the
+// next item's tiles with TMA while warp 1 issues the MMAs of the current one into one of two
+// tensor-memory accumulators and warps 2-5 store the previous one (each reads its quarter of the
+// 128 TMEM lanes).  Every wait is bounded; a timeout sets the device status flag, the roles stop,
+// and the CTA waits for its own copies and MMAs in flight before it releases its memory.
 struct TrsmArgs {
   const int64_t* np;
   const int64_t* tile_off;
@@ -298,118 +304,193 @@ struct TrsmArgs {
   int k;
   int l_slot;             // scratch slot of L_kk^{-1} (U_kk^{-1} is in slot LU_SUB)
   int lower;              // solve the tiles below the diagonal
-  int nbl;                // CTAs of the lower side (the largest subdomain's), the rest take row k
+  int gl;                 // CTAs per subdomain on the lower side (blockIdx.x < gl); the rest take row k
   int ju0, ju1;           // columns of row k to solve
   int32_t* status;
 };
 
-constexpr uint32_t TRSM_CHUNK_BYTES = 6 * TC_BOX_BYTES;  // A_re (2 boxes), A_im (2), B_re, B_im
-static_assert(TRSM_CHUNK_BYTES % 1024 == 0 && 2 * TRSM_CHUNK_BYTES + 2048 <= 227 * 1024, "trsm staging");
+constexpr int TRSM_THREADS = 192;                        // TMA, MMA, 4 epilogue warps
+constexpr int TRSM_STAGES = 2;
+constexpr uint32_t TRSM_A_BYTES = 8 * TC_BOX_BYTES;      // an item: [K half][A_re t0, A_re t1, A_im t0, A_im t1]
+constexpr uint32_t TRSM_B_BYTES = 4 * TC_BOX_BYTES;      // the inverse: [K half][B_re, B_im]
+constexpr size_t TRSM_SMEM = (size_t)TRSM_STAGES * TRSM_A_BYTES + TRSM_B_BYTES + 1024;
+constexpr uint32_t TRSM_TMEM_COLS = 256;                 // two accumulators of 128 columns (D_re, D_im)
+static_assert(TRSM_A_BYTES % 1024 == 0 && TRSM_B_BYTES % 1024 == 0 && TRSM_SMEM + 1024 <= 227 * 1024,
+              "trsm staging");
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_lu_trsm_tc(const __grid_constant__ CUtensorMap tmap, TrsmArgs a) {
+__global__ void __launch_bounds__(TRSM_THREADS, 1) k_lu_trsm_tc(const __grid_constant__ CUtensorMap tmap, TrsmArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ uint64_t full, done;
+  __shared__ uint64_t bfull, full[TRSM_STAGES], empty[TRSM_STAGES], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base;
+  __shared__ int n_issued, n_mma;
   const int s = blockIdx.y;
   const int64_t nts = a.np[s] / TB;
   const int k = a.k;
   if (k >= nts) return;
-  const int64_t b = blockIdx.x;
-  const bool lower = b < a.nbl;
-  int64_t t0, tend;
-  if (lower) {
-    t0 = k + 1 + 2 * b;
-    tend = nts;
-  } else {
-    t0 = a.ju0 + 2 * (b - a.nbl);
-    tend = a.ju1 < nts ? a.ju1 : nts;
-  }
-  if (t0 >= tend) return;
-  const bool two = t0 + 1 < tend;
-  const int64_t t1 = two ? t0 + 1 : t0;
+  const bool lower = (int)blockIdx.x < a.gl;
+  const int64_t first = lower ? k + 1 : a.ju0;
+  const int64_t end = lower ? nts : (a.ju1 < nts ? a.ju1 : nts);
+  const int64_t x = lower ? blockIdx.x : blockIdx.x - a.gl;
+  const int64_t stride = lower ? a.gl : (int)gridDim.x - a.gl;
+  const int64_t npairs = end > first ? (end - first + 1) / 2 : 0;
+  const int nitems = x < npairs ? (int)((npairs - 1 - x) / stride + 1) : 0;
+  if (nitems == 0) return;  // the same for every thread of the CTA
   const int64_t toff = a.tile_off[s];
-  const int zA0 = (int)(lower ? toff + t0 * nts + k : toff + (int64_t)k * nts + t0);
-  const int zA1 = (int)(lower ? toff + t1 * nts + k : toff + (int64_t)k * nts + t1);
+  // arena tiles of item i (z1 == z0 when the item has one tile)
+  auto item_tiles = [&](int i, int& z0, int& z1, bool& two) {
+    const int64_t t0 = first + 2 * (x + (int64_t)i * stride);
+    two = t0 + 1 < end;
+    const int64_t t1 = two ? t0 + 1 : t0;
+    z0 = (int)(lower ? toff + t0 * nts + k : toff + (int64_t)k * nts + t0);
+    z1 = (int)(lower ? toff + t1 * nts + k : toff + (int64_t)k * nts + t1);
+  };
   const int zB = (int)(a.scratch_base + (int64_t)LU_SCRATCH * s + (lower ? LU_SUB : a.l_slot));
   unsigned char* st = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sB = st + (size_t)TRSM_STAGES * TRSM_A_BYTES;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    mbar_init(&full, 1);
-    mbar_init(&done, 1);
+    mbar_init(&bfull, 1);
+    for (int q = 0; q < TRSM_STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&tfull[q], 1);
+      mbar_init(&tempty[q], 4);
+    }
+    n_issued = 0;
+    n_mma = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(128));
+                 "r"(TRSM_TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = tmem_base;
-  if (warp == 0 && lane == 0) {
-    mbar_expect_tx(&full, 2 * TRSM_CHUNK_BYTES);
-    for (int h = 0; h < 2; ++h) {
-      unsigned char* sb = st + (size_t)h * TRSM_CHUNK_BYTES;
-      const int x = h * 32;
-      tma_load_3d(sb + 0 * TC_BOX_BYTES, &tmap, x, 0, zA0, &full);
-      tma_load_3d(sb + 1 * TC_BOX_BYTES, &tmap, x, 0, zA1, &full);
-      tma_load_3d(sb + 2 * TC_BOX_BYTES, &tmap, x, 64, zA0, &full);
-      tma_load_3d(sb + 3 * TC_BOX_BYTES, &tmap, x, 64, zA1, &full);
-      tma_load_3d(sb + 4 * TC_BOX_BYTES, &tmap, x, 0, zB, &full);
-      tma_load_3d(sb + 5 * TC_BOX_BYTES, &tmap, x, 64, zB, &full);
-    }
-  } else if (warp == 1 && lane == 0) {
-    const uint32_t id_pos = idesc_tf32<1>(false), id_neg = idesc_tf32<1>(true);
-    const uint32_t d_re = tbase, d_im = tbase + 64;
-    if (mbar_wait(&full, 0)) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) {
+    // ---------------- TMA: the inverse once, then the items' tiles through the stages
+    if (lane == 0) {
+      mbar_expect_tx(&bfull, TRSM_B_BYTES);
       for (int h = 0; h < 2; ++h) {
-        const uint32_t sb = smem_u32(st + (size_t)h * TRSM_CHUNK_BYTES);
-        const uint64_t are = sdesc(sb), aim = sdesc(sb + 2 * TC_BOX_BYTES);
-        const uint64_t bre = sdesc(sb + 4 * TC_BOX_BYTES), bim = sdesc(sb + 5 * TC_BOX_BYTES);
+        tma_load_3d(sB + (2 * h) * TC_BOX_BYTES, &tmap, 32 * h, 0, zB, &bfull);
+        tma_load_3d(sB + (2 * h + 1) * TC_BOX_BYTES, &tmap, 32 * h, 64, zB, &bfull);
+      }
+      int n = 0;
+      for (int i = 0; i < nitems; ++i) {
+        const int b = i % TRSM_STAGES;
+        const uint32_t round = (uint32_t)(i / TRSM_STAGES);
+        if (i >= TRSM_STAGES && !mbar_wait(&empty[b], (round & 1u) ^ 1u)) {
+          atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
+          break;
+        }
+        int z0, z1;
+        bool two;
+        item_tiles(i, z0, z1, two);
+        unsigned char* sa = st + (size_t)b * TRSM_A_BYTES;
+        mbar_expect_tx(&full[b], TRSM_A_BYTES);
+        for (int h = 0; h < 2; ++h) {
+          unsigned char* base = sa + (size_t)(4 * h) * TC_BOX_BYTES;
+          tma_load_3d(base + 0 * TC_BOX_BYTES, &tmap, 32 * h, 0, z0, &full[b]);
+          tma_load_3d(base + 1 * TC_BOX_BYTES, &tmap, 32 * h, 0, z1, &full[b]);
+          tma_load_3d(base + 2 * TC_BOX_BYTES, &tmap, 32 * h, 64, z0, &full[b]);
+          tma_load_3d(base + 3 * TC_BOX_BYTES, &tmap, 32 * h, 64, z1, &full[b]);
+        }
+        n = i + 1;
+      }
+      n_issued = n;
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA: item i into accumulator i % 2 once the epilogue has emptied it
+    if (lane == 0) {
+      const uint32_t id_pos = idesc_tf32<1>(false), id_neg = idesc_tf32<1>(true);
+      int n = 0;
+      if (!mbar_wait(&bfull, 0)) {
+        atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
+      } else {
+        for (int i = 0; i < nitems; ++i) {
+          const int b = i % TRSM_STAGES, d = i & 1;
+          if (!mbar_wait(&full[b], (uint32_t)(i / TRSM_STAGES) & 1u) ||
+              (i >= 2 && !mbar_wait(&tempty[d], ((uint32_t)(i >> 1) & 1u) ^ 1u))) {
+            atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t d_re = tbase + 128u * d, d_im = d_re + 64;
+          const uint32_t sa = smem_u32(st + (size_t)b * TRSM_A_BYTES), sb = smem_u32(sB);
+          for (int h = 0; h < 2; ++h) {
+            const uint64_t are = sdesc(sa + 4 * h * TC_BOX_BYTES), aim = sdesc(sa + (4 * h + 2) * TC_BOX_BYTES);
+            const uint64_t bre = sdesc(sb + 2 * h * TC_BOX_BYTES), bim = sdesc(sb + (2 * h + 1) * TC_BOX_BYTES);
 #pragma unroll
-        for (int k8 = 0; k8 < 4; ++k8) {
-          const uint64_t dk = (uint64_t)(k8 * 32) >> 4;
-          const uint32_t first = (h == 0 && k8 == 0) ? 0u : 1u;
-          mma_tf32(d_re, are + dk, bre + dk, id_pos, first);
-          mma_tf32(d_re, aim + dk, bim + dk, id_neg, 1u);
-          mma_tf32(d_im, are + dk, bim + dk, id_pos, first);
-          mma_tf32(d_im, aim + dk, bre + dk, id_pos, 1u);
+            for (int k8 = 0; k8 < 4; ++k8) {
+              const uint64_t dk = (uint64_t)(k8 * 32) >> 4;
+              const uint32_t acc = (h == 0 && k8 == 0) ? 0u : 1u;
+              mma_tf32(d_re, are + dk, bre + dk, id_pos, acc);
+              mma_tf32(d_re, aim + dk, bim + dk, id_neg, 1u);
+              mma_tf32(d_im, are + dk, bim + dk, id_pos, acc);
+              mma_tf32(d_im, aim + dk, bre + dk, id_pos, 1u);
+            }
+          }
+          mma_commit(&empty[b]);  // the stage may be refilled once these MMAs have read it
+          mma_commit(&tfull[d]);  // the accumulator is complete
+          n = i + 1;
         }
       }
-    } else {
-      atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
+      n_mma = n;
     }
-    mma_commit(&done);
-  }
-  __syncwarp();
-  const bool fin = mbar_wait(&done, 0);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (fin) {
-    const int row = warp * 32 + lane, ti = row >> 6, li = row & 63;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-    float* T = a.arena + (size_t)(ti ? zA1 : zA0) * 2 * TILE_PLANE;
-#pragma unroll 1
-    for (int cb = 0; cb < 2; ++cb) {
-      float re[32], im[32];
-      tmem_ld32(tbase + lane_off + cb * 32, re);
-      tmem_ld32(tbase + lane_off + 64 + cb * 32, im);
-      if (ti == 1 && !two) continue;
-      float4* cr = (float4*)(T + li * TB + cb * 32);
-      float4* ci = (float4*)(T + TILE_PLANE + li * TB + cb * 32);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        cr[q] = make_float4(re[4 * q], re[4 * q + 1], re[4 * q + 2], re[4 * q + 3]);
-        ci[q] = make_float4(im[4 * q], im[4 * q + 1], im[4 * q + 2], im[4 * q + 3]);
+  } else {
+    // ---------------- epilogue: the rows of TMEM lane quarter q, stored over the item's tiles
+    const int q = warp & 3;
+    const int row = q * 32 + lane, ti = row >> 6, li = row & 63;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    for (int i = 0; i < nitems; ++i) {
+      const int d = i & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull[d], (uint32_t)(i >> 1) & 1u));
+      if (!ok) {
+        if (lane == 0) atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
+        break;
       }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int z0, z1;
+      bool two;
+      item_tiles(i, z0, z1, two);
+      float* T = a.arena + (size_t)(ti ? z1 : z0) * 2 * TILE_PLANE;
+#pragma unroll 1
+      for (int cb = 0; cb < 2; ++cb) {
+        float re[32], im[32];
+        tmem_ld32(tbase + lane_off + 128u * d + cb * 32, re);
+        tmem_ld32(tbase + lane_off + 128u * d + 64 + cb * 32, im);
+        if (ti == 1 && !two) continue;
+        float4* cr = (float4*)(T + li * TB + cb * 32);
+        float4* ci = (float4*)(T + TILE_PLANE + li * TB + cb * 32);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          cr[e] = make_float4(re[4 * e], re[4 * e + 1], re[4 * e + 2], re[4 * e + 3]);
+          ci[e] = make_float4(im[4 * e], im[4 * e + 1], im[4 * e + 2], im[4 * e + 3]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[d]);
     }
-  } else if (tid == 0) {
-    atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
+  }
+  __syncthreads();
+  // After a timeout: the copies and MMAs still in flight must land before the memory goes (the
+  // last phase of each stage and accumulator; earlier phases completed before it).  Without one,
+  // these waits return at once.
+  if (tid == 0) {
+    const uint64_t lim = drain_limit(WAIT_NS_DEFAULT);
+    mbar_wait(&bfull, 0, false, lim);
+    for (int i = n_issued - TRSM_STAGES > 0 ? n_issued - TRSM_STAGES : 0; i < n_issued; ++i)
+      mbar_wait(&full[i % TRSM_STAGES], (uint32_t)(i / TRSM_STAGES) & 1u, false, lim);
+    for (int i = n_mma - 2 > 0 ? n_mma - 2 : 0; i < n_mma; ++i) mbar_wait(&tfull[i & 1], (uint32_t)(i >> 1) & 1u, false, lim);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(128));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TRSM_TMEM_COLS));
 }
 
 // ------------------------------------------------------------------ host side
@@ -461,14 +542,32 @@ bool tc_update_available(oras_handle* h) {
   return h->tc_map_ok;
 }
 
+// CTAs per subdomain of a tile-solve launch: about two per SM over all subdomains, split between
+// the lower side and row k by their item counts, never more than the items.
+static void trsm_grid(int nsub, int64_t nbl, int64_t nbu, int* gl, int* gu) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    sms = (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0) ? n : 148;
+  }
+  const int64_t cap = std::max<int64_t>(1, (2 * (int64_t)sms + nsub - 1) / nsub);
+  int64_t l = 0, u = 0;
+  if (nbl > 0) l = std::min<int64_t>(nbl, std::max<int64_t>(1, nbu > 0 ? cap * nbl / (nbl + nbu) : cap));
+  if (nbu > 0) u = std::min<int64_t>(nbu, std::max<int64_t>(1, cap - l));
+  *gl = (int)l;
+  *gu = (int)u;
+}
+
 int launch_trsm_tc(oras_handle* h, int k, int max_nts, bool lower, int ju0, int ju1, int l_slot) {
   const auto& m = h->mesh;
   const auto& d = h->dev;
   const int64_t nbl = lower ? std::max<int64_t>(0, (max_nts - k - 1 + 1) / 2) : 0;
   const int64_t ue = std::min<int64_t>(ju1, max_nts);
   const int64_t nbu = ue > ju0 ? (ue - ju0 + 1) / 2 : 0;
-  const int64_t blocks = nbl + nbu;
-  if (blocks <= 0) return 0;
+  if (nbl + nbu <= 0) return 0;
+  int gl = 0, gu = 0;
+  trsm_grid(m.nsub, nbl, nbu, &gl, &gu);
   CUtensorMap map;
   std::memcpy(&map, h->tc_map, sizeof(map));
   TrsmArgs a;
@@ -479,13 +578,12 @@ int launch_trsm_tc(oras_handle* h, int k, int max_nts, bool lower, int ju0, int 
   a.k = k;
   a.l_slot = l_slot;
   a.lower = lower ? 1 : 0;
-  a.nbl = (int)nbl;
+  a.gl = gl;
   a.ju0 = ju0;
   a.ju1 = ju1;
   a.status = d.status;
-  const size_t smem = (size_t)2 * TRSM_CHUNK_BYTES + 1024;
   allow_max_smem((const void*)k_lu_trsm_tc);
-  k_lu_trsm_tc<<<dim3((unsigned)blocks, m.nsub), TC_THREADS, smem, d.stream>>>(map, a);
+  k_lu_trsm_tc<<<dim3((unsigned)(gl + gu), m.nsub), TRSM_THREADS, TRSM_SMEM, d.stream>>>(map, a);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
