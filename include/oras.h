@@ -213,7 +213,10 @@ void oras_destroy(oras_handle* h);
  * memory management of the single-GPU library.  Errors: INVALID_ARG (no such device), CUDA. */
 int oras_release_memory(int32_t device);
 
-/* Stream for all device work of h (a cudaStream_t; NULL = legacy default stream).  No
+/* Stream for all device work of h (a cudaStream_t; NULL = legacy default stream).  When the
+ * largest subdomains get four CTAs in the preconditioner apply, their part runs on a side stream
+ * that the handle owns, after an event recorded on h's stream and joined back into it by another
+ * event, so all of h's work stays in the order of h's stream (stream capture included).  No
  * counterpart in the paper.  Errors: INVALID_ARG (h NULL). */
 int oras_set_stream(oras_handle* h, void* stream);
 

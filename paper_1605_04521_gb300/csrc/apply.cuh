@@ -104,43 +104,13 @@ struct ApplySmem {
 
 // v and z are [N][vs] / [N][zs] complex arrays; this pass handles right-hand sides off .. off+nr-1
 // (nr <= KR; the unused lanes of the last group carry zeros and are not stored).
-// The order in which CTA c of a G-CTA group streams its tiles: the forward pass strip by strip
-// (the tiles of its own block columns left of the diagonal, then the diagonal block's L^{-1} when
-// it owns the strip), then the backward pass from the last strip up (its own block columns right
-// of the diagonal, then U^{-1}).  J >= 0: tile (I, J); J == -1: the diagonal inverse of strip I.
+// The first block column right of strip I among the columns J % G == c of CTA c (G a power of
+// two, so the mask is the remainder also for negative differences).
 template <int G>
-struct TileCursor {
-  int64_t nts, I, J;
-  int c, pass;  // pass 0 forward, 1 backward, 2 finished
-  __device__ void init(int64_t n, int cc) {
-    nts = n; c = cc; I = 0; J = cc;
-    pass = n > 0 ? 0 : 2;
-    settle();
-  }
-  __device__ void settle() {  // to the first item at or after (pass, I, J)
-    for (;;) {
-      if (pass == 2) return;
-      if (J >= 0) {
-        if (J < (pass == 0 ? I : nts)) return;
-        J = (I % G == c) ? -1 : -2;
-      }
-      if (J == -1) return;
-      if (pass == 0) {
-        if (++I == nts) { pass = 1; I = nts - 1; }
-      } else if (--I < 0) {
-        pass = 2;
-        return;
-      }
-      J = pass == 0 ? c : first_right(I, c);
-    }
-  }
-  __device__ void next() {
-    J = J >= 0 ? J + G : -2;
-    settle();
-  }
-  // the first block column right of strip I in the columns of CTA c
-  static __device__ int64_t first_right(int64_t I, int c) { return I + 1 + (((int64_t)c - (I + 1)) % G + G) % G; }
-};
+__device__ __forceinline__ int64_t first_right(int64_t I, int c) {
+  static_assert((G & (G - 1)) == 0, "G a power of two");
+  return I + 1 + (((int64_t)c - (I + 1)) & (G - 1));
+}
 
 template <typename R, typename ZT, int KR, int G>
 __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict__ v, int64_t vs,
@@ -214,17 +184,19 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
         return true;
       };
       bool ok = true;
-      TileCursor<G> cur;
-      for (cur.init(nts, c); ok && cur.pass != 2; cur.next()) {
-        if (cur.J < 0) {  // the owned diagonal block's L^{-1} (forward) or U^{-1} (backward)
-          ok = issue(Dinv + cur.I * 4 * TILE_PLANE + (cur.pass ? 2 * TILE_PLANE : 0), nullptr, 0);
-          continue;
-        }
-        // global y: own strip J is the (J/G + 1)-th finalised in the forward pass; in the
-        // backward pass the own strips are finalised again, from the last one down
-        const int64_t jj = cur.J / G;
-        ok = issue(F + (cur.I * nts + cur.J) * 2 * TILE_PLANE, ysm ? nullptr : y + jj * NV,
-                   cur.pass == 0 ? jj + 1 : 2 * nown_s - jj);
+      // forward, strip by strip: the tiles of the own block columns left of the diagonal, then
+      // L^{-1} of an owned strip; own strip J is the (J/G + 1)-th finalised
+      for (int64_t I = 0; I < nts && ok; ++I) {
+        for (int64_t J = c; J < I && ok; J += G)
+          ok = issue(F + (I * nts + J) * 2 * TILE_PLANE, ysm ? nullptr : y + (J / G) * NV, J / G + 1);
+        if (ok && (I % G) == c) ok = issue(Dinv + I * 4 * TILE_PLANE, nullptr, 0);
+      }
+      // backward, from the last strip up: the own block columns right of the diagonal, then
+      // U^{-1}; the own strips are finalised again, from the last one down
+      for (int64_t I = nts - 1; I >= 0 && ok; --I) {
+        for (int64_t J = first_right<G>(I, c); J < nts && ok; J += G)
+          ok = issue(F + (I * nts + J) * 2 * TILE_PLANE, ysm ? nullptr : y + (J / G) * NV, 2 * nown_s - J / G);
+        if (ok && (I % G) == c) ok = issue(Dinv + I * 4 * TILE_PLANE + 2 * TILE_PLANE, nullptr, 0);
       }
       if (!ok) {
         atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
@@ -239,6 +211,10 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
     int slot = 0;
     uint32_t phase = 0;  // parity of the ring round of `slot`
     int nfin = 0;        // strips finalised by this CTA (thread 0 publishes it in ydone)
+    // receive parity of a strip = its owner's count of owned strips before it (both passes):
+    // kr for this CTA's own strips, ks[o] for the strips it sends to owner o
+    int kr = 0;
+    int ks[G] = {};
     bool ok = true;
     // waits for the next stage; T: its tile, Y: its y slice (global y) or nullptr
     auto stage = [&](const R*& T, const CT<R>*& Y) -> bool {
@@ -272,16 +248,13 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
         const int64_t I = fwd ? it : nts - 1 - it;
         const int o = (int)(I % G);                 // owner of strip I
         const bool owner = o == c;
-        // the owner's count of owned strips before this one (both passes): receive parity
-        const int64_t seq = fwd ? I / G : 2 * nown_of(o) - 1 - I / G;
-        const int rb = (int)(seq & 1);
         // partial sums over the owned block columns of strip I
         CT<R> acc[8][KR];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
 #pragma unroll
           for (int r = 0; r < KR; ++r) acc[q][r] = {R(0), R(0)};
-        const int64_t J0 = fwd ? c : TileCursor<G>::first_right(I, c), J1 = fwd ? I : nts;
+        const int64_t J0 = fwd ? c : first_right<G>(I, c), J1 = fwd ? I : nts;
         for (int64_t J = J0; J < J1; J += G) {
           const R* T = nullptr;
           const CT<R>* Y = nullptr;
@@ -324,7 +297,10 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
         named_sync(1, APPLY_CONSUMERS);
         if (!owner) {
           // send the partial sums to this CTA's slot of the owner's receive buffer, then signal it
-          const int d = (c - o + G) % G - 1;
+          const int d = ((c - o) & (G - 1)) - 1;
+          int& cnt = ks[G == 2 ? 0 : o];            // G = 2: one owner besides this CTA
+          const int rb = cnt & 1;
+          ++cnt;
           CT<R>* rs = recv + (rb * (G - 1) + d) * NV;
           for (int q = tid; q < NV; q += APPLY_CONSUMERS) st_remote(map_to_rank(&rs[q], (uint32_t)o), part[q].re, part[q].im);
           named_sync(1, APPLY_CONSUMERS);
@@ -332,7 +308,8 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
           continue;
         }
         // owner: r = b_I - own partial - the other CTAs' partials
-        if (tid == 0 && !mbar_wait(&msg[rb], (uint32_t)((seq >> 1) & 1), true, a.wait_ns)) {
+        const int rb = kr & 1;
+        if (tid == 0 && !mbar_wait(&msg[rb], (uint32_t)((kr >> 1) & 1), true, a.wait_ns)) {
           atomicExch(&a.status[ST_ERR], DEV_TIMEOUT);
           abort_flag = 1;
         }
@@ -349,6 +326,7 @@ __device__ bool apply_cluster(const ApplyGeom& a, int s, const cplx* __restrict_
           }
           rvec[q] = t;
         }
+        ++kr;
         named_sync(1, APPLY_CONSUMERS);
         // y_I = inv(diag block) r
         const R* T = nullptr;
