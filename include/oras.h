@@ -396,13 +396,13 @@ int oras_wait_selftest(oras_handle* h, int32_t* detail);
  * (tiles of 64 columns per trailing update; trades the updates inside a panel against the passes
  * over the trailing matrix) and the raster group of the tensor-core update (output blocks that
  * share operands in L2).  Factorises the handle's current problem (materials of the last
- * oras_factor, on the handle's stream) once per candidate width 4, 8, 12, 16, 24, 32, 48, 64, 96
- * (group 8), then once per group 16, 32, 64 at the best width, keeps the fastest pair in the
+ * oras_factor, on the handle's stream) once per candidate width 4, 8, 12, 16, 24, 32, 48, 64, 96,
+ * 128, 192 (group 8), then once per group 16, 32, 64 at the best width, keeps the fastest pair in the
  * handle's options (lu_panel, lu_group) and leaves the factors of that pair.  The choice is
  * cached for the process under the problem's shape (factor precision, LU engine, padded
  * subdomain orders): a later handle of the same shape takes it without timing.  panel: chosen
  * width (or NULL); ms[0..nms): the candidates' factorisation times in milliseconds, widths then
- * groups (12 entries; -1 when taken from the cache; NULL allowed).
+ * groups (14 entries; -1 when taken from the cache; NULL allowed).
  * Errors: INVALID_ARG, STATE (no oras_factor yet), and those of oras_factor. */
 int oras_autotune(oras_handle* h, int32_t* panel, double* ms, int32_t nms);
 /* The raster group oras_autotune chose for the handle (0 before tuning: the default); -1 for

@@ -545,7 +545,7 @@ static std::map<std::vector<int64_t>, std::pair<int, int>> g_tune_cache;  // sha
 int oras_autotune(oras_handle* h, int32_t* panel, double* ms, int32_t nms) {
   if (!h) return ORAS_ERR_INVALID_ARG;
   if (!h->factored) { h->err = "oras_autotune: call oras_factor first"; return ORAS_ERR_STATE; }
-  static const int widths[] = {4, 8, 12, 16, 24, 32, 48, 64, 96};
+  static const int widths[] = {4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192};
   static const int groups[] = {16, 32, 64};  // after the widths, which run with the default group 8
   constexpr int NW = sizeof(widths) / sizeof(widths[0]), NG = sizeof(groups) / sizeof(groups[0]);
   std::vector<int64_t> key = {h->opt.factor_bits, h->opt.lu_engine, h->mesh.nsub};

@@ -520,7 +520,7 @@ def oras_wait_selftest(h):
     return rc, detail.value
 
 
-AUTOTUNE_WIDTHS = (4, 8, 12, 16, 24, 32, 48, 64, 96)
+AUTOTUNE_WIDTHS = (4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192)
 
 
 def oras_autotune(h):
