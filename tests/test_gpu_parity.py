@@ -175,13 +175,16 @@ def test_grouped_apply_matches_oracle(O, bits, tol):
 
 
 def test_grouped_apply_global_local_vectors(O):
-    """Subdomains of about 12k DOFs: a group of four keeps its local vectors in global memory,
-    a single vector keeps them in shared memory; both give the same z."""
-    w = synth.small(n=8, r=2, nsub=2, overlap=1)
+    """One subdomain of about 21k DOFs (a cluster of four CTAs): a group of four right-hand
+    sides keeps its local vectors in global memory (a CTA's quarter of the strips takes 172 KB
+    for four vectors, more than fits beside two ring stages), a single vector keeps them in
+    shared memory; both give the same z.  (The two-CTA kernel's global-memory path runs in the
+    allocation-free apply, tests/test_zz_no_alloc.py.)"""
+    w = synth.small(n=8, r=2, nsub=1, overlap=0)
     h = gpu_handle(O, w)
     try:
         n = O.oras_ndof(h)
-        assert max(O.oras_subdomain_size(h, s)[2] for s in range(2)) > 9000
+        assert O.oras_subdomain_size(h, 0)[2] > 20000
         rng = np.random.default_rng(22)
         k = 6
         V = rng.normal(size=(n, k)) + 1j * rng.normal(size=(n, k))
