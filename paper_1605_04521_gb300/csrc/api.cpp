@@ -231,6 +231,7 @@ static int upload(oras_handle* h) {
   {  // the apply's work split (which subdomains take four CTAs)
     int nsm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, d.device));
+    d.num_sms = nsm;
     std::vector<int32_t> order;
     d.apply_n4 = plan_apply_groups(h, nsm, order);
     // the split is an optimisation: without its side stream the apply keeps two CTAs each

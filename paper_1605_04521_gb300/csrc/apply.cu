@@ -46,14 +46,25 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(APPLY_THREADS, 1)
 }
 
 constexpr size_t SMEM_LIMIT = 227 * 1024 - 2048;  // opt-in shared memory per block less the static part
+constexpr size_t SMEM_PAIR = 112 * 1024;          // dynamic shared memory that lets two CTAs share an SM
+constexpr int APPLY_PAIR_STAGES = 3;              // ring depth of such a CTA
 
 // Ring depth and dynamic shared memory for KR right-hand sides per pass and G CTAs per subdomain,
 // for subdomains of padded order up to max_np; y in shared memory when `allow_smem_y` and it fits
-// next to a ring of at least 2 stages.
+// next to a ring of at least 2 stages.  `paired`: the launch has more CTAs than SMs (they run in
+// waves); then, for one right-hand side per pass (a CTA's registers leave room for a second one
+// only there) and if a 3-stage ring and y fit in SMEM_PAIR, two CTAs share each SM, so one
+// CTA's gather, scatter and ring fill overlap the other's stream.
 template <typename R, int KR, int G>
-static void apply_config(int64_t max_np, bool allow_smem_y, int* S, size_t* smem, bool* y_smem) {
+static void apply_config(int64_t max_np, bool allow_smem_y, int* S, size_t* smem, bool* y_smem, bool paired = false) {
   using Sm = ApplySmem<R, KR, G>;
   const int64_t ystrips = (max_np / TB + G - 1) / G;
+  if (paired && KR == 1 && allow_smem_y && Sm::total(APPLY_PAIR_STAGES, ystrips) <= SMEM_PAIR) {
+    *S = APPLY_PAIR_STAGES;
+    *smem = Sm::total(APPLY_PAIR_STAGES, ystrips);
+    *y_smem = true;
+    return;
+  }
   if (allow_smem_y)
     for (int q = 8; q >= 2; --q)
       if (Sm::total(q, ystrips) <= SMEM_LIMIT) {
@@ -67,6 +78,11 @@ static void apply_config(int64_t max_np, bool allow_smem_y, int* S, size_t* smem
   *S = q;
   *smem = Sm::total(q, 0);
   *y_smem = false;
+}
+
+// The 2-CTA launch of an apply pass has more CTAs than the SMs hold (one per SM otherwise).
+static bool apply_paired(const oras_handle* h) {
+  return h->dev.num_sms > 0 && 2 * (int64_t)(h->mesh.nsub - h->dev.apply_n4) > h->dev.num_sms;
 }
 
 ApplyGeom apply_geom(const oras_handle* h) {
@@ -106,7 +122,7 @@ static int apply_group(const oras_handle* h, const cplx* v, ZT* z, int k, int r0
   ApplyGeom a2 = apply_geom(h), a4 = apply_geom(h);
   size_t smem2 = 0, smem4 = 0;
   bool ys2 = true, ys4 = true;
-  if (m.nsub > n4) apply_config<R, KR, 2>(group_max_np(h, 2), true, &a2.stages, &smem2, &ys2);
+  if (m.nsub > n4) apply_config<R, KR, 2>(group_max_np(h, 2), true, &a2.stages, &smem2, &ys2, apply_paired(h));
   if (n4 > 0) apply_config<R, KR, 4>(group_max_np(h, 4), true, &a4.stages, &smem4, &ys4);
   if (!ys2 || !ys4) {
     if (!d.ybuf || d.ybuf_bytes < apply_yglob_bytes(h, KR)) return -1;
@@ -187,7 +203,8 @@ static size_t yglob_bytes_kr(const oras_handle* h) {
   int S;
   size_t smem;
   bool y_smem = true, y4 = true;
-  if (h->mesh.nsub > h->dev.apply_n4) apply_config<R, KR, 2>(group_max_np(h, 2), true, &S, &smem, &y_smem);
+  if (h->mesh.nsub > h->dev.apply_n4)
+    apply_config<R, KR, 2>(group_max_np(h, 2), true, &S, &smem, &y_smem, apply_paired(h));
   if (h->dev.apply_n4 > 0) apply_config<R, KR, 4>(group_max_np(h, 4), true, &S, &smem, &y4);
   if (y_smem && y4) return 0;
   int64_t total = 0;

@@ -172,6 +172,7 @@ struct Device {
   // (largest padded order apply_np4), the rest two (apply_np2); apply_n4 == 0: two CTAs each
   int32_t* apply_subs = nullptr;
   int apply_n4 = 0;
+  int num_sms = 0;                              // SMs of the handle's device
   int64_t apply_np4 = 0, apply_np2 = 0;
   cplx* io = nullptr;                           // staging for host I/O [N][k] col-major
   size_t io_elems = 0;

@@ -132,6 +132,30 @@ def test_preconditioner_apply(O, bits, tol):
         O.oras_destroy(h)
 
 
+@pytest.mark.parametrize("bits,tol", [(64, 1e-9), (32, TOL_APPLY_F32)])
+def test_apply_many_subdomains(O, bits, tol):
+    """128 subdomains without overlap: 256 CTAs (two per subdomain), more than the SMs hold at
+    once, so with FP32 factors two CTAs share an SM on 3-stage rings (FP64 tiles keep one CTA
+    per SM).  z = M^-1 v against the oracle's ORAS, and against the allocation-free apply of the
+    same factors, which keeps its local vectors in global memory with one CTA per SM."""
+    torch = pytest.importorskip("torch")
+    w = synth.small(n=6, r=2, nsub=128, overlap=0)
+    h = gpu_handle(O, w, factor_bits=bits)
+    try:
+        p = problem.from_workload(w)
+        rng = np.random.default_rng(13)
+        v = rng.normal(size=p.topo.ndof) + 1j * rng.normal(size=p.topo.ndof)
+        z = O.oras_precond(h, v)
+        assert rel(z, p.oras.apply(v)) <= tol
+        vd = torch.from_numpy(v.copy()).cuda()
+        zd = torch.full_like(vd, complex(np.nan, np.nan))
+        O.oras_precond_noalloc(h, vd, zd, 1)
+        torch.cuda.synchronize()
+        assert rel(zd.cpu().numpy(), z) <= (1e-12 if bits == 64 else 1e-5)
+    finally:
+        O.oras_destroy(h)
+
+
 @pytest.mark.parametrize("n,nsub,overlap,bits,panel", [
     (3, 1, 0, 64, 0), (3, 1, 0, 64, 2), (3, 1, 0, 32, 3), (3, 1, 0, 32, 24), (3, 1, 0, 32, 12), (3, 1, 0, 32, 20),
     (3, 1, 0, 64, 20), (4, 8, 1, 64, 0), (4, 8, 1, 32, 0), (4, 8, 1, 32, 2), (4, 8, 1, 64, 24)])
